@@ -1,0 +1,152 @@
+"""Full-image render, loss and exact active-set gradient in float64.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Sec. 3.3 ("Local Optimization Kernel") and Supp. "Local Optimization Kernel":
+the local kernel renders only tiles touched by O^t and back-propagates only
+into O^t, and must produce exactly the gradients that O^t receives in a
+full-scene 3DGS step. This module computes that reference: the whole image of
+every view (every tile, static Gaussians included), the loss over all pixels,
+and the gradient of that loss by reverse-mode autodiff in float64, restricted
+afterwards to O^t.
+
+Loss reading (the paper adopts the base method's photometric loss; the
+workloads use L1 or L2): L = (1/V) sum_views (1 / (3 H W)) sum_pixels,channels
+l(C - C*), l = |.| or (.)^2, normalised by the full image so that the gradient
+of O^t does not depend on how many tiles are rendered.
+
+The per-pixel Gaussian lists use the float32 decisions of `fp32_index` (culling,
+tile rectangles, depth order); all values are float64.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import fp32_index as fx
+from .composite import composite
+from .projection import project, scene64, T64
+
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+def tile_list(pidx: Dict[str, np.ndarray], tx: int, ty: int) -> np.ndarray:
+    """Gaussians whose rectangle holds tile (tx, ty), by (depth bits, index)."""
+    sel = pidx["valid"] & (pidx["tx0"] <= tx) & (pidx["tx1"] >= tx) & \
+        (pidx["ty0"] <= ty) & (pidx["ty1"] >= ty)
+    ids = np.flatnonzero(sel)
+    order = np.lexsort((ids, pidx["zbits"][ids]))
+    return ids[order]
+
+
+def tile_pixels(cam, tx: int, ty: int):
+    W, H = int(cam["width"]), int(cam["height"])
+    xs = np.arange(tx * fx.TILE, min((tx + 1) * fx.TILE, W))
+    ys = np.arange(ty * fx.TILE, min((ty + 1) * fx.TILE, H))
+    X, Y = np.meshgrid(xs, ys)
+    return torch.tensor(X.ravel()), torch.tensor(Y.ravel())
+
+
+def loss_terms(colour, target, kind: str):
+    d = colour - target
+    return d.abs() if kind == "l1" else d * d
+
+
+def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
+           bg=(0.0, 0.0, 0.0), targets: Optional[Sequence[np.ndarray]] = None,
+           loss: str = "l1", need_grad: bool = False,
+           tiles: Optional[Sequence[Sequence[tuple]]] = None,
+           margin: float = 1e-3):
+    """Render every view (or only `tiles[j]` of view j).
+
+    Returns a dict with per-view `image` [3, H, W] (NaN where not rendered),
+    `T_final`, `n_contrib`, `n_incl`, `near` ([H, W] bools), the per-view index-mode
+    projections `pidx`, `near_ids` (set of Gaussian ids with a threshold
+    decision), `loss` (float, over rendered pixels) and, if `need_grad`, the
+    float64 gradient of every parameter array (`grads`, numpy, same shapes as
+    the scene)."""
+    V = len(cams)
+    bg_t = torch.tensor(bg, dtype=T64)
+    g = scene64(scene, requires_grad=need_grad)
+    out = {"image": [], "T_final": [], "n_contrib": [], "n_incl": [], "near": [], "pidx": [],
+           "near_ids": set(), "loss": 0.0}
+    proj_outs, proj_grads = [], []
+    for j, cam in enumerate(cams):
+        W, H = int(cam["width"]), int(cam["height"])
+        Tx, Ty = fx.tiles_of(cam)
+        pidx = fx.project_index(scene, cam)
+        out["pidx"].append(pidx)
+        P = project(g, cam, sh_degree)
+        leaves = {k: P[k].detach().clone().requires_grad_(need_grad)
+                  for k in ("u", "v", "conic", "opacity", "rgb")}
+        img = np.full((3, H, W), np.nan)
+        Tf = np.full((H, W), np.nan)
+        nc = np.full((H, W), -1, np.int64)
+        ni = np.full((H, W), -1, np.int64)
+        near = np.zeros((H, W), bool)
+        tgt = None if targets is None else torch.tensor(
+            np.asarray(targets[j], np.float64), dtype=T64)
+        norm = 1.0 / (3.0 * H * W * V)
+        todo = tiles[j] if tiles is not None else [(x, y) for y in range(Ty) for x in range(Tx)]
+        for (tx, ty) in todo:
+            ids_np = tile_list(pidx, tx, ty)
+            ids = torch.tensor(ids_np, dtype=torch.int64)
+            px, py = tile_pixels(cam, tx, ty)
+            cr = composite(leaves["u"][ids], leaves["v"][ids], leaves["conic"][ids],
+                           leaves["opacity"][ids], leaves["rgb"][ids], px, py, bg_t, margin)
+            col = cr["colour"]
+            pxn, pyn = px.numpy(), py.numpy()
+            img[:, pyn, pxn] = col.detach().numpy().T
+            Tf[pyn, pxn] = cr["T_final"].detach().numpy()
+            nc[pyn, pxn] = cr["n_contrib"].numpy()
+            ni[pyn, pxn] = cr["n_incl"].numpy()
+            near[pyn, pxn] = cr["near"].numpy()
+            out["near_ids"].update(ids_np[cr["near_ids"].numpy()].tolist())
+            if tgt is not None:
+                lt = loss_terms(col, tgt[:, py, px].T, loss).sum() * norm
+                out["loss"] += float(lt.detach())
+                if need_grad and lt.requires_grad:
+                    lt.backward()
+        out["image"].append(img)
+        out["T_final"].append(Tf)
+        out["n_contrib"].append(nc)
+        out["n_incl"].append(ni)
+        out["near"].append(near)
+        if need_grad:
+            for k, leaf in leaves.items():
+                if leaf.grad is not None:
+                    proj_outs.append(P[k])
+                    proj_grads.append(leaf.grad)
+    if need_grad:
+        if proj_outs:
+            torch.autograd.backward(proj_outs, proj_grads)
+        out["grads"] = {k: (g[k].grad.numpy().copy() if g[k].grad is not None
+                            else np.zeros(g[k].shape)) for k in PARAM_KEYS}
+    return out
+
+
+def loss_value(scene, cams, sh_degree, targets, loss="l1", bg=(0.0, 0.0, 0.0)) -> float:
+    return render(scene, cams, sh_degree, bg, targets, loss, need_grad=False)["loss"]
+
+
+def active_tiles(scene, cams, active: np.ndarray) -> List[List[tuple]]:
+    """Per view, the tiles touched by a non-culled Gaussian of O^t."""
+    res = []
+    for cam in cams:
+        pidx = fx.project_index(scene, cam)
+        m = fx.tile_mask(pidx, active, cam)
+        ys, xs = np.nonzero(m)
+        res.append(list(zip(xs.tolist(), ys.tolist())))
+    return res
+
+
+def local_step_reference(scene, cams, sh_degree, targets, active, loss="l1",
+                         bg=(0.0, 0.0, 0.0)):
+    """Full-image gradient restricted to O^t (rows of static Gaussians are
+    zero), plus the full-image render."""
+    r = render(scene, cams, sh_degree, bg, targets, loss, need_grad=True)
+    for k in PARAM_KEYS:
+        r["grads"][k][~active] = 0.0
+    return r
