@@ -1,0 +1,371 @@
+"""Benchmark: active-set local-optimisation iterations per second.
+
+Workload: a 1,000,000-Gaussian clustered room scene (20 clusters, sigma 0.3,
+[-5,5]^3), SH degree 3, four 1920x1080 views at 0, pi/2, pi, 3pi/2 on a ring of
+radius 4, a change box around the cluster nearest view 0's image centre
+holding 5% of the Gaussians, its Gaussians perturbed by N(0, 0.05) to make the
+target scene; the active set comes from change-mask lifting (majority vote).
+A step is one iteration of the hot path over all four views: project_and_bin
+(active Gaussians re-projected, static ones cached per update), sort_keys,
+render_forward with the fused L1 loss, render_backward, adam_step_active.
+
+Prints one JSON line (rank 0). With --impl reference the CPU oracle is timed
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "active-set iters/s (fwd+bwd+Adam) @1M Gaussians 1080p"
+UNIT = "iters/s"
+WORKLOAD = "1M-Gaussian clustered room, SH3, 4 views 1920x1080, 5% change box, L1"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=1_000_000)
+    p.add_argument("--fraction", type=float, default=0.05)
+    p.add_argument("--width", type=int, default=1920)
+    p.add_argument("--height", type=int, default=1080)
+    p.add_argument("--views", type=int, default=4)
+    p.add_argument("--e2e-updates", type=int, default=3)
+    p.add_argument("--iters-per-update", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-tiles", type=int, default=4)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- helpers ---
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback", 2070.0
+
+
+# ALU peak of the FP32 pipes: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock.
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+FWD_FLOP_PER_EVAL = 24   # power (11), exp (2), alpha (2), test (2), weight and colour (7)
+BWD_FLOP_PER_EVAL = 24   # the same recomputation, T recovery, colour behind
+
+
+def setup_workload(args, seed):
+    from paper_2506_21117_gb300 import synthetic as S
+    return S.workload_large(n=args.n, n_views=args.views, width=args.width, height=args.height,
+                            fraction=args.fraction, sh_degree=3, seed=seed)
+
+
+# -------------------------------------------------------------- CPU oracle ---
+
+def oracle_sample(scene, cams, targets, active, n_tiles_total, n_tiles, proj_frac=1.0,
+                  seed=0):
+    """Time the oracle on a bounded sample: the float64 projection of a
+    fraction of the Gaussians in view 0 and forward+backward of `n_tiles`
+    active tiles of view 0; extrapolated to one iteration (every view, every
+    active tile). Returns (seconds per iteration, description)."""
+    import torch
+    from oracle import fp32_index as fx
+    from oracle import projection as pj
+    from oracle import step as ostep
+    n = scene["means"].shape[0]
+    rng = np.random.default_rng(seed)
+    m = max(1, int(n * proj_frac))
+    sub = {k: v[:m] for k, v in scene.items()}
+    t0 = time.perf_counter()
+    fx.project_index(sub, cams[0])
+    g = pj.scene64(sub, requires_grad=True)
+    P = pj.project(g, cams[0], 3)
+    (P["u"].sum() + P["conic"].sum() + P["rgb"].sum()).backward()
+    t_proj = (time.perf_counter() - t0) / proj_frac
+    tiles = ostep.active_tiles(scene, cams[:1], active)[0]
+    pick = [tiles[i] for i in rng.choice(len(tiles), size=min(n_tiles, len(tiles)),
+                                          replace=False)]
+    t1 = time.perf_counter()
+    ostep.render(scene, cams[:1], 3, targets=targets[:1], loss="l1", need_grad=True,
+                 tiles=[pick])
+    t_render_all = time.perf_counter() - t1
+    # render() also projects all n Gaussians once with autograd; remove that share
+    t_tiles = max(t_render_all - t_proj, 1e-3)
+    per_tile = t_tiles / max(len(pick), 1)
+    it = len(cams) * t_proj + n_tiles_total * per_tile
+    desc = (f"float64 oracle: projection+backward of {m} of {n} Gaussians in view 0 "
+            f"(scaled to all {n} and {len(cams)} views) and forward+backward of {len(pick)} "
+            f"active tiles of view 0 (scaled to all {n_tiles_total} active tiles of "
+            f"{len(cams)} views)")
+    return it, desc
+
+
+# ---------------------------------------------------------------- our arm ---
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2506_21117_gb300 import build as b
+    b.build()
+    from paper_2506_21117_gb300.update import LocalUpdate
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+
+    scene, target_scene, cams, masks, box = setup_workload(args, seed=rank)
+    n = scene["means"].shape[0]
+    # target images: full renders of the changed scene with this library
+    tgt = LocalUpdate(target_scene, cams, 3, active=np.ones(n, bool), capacity_slack=1.05)
+    tgt.render_pass(with_backward=False)
+    torch.cuda.synchronize()
+    tgt.batch.check_status()
+    targets = [t.cpu().numpy().copy() for t in tgt.batch.per_view(tgt.batch.image, 3)]
+    del tgt
+    torch.cuda.empty_cache()
+
+    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
+    bt = lu.batch
+    A = lu.state.n_active
+    for _ in range(args.warmup):
+        lu.step()
+    torch.cuda.synchronize()
+    bt.check_status()
+
+    stages = ["project_and_bin", "sort_keys", "render_forward", "render_backward",
+              "adam_step_active"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    clocks = Clocks(dev.index)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for k in range(args.steps):
+        e = ev[k]
+        e[0].record()
+        bt.project_and_bin(1)
+        e[1].record()
+        bt.sort()
+        e[2].record()
+        bt.forward(lu.loss_mode, lu.bg, write_image=False)
+        e[3].record()
+        bt.backward(lu.bg)
+        e[4].record()
+        bt.adam(lu.lr)
+        e[5].record()
+    end.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    bt.check_status()
+    stage_ms = {s: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+                for i, s in enumerate(stages)}
+
+    # counters of one more pass (not timed)
+    bt.n_contrib.zero_()
+    lu.render_pass(with_backward=False)
+    torch.cuda.synchronize()
+    D = int(bt.n_pairs.item())
+    tiles_on = int(bt.n_active_tiles.item())
+    evals = int(bt.n_contrib.sum(dtype=torch.int64).item())
+    V = len(cams)
+    passes = math.ceil(bt.info.key_bits / 8)
+    P_act = tiles_on * 256
+
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+    hbm_peak, peak_kind, sm_max = load_peaks()
+    # algorithmic bytes per stage launch (design notes give the derivation)
+    bytes_stage = {
+        "project_and_bin": A * (236 + 48) * V + 16 * n * V + 12 * D,
+        "sort_keys": 12 * D * (2 * passes + 1) + 8 * D,
+        "adam_step_active": 28 * 59 * A,
+    }
+    dominant = max(stage_ms, key=stage_ms.get)
+    alu_peak = fp32_peak_tflops(sm_max)
+    if dominant in ("render_forward", "render_backward"):
+        flops = evals * (FWD_FLOP_PER_EVAL if dominant == "render_forward" else BWD_FLOP_PER_EVAL)
+        ach = flops / (stage_ms[dominant] * 1e-3) / 1e12
+        roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "units_per_launch": evals, "unit_work": "(pixel, list entry) evaluations"}
+    else:
+        ach = bytes_stage[dominant] / (stage_ms[dominant] * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                "peak_kind": peak_kind}
+    B_iter = (A * (236 + 48 * V) + 12 * D * (2 * passes + 1) + 2 * 48 * D +
+              P_act * (12 + 8 + 12 + 12 + 8) + A * (36 * V + 236 + 236) + 28 * 59 * A)
+    iteration_roof = {"bytes_per_iter": B_iter,
+                      "achieved_gbs": B_iter * value / world / 1e9,
+                      "frac_of_hbm": B_iter * value / world / 1e9 / hbm_peak}
+
+    e2e = run_e2e(args, lu, targets, masks, cams)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": n, "views": V,
+                   "resolution": f"{args.width}x{args.height}", "sh_degree": 3,
+                   "change_fraction": args.fraction, "active_gaussians": A,
+                   "active_tiles": tiles_on, "pairs": D, "sort_passes": passes,
+                   "parallelism": f"replicas x{world} (independent scenes, no collective)",
+                   "l2": "inputs larger than L2 (params 256 MB, keys >= 100 MB per step)"},
+        "stages_ms": stage_ms,
+        "roofline": roof,
+        "iteration_hbm_roofline": iteration_roof,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": int(bt.launches_per_step() * args.steps),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import torch as _t
+        sec, desc = oracle_sample(scene, cams, targets, lu.state.active.cpu().numpy().astype(bool),
+                                  tiles_on, args.cpu_tiles, proj_frac=0.1)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": _t.get_num_threads(),
+                                "kind": "oracle", "sample": desc}
+    return line
+
+
+def run_e2e(args, lu, targets, masks, cams):
+    """End to end through the public update API: every step is one scene update
+    on the resident scene: pinned host targets and masks copied to the device,
+    change-mask lifting, planning, `iters_per_update` iterations, the loss read
+    back to the host."""
+    import torch
+    from paper_2506_21117_gb300.update import LocalUpdate
+    tg = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets])).pin_memory()
+    mk = torch.from_numpy(np.concatenate([m.reshape(-1) for m in masks])).pin_memory()
+    state = lu.state
+    h2d = tg.numel() * 4 + mk.numel()
+    its = args.iters_per_update
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_updates):
+        u = LocalUpdate.from_resident(state, cams, tg, mk, loss="l1")
+        u.run(its)
+        loss = float(u.batch.loss[0].item())
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": args.e2e_updates * its / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": 4, "step": f"one scene update of {its} iterations",
+            "loss": loss}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle on the machine's host cores, each step a bounded sample."""
+    import torch
+    from oracle import fp32_index as fx
+    scene, target_scene, cams, masks, box = setup_workload(args, seed=0)
+    c, o = fx.votes(scene["means"], cams, masks)
+    active = fx.vote_rule(c, o, len(cams))
+    tiles_total = sum(int(fx.tile_mask(fx.project_index(scene, cam), active, cam).sum())
+                      for cam in cams)
+    from paper_2506_21117_gb300 import synthetic as S
+    targets = [S.random_image(cam, 0) for cam in cams]
+    times = []
+    for k in range(args.warmup + args.steps):
+        sec, desc = oracle_sample(scene, cams, targets, active, tiles_total, 1, proj_frac=0.02,
+                                  seed=k)
+        if k >= args.warmup:
+            times.append(sec)
+    sec = sum(times) / len(times)
+    v = 1.0 / sec
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank, world)))
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

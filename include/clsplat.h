@@ -1,0 +1,281 @@
+/*
+ * clsplat.h - C ABI of the GB300 (sm_103a) active-set Gaussian-splatting
+ * library: the local-optimisation hot path of CL-Splats (arXiv 2506.21117).
+ *
+ * The paper updates an existing 3D Gaussian Splatting scene after a local
+ * change: Gaussians whose centres project into the 2D change masks of enough
+ * new views form the active set O^t (Sec. 3.2, Supp. majority-voting
+ * equation); only O^t is optimised, while every other Gaussian is still
+ * rendered as a frozen occluder (Table 4 (a)); rendering and back-propagation
+ * run only on the 16x16 tiles that O^t touches, and the gradients of O^t are
+ * the full-scene gradients (Sec. 3.3 and Supp. "Local Optimization Kernel").
+ * The rasterizer itself is the base 3DGS method's (Supp. "Implementation
+ * Details"): EWA projection with SH colour, 3-sigma tile binning, a
+ * (tile, depth) sort and front-to-back alpha compositing.
+ *
+ * Conventions shared by every call
+ *  - All pointers named *_dev, and every array argument unless stated
+ *    otherwise, are DEVICE pointers owned by the caller. The library never
+ *    allocates, frees or synchronises; it only enqueues work on `stream`.
+ *  - Work buffers come from the caller; their sizes come from the matching
+ *    *_workspace_size query. Workspaces must be 256-byte aligned.
+ *  - Every call returns CLS_OK or an error code. Argument errors are detected
+ *    on the host before anything is launched. Errors found on the device
+ *    (pair capacity exceeded, a wait that gave up) are written to the caller's
+ *    device status word `status_dev` (CLS_OK is never written there, so the
+ *    caller zeroes it once and reads it after a synchronisation); the kernels
+ *    stay within every buffer whatever the status.
+ *  - float32 throughout; row-major; no ownership is transferred.
+ *
+ * Gaussian parameter rows (one row of `row_stride` floats per Gaussian):
+ *   [0..2] mean xyz   [3] opacity logit   [4..6] log scale xyz   [7] unused
+ *   [8..11] rotation quaternion (w, x, y, z), any non-zero norm
+ *   [12 ..] SH coefficients, coefficient-major: sh[k*3 + channel], k < (deg+1)^2
+ *   row_stride = cls_row_stride(sh_degree): 16, 24, 40, 64 for degree 0..3.
+ */
+#ifndef CLSPLAT_H
+#define CLSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cls_stream_t; /* the same handle as cudaStream_t */
+
+enum {
+    CLS_OK = 0,
+    CLS_ERR_INVALID_ARG = 1, /* bad size, NULL pointer or unsupported option */
+    CLS_ERR_CAPACITY = 2,    /* more (Gaussian, tile) pairs than key capacity */
+    CLS_ERR_CUDA = 3,        /* a launch failed (cudaGetLastError) */
+    CLS_ERR_TIMEOUT = 4      /* a bounded device wait gave up */
+};
+
+#define CLS_TILE 16
+#define CLS_MAX_SH_DEGREE 3
+
+/* Pinhole camera (Supp. "Camera Pose Estimation": poses are inputs).
+ * p_cam = R * p_world + t; x right, y down, z forward; pixel (i, j) covers
+ * [i, i+1) x [j, j+1); u = fx * x / z + cx. `pos` is the camera centre in
+ * world space (origin of the SH view direction). Points with z <= znear are
+ * culled. */
+typedef struct ClsCamera {
+    float R[9];
+    float t[3];
+    float pos[3];
+    float fx, fy, cx, cy;
+    float znear;
+    int32_t width, height;
+} ClsCamera;
+
+/* One scene of a batch. `params`, `adam_m`, `adam_v` are [n][row_stride].
+ * `active_idx` lists O^t in ascending order (n_active entries). `adam_step`
+ * is one device int per scene (the shared Adam step counter t). Fields marked
+ * "derived" are filled by cls_batch_prepare. */
+typedef struct ClsScene {
+    float* params;
+    float* adam_m;
+    float* adam_v;
+    const int32_t* active_idx;
+    int32_t* adam_step;
+    int32_t n;
+    int32_t row_stride;
+    int32_t sh_degree;
+    int32_t n_active;
+    int32_t first_view; /* views of a scene are contiguous in the view table */
+    int32_t n_views;
+    int64_t grad_base;  /* derived: first row of this scene in `grads` */
+} ClsScene;
+
+/* One rendered view of a batch. Every view belongs to one scene. */
+typedef struct ClsView {
+    ClsCamera cam;
+    int32_t scene;
+    int32_t tiles_x, tiles_y; /* derived: ceil(W/16), ceil(H/16) */
+    int32_t tile_base;        /* derived: first global tile id */
+    int32_t sat_base;         /* derived: first entry of its tile-count table */
+    int32_t pad0;
+    int64_t rec_base;         /* derived: first projected record (= sum of n of earlier views) */
+    int64_t pix_base;         /* derived: first pixel in per-pixel buffers */
+    int64_t g2_base;          /* derived: first 2D-gradient slot (sum of n_active of earlier views) */
+    float loss_scale;         /* derived: 1 / (3 W H n_views(scene)) */
+    int32_t pad1;
+} ClsView;
+
+/* Totals of a batch, filled by cls_batch_prepare (host struct). */
+typedef struct ClsBatchInfo {
+    int32_t n_scenes, n_views;
+    int32_t max_n, max_active;
+    int32_t max_row_stride;
+    int32_t key_bits;      /* 32 + bits of the largest global tile id */
+    int64_t total_tiles;   /* sum of tiles_x * tiles_y */
+    int64_t total_sat;     /* sum of (tiles_x + 1) * (tiles_y + 1) */
+    int64_t total_records; /* sum over views of n(scene) */
+    int64_t total_pixels;  /* sum over views of W * H */
+    int64_t total_g2;      /* sum over views of n_active(scene) */
+    int64_t total_grad_rows; /* sum over scenes of n_active */
+} ClsBatchInfo;
+
+/* Projected 2D record of one Gaussian in one view (48 bytes), written by
+ * cls_project_and_bin at record index view.rec_base + gaussian index.
+ * radius == 0 marks a culled Gaussian. `g2_slot` is the 2D-gradient slot of an
+ * active Gaussian (view.g2_base + rank in active_idx) or -1 (static). */
+typedef struct ClsProjected {
+    float u, v, conic_a, conic_b;
+    float conic_c, opacity, r, g;
+    float b;
+    int32_t g2_slot;
+    float z;
+    int32_t radius;
+} ClsProjected;
+
+/* Floats per parameter row for an SH degree (0..3); -1 if out of range. */
+int32_t cls_row_stride(int32_t sh_degree);
+
+/* Fill the derived fields of `scenes` and `views` (host arrays) and the batch
+ * totals. Views must be grouped by scene (scene s owns views
+ * [first_view, first_view + n_views)). Pure host code; copy both tables to
+ * the device afterwards. Returns CLS_ERR_INVALID_ARG on inconsistent tables. */
+int cls_batch_prepare(ClsScene* scenes, int32_t n_scenes, ClsView* views, int32_t n_views,
+                      ClsBatchInfo* info);
+
+/* ------------------------------------------------------------------------
+ * Change-mask lifting (Sec. 3.2 "Mask Majority Voting"; Supp. "Identifying
+ * Changed 3D Regions via Majority Voting", voting equation).
+ * For every Gaussian of one scene and every one of its views: project the
+ * centre, c = views whose binary mask is non-zero at the centre's pixel,
+ * o = views where the centre is outside the image or behind znear.
+ * vote_mode 0: active iff 4 o < 3 V and V < 2 c  ((4/3) o < |I^t| < 2 c).
+ * vote_mode 1 ("All Vote", Table 4 (b)): active iff c == V.
+ *   params      [n][row_stride] of the scene (only the mean is read)
+ *   views_dev   the batch view table; this scene's views are
+ *               [first_view, first_view + n_views)
+ *   masks       uint8, view j's H x W mask at offset views[j].pix_base
+ *   active_out  uint8 [n] (1 = in O^t)
+ *   active_idx_out int32 [n] capacity; ascending indices of O^t
+ *   n_active_out   device int32 (count)
+ *   votes_out   optional int32 [n][2] = (c, o), may be NULL
+ * The float32 projection uses one fixed sequence of correctly rounded
+ * operations, so the votes are bit-reproducible. */
+size_t cls_lift_workspace_size(int32_t n);
+int cls_lift_change_masks(const float* params, int32_t n, int32_t row_stride,
+                          const ClsView* views_dev, int32_t first_view, int32_t n_views,
+                          const uint8_t* masks, int32_t vote_mode, uint8_t* active_out,
+                          int32_t* active_idx_out, int32_t* n_active_out, int32_t* votes_out,
+                          void* workspace, size_t workspace_bytes, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Projection, dynamic render mask and binning (Supp. "Local Optimization
+ * Kernel", item 1; base 3DGS preprocessing).
+ * project_mode 0 projects every Gaussian of every view (the frozen occluders;
+ * do this once per camera set), mode 1 re-projects only the active Gaussians
+ * (every iteration, after the parameters change). Then:
+ *   tile_active[total_tiles]  uint8: 1 iff a non-culled active Gaussian's
+ *                             tile rectangle holds the tile
+ *   active_tiles[total_tiles] int32: ascending global ids of active tiles,
+ *                             n_active_tiles_dev = their count
+ *   keys/vals [capacity]      one (key, value) per (Gaussian, active tile)
+ *                             pair, static and active Gaussians alike:
+ *                             key = (global tile id << 32) | bits(depth z),
+ *                             value = record index; emitted in view order,
+ *                             then Gaussian order, then row-major tile order
+ *   n_pairs_dev               device int64: number of pairs needed; if it
+ *                             exceeds `capacity`, CLS_ERR_CAPACITY is written
+ *                             to status_dev and only `capacity` pairs are kept.
+ * Tile rectangle: radius r = ceil(3 sqrt(lambda_max(Sigma'))), tiles
+ * floor((u - r)/16) .. floor((u + r)/16) clamped to the grid (same for v).
+ * records [total_records] ClsProjected. */
+size_t cls_project_workspace_size(const ClsBatchInfo* info);
+int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
+                        const ClsBatchInfo* info, int32_t project_mode, ClsProjected* records,
+                        uint8_t* tile_active, int32_t* active_tiles, int32_t* n_active_tiles_dev,
+                        uint64_t* keys, uint32_t* vals, int64_t capacity, int64_t* n_pairs_dev,
+                        int32_t* status_dev, void* workspace, size_t workspace_bytes,
+                        cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Stable LSD radix sort of the (tile, depth) keys with their values
+ * (Supp. "Local Optimization Kernel", item 1: per-tile depth order), one
+ * 8-bit digit per pass, single-pass digit scattering with decoupled
+ * look-back, then the per-tile [start, end) ranges.
+ *   keys, vals        [capacity] in/out; sorted result ends here
+ *   keys_alt, vals_alt [capacity] ping-pong buffers
+ *   n_pairs_dev       device int64 count (values above capacity are clamped)
+ *   key_bits          significant key bits (<= 64); passes = ceil(bits / 8)
+ *   ranges            optional uint32 [n_tiles][2] (start, end); tiles with
+ *                     no pair get (0, 0); may be NULL
+ * A look-back wait that exceeds its iteration bound writes CLS_ERR_TIMEOUT
+ * to status_dev and the pass completes with unspecified order. */
+size_t cls_sort_workspace_size(int64_t capacity, int32_t key_bits);
+int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                  const int64_t* n_pairs_dev, int64_t capacity, int32_t key_bits,
+                  uint32_t* ranges, int64_t n_tiles, int32_t* status_dev, void* workspace,
+                  size_t workspace_bytes, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Forward render of the active tiles only (Supp. "Local Optimization
+ * Kernel", item 2). Per pixel of an active tile, over its tile's sorted list:
+ * alpha = min(0.99, opacity * exp(-1/2 (A dx^2 + C dy^2) - B dx dy)), skipped
+ * if the exponent is > 0 or alpha < 1/255; stop before a Gaussian when
+ * T (1 - alpha) < 1e-4; C += colour alpha T; T *= 1 - alpha; C += T bg.
+ * Outputs at the view's pix_base (pixels of inactive tiles are not written):
+ *   image      [3][H][W] per view (planar), may be NULL
+ *   T_final    [H][W], n_contrib [H][W] (one past the last list position
+ *              composited, counted from the tile's range start)
+ *   loss_mode  0 none, 1 L1, 2 L2 against `target` ([3][H][W] per view):
+ *              dL_dimage = l'(C - C*) * loss_scale and loss_per_scene[scene]
+ *              += sum l(C - C*) * loss_scale over the rendered pixels.
+ *              dL_dimage and loss_per_scene may be NULL when loss_mode is 0;
+ *              loss_per_scene is accumulated, the caller zeroes it.
+ *   work_counter device int32 scratch (reset by the call).
+ * bg is a host array of 3 floats. */
+int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
+                       const ClsProjected* records, const uint32_t* vals, const uint32_t* ranges,
+                       const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
+                       const float* bg, const float* target, int32_t loss_mode, float* image,
+                       float* T_final, int32_t* n_contrib, float* dL_dimage,
+                       float* loss_per_scene, int32_t* work_counter, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Backward pass (Supp. "Local Optimization Kernel", items 2 and 3). Pixel
+ * part: per active-tile pixel, walk its list from the last contributor back
+ * to the front, recovering T before each Gaussian as T_after / (1 - alpha)
+ * (no per-Gaussian-per-pixel state is stored); static Gaussians update T and
+ * the colour behind but produce no gradient; the 2D gradients of each active
+ * Gaussian are reduced over the tile's pixels and added into
+ *   grad2d [total_g2][12]: du, dv, dA, dB, dC, d opacity, d r, d g, d b, 0, 0, 0
+ * (zeroed by the call). Gaussian part (active Gaussians only): chain rule to
+ * every parameter of the row, summed over the scene's views, written to
+ *   grads [total_grad_rows][row_stride] at row scene.grad_base + rank
+ * (every float of the row is written). dL_dimage as written by the forward
+ * call or supplied by the caller ([3][H][W] per view). */
+int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
+                        const ClsBatchInfo* info, const ClsProjected* records,
+                        const uint32_t* vals, const uint32_t* ranges, const int32_t* active_tiles,
+                        const int32_t* n_active_tiles_dev, const float* bg, const float* T_final,
+                        const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
+                        float* grads, int32_t* work_counter, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Masked Adam on the active set (Supp. "3DGS Optimization in Changed
+ * Regions"): increments each scene's adam_step t, then for every active row
+ * and every float of it: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). Rows of
+ * Gaussians outside O^t (params, adam_m, adam_v) are never touched.
+ *   grads   [total_grad_rows][row_stride] as written by cls_render_backward
+ *   workspace: cls_adam_workspace_size(n_scenes) bytes */
+size_t cls_adam_workspace_size(int32_t n_scenes);
+int cls_adam_step_active(const ClsScene* scenes_dev, const ClsBatchInfo* info, const float* grads,
+                         float lr, float beta1, float beta2, float eps, void* workspace,
+                         size_t workspace_bytes, cls_stream_t stream);
+
+/* Library version string. */
+const char* cls_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLSPLAT_H */

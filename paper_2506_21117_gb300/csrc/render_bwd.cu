@@ -1,0 +1,425 @@
+// Backward pass of the local optimisation (Supp. "Local Optimization Kernel",
+// items 2 and 3).
+//
+// Pixel part: one 256-thread block per active tile (persistent, queue of
+// tiles). Each pixel walks its list from its last contributor back to the
+// front, recovering the transmittance in front of each Gaussian as
+// T_after / (1 - alpha) and keeping the colour already composited behind it,
+// so nothing per (pixel, Gaussian) is stored by the forward pass. Static
+// Gaussians update T and the colour behind but skip all gradient work. The 2D
+// gradients of an active Gaussian are reduced over the tile with warp shuffles
+// and a shared-memory sum over warps, then added to global memory with one
+// atomic per component per tile.
+//
+// Gaussian part: one thread per active Gaussian; the chain rule from the 2D
+// gradients of every view of its scene to every float of its parameter row.
+#include "common.cuh"
+
+namespace cls {
+
+constexpr int kSub = 32;      // list entries reduced per shared-memory flush
+constexpr int kGradComps = 9; // du dv dA dB dC dopacity dr dg db
+constexpr int kG2Stride = 12;
+
+__global__ void __launch_bounds__(kTilePixels)
+render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
+                  const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
+                  const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
+                  const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
+                  const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib,
+                  const float* __restrict__ dL_dimage, float* __restrict__ grad2d,
+                  int* __restrict__ work_counter) {
+    __shared__ float4 s_a[kTilePixels];
+    __shared__ float4 s_b[kTilePixels];
+    __shared__ float s_c[kTilePixels];
+    __shared__ int s_slot[kTilePixels];
+    __shared__ float s_g[kSub][kTilePixels / 32][kGradComps + 1];
+    __shared__ int s_tile;
+    __shared__ int s_maxlast;
+    const int n_tiles = *n_active_tiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(work_counter, 1);
+            s_maxlast = 0;
+        }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= n_tiles) break;
+        const int tile = active_tiles[t];
+        const ClsView& view = views[view_of_tile(views, n_views, tile)];
+        const int local = tile - view.tile_base;
+        const int tx = local % view.tiles_x, ty = local / view.tiles_x;
+        const int W = view.cam.width, H = view.cam.height;
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+        const uint32_t start = ranges[2 * (int64_t)tile];
+
+        float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        int last = 0;
+        if (inside) {
+            const int64_t pix = view.pix_base + (int64_t)py * W + px;
+            const int64_t plane = (int64_t)W * H;
+            const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
+            T = T_final[pix];
+            last = n_contrib[pix];
+            g0 = dL_dimage[p3];
+            g1 = dL_dimage[p3 + plane];
+            g2 = dL_dimage[p3 + 2 * plane];
+            atomicMax(&s_maxlast, last);
+        }
+        float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;  // colour behind
+        __syncthreads();
+        const int max_last = s_maxlast;
+
+        for (int hi = max_last; hi > 0; hi -= kTilePixels) {
+            const int lo = hi > kTilePixels ? hi - kTilePixels : 0;
+            const int nb = hi - lo;
+            if ((int)threadIdx.x < nb) {
+                const float4* rec =
+                    reinterpret_cast<const float4*>(records + vals[start + lo + threadIdx.x]);
+                s_a[threadIdx.x] = rec[0];
+                s_b[threadIdx.x] = rec[1];
+                const float4 c = rec[2];
+                s_c[threadIdx.x] = c.x;
+                s_slot[threadIdx.x] = __float_as_int(c.y);
+            }
+            __syncthreads();
+            for (int kk = nb - 1; kk >= 0; kk -= kSub) {
+                const int sub_lo = kk >= kSub - 1 ? kk - (kSub - 1) : 0;
+                bool any_active = false;
+                for (int k = kk; k >= sub_lo; --k) {
+                    const int pos = lo + k;
+                    const float4 a = s_a[k];
+                    const float4 bb = s_b[k];
+                    const float dx = fx - a.x, dy = fy - a.y;
+                    bool contrib = inside && pos < last;
+                    float alpha = 0.f, G = 0.f, power = 0.f;
+                    if (contrib) {
+                        power = pair_power(dx, dy, a.z, a.w, bb.x);
+                        contrib = power <= 0.0f;
+                        if (contrib) {
+                            G = __expf(power);
+                            alpha = fminf(kAlphaMax, bb.y * G);
+                            contrib = alpha >= kAlphaMin;
+                        }
+                    }
+                    const float cr = bb.z, cg = bb.w, cb = s_c[k];
+                    const bool active = s_slot[k] >= 0;
+                    float gr[kGradComps];
+                    if (contrib) {
+                        const float om = 1.0f - alpha;
+                        T = T / om;
+                        const float w = alpha * T;
+                        if (active) {
+                            const float inv_om = 1.0f / om;
+                            const float dLda = g0 * (cr * T - S0 * inv_om) +
+                                               g1 * (cg * T - S1 * inv_om) +
+                                               g2 * (cb * T - S2 * inv_om);
+                            const bool clamped = bb.y * G > kAlphaMax;
+                            const float dpow = clamped ? 0.f : dLda * alpha;
+                            gr[0] = dpow * (a.z * dx + a.w * dy);
+                            gr[1] = dpow * (bb.x * dy + a.w * dx);
+                            gr[2] = -0.5f * dx * dx * dpow;
+                            gr[3] = -dx * dy * dpow;
+                            gr[4] = -0.5f * dy * dy * dpow;
+                            gr[5] = clamped ? 0.f : dLda * G;
+                            gr[6] = w * g0;
+                            gr[7] = w * g1;
+                            gr[8] = w * g2;
+                        }
+                        S0 += cr * w;
+                        S1 += cg * w;
+                        S2 += cb * w;
+                    }
+                    if (active) {  // uniform over the block
+                        any_active = true;
+                        if (!(contrib)) {
+#pragma unroll
+                            for (int c = 0; c < kGradComps; ++c) gr[c] = 0.f;
+                        }
+                        if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                            for (int c = 0; c < kGradComps; ++c) {
+                                float x = gr[c];
+#pragma unroll
+                                for (int o = 16; o > 0; o >>= 1)
+                                    x += __shfl_xor_sync(0xffffffffu, x, o);
+                                gr[c] = x;
+                            }
+                        }
+                        if (lane == 0) {
+#pragma unroll
+                            for (int c = 0; c < kGradComps; ++c) s_g[k - sub_lo][warp][c] = gr[c];
+                        }
+                    }
+                }
+                if (any_active) {  // uniform over the block
+                    __syncthreads();
+                    const int cnt = kk - sub_lo + 1;
+                    for (int e = threadIdx.x; e < cnt * kGradComps; e += kTilePixels) {
+                        const int ent = e / kGradComps, comp = e - ent * kGradComps;
+                        const int slot = s_slot[sub_lo + ent];
+                        if (slot < 0) continue;
+                        float sum = 0.f;
+#pragma unroll
+                        for (int w = 0; w < kTilePixels / 32; ++w) sum += s_g[ent][w][comp];
+                        if (sum != 0.f) atomicAdd(grad2d + (int64_t)slot * kG2Stride + comp, sum);
+                    }
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+        }
+        __syncthreads();  // s_tile / s_maxlast are rewritten for the next tile
+    }
+}
+
+// d Y_k / d(x, y, z) contracted with coefficients dY[k], accumulated in g.
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, int degree,
+                                             const float* dY, float& gx, float& gy, float& gz) {
+    const float C1 = 0.4886025119029199f;
+    if (degree < 1) return;
+    gy += -C1 * dY[1];
+    gz += C1 * dY[2];
+    gx += -C1 * dY[3];
+    if (degree < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    const float a0 = 1.0925484305920792f, a1 = -1.0925484305920792f, a2 = 0.31539156525252005f,
+                a3 = -1.0925484305920792f, a4 = 0.5462742152960396f;
+    gx += a0 * y * dY[4];              gy += a0 * x * dY[4];
+    gy += a1 * z * dY[5];              gz += a1 * y * dY[5];
+    gx += -2.f * a2 * x * dY[6];       gy += -2.f * a2 * y * dY[6];   gz += 4.f * a2 * z * dY[6];
+    gx += a3 * z * dY[7];              gz += a3 * x * dY[7];
+    gx += 2.f * a4 * x * dY[8];        gy += -2.f * a4 * y * dY[8];
+    if (degree < 3) return;
+    const float b0 = -0.5900435899266435f, b1 = 2.890611442640554f, b2 = -0.4570457994644658f,
+                b3 = 0.3731763325901154f, b4 = -0.4570457994644658f, b5 = 1.445305721320277f,
+                b6 = -0.5900435899266435f;
+    gx += 6.f * b0 * x * y * dY[9];    gy += b0 * (3.f * xx - 3.f * yy) * dY[9];
+    gx += b1 * y * z * dY[10];         gy += b1 * x * z * dY[10];    gz += b1 * x * y * dY[10];
+    gx += -2.f * b2 * x * y * dY[11];  gy += b2 * (4.f * zz - xx - 3.f * yy) * dY[11];
+    gz += 8.f * b2 * y * z * dY[11];
+    gx += -6.f * b3 * x * z * dY[12];  gy += -6.f * b3 * y * z * dY[12];
+    gz += b3 * (6.f * zz - 3.f * xx - 3.f * yy) * dY[12];
+    gx += b4 * (4.f * zz - 3.f * xx - yy) * dY[13];  gy += -2.f * b4 * x * y * dY[13];
+    gz += 8.f * b4 * x * z * dY[13];
+    gx += 2.f * b5 * x * z * dY[14];   gy += -2.f * b5 * y * z * dY[14];
+    gz += b5 * (xx - yy) * dY[14];
+    gx += b6 * (3.f * xx - 3.f * yy) * dY[15];  gy += -6.f * b6 * x * y * dY[15];
+}
+
+__global__ void __launch_bounds__(128)
+backward_gaussian_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
+                         const float* __restrict__ grad2d, float* __restrict__ grads) {
+    const ClsScene& sc = scenes[blockIdx.y];
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= sc.n_active) return;
+    const int g = sc.active_idx[a];
+    const float* row = sc.params + (int64_t)g * sc.row_stride;
+    const float4 m = *reinterpret_cast<const float4*>(row);
+    const float4 ls = *reinterpret_cast<const float4*>(row + 4);
+    const float4 q = *reinterpret_cast<const float4*>(row + 8);
+    const int deg = sc.sh_degree;
+    const int K = (deg + 1) * (deg + 1);
+    const float* sh = row + 12;
+
+    float dmean[3] = {0.f, 0.f, 0.f}, dls[3] = {0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+    float dlogit = 0.f;
+    float dsh[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) dsh[i] = 0.f;
+
+    for (int j = sc.first_view; j < sc.first_view + sc.n_views; ++j) {
+        const ClsView& view = views[j];
+        const float4* g2p = reinterpret_cast<const float4*>(grad2d + (view.g2_base + a) * kG2Stride);
+        const float4 e0 = g2p[0], e1 = g2p[1], e2 = g2p[2];
+        const float du = e0.x, dv = e0.y, dA = e0.z, dB = e0.w, dC = e1.x, dop = e1.y;
+        const float dcol[3] = {e1.z, e1.w, e2.x};
+        if (du == 0.f && dv == 0.f && dA == 0.f && dB == 0.f && dC == 0.f && dop == 0.f &&
+            dcol[0] == 0.f && dcol[1] == 0.f && dcol[2] == 0.f)
+            continue;
+        const ClsCamera& cam = view.cam;
+        Proj P;
+        project_gaussian(cam, m, ls, q, P);
+
+        // colour
+        float ddx = m.x - cam.pos[0], ddy = m.y - cam.pos[1], ddz = m.z - cam.pos[2];
+        const float len = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+        const float il = 1.0f / len;
+        const float dxn = ddx * il, dyn = ddy * il, dzn = ddz * il;
+        float Y[16];
+        sh_basis(dxn, dyn, dzn, deg, Y);
+        float raw[3] = {0.5f, 0.5f, 0.5f};
+        for (int k = 0; k < K; ++k) {
+            raw[0] += Y[k] * sh[3 * k];
+            raw[1] += Y[k] * sh[3 * k + 1];
+            raw[2] += Y[k] * sh[3 * k + 2];
+        }
+        float draw[3];
+        for (int c = 0; c < 3; ++c) draw[c] = raw[c] >= 0.f ? dcol[c] : 0.f;
+        float dY[16];
+        for (int k = 0; k < K; ++k) {
+            dsh[3 * k] += Y[k] * draw[0];
+            dsh[3 * k + 1] += Y[k] * draw[1];
+            dsh[3 * k + 2] += Y[k] * draw[2];
+            dY[k] = sh[3 * k] * draw[0] + sh[3 * k + 1] * draw[1] + sh[3 * k + 2] * draw[2];
+        }
+        float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+        sh_basis_vjp(dxn, dyn, dzn, deg, dY, gdx, gdy, gdz);
+        const float dotd = gdx * dxn + gdy * dyn + gdz * dzn;
+        dmean[0] += (gdx - dxn * dotd) * il;
+        dmean[1] += (gdy - dyn * dotd) * il;
+        dmean[2] += (gdz - dzn * dotd) * il;
+
+        // opacity
+        const float sig = 1.0f / (1.0f + __expf(-m.w));
+        dlogit += dop * sig * (1.0f - sig);
+
+        // conic -> 2D covariance (a, b, c)
+        const float ca = P.a, cb = P.b, cc = P.c;
+        const float det = P.det;
+        const float id2 = 1.0f / (det * det);
+        const float da = (-cc * cc * dA + cb * cc * dB - cb * cb * dC) * id2;
+        const float dc = (-cb * cb * dA + ca * cb * dB - ca * ca * dC) * id2;
+        const float db = (2.f * cb * cc * dA - (ca * cc + cb * cb) * dB + 2.f * ca * cb * dC) * id2;
+
+        // 2D covariance -> 3D covariance and T = J W
+        const float* T = P.T;
+        const float* S = P.Sig;
+        // Sigma T0^T and Sigma T1^T
+        const float ST0[3] = {S[0] * T[0] + S[1] * T[1] + S[2] * T[2],
+                              S[1] * T[0] + S[3] * T[1] + S[4] * T[2],
+                              S[2] * T[0] + S[4] * T[1] + S[5] * T[2]};
+        const float ST1[3] = {S[0] * T[3] + S[1] * T[4] + S[2] * T[5],
+                              S[1] * T[3] + S[3] * T[4] + S[4] * T[5],
+                              S[2] * T[3] + S[4] * T[4] + S[5] * T[5]};
+        float dT0[3], dT1[3];
+        for (int i = 0; i < 3; ++i) {
+            dT0[i] = 2.f * da * ST0[i] + db * ST1[i];
+            dT1[i] = 2.f * dc * ST1[i] + db * ST0[i];
+        }
+        // symmetric gradient of Sigma: G = da T0'T0 + db sym(T0'T1) + dc T1'T1
+        float Gs[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k)
+                Gs[i][k] = da * T[i] * T[k] + 0.5f * db * (T[i] * T[3 + k] + T[3 + i] * T[k]) +
+                           dc * T[3 + i] * T[3 + k];
+        // M = Rq diag(s); dL/dM = 2 G M
+        float Mx[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) Mx[i][k] = P.Rq[i * 3 + k] * P.s[k];
+        float dRq[9];
+        float ds[3] = {0.f, 0.f, 0.f};
+        for (int i = 0; i < 3; ++i) {
+            for (int k = 0; k < 3; ++k) {
+                const float dM = 2.f * (Gs[i][0] * Mx[0][k] + Gs[i][1] * Mx[1][k] + Gs[i][2] * Mx[2][k]);
+                dRq[i * 3 + k] = dM * P.s[k];
+                ds[k] += dM * P.Rq[i * 3 + k];
+            }
+        }
+        for (int k = 0; k < 3; ++k) dls[k] += ds[k] * P.s[k];
+        // rotation matrix -> normalised quaternion -> raw quaternion
+        {
+            const float w = P.qn[0], x = P.qn[1], y = P.qn[2], z = P.qn[3];
+            const float* Gq = dRq;
+            const float dw = 2.f * (-z * Gq[1] + y * Gq[2] + z * Gq[3] - x * Gq[5] - y * Gq[6] +
+                                    x * Gq[7]);
+            const float dx_ = 2.f * (y * Gq[1] + z * Gq[2] + y * Gq[3] - 2.f * x * Gq[4] - w * Gq[5] +
+                                     z * Gq[6] + w * Gq[7] - 2.f * x * Gq[8]);
+            const float dy_ = 2.f * (-2.f * y * Gq[0] + x * Gq[1] + w * Gq[2] + x * Gq[3] + z * Gq[5] -
+                                     w * Gq[6] + z * Gq[7] - 2.f * y * Gq[8]);
+            const float dz_ = 2.f * (-2.f * z * Gq[0] - w * Gq[1] + x * Gq[2] + w * Gq[3] -
+                                     2.f * z * Gq[4] + y * Gq[5] + x * Gq[6] + y * Gq[7]);
+            const float dot = w * dw + x * dx_ + y * dy_ + z * dz_;
+            const float inv = 1.0f / P.qnorm;
+            dq[0] += (dw - w * dot) * inv;
+            dq[1] += (dx_ - x * dot) * inv;
+            dq[2] += (dy_ - y * dot) * inv;
+            dq[3] += (dz_ - z * dot) * inv;
+        }
+        // T = J W -> J entries -> camera-space point
+        const float* Wr = cam.R;
+        const float dJ00 = dT0[0] * Wr[0] + dT0[1] * Wr[1] + dT0[2] * Wr[2];
+        const float dJ02 = dT0[0] * Wr[6] + dT0[1] * Wr[7] + dT0[2] * Wr[8];
+        const float dJ11 = dT1[0] * Wr[3] + dT1[1] * Wr[4] + dT1[2] * Wr[5];
+        const float dJ12 = dT1[0] * Wr[6] + dT1[1] * Wr[7] + dT1[2] * Wr[8];
+        const float pz = P.pz;
+        const float iz = 1.0f / pz, iz2 = iz * iz, iz3 = iz2 * iz;
+        const float limx = 1.3f * (0.5f * (float)cam.width / cam.fx);
+        const float limy = 1.3f * (0.5f * (float)cam.height / cam.fy);
+        const float txz = fminf(fmaxf(P.xz, -limx), limx);
+        const float tyz = fminf(fmaxf(P.yz, -limy), limy);
+        const float tx = txz * pz, ty = tyz * pz;
+        const float dtx = -cam.fx * iz2 * dJ02;
+        const float dty = -cam.fy * iz2 * dJ12;
+        float dpx = 0.f, dpy = 0.f;
+        float dpz = -cam.fx * iz2 * dJ00 + 2.f * cam.fx * tx * iz3 * dJ02 - cam.fy * iz2 * dJ11 +
+                    2.f * cam.fy * ty * iz3 * dJ12;
+        if (P.clamp_x) dpz += dtx * txz; else dpx += dtx;
+        if (P.clamp_y) dpz += dty * tyz; else dpy += dty;
+        // image position
+        dpx += du * cam.fx * iz;
+        dpy += dv * cam.fy * iz;
+        dpz += -(du * cam.fx * P.px + dv * cam.fy * P.py) * iz2;
+        dmean[0] += Wr[0] * dpx + Wr[3] * dpy + Wr[6] * dpz;
+        dmean[1] += Wr[1] * dpx + Wr[4] * dpy + Wr[7] * dpz;
+        dmean[2] += Wr[2] * dpx + Wr[5] * dpy + Wr[8] * dpz;
+    }
+
+    float* out = grads + (sc.grad_base + a) * sc.row_stride;
+    reinterpret_cast<float4*>(out)[0] = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
+    reinterpret_cast<float4*>(out)[1] = make_float4(dls[0], dls[1], dls[2], 0.f);
+    reinterpret_cast<float4*>(out)[2] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+    for (int i = 0; i < sc.row_stride - 12; i += 4) {
+        float4 v;
+        v.x = i < 3 * K ? dsh[i] : 0.f;
+        v.y = i + 1 < 3 * K ? dsh[i + 1] : 0.f;
+        v.z = i + 2 < 3 * K ? dsh[i + 2] : 0.f;
+        v.w = i + 3 < 3 * K ? dsh[i + 3] : 0.f;
+        reinterpret_cast<float4*>(out + 12)[i / 4] = v;
+    }
+}
+
+static int g_bwd_blocks = 0;
+
+}  // namespace cls
+
+using namespace cls;
+
+extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
+                                   const ClsBatchInfo* info, const ClsProjected* records,
+                                   const uint32_t* vals, const uint32_t* ranges,
+                                   const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
+                                   const float* bg, const float* T_final, const int32_t* n_contrib,
+                                   const float* dL_dimage, float* grad2d, float* grads,
+                                   int32_t* work_counter, cls_stream_t stream) {
+    if (!scenes_dev || !views_dev || !info || !records || !ranges || !active_tiles ||
+        !n_active_tiles_dev || !bg || !T_final || !n_contrib || !dL_dimage || !work_counter ||
+        info->n_views <= 0 || info->total_tiles <= 0 || info->n_scenes > 65535 ||
+        (info->total_g2 > 0 && !grad2d) || (info->total_grad_rows > 0 && !grads))
+        return CLS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (info->total_g2 > 0)
+        cudaMemsetAsync(grad2d, 0, (size_t)info->total_g2 * kG2Stride * sizeof(float), s);
+    if (g_bwd_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel, kTilePixels, 0);
+        g_bwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = (int)hmin64(info->total_tiles, g_bwd_blocks);
+    cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
+    render_bwd_kernel<<<blocks, kTilePixels, 0, s>>>(
+        views_dev, info->n_views, records, vals, ranges, active_tiles, n_active_tiles_dev, bg[0],
+        bg[1], bg[2], T_final, n_contrib, dL_dimage, grad2d, work_counter);
+    if (info->max_active > 0 && info->total_grad_rows > 0) {
+        backward_gaussian_kernel<<<dim3((info->max_active + 127) / 128, info->n_scenes), 128, 0,
+                                   s>>>(scenes_dev, views_dev, grad2d, grads);
+    }
+    CLS_CHECK_LAUNCH();
+    return CLS_OK;
+}

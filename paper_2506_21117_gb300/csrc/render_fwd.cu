@@ -1,0 +1,161 @@
+// Forward rendering of the active tiles (Supp. "Local Optimization Kernel",
+// item 2): one 256-thread block per 16x16 tile, one pixel per thread, the
+// tile's depth-sorted list staged through shared memory in batches of 256
+// records; blocks are persistent and take tiles from a queue. The photometric
+// loss and its pixel gradient are fused into the epilogue.
+#include "common.cuh"
+
+namespace cls {
+
+__global__ void __launch_bounds__(kTilePixels)
+render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
+                  const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
+                  const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
+                  const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
+                  const float* __restrict__ target, int loss_mode, float* __restrict__ image,
+                  float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
+                  float* __restrict__ dL_dimage, float* __restrict__ loss_per_scene,
+                  int* __restrict__ work_counter) {
+    __shared__ float4 s_a[kTilePixels];
+    __shared__ float4 s_b[kTilePixels];
+    __shared__ float s_c[kTilePixels];
+    __shared__ int s_tile;
+    __shared__ float s_red[kTilePixels / 32];
+    const int n_tiles = *n_active_tiles;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(work_counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= n_tiles) break;
+        const int tile = active_tiles[t];
+        const int vi = view_of_tile(views, n_views, tile);
+        const ClsView& view = views[vi];
+        const int local = tile - view.tile_base;
+        const int tx = local % view.tiles_x, ty = local / view.tiles_x;
+        const int W = view.cam.width, H = view.cam.height;
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+        const uint32_t start = ranges[2 * (int64_t)tile], end = ranges[2 * (int64_t)tile + 1];
+
+        float T = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+        uint32_t last = 0;
+        bool done = !inside;
+        for (uint32_t b = start; b < end; b += kTilePixels) {
+            if (__syncthreads_count(done) == kTilePixels) break;
+            const uint32_t idx = b + threadIdx.x;
+            if (idx < end) {
+                const float4* rec = reinterpret_cast<const float4*>(records + vals[idx]);
+                s_a[threadIdx.x] = rec[0];
+                s_b[threadIdx.x] = rec[1];
+                s_c[threadIdx.x] = rec[2].x;
+            }
+            __syncthreads();
+            const int nb = (int)min((uint32_t)kTilePixels, end - b);
+            for (int k = 0; k < nb && !done; ++k) {
+                const float4 a = s_a[k];
+                const float4 bb = s_b[k];
+                const float power = pair_power(fx - a.x, fy - a.y, a.z, a.w, bb.x);
+                if (power > 0.0f) continue;
+                const float alpha = fminf(kAlphaMax, bb.y * __expf(power));
+                if (alpha < kAlphaMin) continue;
+                const float test_T = T * (1.0f - alpha);
+                if (test_T < kTMin) {
+                    done = true;
+                    break;
+                }
+                const float w = alpha * T;
+                c0 += bb.z * w;
+                c1 += bb.w * w;
+                c2 += s_c[k] * w;
+                T = test_T;
+                last = b - start + k + 1;
+            }
+        }
+
+        float lsum = 0.0f;
+        if (inside) {
+            c0 += T * bg0;
+            c1 += T * bg1;
+            c2 += T * bg2;
+            const int64_t pix = view.pix_base + (int64_t)py * W + px;
+            const int64_t plane = (int64_t)W * H;
+            const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
+            T_final[pix] = T;
+            n_contrib[pix] = (int32_t)last;
+            if (image) {
+                image[p3] = c0;
+                image[p3 + plane] = c1;
+                image[p3 + 2 * plane] = c2;
+            }
+            if (loss_mode != 0) {
+                const float d0 = c0 - target[p3], d1 = c1 - target[p3 + plane],
+                            d2 = c2 - target[p3 + 2 * plane];
+                const float sc = view.loss_scale;
+                float g0, g1, g2;
+                if (loss_mode == 1) {
+                    g0 = (d0 > 0.f) - (d0 < 0.f);
+                    g1 = (d1 > 0.f) - (d1 < 0.f);
+                    g2 = (d2 > 0.f) - (d2 < 0.f);
+                    lsum = fabsf(d0) + fabsf(d1) + fabsf(d2);
+                } else {
+                    g0 = 2.f * d0; g1 = 2.f * d1; g2 = 2.f * d2;
+                    lsum = d0 * d0 + d1 * d1 + d2 * d2;
+                }
+                dL_dimage[p3] = g0 * sc;
+                dL_dimage[p3 + plane] = g1 * sc;
+                dL_dimage[p3 + 2 * plane] = g2 * sc;
+                lsum *= sc;
+            }
+        }
+        if (loss_mode != 0 && loss_per_scene) {
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = lsum;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float tot = 0.f;
+                for (int w = 0; w < kTilePixels / 32; ++w) tot += s_red[w];
+                atomicAdd(loss_per_scene + view.scene, tot);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static int g_fwd_blocks = 0;
+
+}  // namespace cls
+
+using namespace cls;
+
+extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
+                                  const ClsProjected* records, const uint32_t* vals,
+                                  const uint32_t* ranges, const int32_t* active_tiles,
+                                  const int32_t* n_active_tiles_dev, const float* bg,
+                                  const float* target, int32_t loss_mode, float* image,
+                                  float* T_final, int32_t* n_contrib, float* dL_dimage,
+                                  float* loss_per_scene, int32_t* work_counter,
+                                  cls_stream_t stream) {
+    if (!views_dev || !info || !records || !ranges || !active_tiles || !n_active_tiles_dev ||
+        !bg || !T_final || !n_contrib || !work_counter || loss_mode < 0 || loss_mode > 2 ||
+        (loss_mode != 0 && (!target || !dL_dimage)) || info->n_views <= 0 ||
+        info->total_tiles <= 0)
+        return CLS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (g_fwd_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel, kTilePixels, 0);
+        g_fwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = (int)hmin64(info->total_tiles, g_fwd_blocks);
+    cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
+    render_fwd_kernel<<<blocks, kTilePixels, 0, s>>>(
+        views_dev, info->n_views, records, vals, ranges, active_tiles, n_active_tiles_dev, bg[0],
+        bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
+        work_counter);
+    CLS_CHECK_LAUNCH();
+    return CLS_OK;
+}

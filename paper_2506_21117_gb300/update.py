@@ -1,0 +1,363 @@
+"""Local scene update on the GPU: the CL-Splats local optimisation loop.
+
+Sec. 3 of the paper: lift the 2D change masks of the new views to the active
+set O^t (Sec. 3.2), then optimise only O^t with a rasterizer restricted to the
+tiles O^t touches, static Gaussians rendered as frozen occluders (Sec. 3.3,
+Supp. "Local Optimization Kernel", Supp. "3DGS Optimization in Changed
+Regions"). Every step runs in libclsplat's CUDA kernels; this module owns the
+device buffers (PyTorch tensors, used for memory and streams only) and the
+order of the calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _abi as abi
+
+LOSS_MODES = {"none": 0, "l1": 1, "l2": 2}
+
+
+def sh_coeffs(degree: int) -> int:
+    return (degree + 1) ** 2
+
+
+def pack_params(scene: Dict[str, np.ndarray], sh_degree: int) -> np.ndarray:
+    """Scene dict -> float32 rows [n][row_stride] in the library's layout."""
+    n = scene["means"].shape[0]
+    stride = abi.cls_row_stride(sh_degree)
+    k = sh_coeffs(sh_degree)
+    rows = np.zeros((n, stride), np.float32)
+    rows[:, 0:3] = scene["means"]
+    rows[:, 3] = scene["opacity_logits"]
+    rows[:, 4:7] = scene["log_scales"]
+    rows[:, 8:12] = scene["quats"]
+    rows[:, 12:12 + 3 * k] = np.asarray(scene["sh"], np.float32)[:, :k, :].reshape(n, 3 * k)
+    return rows
+
+
+def unpack_rows(rows: np.ndarray, sh_degree: int) -> Dict[str, np.ndarray]:
+    """Rows (parameters or gradients) -> dict shaped like a scene."""
+    k = sh_coeffs(sh_degree)
+    n = rows.shape[0]
+    return {"means": rows[:, 0:3], "opacity_logits": rows[:, 3], "log_scales": rows[:, 4:7],
+            "quats": rows[:, 8:12], "sh": rows[:, 12:12 + 3 * k].reshape(n, k, 3)}
+
+
+def make_camera(cam) -> abi.ClsCamera:
+    c = abi.ClsCamera()
+    R = np.asarray(cam["R"], np.float64).reshape(9)
+    for i in range(9):
+        c.R[i] = float(R[i])
+    for i in range(3):
+        c.t[i] = float(cam["t"][i])
+        c.pos[i] = float(cam["pos"][i])
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    c.znear = float(cam["znear"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else t.data_ptr()
+
+
+def _bytes(ctypes_array) -> torch.Tensor:
+    raw = bytes(memoryview(ctypes_array).cast("B"))
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8)
+
+
+class SceneState:
+    """One scene resident on the device: parameter rows, Adam moments and step."""
+
+    def __init__(self, scene: Dict[str, np.ndarray], sh_degree: int, device="cuda"):
+        self.sh_degree = sh_degree
+        self.stride = abi.cls_row_stride(sh_degree)
+        rows = pack_params(scene, sh_degree)
+        self.n = rows.shape[0]
+        self.params = torch.from_numpy(rows).to(device)
+        self.adam_m = torch.zeros_like(self.params)
+        self.adam_v = torch.zeros_like(self.params)
+        self.adam_step = torch.zeros(1, dtype=torch.int32, device=device)
+        self.active = torch.zeros(self.n, dtype=torch.uint8, device=device)
+        self.active_idx = torch.zeros(max(self.n, 1), dtype=torch.int32, device=device)
+        self.n_active = 0
+
+    def set_active(self, active: np.ndarray):
+        a = np.asarray(active, bool)
+        idx = np.flatnonzero(a).astype(np.int32)
+        self.active.copy_(torch.from_numpy(a.astype(np.uint8)))
+        self.active_idx[: idx.size].copy_(torch.from_numpy(idx))
+        self.n_active = int(idx.size)
+
+    def bytes_resident(self) -> int:
+        return 3 * self.params.numel() * 4 + self.active.numel() * 5
+
+
+class Batch:
+    """Scene/view tables of one launch batch and every buffer the hot path uses."""
+
+    def __init__(self, scenes: Sequence[SceneState], cams_per_scene: Sequence[Sequence],
+                 device="cuda"):
+        self.device = device
+        self.scenes = list(scenes)
+        S = len(scenes)
+        views = []
+        for s, cams in enumerate(cams_per_scene):
+            for cam in cams:
+                v = abi.ClsView()
+                v.cam = make_camera(cam)
+                v.scene = s
+                views.append(v)
+        self.n_views = len(views)
+        self.scene_tab = (abi.ClsScene * S)()
+        first = 0
+        for s, st in enumerate(scenes):
+            sc = self.scene_tab[s]
+            sc.params, sc.adam_m, sc.adam_v = _ptr(st.params), _ptr(st.adam_m), _ptr(st.adam_v)
+            sc.active_idx, sc.adam_step = _ptr(st.active_idx), _ptr(st.adam_step)
+            sc.n, sc.row_stride, sc.sh_degree = st.n, st.stride, st.sh_degree
+            sc.n_active = st.n_active
+            sc.first_view, sc.n_views = first, len(cams_per_scene[s])
+            first += len(cams_per_scene[s])
+        self.view_tab = (abi.ClsView * self.n_views)(*views)
+        self.info = abi.ClsBatchInfo()
+        abi.check(abi.cls_batch_prepare(self.scene_tab, self.view_tab, self.info),
+                  "cls_batch_prepare")
+        self.scenes_dev = _bytes(self.scene_tab).to(device)
+        self.views_dev = _bytes(self.view_tab).to(device)
+        info = self.info
+        dev = device
+        self.records = torch.zeros(info.total_records * 12, dtype=torch.float32, device=dev)
+        self.tile_active = torch.zeros(info.total_tiles, dtype=torch.uint8, device=dev)
+        self.active_tiles = torch.zeros(info.total_tiles, dtype=torch.int32, device=dev)
+        self.n_active_tiles = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.n_pairs = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.ranges = torch.zeros(info.total_tiles * 2, dtype=torch.int32, device=dev)
+        self.T_final = torch.zeros(info.total_pixels, dtype=torch.float32, device=dev)
+        self.n_contrib = torch.zeros(info.total_pixels, dtype=torch.int32, device=dev)
+        self.image = torch.zeros(info.total_pixels * 3, dtype=torch.float32, device=dev)
+        self.dL_dimage = torch.zeros(info.total_pixels * 3, dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(S, dtype=torch.float32, device=dev)
+        self.grad2d = torch.zeros(max(info.total_g2, 1) * abi.G2_STRIDE, dtype=torch.float32,
+                                  device=dev)
+        self.grads = torch.zeros(max(info.total_grad_rows, 1) * info.max_row_stride,
+                                 dtype=torch.float32, device=dev)
+        self.counter = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
+                                   device=dev)
+        self.adam_ws = torch.zeros(max(abi.cls_adam_workspace_size(S), 256), dtype=torch.uint8,
+                                   device=dev)
+        self.capacity = 0
+        self.keys = self.vals = self.keys_alt = self.vals_alt = self.sort_ws = None
+        self.target = None
+
+    # -- geometry of per-pixel buffers ---------------------------------------
+    def view_slices(self):
+        out = []
+        for j in range(self.n_views):
+            v = self.view_tab[j]
+            out.append((int(v.pix_base), int(v.cam.height), int(v.cam.width)))
+        return out
+
+    def set_targets(self, targets: Sequence[np.ndarray]):
+        t = torch.zeros(self.info.total_pixels * 3, dtype=torch.float32)
+        for (base, H, W), img in zip(self.view_slices(), targets):
+            t[3 * base: 3 * base + 3 * H * W] = torch.from_numpy(
+                np.ascontiguousarray(img, np.float32).reshape(-1))
+        self.target = t.to(self.device)
+
+    def per_view(self, flat: torch.Tensor, channels: int) -> List[torch.Tensor]:
+        out = []
+        for base, H, W in self.view_slices():
+            out.append(flat[channels * base: channels * (base + H * W)].view(channels, H, W)
+                       if channels > 1 else flat[base: base + H * W].view(H, W))
+        return out
+
+    # -- the hot path -----------------------------------------------------------
+    def stream(self):
+        return torch.cuda.current_stream().cuda_stream
+
+    def project_and_bin(self, mode: int):
+        b = self
+        abi.check(abi.cls_project_and_bin(
+            _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, mode, _ptr(b.records),
+            _ptr(b.tile_active), _ptr(b.active_tiles), _ptr(b.n_active_tiles),
+            _ptr(b.keys), _ptr(b.vals), b.capacity, _ptr(b.n_pairs), _ptr(b.status),
+            _ptr(b.proj_ws), b.proj_ws.numel(), b.stream()), "cls_project_and_bin")
+
+    def plan_capacity(self, slack: float = 1.5, extra: int = 1 << 16):
+        """Count the pairs once (mode 0 projection, no keys) and size the key
+        buffers; the only host synchronisation of an update besides lifting."""
+        cap_before = self.capacity
+        self.capacity = 0
+        self.project_and_bin(0)
+        need = int(self.n_pairs.item())
+        self.status.zero_()
+        cap = max(int(need * slack) + extra, cap_before)
+        self.allocate_keys(cap)
+        return need
+
+    def allocate_keys(self, capacity: int):
+        dev = self.device
+        self.capacity = capacity
+        self.keys = torch.empty(capacity, dtype=torch.int64, device=dev)
+        self.keys_alt = torch.empty(capacity, dtype=torch.int64, device=dev)
+        self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
+        self.vals_alt = torch.empty(capacity, dtype=torch.int32, device=dev)
+        self.sort_ws = torch.empty(abi.cls_sort_workspace_size(capacity, self.info.key_bits),
+                                   dtype=torch.uint8, device=dev)
+
+    def sort(self):
+        b = self
+        abi.check(abi.cls_sort_keys(
+            _ptr(b.keys), _ptr(b.vals), _ptr(b.keys_alt), _ptr(b.vals_alt), _ptr(b.n_pairs),
+            b.capacity, b.info.key_bits, _ptr(b.ranges), b.info.total_tiles, _ptr(b.status),
+            _ptr(b.sort_ws), b.sort_ws.numel(), b.stream()), "cls_sort_keys")
+
+    def forward(self, loss_mode: int, bg=(0.0, 0.0, 0.0), write_image: bool = True):
+        b = self
+        if loss_mode:
+            b.loss.zero_()
+        abi.check(abi.cls_render_forward(
+            _ptr(b.views_dev), b.info, _ptr(b.records), _ptr(b.vals), _ptr(b.ranges),
+            _ptr(b.active_tiles), _ptr(b.n_active_tiles), bg,
+            _ptr(b.target) if loss_mode else None, loss_mode,
+            _ptr(b.image) if write_image else None, _ptr(b.T_final), _ptr(b.n_contrib),
+            _ptr(b.dL_dimage) if loss_mode else None, _ptr(b.loss) if loss_mode else None,
+            _ptr(b.counter), b.stream()), "cls_render_forward")
+
+    def backward(self, bg=(0.0, 0.0, 0.0)):
+        b = self
+        abi.check(abi.cls_render_backward(
+            _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, _ptr(b.records), _ptr(b.vals),
+            _ptr(b.ranges), _ptr(b.active_tiles), _ptr(b.n_active_tiles), bg, _ptr(b.T_final),
+            _ptr(b.n_contrib), _ptr(b.dL_dimage), _ptr(b.grad2d), _ptr(b.grads),
+            _ptr(b.counter) + 4, b.stream()), "cls_render_backward")
+
+    def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15):
+        b = self
+        abi.check(abi.cls_adam_step_active(
+            _ptr(b.scenes_dev), b.info, _ptr(b.grads), lr, beta1, beta2, eps,
+            _ptr(b.adam_ws), b.adam_ws.numel(), b.stream()), "cls_adam_step_active")
+
+    def launches_per_step(self) -> int:
+        """Kernels of one iteration: project_and_bin 7, sort 3 + passes (+1
+        copy if the pass count is odd), forward 1, backward 2, Adam 2."""
+        passes = -(-self.info.key_bits // 8)
+        active = 1 if self.info.max_active > 0 else 0
+        return (5 + 2 * active) + (3 + passes + passes % 2) + 1 + (1 + active) + (1 + active)
+
+    def check_status(self):
+        code = int(self.status.item())
+        if code != abi.CLS_OK:
+            raise abi.ClsError(f"device status {abi.STATUS_NAMES.get(code, code)}")
+
+
+def _views_for(cams):
+    views = (abi.ClsView * len(cams))()
+    pix = 0
+    for j, cam in enumerate(cams):
+        views[j].cam = make_camera(cam)
+        views[j].pix_base = pix
+        pix += int(cam["width"]) * int(cam["height"])
+    return views, pix
+
+
+def lift(state: SceneState, cams: Sequence, masks, vote_mode: int = 0, device="cuda",
+         want_votes: bool = False):
+    """Change-mask lifting on the GPU; sets the scene's active set. `masks` is a
+    list of H x W uint8 arrays or one flat uint8 tensor (views concatenated).
+    Returns (active uint8 numpy, votes [n, 2] numpy or None)."""
+    views, pix = _views_for(cams)
+    views_dev = _bytes(views).to(device)
+    if isinstance(masks, torch.Tensor):
+        masks_dev = masks.to(device, non_blocking=True)
+    else:
+        masks_dev = torch.from_numpy(np.concatenate(
+            [np.ascontiguousarray(m, np.uint8).reshape(-1) for m in masks])).to(device)
+    if masks_dev.numel() != pix:
+        raise ValueError("mask size does not match the cameras")
+    n = state.n
+    ws = torch.zeros(max(abi.cls_lift_workspace_size(n), 256), dtype=torch.uint8, device=device)
+    n_act = torch.zeros(1, dtype=torch.int32, device=device)
+    votes = torch.zeros(2 * max(n, 1), dtype=torch.int32, device=device) if want_votes else None
+    stream = torch.cuda.current_stream().cuda_stream
+    abi.check(abi.cls_lift_change_masks(
+        _ptr(state.params), n, state.stride, _ptr(views_dev), 0, len(cams), _ptr(masks_dev),
+        vote_mode, _ptr(state.active), _ptr(state.active_idx), _ptr(n_act), _ptr(votes),
+        _ptr(ws), ws.numel(), stream), "cls_lift_change_masks")
+    state.n_active = int(n_act.item())
+    if not want_votes:
+        return None, None
+    return state.active.cpu().numpy(), votes.view(-1, 2)[:n].cpu().numpy()
+
+
+class LocalUpdate:
+    """One scene, a handful of posed views and their change masks: lift, then
+    iterate project/bin -> sort -> render forward (+loss) -> render backward ->
+    masked Adam, all on the device."""
+
+    def __init__(self, scene, cams, sh_degree: int, targets=None, masks=None, active=None,
+                 vote_mode: int = 0, loss: str = "l1", lr: float = 1e-3,
+                 bg=(0.0, 0.0, 0.0), device="cuda", capacity_slack: float = 1.5):
+        self.cams = list(cams)
+        self.loss_mode = LOSS_MODES[loss]
+        self.lr = lr
+        self.bg = tuple(float(x) for x in bg)
+        self.state = SceneState(scene, sh_degree, device)
+        if active is not None:
+            self.state.set_active(active)
+        elif masks is not None:
+            lift(self.state, self.cams, masks, vote_mode, device)
+        else:
+            raise ValueError("give either an active set or change masks")
+        self.batch = Batch([self.state], [self.cams], device)
+        if targets is not None:
+            self.batch.set_targets(targets)
+        self.pairs_planned = self.batch.plan_capacity(capacity_slack)
+        torch.cuda.synchronize()
+
+    @classmethod
+    def from_resident(cls, state: SceneState, cams, targets, masks, vote_mode: int = 0,
+                      loss: str = "l1", lr: float = 1e-3, bg=(0.0, 0.0, 0.0),
+                      capacity_slack: float = 1.5):
+        """A new update of a scene already resident on the device. `targets`
+        (float32, [3][H][W] per view, concatenated) and `masks` (uint8, [H][W]
+        per view, concatenated) are flat tensors, typically pinned host memory;
+        they are copied to the device here."""
+        self = cls.__new__(cls)
+        self.cams = list(cams)
+        self.loss_mode = LOSS_MODES[loss]
+        self.lr = lr
+        self.bg = tuple(float(x) for x in bg)
+        self.state = state
+        dev = state.params.device
+        lift(state, self.cams, masks, vote_mode, dev)
+        self.batch = Batch([state], [self.cams], dev)
+        self.batch.target = targets.to(dev, non_blocking=True)
+        self.pairs_planned = self.batch.plan_capacity(capacity_slack)
+        return self
+
+    def render_pass(self, with_backward: bool = True, with_adam: bool = True):
+        b = self.batch
+        b.project_and_bin(1)
+        b.sort()
+        b.forward(self.loss_mode if b.target is not None else 0, self.bg)
+        if with_backward:
+            b.backward(self.bg)
+            if with_adam:
+                b.adam(self.lr)
+
+    def step(self):
+        self.render_pass(True, True)
+
+    def run(self, iters: int):
+        for _ in range(iters):
+            self.step()
+        self.batch.check_status()

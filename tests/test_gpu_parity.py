@@ -1,0 +1,345 @@
+"""Parity of the CUDA path (called through the C ABI) with the CPU oracle.
+
+Bit-exact: projected centres/radii/depth bits, change votes, the tile mask,
+sorted keys and values, tile ranges. Float: pixels within 1e-4 absolute per
+channel, gradients within 1e-3 relative with a floor of 1e-3 x the RMS of
+the parameter group. Pixels and Gaussians whose float64 branch sits within a
+relative 1e-3 of a threshold (alpha = 1/255, the T < 1e-4 stop, the 0.99
+clamp) are reported and excluded; their share is asserted to be small.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import adam as oadam
+from oracle import fp32_index as fx
+from oracle import step as ostep
+from paper_2506_21117_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-4
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_21117_gb300 import build
+    build.build()
+
+
+def _update(scene, cams, deg, targets=None, active=None, loss="l1", masks=None):
+    from paper_2506_21117_gb300.update import LocalUpdate
+    lu = LocalUpdate(scene, cams, deg, targets=targets, active=active, loss=loss, masks=masks)
+    lu.render_pass(with_backward=targets is not None, with_adam=False)
+    torch.cuda.synchronize()
+    lu.batch.check_status()
+    return lu
+
+
+def _records(lu):
+    r = lu.batch.records.view(-1, 12).cpu().numpy()
+    return r, r.view(np.int32)
+
+
+def _gpu_pairs(lu):
+    b = lu.batch
+    n = int(b.n_pairs.item())
+    keys = b.keys[:n].cpu().numpy().view(np.uint64)
+    vals = b.vals[:n].cpu().numpy().view(np.uint32)
+    ranges = b.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+    return keys, vals, ranges
+
+
+def _oracle_index(scene, cams, active):
+    projs = [fx.project_index(scene, c) for c in cams]
+    masks = [fx.tile_mask(p, active, c) for p, c in zip(projs, cams)]
+    keys, vals, n_tiles = fx.pairs(projs, masks, cams, scene["means"].shape[0])
+    sk, sv = fx.sort_pairs(keys, vals)
+    return projs, masks, sk, sv, fx.tile_ranges(sk, n_tiles)
+
+
+def _small_local(seed=0, n=6000, deg=3, size=(100, 75), views=3, frac=0.05):
+    scene = S.uniform_scene(n, deg, seed)
+    cams = S.ring_cameras(views, 4.0, size[0], size[1])
+    box = S.random_box_in_unit_cube(frac, seed)
+    masks = [S.box_change_mask(c, box) for c in cams]
+    targets = [S.random_image(c, seed + j) for j, c in enumerate(cams)]
+    return scene, cams, masks, targets
+
+
+def _compare_grads(lu, ref, active, deg, exclude=()):
+    from paper_2506_21117_gb300.update import unpack_rows
+    A = int(active.sum())
+    rows = lu.batch.grads[: A * lu.state.stride].view(A, lu.state.stride).cpu().numpy()
+    got = unpack_rows(rows.astype(np.float64), deg)
+    idx = np.flatnonzero(active)
+    keep = ~np.isin(idx, np.array(sorted(exclude), dtype=np.int64))
+    worst = 0.0
+    for k in ostep.PARAM_KEYS:
+        r = ref["grads"][k][idx].reshape(A, -1)[keep]
+        g = got[k].reshape(A, -1)[keep]
+        rms = math.sqrt(float(np.mean(r * r))) if r.size else 0.0
+        floor = 1e-3 * rms
+        bound = GRAD_RTOL * np.maximum(np.abs(r), floor)
+        excess = np.abs(g - r) / np.maximum(bound, 1e-30)
+        worst = max(worst, float(excess.max()) if excess.size else 0.0)
+        bad = np.argwhere(np.abs(g - r) > bound)
+        assert bad.size == 0, (k, bad[:5].tolist(), g[tuple(bad[0])], r[tuple(bad[0])], floor)
+    return worst, int((~keep).sum())
+
+
+# ---------------------------------------------------------------- indexing --
+
+@pytest.mark.parametrize("case", ["plain", "local"])
+def test_projection_and_tile_lists_bit_exact(case):
+    if case == "plain":
+        scene, cams, targets = S.workload_plain()
+        deg, active = 0, np.ones(2000, bool)
+    else:
+        scene, cams, masks, targets = _small_local()
+        deg = 3
+        active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
+        assert 0 < active.sum() < 0.5 * active.size
+    lu = _update(scene, cams, deg, active=active)
+    rec, reci = _records(lu)
+    projs, masks_o, sk, sv, rng = _oracle_index(scene, cams, active)
+    n = scene["means"].shape[0]
+    for j, p in enumerate(projs):
+        r = rec[j * n:(j + 1) * n]
+        ri = reci[j * n:(j + 1) * n]
+        valid = ri[:, 11] > 0
+        assert np.array_equal(valid, p["valid"]), j
+        assert np.array_equal(r[valid, 0].view(np.uint32), p["u"][valid].view(np.uint32))
+        assert np.array_equal(r[valid, 1].view(np.uint32), p["v"][valid].view(np.uint32))
+        assert np.array_equal(r[valid, 10].view(np.uint32), p["zbits"][valid])
+        assert np.array_equal(ri[valid, 11], p["radius"][valid].astype(np.int32))
+    tile_mask = np.concatenate([m.ravel() for m in masks_o])
+    assert np.array_equal(lu.batch.tile_active.cpu().numpy(), tile_mask)
+    nt = int(lu.batch.n_active_tiles.item())
+    assert np.array_equal(lu.batch.active_tiles[:nt].cpu().numpy(), np.flatnonzero(tile_mask))
+    keys, vals, ranges = _gpu_pairs(lu)
+    assert keys.size == sk.size > 0
+    assert np.array_equal(keys, sk)
+    assert np.array_equal(vals, sv)
+    assert np.array_equal(ranges, rng)
+
+
+def test_votes_bit_exact():
+    from paper_2506_21117_gb300.update import SceneState, lift
+    scene, _, cams, masks, box = S.workload_local(n=30000, n_views=8, size=160)
+    st = SceneState(scene, 3)
+    act, votes = lift(st, cams, masks, want_votes=True)
+    c, o = fx.votes(scene["means"], cams, masks)
+    assert np.array_equal(votes[:, 0], c) and np.array_equal(votes[:, 1], o)
+    ref = fx.vote_rule(c, o, len(cams))
+    assert np.array_equal(act.astype(bool), ref)
+    assert st.n_active == int(ref.sum()) > 0
+    assert np.array_equal(st.active_idx[: st.n_active].cpu().numpy(), np.flatnonzero(ref))
+    act1, _ = lift(st, cams, masks, vote_mode=1, want_votes=True)
+    assert np.array_equal(act1.astype(bool), c == len(cams))
+
+
+@pytest.mark.parametrize("n", [0, 1, 3839, 3840, 3841, 100_000, 777_777])
+def test_sort_random_keys_bit_exact(n):
+    from paper_2506_21117_gb300 import _abi
+    rng = np.random.default_rng(n)
+    tiles = rng.integers(0, 3000, n).astype(np.uint64)
+    depth = rng.integers(0, 64, n).astype(np.uint64) + np.uint64(0x3F000000)  # many ties
+    keys = (tiles << np.uint64(32)) | depth
+    vals = np.arange(n, dtype=np.uint32)
+    cap = n + 5
+    kd = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    vd = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    kd[:n] = torch.from_numpy(keys.view(np.int64))
+    vd[:n] = torch.from_numpy(vals.view(np.int32))
+    ka, va = torch.empty_like(kd), torch.empty_like(vd)
+    nd = torch.tensor([n], dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bits = 32 + 12
+    ws = torch.zeros(_abi.cls_sort_workspace_size(cap, bits), dtype=torch.uint8, device="cuda")
+    ranges = torch.zeros(2 * 3000, dtype=torch.int32, device="cuda")
+    code = _abi.cls_sort_keys(kd.data_ptr(), vd.data_ptr(), ka.data_ptr(), va.data_ptr(),
+                              nd.data_ptr(), cap, bits, ranges.data_ptr(), 3000, st.data_ptr(),
+                              ws.data_ptr(), ws.numel(), torch.cuda.current_stream().cuda_stream)
+    assert code == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(kd[:n].cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(vd[:n].cpu().numpy().view(np.uint32), vals[order])
+    assert np.array_equal(ranges.view(-1, 2).cpu().numpy().astype(np.int64),
+                          fx.tile_ranges(keys[order], 3000))
+
+
+# ------------------------------------------------------------------ pixels --
+
+def _compare_pixels(lu, ref, cams):
+    imgs = lu.batch.per_view(lu.batch.image, 3)
+    Tf = lu.batch.per_view(lu.batch.T_final, 1)
+    nc = lu.batch.per_view(lu.batch.n_contrib, 1)
+    tm = lu.batch.tile_active.cpu().numpy()
+    checked = near_total = 0
+    base = 0
+    for j, cam in enumerate(cams):
+        Tx, Ty = fx.tiles_of(cam)
+        m = tm[base:base + Tx * Ty].reshape(Ty, Tx)
+        base += Tx * Ty
+        pix = np.kron(m, np.ones((16, 16), np.uint8))[:cam["height"], :cam["width"]].astype(bool)
+        near = ref["near"][j]
+        ok = pix & ~near
+        g = imgs[j].cpu().numpy()
+        r = ref["image"][j]
+        err = np.abs(g - r)[:, ok]
+        assert err.max() <= PIX_TOL, (j, float(err.max()))
+        assert np.abs(Tf[j].cpu().numpy() - ref["T_final"][j])[ok].max() <= PIX_TOL
+        agree = nc[j].cpu().numpy()[ok] == ref["n_contrib"][j][ok]
+        assert agree.mean() > 0.999, agree.mean()
+        checked += int(ok.sum())
+        near_total += int((pix & near).sum())
+    assert near_total <= 0.01 * (checked + near_total), (near_total, checked)
+    return checked, near_total
+
+
+def test_forward_pixels_plain():
+    scene, cams, targets = S.workload_plain()
+    active = np.ones(2000, bool)
+    lu = _update(scene, cams, 0, targets=targets, active=active)
+    ref = ostep.render(scene, cams, 0, targets=targets)
+    checked, near = _compare_pixels(lu, ref, cams)
+    assert checked > 4000
+    print(f"plain: {checked} pixels within {PIX_TOL}, {near} near-threshold excluded")
+
+
+def test_forward_pixels_local_tiles_only():
+    scene, cams, masks, targets = _small_local(seed=3)
+    active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
+    lu = _update(scene, cams, 3, targets=targets, active=active)
+    tiles = ostep.active_tiles(scene, cams, active)
+    ref = ostep.render(scene, cams, 3, targets=targets, tiles=tiles)
+    checked, near = _compare_pixels(lu, ref, cams)
+    assert checked > 1000
+    # the fused loss equals the oracle's loss over the same (active-tile) pixels
+    assert abs(float(lu.batch.loss[0].item()) - ref["loss"]) <= 1e-4 * abs(ref["loss"]) + 1e-7
+
+
+# --------------------------------------------------------------- gradients --
+
+def test_gradients_plain_l1():
+    scene, cams, targets = S.workload_plain()
+    active = np.ones(2000, bool)
+    lu = _update(scene, cams, 0, targets=targets, active=active, loss="l1")
+    ref = ostep.local_step_reference(scene, cams, 0, targets, active, "l1")
+    worst, excl = _compare_grads(lu, ref, active, 0, exclude=ref["near_ids"])
+    print(f"plain L1 gradients: worst error/bound {worst:.3f}, {excl} Gaussians excluded")
+    assert excl <= 0.05 * active.sum()
+
+
+def test_gradients_two_view_l2_sh1():
+    scene, cams, targets = S.workload_fd()
+    active = np.ones(500, bool)
+    lu = _update(scene, cams, 1, targets=targets, active=active, loss="l2")
+    ref = ostep.local_step_reference(scene, cams, 1, targets, active, "l2")
+    worst, excl = _compare_grads(lu, ref, active, 1, exclude=ref["near_ids"])
+    print(f"two-view L2 gradients: worst error/bound {worst:.3f}, {excl} excluded")
+    assert excl <= 0.05 * active.sum()
+
+
+def test_gradients_local_active_set_equal_full_image_gradients():
+    """Exactness of the local kernel: O^t's gradients from the active tiles
+    equal the oracle's full-image, full-scene gradients."""
+    scene, cams, masks, targets = _small_local(seed=5)
+    active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
+    lu = _update(scene, cams, 3, targets=targets, active=active, loss="l1")
+    ref = ostep.local_step_reference(scene, cams, 3, targets, active, "l1")
+    worst, excl = _compare_grads(lu, ref, active, 3, exclude=ref["near_ids"])
+    print(f"local SH3 gradients: {int(active.sum())} active, worst {worst:.3f}, {excl} excluded")
+    assert excl <= 0.1 * active.sum()
+
+
+# -------------------------------------------------------------------- Adam --
+
+def test_adam_step_matches_oracle_and_freezes_static_rows():
+    from paper_2506_21117_gb300.update import LocalUpdate
+    scene, cams, masks, targets = _small_local(seed=7, n=3000, deg=1)
+    active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
+    lu = LocalUpdate(scene, cams, 1, targets=targets, active=active, loss="l1")
+    st = lu.state
+    n, w = st.n, st.stride
+    theta, m, v, _ = S.random_adam_state(n, w, seed=7)
+    st.params.copy_(torch.from_numpy(theta))
+    st.adam_m.copy_(torch.from_numpy(m))
+    st.adam_v.copy_(torch.from_numpy(v))
+    st.adam_step.fill_(4)
+    A = st.n_active
+    g = S.random_adam_state(A, w, seed=8)[3]
+    lu.batch.grads[: A * w].copy_(torch.from_numpy(g.reshape(-1)))
+    lu.batch.adam(lr=1e-3, eps=1e-8)
+    torch.cuda.synchronize()
+    full_g = np.zeros((n, w))
+    full_g[active] = g
+    th, mo, vo = oadam.masked_adam_step(theta, m, v, full_g, active, 5, 1e-3, eps=1e-8)
+    P = st.params.cpu().numpy()
+    M = st.adam_m.cpu().numpy()
+    V = st.adam_v.cpu().numpy()
+    assert np.array_equal(P[~active], theta[~active])
+    assert np.array_equal(M[~active], m[~active]) and np.array_equal(V[~active], v[~active])
+    np.testing.assert_allclose(P[active], th[active], rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(M[active], mo[active], rtol=1e-5, atol=1e-9)
+    np.testing.assert_allclose(V[active], vo[active], rtol=1e-5, atol=1e-12)
+    assert int(st.adam_step.item()) == 5
+
+
+def test_iterations_keep_static_gaussians_bit_identical():
+    from paper_2506_21117_gb300.update import LocalUpdate, pack_params
+    scene, cams, masks, targets = _small_local(seed=9, n=4000, deg=3)
+    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
+    active = lu.state.active.cpu().numpy().astype(bool)
+    rows0 = pack_params(scene, 3)
+    losses = []
+    for _ in range(5):
+        lu.step()
+        losses.append(float(lu.batch.loss[0].item()))
+    torch.cuda.synchronize()
+    lu.batch.check_status()
+    P = lu.state.params.cpu().numpy()
+    assert np.array_equal(P[~active], rows0[~active])
+    assert not np.array_equal(P[active], rows0[active])
+    assert np.all(lu.state.adam_m.cpu().numpy()[~active] == 0)
+    assert np.isfinite(losses).all()
+
+
+# ------------------------------------------------------------- edge cases --
+
+def test_empty_active_set_renders_nothing():
+    scene, cams, masks, targets = _small_local(seed=11, n=1000)
+    lu = _update(scene, cams, 3, targets=targets, active=np.zeros(1000, bool))
+    assert int(lu.batch.n_active_tiles.item()) == 0
+    assert int(lu.batch.n_pairs.item()) == 0
+    lu.batch.adam()
+    torch.cuda.synchronize()
+
+
+def test_all_gaussians_culled():
+    scene = S.uniform_scene(500, 0, 12)
+    cam = S.look_at_camera((0.0, 0.0, -4.0), (0.0, 0.0, -10.0), 48, 40)  # looking away
+    lu = _update(scene, [cam], 0, targets=[S.random_image(cam)], active=np.ones(500, bool))
+    assert int(lu.batch.n_active_tiles.item()) == 0
+    rec, reci = _records(lu)
+    assert (reci[:, 11] == 0).all()
+
+
+def test_capacity_overflow_is_reported():
+    from paper_2506_21117_gb300 import _abi
+    scene, cams, targets = S.workload_plain()
+    from paper_2506_21117_gb300.update import LocalUpdate
+    lu = LocalUpdate(scene, cams, 0, targets=targets, active=np.ones(2000, bool))
+    need = lu.pairs_planned
+    lu.batch.allocate_keys(need // 2)
+    lu.batch.status.zero_()
+    lu.batch.project_and_bin(1)
+    torch.cuda.synchronize()
+    assert int(lu.batch.status.item()) == _abi.CLS_ERR_CAPACITY
+    assert int(lu.batch.n_pairs.item()) == need
