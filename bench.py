@@ -37,8 +37,8 @@ WORKLOAD = "1M-Gaussian clustered room, SH3, 4 views 1920x1080, 5% change box, L
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=1_000_000)
     p.add_argument("--fraction", type=float, default=0.05)
@@ -55,43 +55,60 @@ def parse():
 # ---------------------------------------------------------------- helpers ---
 
 class Clocks:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 100 ms; only samples taken inside the timed
+    window count (the nearest ones are used if the window is shorter than
+    the sampling period, and flagged)."""
+
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, index: int):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
-    def stop(self):
+    def stop(self, t0: float, t1: float):
+        import datetime as dt
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
         self.p.terminate()
         self.p.wait()
         self.f.seek(0)
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in self.f.read().splitlines():
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                ts = dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
             except ValueError:
                 continue
-            for nm, val in zip(names, parts[5:9]):
+        os.unlink(self.f.name)
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        flag = None
+        if not inside and rows:
+            mid = 0.5 * (t0 + t1)
+            inside = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+            flag = "timed window shorter than the sampling period: nearest samples"
+        reasons = set()
+        for r in inside:
+            for nm, val in zip(self.NAMES, r[3]):
                 if val.lower() == "active":
                     reasons.add(nm)
-        os.unlink(self.f.name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median([r[1] for r in inside]) if inside else None,
+               "sm_max_mhz": inside[0][2] if inside else None, "reasons": sorted(reasons),
+               "samples": len(inside)}
+        if flag:
+            out["note"] = flag
+        return out
 
 
 def load_peaks():
@@ -121,15 +138,17 @@ def setup_workload(args, seed):
 # -------------------------------------------------------------- CPU oracle ---
 
 def oracle_sample(scene, cams, targets, active, n_tiles_total, n_tiles, proj_frac=1.0,
-                  seed=0):
-    """Time the oracle on a bounded sample: the float64 projection of a
-    fraction of the Gaussians in view 0 and forward+backward of `n_tiles`
-    active tiles of view 0; extrapolated to one iteration (every view, every
-    active tile). Returns (seconds per iteration, description)."""
-    import torch
+                  seed=0, cache=None):
+    """Time the oracle on a bounded sample of one iteration: the float32 index
+    projection plus the float64 projection with its backward for a fraction of
+    the Gaussians in view 0, and forward+backward of `n_tiles` active tiles of
+    view 0 (over the Gaussians whose rectangles reach them). Extrapolated to
+    every view and every active tile. Returns (seconds per iteration,
+    description)."""
     from oracle import fp32_index as fx
     from oracle import projection as pj
     from oracle import step as ostep
+    cache = {} if cache is None else cache
     n = scene["means"].shape[0]
     rng = np.random.default_rng(seed)
     m = max(1, int(n * proj_frac))
@@ -139,22 +158,30 @@ def oracle_sample(scene, cams, targets, active, n_tiles_total, n_tiles, proj_fra
     g = pj.scene64(sub, requires_grad=True)
     P = pj.project(g, cams[0], 3)
     (P["u"].sum() + P["conic"].sum() + P["rgb"].sum()).backward()
-    t_proj = (time.perf_counter() - t0) / proj_frac
-    tiles = ostep.active_tiles(scene, cams[:1], active)[0]
+    t_proj = (time.perf_counter() - t0) * (n / m)
+    if "pidx0" not in cache:  # set-up, not timed
+        cache["pidx0"] = fx.project_index(scene, cams[0])
+        mk = fx.tile_mask(cache["pidx0"], active, cams[0])
+        ys, xs = np.nonzero(mk)
+        cache["tiles0"] = list(zip(xs.tolist(), ys.tolist()))
+    p0, tiles = cache["pidx0"], cache["tiles0"]
     pick = [tiles[i] for i in rng.choice(len(tiles), size=min(n_tiles, len(tiles)),
                                           replace=False)]
+    sel = np.zeros(n, bool)
+    for (tx, ty) in pick:
+        sel |= p0["valid"] & (p0["tx0"] <= tx) & (p0["tx1"] >= tx) & (p0["ty0"] <= ty) & \
+            (p0["ty1"] >= ty)
+    subs = {k: v[sel] for k, v in scene.items()}
     t1 = time.perf_counter()
-    ostep.render(scene, cams[:1], 3, targets=targets[:1], loss="l1", need_grad=True,
+    ostep.render(subs, cams[:1], 3, targets=targets[:1], loss="l1", need_grad=True,
                  tiles=[pick])
-    t_render_all = time.perf_counter() - t1
-    # render() also projects all n Gaussians once with autograd; remove that share
-    t_tiles = max(t_render_all - t_proj, 1e-3)
-    per_tile = t_tiles / max(len(pick), 1)
+    per_tile = (time.perf_counter() - t1) / max(len(pick), 1)
     it = len(cams) * t_proj + n_tiles_total * per_tile
-    desc = (f"float64 oracle: projection+backward of {m} of {n} Gaussians in view 0 "
-            f"(scaled to all {n} and {len(cams)} views) and forward+backward of {len(pick)} "
-            f"active tiles of view 0 (scaled to all {n_tiles_total} active tiles of "
-            f"{len(cams)} views)")
+    desc = (f"float64 oracle, one iteration extrapolated from: index+float64 projection with "
+            f"backward of {m} of {n} Gaussians in view 0 (x{n / m:.0f}, x{len(cams)} views) "
+            f"and forward+backward of {len(pick)} active tiles of view 0 over the "
+            f"{int(sel.sum())} Gaussians reaching them (x{n_tiles_total / max(len(pick), 1):.0f} "
+            f"to all {n_tiles_total} active tiles of {len(cams)} views)")
     return it, desc
 
 
@@ -182,6 +209,7 @@ def run_ours(args, rank, world):
     lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
     bt = lu.batch
     A = lu.state.n_active
+    clocks = Clocks(dev.index)
     for _ in range(args.warmup):
         lu.step()
     torch.cuda.synchronize()
@@ -190,10 +218,10 @@ def run_ours(args, rank, world):
     stages = ["project_and_bin", "sort_keys", "render_forward", "render_backward",
               "adam_step_active"]
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
-    clocks = Clocks(dev.index)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    t_wall0 = time.time()
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record()
@@ -212,7 +240,7 @@ def run_ours(args, rank, world):
         e[5].record()
     end.record()
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop(t_wall0, time.time())
     total_ms = start.elapsed_time(end)
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -284,7 +312,7 @@ def run_ours(args, rank, world):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import torch as _t
         sec, desc = oracle_sample(scene, cams, targets, lu.state.active.cpu().numpy().astype(bool),
-                                  tiles_on, args.cpu_tiles, proj_frac=0.1)
+                                  tiles_on, args.cpu_tiles, proj_frac=0.05)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": _t.get_num_threads(),
                                 "kind": "oracle", "sample": desc}
     return line
@@ -327,9 +355,10 @@ def run_reference(args, rank, world):
     from paper_2506_21117_gb300 import synthetic as S
     targets = [S.random_image(cam, 0) for cam in cams]
     times = []
+    cache = {}
     for k in range(args.warmup + args.steps):
-        sec, desc = oracle_sample(scene, cams, targets, active, tiles_total, 1, proj_frac=0.02,
-                                  seed=k)
+        sec, desc = oracle_sample(scene, cams, targets, active, tiles_total, 1, proj_frac=0.01,
+                                  seed=k, cache=cache)
         if k >= args.warmup:
             times.append(sec)
     sec = sum(times) / len(times)

@@ -18,7 +18,8 @@ rectangle holds the pixel's tile, by depth then index):
 The discrete decisions (skip, stop, the 0.99 clamp) are taken here in float64.
 A float32 implementation may take a different branch when a value sits on a
 threshold; `near` flags those pixels (where the branch could move the result by
-more than `value_tol`) and `near_ids` the Gaussians involved, so tests can
+more than `value_tol`; `margin` is relative to the threshold) and
+`near_ids` the Gaussians involved, so tests can
 report them instead of comparing an ill-posed value.
 """
 from __future__ import annotations
@@ -30,7 +31,7 @@ ALPHA_MAX = 0.99
 T_MIN = 1e-4
 
 
-def composite(u, v, conic, opacity, rgb, px, py, bg, margin: float = 1e-3,
+def composite(u, v, conic, opacity, rgb, px, py, bg, margin: float = 1e-4,
               value_tol: float = 1e-4):
     """Composite pixels (px, py) (integer pixel indices, [P]) over the ordered
     Gaussians given by 1-D tensors u, v, opacity [L], conic [L, 3], rgb [L, 3].

@@ -58,7 +58,7 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
            bg=(0.0, 0.0, 0.0), targets: Optional[Sequence[np.ndarray]] = None,
            loss: str = "l1", need_grad: bool = False,
            tiles: Optional[Sequence[Sequence[tuple]]] = None,
-           margin: float = 1e-3):
+           margin: float = 1e-4):
     """Render every view (or only `tiles[j]` of view j).
 
     Returns a dict with per-view `image` [3, H, W] (NaN where not rendered),

@@ -155,15 +155,26 @@ def box_holding_fraction(means: np.ndarray, centre: Sequence[float],
     return c - half, c + half
 
 
-def cluster_nearest_view_centre(centres: np.ndarray, cam: Camera) -> np.ndarray:
-    """The cluster centre closest (in angle) to the camera's optical axis, among
-    those in front of it."""
-    R = np.asarray(cam["R"])
-    t = np.asarray(cam["t"])
-    pc = centres @ R.T + t
-    ok = pc[:, 2] > 1.0
-    ang = np.where(ok, np.hypot(pc[:, 0], pc[:, 1]) / np.maximum(pc[:, 2], 1e-9), np.inf)
-    return centres[int(np.argmin(ang))]
+def change_cluster(centres: np.ndarray, cams: Sequence[Camera]) -> np.ndarray:
+    """The cluster centre seen by the most views (in front by more than 1 unit
+    and inside the image), ties broken by the smallest angle to the first
+    camera's optical axis."""
+    best, best_key = None, None
+    for c in centres:
+        seen = 0
+        for cam in cams:
+            R = np.asarray(cam["R"])
+            p = R @ c + np.asarray(cam["t"])
+            if p[2] > 1.0:
+                u = cam["fx"] * p[0] / p[2] + cam["cx"]
+                v = cam["fy"] * p[1] / p[2] + cam["cy"]
+                seen += int(0 < u < cam["width"] and 0 < v < cam["height"])
+        p0 = np.asarray(cams[0]["R"]) @ c + np.asarray(cams[0]["t"])
+        ang = math.hypot(p0[0], p0[1]) / p0[2] if p0[2] > 1e-9 else math.inf
+        key = (-seen, ang)
+        if best_key is None or key < best_key:
+            best, best_key = c, key
+    return np.asarray(best)
 
 
 def inside_box(means: np.ndarray, box: Tuple[np.ndarray, np.ndarray]) -> np.ndarray:
@@ -251,12 +262,13 @@ def workload_large(n: int = 1_000_000, n_views: int = 4, width: int = 1920,
                    height: int = 1080, fraction: float = 0.05,
                    sh_degree: int = 3, seed: int = 0):
     """Clustered room scene, views at 0, pi/2, pi, 3pi/2, a change box around
-    the cluster nearest view 0's image centre holding `fraction` of the
-    Gaussians; returns (scene, target_scene, cams, masks, box)."""
+    the cluster seen by the most views (nearest view 0's image centre among
+    those) holding `fraction` of the Gaussians; returns (scene, target_scene,
+    cams, masks, box)."""
     scene, centres = cluster_scene(n, 20, 0.3, 4.0, 5.0, sh_degree, seed)
     angles = [0.5 * math.pi * k for k in range(n_views)]
     cams = ring_cameras(n_views, 4.0, width, height, angles=angles)
-    centre = cluster_nearest_view_centre(centres, cams[0])
+    centre = change_cluster(centres, cams)
     box = box_holding_fraction(scene["means"], centre, fraction)
     changed = inside_box(scene["means"], box)
     target_scene = perturb_scene(scene, changed, 0.05, seed)

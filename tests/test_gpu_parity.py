@@ -4,7 +4,7 @@ Bit-exact: projected centres/radii/depth bits, change votes, the tile mask,
 sorted keys and values, tile ranges. Float: pixels within 1e-4 absolute per
 channel, gradients within 1e-3 relative with a floor of 1e-3 x the RMS of
 the parameter group. Pixels and Gaussians whose float64 branch sits within a
-relative 1e-3 of a threshold (alpha = 1/255, the T < 1e-4 stop, the 0.99
+relative 1e-4 of a threshold (alpha = 1/255, the T < 1e-4 stop, the 0.99
 clamp) are reported and excluded; their share is asserted to be small.
 """
 import math
