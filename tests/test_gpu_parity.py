@@ -2,8 +2,12 @@
 
 Bit-exact: projected centres/radii/depth bits, change votes, the tile mask,
 sorted keys and values, tile ranges. Float: pixels within 1e-4 absolute per
-channel, gradients within 1e-3 relative with a floor of 1e-3 x the RMS of
-the parameter group. Pixels and Gaussians whose float64 branch sits within a
+channel; gradients within 1e-3 relative, |g - g_ref| <= 1e-3 max(|g_ref|,
+floor), floor = 5e-2 x the RMS of the parameter group. Below 5% of the RMS an
+entry is a cancellation of per-pixel terms of up to ~10x RMS size; summing
+~10^3 of them in float32 (unit roundoff 6e-8, error growing like sqrt(n))
+leaves ~2e-5 x RMS of rounding, so those entries are held to 5e-5 x RMS
+absolute. Pixels and Gaussians whose float64 branch sits within a
 relative 1e-4 of a threshold (alpha = 1/255, the T < 1e-4 stop, the 0.99
 clamp) are reported and excluded; their share is asserted to be small.
 """
@@ -22,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 PIX_TOL = 1e-4
 GRAD_RTOL = 1e-3
+GRAD_FLOOR = 5e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -82,7 +87,7 @@ def _compare_grads(lu, ref, active, deg, exclude=()):
         r = ref["grads"][k][idx].reshape(A, -1)[keep]
         g = got[k].reshape(A, -1)[keep]
         rms = math.sqrt(float(np.mean(r * r))) if r.size else 0.0
-        floor = 1e-3 * rms
+        floor = GRAD_FLOOR * rms
         bound = GRAD_RTOL * np.maximum(np.abs(r), floor)
         excess = np.abs(g - r) / np.maximum(bound, 1e-30)
         worst = max(worst, float(excess.max()) if excess.size else 0.0)
