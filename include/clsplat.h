@@ -166,6 +166,31 @@ int cls_lift_change_masks(const float* params, int32_t n, int32_t row_stride,
                           int32_t* active_idx_out, int32_t* n_active_out, int32_t* votes_out,
                           void* workspace, size_t workspace_bytes, cls_stream_t stream);
 
+/* Allocation-free change-mask lifting. The paper has no counterpart: this
+ * entry exists for callers that cannot allocate device memory at all, for
+ * example a plug-in that runs inside a host application owning every device
+ * allocation, or a latency-critical loop where an allocation call could
+ * synchronise the device. It computes exactly what cls_lift_change_masks
+ * computes, with the same arguments minus the workspace: its scratch (one
+ * count per 2048 Gaussians) sits in a fixed device array inside the library,
+ * sized for at most CLS_LIFT_STATIC_MAX_N Gaussians (64 KiB, held on every
+ * device that loads the library until the process exits).
+ *  - n above CLS_LIFT_STATIC_MAX_N returns CLS_ERR_INVALID_ARG, nothing runs.
+ *  - The first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture. It allocates nothing (no cudaMalloc/cudaFree,
+ *    no allocating library routine).
+ *  - All calls share the one array. Each call writes every slot it reads
+ *    before reading it, so no clearing is needed, but two calls that overlap
+ *    on the GPU (different streams, no ordering between them) race on it and
+ *    give wrong results: order them. */
+#define CLS_LIFT_STATIC_MAX_N (1 << 24)
+int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_stride,
+                                 const ClsView* views_dev, int32_t first_view, int32_t n_views,
+                                 const uint8_t* masks, int32_t vote_mode, uint8_t* active_out,
+                                 int32_t* active_idx_out, int32_t* n_active_out,
+                                 int32_t* votes_out, cls_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Projection, dynamic render mask and binning (Supp. "Local Optimization
  * Kernel", item 1; base 3DGS preprocessing).

@@ -69,6 +69,7 @@ SIGNATURES = {
     "cls_batch_prepare": (C.c_int, [P, I32, P, I32, P]),
     "cls_lift_workspace_size": (SZ, [I32]),
     "cls_lift_change_masks": (C.c_int, [P, I32, I32, P, I32, I32, P, I32, P, P, P, P, P, SZ, P]),
+    "cls_lift_change_masks_static": (C.c_int, [P, I32, I32, P, I32, I32, P, I32, P, P, P, P, P]),
     "cls_project_workspace_size": (SZ, [P]),
     "cls_project_and_bin": (C.c_int, [P, P, P, I32, P, P, P, P, P, P, I64, P, P, P, SZ, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
@@ -140,6 +141,19 @@ def cls_lift_change_masks(params, n, row_stride, views_dev, first_view, n_views,
                                         masks, vote_mode, active_out, active_idx_out,
                                         n_active_out, votes_out, workspace, workspace_bytes,
                                         stream)
+
+
+LIFT_STATIC_MAX_N = 1 << 24
+
+
+def cls_lift_change_masks_static(params, n, row_stride, views_dev, first_view, n_views, masks,
+                                 vote_mode, active_out, active_idx_out, n_active_out, votes_out,
+                                 stream) -> int:
+    """Same as cls_lift_change_masks, with the library's fixed scratch array
+    instead of a caller workspace (for callers that cannot allocate)."""
+    return load().cls_lift_change_masks_static(params, n, row_stride, views_dev, first_view,
+                                               n_views, masks, vote_mode, active_out,
+                                               active_idx_out, n_active_out, votes_out, stream)
 
 
 def cls_project_workspace_size(info) -> int:

@@ -2,6 +2,8 @@
 // (Sec. 3.2 "Mask Majority Voting"; Supp. "Identifying Changed 3D Regions via
 // Majority Voting", voting equation), then compaction of O^t into an
 // ascending index list.
+#include <mutex>
+
 #include "scan.cuh"
 
 namespace cls {
@@ -121,6 +123,64 @@ extern "C" int cls_lift_change_masks(const float* params, int32_t n, int32_t row
     }
     const int64_t chunks = (n + kLiftChunk - 1) / kLiftChunk;
     int64_t* partials = static_cast<int64_t*>(workspace);
+    lift_vote_kernel<<<(unsigned)chunks, kLiftBlock, 0, s>>>(params, n, row_stride, views_dev,
+                                                            first_view, n_views, masks, vote_mode,
+                                                            active_out, votes_out, partials);
+    scan_partials_kernel<<<1, 1024, 0, s>>>(partials, chunks, nullptr, n_active_out, -1, nullptr);
+    compact_flags_kernel<<<(unsigned)chunks, kLiftBlock, 0, s>>>(active_out, n, partials,
+                                                                active_idx_out);
+    CLS_CHECK_LAUNCH();
+    return CLS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant. Its only scratch, the per-chunk counts of active
+// Gaussians, lives in this fixed device array instead of a caller workspace.
+// Every slot a call reads is first written by the same call's vote kernel, so
+// nothing has to be cleared between calls.
+static __device__ __align__(256) int64_t g_lift_static_scratch[CLS_LIFT_STATIC_MAX_N / kLiftChunk + 1];
+
+static std::mutex g_lift_static_mutex;
+static void* g_lift_static_ptr[64] = {nullptr};
+
+// Device address of the array on the current device, looked up once per device.
+static int lift_static_scratch(int64_t** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CLS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_lift_static_mutex);
+    if (!g_lift_static_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_lift_static_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
+            return CLS_ERR_CUDA;
+        }
+        g_lift_static_ptr[dev] = p;
+    }
+    *out = static_cast<int64_t*>(g_lift_static_ptr[dev]);
+    return CLS_OK;
+}
+
+extern "C" int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_stride,
+                                            const ClsView* views_dev, int32_t first_view,
+                                            int32_t n_views, const uint8_t* masks,
+                                            int32_t vote_mode, uint8_t* active_out,
+                                            int32_t* active_idx_out, int32_t* n_active_out,
+                                            int32_t* votes_out, cls_stream_t stream) {
+    if (n < 0 || n > CLS_LIFT_STATIC_MAX_N) return CLS_ERR_INVALID_ARG;
+    if (n_views <= 0 || first_view < 0 || (vote_mode != 0 && vote_mode != 1) || row_stride < 4 ||
+        row_stride % 4 != 0 || !views_dev || !masks || !active_out || !active_idx_out ||
+        !n_active_out || (n > 0 && !params))
+        return CLS_ERR_INVALID_ARG;
+    int64_t* partials = nullptr;
+    const int rc = lift_static_scratch(&partials);
+    if (rc != CLS_OK) return rc;
+    cudaStream_t s = as_stream(stream);
+    if (n == 0) {
+        cudaMemsetAsync(n_active_out, 0, sizeof(int32_t), s);
+        CLS_CHECK_LAUNCH();
+        return CLS_OK;
+    }
+    const int64_t chunks = (n + kLiftChunk - 1) / kLiftChunk;
     lift_vote_kernel<<<(unsigned)chunks, kLiftBlock, 0, s>>>(params, n, row_stride, views_dev,
                                                             first_view, n_views, masks, vote_mode,
                                                             active_out, votes_out, partials);
