@@ -201,29 +201,55 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  *                             tile rectangle holds the tile
  *   active_tiles[total_tiles] int32: ascending global ids of active tiles,
  *                             n_active_tiles_dev = their count
- *   keys/vals [capacity]      one (key, value) per (Gaussian, active tile)
- *                             pair, static and active Gaussians alike:
- *                             key = (global tile id << 32) | bits(depth z),
- *                             value = record index; emitted in view order,
- *                             then Gaussian order, then row-major tile order
+ *   one pair per (Gaussian, active tile), static and active Gaussians alike,
+ *   in one of two layouts:
+ *   layout 0 (flat, for cls_sort_keys): keys[i] = (global tile id << 32) |
+ *     bits(depth z), vals[i] = record index, emitted in view order, then
+ *     Gaussian order, then row-major tile order.
+ *   layout 1 (bucketed, for cls_sort_tiles): keys[i] = (bits(z) << 32) |
+ *     record index; `vals` is unused. Pairs are grouped by tile (tiles in
+ *     active-tile order) and, inside a tile, by CLS_DEPTH_BINS depth bins
+ *     that split the view's depth range of pair-producing Gaussians evenly in
+ *     float-bit space (monotone in depth); the order inside a bin is
+ *     unspecified until cls_sort_tiles. ranges[tile] = (start, end) of each
+ *     tile ((0, 0) if inactive) and bin_offsets[r * CLS_DEPTH_BINS + b] the
+ *     start of bin b of the r-th active tile (cls_bin_offsets_size entries).
  *   n_pairs_dev               device int64: number of pairs needed; if it
  *                             exceeds `capacity`, CLS_ERR_CAPACITY is written
- *                             to status_dev and only `capacity` pairs are kept.
+ *                             to status_dev and only `capacity` pairs are kept
+ *                             (offsets and ranges are clamped to capacity).
  * Tile rectangle: radius r = ceil(3 sqrt(lambda_max(Sigma'))), tiles
  * floor((u - r)/16) .. floor((u + r)/16) clamped to the grid (same for v).
  * records [total_records] ClsProjected. */
+#define CLS_DEPTH_BINS 64
 size_t cls_project_workspace_size(const ClsBatchInfo* info);
+size_t cls_bin_offsets_size(const ClsBatchInfo* info); /* uint32 entries */
 int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
-                        const ClsBatchInfo* info, int32_t project_mode, ClsProjected* records,
-                        uint8_t* tile_active, int32_t* active_tiles, int32_t* n_active_tiles_dev,
-                        uint64_t* keys, uint32_t* vals, int64_t capacity, int64_t* n_pairs_dev,
-                        int32_t* status_dev, void* workspace, size_t workspace_bytes,
-                        cls_stream_t stream);
+                        const ClsBatchInfo* info, int32_t project_mode, int32_t layout,
+                        ClsProjected* records, uint8_t* tile_active, int32_t* active_tiles,
+                        int32_t* n_active_tiles_dev, uint64_t* keys, uint32_t* vals,
+                        int64_t capacity, int64_t* n_pairs_dev, uint32_t* ranges,
+                        uint32_t* bin_offsets, int32_t* status_dev, void* workspace,
+                        size_t workspace_bytes, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
- * Stable LSD radix sort of the (tile, depth) keys with their values
- * (Supp. "Local Optimization Kernel", item 1: per-tile depth order), one
- * 8-bit digit per pass, single-pass digit scattering with decoupled
+ * Per-tile depth sort of the bucketed layout (Supp. "Local Optimization
+ * Kernel", item 1: per-tile depth order). Binning already did the most
+ * significant radix pass (tile, then depth bin); this sorts every bucket by
+ * its key, i.e. by depth, equal depths by record index, in shared memory, so
+ * each tile's pairs end in (depth, index) order.
+ *   keys        [capacity] in/out, layout 1 of cls_project_and_bin
+ *   keys_alt    [capacity] scratch (used only for bins above 4096 pairs)
+ *   bin_offsets as written by cls_project_and_bin
+ *   work_counter device int32 scratch (reset by the call) */
+int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offsets,
+                   const int32_t* n_active_tiles_dev, int64_t total_tiles, int32_t* work_counter,
+                   cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Stable LSD radix sort of the flat layout's (tile, depth) keys with their
+ * values (Supp. "Local Optimization Kernel", item 1: per-tile depth order),
+ * one 8-bit digit per pass, single-pass digit scattering with decoupled
  * look-back, then the per-tile [start, end) ranges.
  *   keys, vals        [capacity] in/out; sorted result ends here
  *   keys_alt, vals_alt [capacity] ping-pong buffers
@@ -245,6 +271,8 @@ int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* 
  * alpha = min(0.99, opacity * exp(-1/2 (A dx^2 + C dy^2) - B dx dy)), skipped
  * if the exponent is > 0 or alpha < 1/255; stop before a Gaussian when
  * T (1 - alpha) < 1e-4; C += colour alpha T; T *= 1 - alpha; C += T bg.
+ * The record index of sorted pair i is vals[i * vals_stride]: vals_stride 1
+ * with the flat layout's vals, 2 with the bucketed layout's keys (low words).
  * Outputs at the view's pix_base (pixels of inactive tiles are not written):
  *   image      [3][H][W] per view (planar), may be NULL
  *   T_final    [H][W], n_contrib [H][W] (one past the last list position
@@ -257,7 +285,8 @@ int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* 
  *   work_counter device int32 scratch (reset by the call).
  * bg is a host array of 3 floats. */
 int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
-                       const ClsProjected* records, const uint32_t* vals, const uint32_t* ranges,
+                       const ClsProjected* records, const uint32_t* vals, int32_t vals_stride,
+                       const uint32_t* ranges,
                        const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
                        const float* bg, const float* target, int32_t loss_mode, float* image,
                        float* T_final, int32_t* n_contrib, float* dL_dimage,
@@ -278,7 +307,8 @@ int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
  * call or supplied by the caller ([3][H][W] per view). */
 int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
                         const ClsBatchInfo* info, const ClsProjected* records,
-                        const uint32_t* vals, const uint32_t* ranges, const int32_t* active_tiles,
+                        const uint32_t* vals, int32_t vals_stride, const uint32_t* ranges,
+                        const int32_t* active_tiles,
                         const int32_t* n_active_tiles_dev, const float* bg, const float* T_final,
                         const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
                         float* grads, int32_t* work_counter, cls_stream_t stream);

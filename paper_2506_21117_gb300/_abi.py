@@ -71,11 +71,14 @@ SIGNATURES = {
     "cls_lift_change_masks": (C.c_int, [P, I32, I32, P, I32, I32, P, I32, P, P, P, P, P, SZ, P]),
     "cls_lift_change_masks_static": (C.c_int, [P, I32, I32, P, I32, I32, P, I32, P, P, P, P, P]),
     "cls_project_workspace_size": (SZ, [P]),
-    "cls_project_and_bin": (C.c_int, [P, P, P, I32, P, P, P, P, P, P, I64, P, P, P, SZ, P]),
+    "cls_bin_offsets_size": (SZ, [P]),
+    "cls_project_and_bin": (C.c_int, [P, P, P, I32, I32, P, P, P, P, P, P, I64, P, P, P, P, P,
+                                      SZ, P]),
+    "cls_sort_tiles": (C.c_int, [P, P, P, P, I64, P, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
     "cls_sort_keys": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, P]),
-    "cls_render_forward": (C.c_int, [P, P, P, P, P, P, P, P, P, I32, P, P, P, P, P, P, P]),
-    "cls_render_backward": (C.c_int, [P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P]),
+    "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, I32, P, P, P, P, P, P, P]),
+    "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P]),
     "cls_adam_workspace_size": (SZ, [I32]),
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
 }
@@ -160,13 +163,24 @@ def cls_project_workspace_size(info) -> int:
     return load().cls_project_workspace_size(C.byref(info))
 
 
-def cls_project_and_bin(scenes_dev, views_dev, info, project_mode, records, tile_active,
+def cls_bin_offsets_size(info) -> int:
+    return load().cls_bin_offsets_size(C.byref(info))
+
+
+def cls_project_and_bin(scenes_dev, views_dev, info, project_mode, layout, records, tile_active,
                         active_tiles, n_active_tiles_dev, keys, vals, capacity, n_pairs_dev,
-                        status_dev, workspace, workspace_bytes, stream) -> int:
-    return load().cls_project_and_bin(scenes_dev, views_dev, C.byref(info), project_mode,
+                        ranges, bin_offsets, status_dev, workspace, workspace_bytes,
+                        stream) -> int:
+    return load().cls_project_and_bin(scenes_dev, views_dev, C.byref(info), project_mode, layout,
                                       records, tile_active, active_tiles, n_active_tiles_dev,
-                                      keys, vals, capacity, n_pairs_dev, status_dev, workspace,
-                                      workspace_bytes, stream)
+                                      keys, vals, capacity, n_pairs_dev, ranges, bin_offsets,
+                                      status_dev, workspace, workspace_bytes, stream)
+
+
+def cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles, work_counter,
+                   stream) -> int:
+    return load().cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles,
+                                 work_counter, stream)
 
 
 def cls_sort_workspace_size(capacity, key_bits) -> int:
@@ -179,22 +193,22 @@ def cls_sort_keys(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bit
                                 ranges, n_tiles, status_dev, workspace, workspace_bytes, stream)
 
 
-def cls_render_forward(views_dev, info, records, vals, ranges, active_tiles, n_active_tiles_dev,
-                       bg, target, loss_mode, image, T_final, n_contrib, dL_dimage,
-                       loss_per_scene, work_counter, stream) -> int:
+def cls_render_forward(views_dev, info, records, vals, vals_stride, ranges, active_tiles,
+                       n_active_tiles_dev, bg, target, loss_mode, image, T_final, n_contrib,
+                       dL_dimage, loss_per_scene, work_counter, stream) -> int:
     bg3 = (C.c_float * 3)(*bg)
-    return load().cls_render_forward(views_dev, C.byref(info), records, vals, ranges,
+    return load().cls_render_forward(views_dev, C.byref(info), records, vals, vals_stride, ranges,
                                      active_tiles, n_active_tiles_dev, bg3, target, loss_mode,
                                      image, T_final, n_contrib, dL_dimage, loss_per_scene,
                                      work_counter, stream)
 
 
-def cls_render_backward(scenes_dev, views_dev, info, records, vals, ranges, active_tiles,
-                        n_active_tiles_dev, bg, T_final, n_contrib, dL_dimage, grad2d, grads,
-                        work_counter, stream) -> int:
+def cls_render_backward(scenes_dev, views_dev, info, records, vals, vals_stride, ranges,
+                        active_tiles, n_active_tiles_dev, bg, T_final, n_contrib, dL_dimage,
+                        grad2d, grads, work_counter, stream) -> int:
     bg3 = (C.c_float * 3)(*bg)
     return load().cls_render_backward(scenes_dev, views_dev, C.byref(info), records, vals,
-                                      ranges, active_tiles, n_active_tiles_dev, bg3, T_final,
+                                      vals_stride, ranges, active_tiles, n_active_tiles_dev, bg3, T_final,
                                       n_contrib, dL_dimage, grad2d, grads, work_counter, stream)
 
 

@@ -8,6 +8,8 @@ constexpr int kProjBlock = 128;
 constexpr int kBinBlock = 256;
 constexpr int kBinItems = 8;
 constexpr int kBinChunk = kBinBlock * kBinItems;
+constexpr int kDepthBins = CLS_DEPTH_BINS;  // depth buckets per tile (bucketed layout)
+constexpr int kBigArea = 128;               // rectangles above this many tiles: one warp each
 
 // ---------------------------------------------------------------------------
 // Projection. mode 0: every Gaussian of the view's scene (slot -1); mode 1:
@@ -72,52 +74,77 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
     out[2] = r2;
 }
 
-// Mark the tiles of every active Gaussian's rectangle.
+// ---------------------------------------------------------------------------
+// Dynamic render mask: every active Gaussian adds +1 over its tile rectangle
+// in a per-view difference grid (four corner updates), whose 2D prefix sum is
+// the number of active rectangles covering each tile.
+__device__ __forceinline__ void stamp_rect(int32_t* grid, int Wd, int x0, int x1, int y0, int y1) {
+    atomicAdd(grid + (int64_t)y0 * Wd + x0, 1);
+    atomicAdd(grid + (int64_t)y0 * Wd + x1 + 1, -1);
+    atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x0, -1);
+    atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x1 + 1, 1);
+}
+
+__device__ __forceinline__ bool record_rect(const ClsView& view, const ClsProjected* records,
+                                            int64_t rec, int& x0, int& x1, int& y0, int& y1,
+                                            uint32_t& zbits) {
+    const float4 c0 = reinterpret_cast<const float4*>(records + rec)[0];
+    const float4 c2 = reinterpret_cast<const float4*>(records + rec)[2];
+    const int radius = __float_as_int(c2.w);
+    zbits = __float_as_uint(c2.z);
+    if (radius <= 0) return false;
+    return tile_rect(c0.x, c0.y, (float)radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1);
+}
+
 __global__ void __launch_bounds__(256)
-mark_tiles_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-                  const ClsProjected* __restrict__ records, uint8_t* __restrict__ tile_active) {
+stamp_active_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
+                    const ClsProjected* __restrict__ records, int32_t* __restrict__ diff) {
     const ClsView& view = views[blockIdx.y];
     const ClsScene& sc = scenes[view.scene];
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= sc.n_active) return;
-    const int g = sc.active_idx[i];
-    const ClsProjected rec = records[view.rec_base + g];
-    if (rec.radius <= 0) return;
     int x0, x1, y0, y1;
-    if (!tile_rect(rec.u, rec.v, (float)rec.radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1))
-        return;
-    for (int ty = y0; ty <= y1; ++ty) {
-        uint8_t* row = tile_active + view.tile_base + (int64_t)ty * view.tiles_x;
-        for (int tx = x0; tx <= x1; ++tx) row[tx] = 1;
-    }
+    uint32_t zb;
+    if (!record_rect(view, records, view.rec_base + sc.active_idx[i], x0, x1, y0, y1, zb)) return;
+    stamp_rect(diff + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
 }
 
-// Ascending list of active tiles (one block, 1024 threads).
-__global__ void __launch_bounds__(1024)
-compact_tiles_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
-                     int32_t* __restrict__ active_tiles, int32_t* __restrict__ n_active_tiles) {
-    __shared__ int32_t smem[1024 / 32 + 1];
-    int32_t carry = 0;
-    for (int64_t base = 0; base < n_tiles; base += 1024) {
-        const int64_t t = base + threadIdx.x;
-        const int32_t f = (t < n_tiles && tile_active[t]) ? 1 : 0;
-        int32_t tot;
-        const int32_t ex = block_exclusive_sum<1024>(f, smem, tot);
-        if (f) active_tiles[carry + ex] = (int32_t)t;
-        carry += tot;
+// In-place 2D inclusive prefix sum of a (rows x cols) grid with row pitch Wd.
+__device__ __forceinline__ void prefix2d(int32_t* G, int rows, int cols, int Wd) {
+    for (int y = threadIdx.x; y < rows; y += blockDim.x) {
+        int32_t run = 0;
+        for (int x = 0; x < cols; ++x) {
+            run += G[(int64_t)y * Wd + x];
+            G[(int64_t)y * Wd + x] = run;
+        }
     }
-    if (threadIdx.x == 0) *n_active_tiles = carry;
+    __syncthreads();
+    for (int x = threadIdx.x; x < cols; x += blockDim.x) {
+        int32_t run = 0;
+        for (int y = 0; y < rows; ++y) {
+            run += G[(int64_t)y * Wd + x];
+            G[(int64_t)y * Wd + x] = run;
+        }
+    }
+    __syncthreads();
 }
 
-// Summed-area table of the active-tile mask per view:
+// Per view: coverage of the active stamps -> tile mask -> summed-area table
 // S[y][x] = number of active tiles with ty < y and tx < x.
 __global__ void __launch_bounds__(256)
-tile_sat_kernel(const ClsView* __restrict__ views, const uint8_t* __restrict__ tile_active,
-                int32_t* __restrict__ sat) {
+tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
+                 uint8_t* __restrict__ tile_active, int32_t* __restrict__ sat) {
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
+    int32_t* D = diff + view.sat_base;
+    prefix2d(D, Ty, Tx, Wd);
+    uint8_t* act = tile_active + view.tile_base;
+    for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+        const int y = t / Tx, x = t - y * Tx;
+        act[t] = D[(int64_t)y * Wd + x] > 0 ? 1 : 0;
+    }
+    __syncthreads();
     int32_t* S = sat + view.sat_base;
-    const uint8_t* act = tile_active + view.tile_base;
     for (int y = threadIdx.x; y <= Ty; y += blockDim.x) {
         int32_t run = 0;
         S[(int64_t)y * Wd] = 0;
@@ -136,74 +163,290 @@ tile_sat_kernel(const ClsView* __restrict__ views, const uint8_t* __restrict__ t
     }
 }
 
+// Ascending list of active tiles and each tile's rank in it (-1 if inactive).
+__global__ void __launch_bounds__(1024)
+compact_tiles_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
+                     int32_t* __restrict__ active_tiles, int32_t* __restrict__ n_active_tiles,
+                     int32_t* __restrict__ tile_rank) {
+    __shared__ int32_t smem[1024 / 32 + 1];
+    int32_t carry = 0;
+    for (int64_t base = 0; base < n_tiles; base += 1024) {
+        const int64_t t = base + threadIdx.x;
+        const int32_t f = (t < n_tiles && tile_active[t]) ? 1 : 0;
+        int32_t tot;
+        const int32_t ex = block_exclusive_sum<1024>(f, smem, tot);
+        if (f) active_tiles[carry + ex] = (int32_t)t;
+        if (t < n_tiles) tile_rank[t] = f ? carry + ex : -1;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *n_active_tiles = carry;
+}
+
 __device__ __forceinline__ int rect_count(const int32_t* S, int Wd, int x0, int x1, int y0,
                                           int y1) {
     return S[(int64_t)(y1 + 1) * Wd + x1 + 1] - S[(int64_t)y0 * Wd + x1 + 1] -
            S[(int64_t)(y1 + 1) * Wd + x0] + S[(int64_t)y0 * Wd + x0];
 }
 
+// Pairs of one record (active tiles inside its rectangle), O(1) from the SAT.
 __device__ __forceinline__ int pair_count(const ClsView& view, const ClsProjected* records,
                                           const int32_t* sat, int g, int& x0, int& x1, int& y0,
-                                          int& y1) {
-    const float4 c0 = reinterpret_cast<const float4*>(records + view.rec_base + g)[0];
-    const float4 c2 = reinterpret_cast<const float4*>(records + view.rec_base + g)[2];
-    const int radius = __float_as_int(c2.w);
-    if (radius <= 0) return 0;
-    if (!tile_rect(c0.x, c0.y, (float)radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1))
-        return 0;
+                                          int& y1, uint32_t& zbits) {
+    if (!record_rect(view, records, view.rec_base + g, x0, x1, y0, y1, zbits)) return 0;
     return rect_count(sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
 }
 
+// Per-chunk pair totals (flat layout) and, per view, the depth range of the
+// Gaussians that produce pairs (bucketed layout).
 __global__ void __launch_bounds__(kBinBlock)
 count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                    const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
-                   int chunks_per_view, int64_t* __restrict__ partials) {
+                   int chunks_per_view, int64_t* __restrict__ partials,
+                   uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
+    __shared__ uint32_t s_lo, s_hi;
     const ClsView& view = views[blockIdx.y];
     const int n = scenes[view.scene].n;
+    if (threadIdx.x == 0) { s_lo = 0xffffffffu; s_hi = 0u; }
+    __syncthreads();
     int64_t cnt = 0;
+    uint32_t lo = 0xffffffffu, hi = 0u;
     for (int it = 0; it < kBinItems; ++it) {
         const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
         if (g < n) {
             int x0, x1, y0, y1;
-            cnt += pair_count(view, records, sat, g, x0, x1, y0, y1);
+            uint32_t zb;
+            const int c = pair_count(view, records, sat, g, x0, x1, y0, y1, zb);
+            if (c > 0) {
+                cnt += c;
+                lo = min(lo, zb);
+                hi = max(hi, zb);
+            }
         }
     }
     int64_t tot;
     block_exclusive_sum<kBinBlock>(cnt, smem, tot);
     if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] = tot;
+    if (zmin) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if ((threadIdx.x & 31) == 0 && hi >= lo) {
+            atomicMin(&s_lo, lo);
+            atomicMax(&s_hi, hi);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && s_hi >= s_lo) {
+            atomicMin(zmin + blockIdx.y, s_lo);
+            atomicMax(zmax + blockIdx.y, s_hi);
+        }
+    }
+}
+
+// Depth bin of a key inside its view's depth range (monotone in depth).
+__device__ __forceinline__ int depth_bin(uint32_t zb, uint32_t lo, uint32_t hi) {
+    if (zb <= lo) return 0;
+    if (zb >= hi) return kDepthBins - 1;
+    return (int)(((uint64_t)(zb - lo) * kDepthBins) / ((uint64_t)(hi - lo) + 1));
+}
+
+// Bucketed layout: stamp every pair-producing rectangle into its depth bin's
+// difference grid; the prefix sums then give pairs per (tile, depth bin).
+__global__ void __launch_bounds__(kBinBlock)
+stamp_bins_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
+                  const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
+                  const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
+                  int32_t* __restrict__ bins, int64_t total_sat) {
+    const ClsView& view = views[blockIdx.y];
+    const int n = scenes[view.scene].n;
+    const uint32_t lo = zmin[blockIdx.y], hi = zmax[blockIdx.y];
+    for (int it = 0; it < kBinItems; ++it) {
+        const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
+        if (g >= n) break;
+        int x0, x1, y0, y1;
+        uint32_t zb;
+        if (pair_count(view, records, sat, g, x0, x1, y0, y1, zb) == 0) continue;
+        const int b = depth_bin(zb, lo, hi);
+        stamp_rect(bins + b * total_sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins,
+                   int64_t total_sat) {
+    const ClsView& view = views[blockIdx.y];
+    prefix2d(bins + blockIdx.x * total_sat + view.sat_base, view.tiles_y, view.tiles_x,
+             view.tiles_x + 1);
+}
+
+// Pairs per (active tile rank, depth bin), entry e = rank * kDepthBins + bin.
+__device__ __forceinline__ int64_t sub_count(const ClsView* views, int n_views,
+                                             const int32_t* active_tiles, const int32_t* bins,
+                                             int64_t total_sat, int64_t e) {
+    const int t = (int)(e / kDepthBins), b = (int)(e - (int64_t)t * kDepthBins);
+    const int tile = active_tiles[t];
+    const ClsView& view = views[view_of_tile(views, n_views, tile)];
+    const int local = tile - view.tile_base;
+    const int ty = local / view.tiles_x, tx = local - ty * view.tiles_x;
+    return bins[b * total_sat + view.sat_base + (int64_t)ty * (view.tiles_x + 1) + tx];
 }
 
 __global__ void __launch_bounds__(kBinBlock)
+sub_count_kernel(const ClsView* __restrict__ views, int n_views,
+                 const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
+                 const int32_t* __restrict__ bins, int64_t total_sat,
+                 int64_t* __restrict__ partials) {
+    __shared__ int64_t smem[kBinBlock / 32 + 1];
+    const int64_t ne = (int64_t)(*n_active) * kDepthBins;
+    int64_t cnt = 0;
+    for (int it = 0; it < kBinItems; ++it) {
+        const int64_t e = (int64_t)blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
+        if (e < ne) cnt += sub_count(views, n_views, active_tiles, bins, total_sat, e);
+    }
+    int64_t tot;
+    block_exclusive_sum<kBinBlock>(cnt, smem, tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+// Offsets of every (tile, bin) bucket and the per-tile ranges, clamped to the
+// key capacity so every later access stays inside the key buffer.
+__global__ void __launch_bounds__(kBinBlock)
+sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
+                   const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
+                   const int32_t* __restrict__ bins, int64_t total_sat,
+                   const int64_t* __restrict__ partials, int64_t capacity,
+                   uint32_t* __restrict__ bin_offsets, uint32_t* __restrict__ ranges) {
+    __shared__ int64_t smem[kBinBlock / 32 + 1];
+    const int64_t ne = (int64_t)(*n_active) * kDepthBins;
+    int64_t base = partials[blockIdx.x];
+    for (int it = 0; it < kBinItems; ++it) {
+        const int64_t e = (int64_t)blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
+        const int64_t c = e < ne ? sub_count(views, n_views, active_tiles, bins, total_sat, e) : 0;
+        int64_t tot;
+        const int64_t off = base + block_exclusive_sum<kBinBlock>(c, smem, tot);
+        base += tot;
+        if (e < ne) {
+            const uint32_t o = (uint32_t)(off < capacity ? off : capacity);
+            const uint32_t o_end = (uint32_t)(off + c < capacity ? off + c : capacity);
+            bin_offsets[e] = o;
+            const int t = (int)(e / kDepthBins), b = (int)(e - (int64_t)t * kDepthBins);
+            const int64_t tile = active_tiles[t];
+            if (b == 0) ranges[2 * tile] = o;
+            if (b == kDepthBins - 1) {
+                ranges[2 * tile + 1] = o_end;
+                bin_offsets[e + 1] = o_end;  // sentinel: end of the tile's last bin
+            }
+        }
+    }
+}
+
+// Flat layout: pairs in view, Gaussian, row-major tile order at scanned offsets.
+// Bucketed layout: pair (g, tile) goes to bucket (rank(tile), bin(g)) at an
+// atomically claimed slot; the order inside a bucket is fixed later by the
+// per-bucket sort. Rectangles larger than kBigArea tiles go to a list that one
+// warp per Gaussian emits.
+template <int LAYOUT>
+__global__ void __launch_bounds__(kBinBlock)
 emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                   const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
-                  const uint8_t* __restrict__ tile_active, int chunks_per_view,
-                  const int64_t* __restrict__ offsets, uint64_t* __restrict__ keys,
-                  uint32_t* __restrict__ vals, int64_t capacity) {
+                  const uint8_t* __restrict__ tile_active, const int32_t* __restrict__ tile_rank,
+                  int chunks_per_view, const int64_t* __restrict__ offsets,
+                  const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
+                  const uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
+                  uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
+                  uint4* __restrict__ big_list, int32_t* __restrict__ big_count) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     const ClsView& view = views[blockIdx.y];
     const int n = scenes[view.scene].n;
-    int64_t base = offsets[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x];
+    int64_t base = LAYOUT == 0 ? offsets[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] : 0;
+    const uint32_t lo = LAYOUT == 1 ? zmin[blockIdx.y] : 0u;
+    const uint32_t hi = LAYOUT == 1 ? zmax[blockIdx.y] : 0u;
     for (int it = 0; it < kBinItems; ++it) {
         const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
         int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
-        const int64_t cnt = g < n ? pair_count(view, records, sat, g, x0, x1, y0, y1) : 0;
-        int64_t tot;
-        int64_t pos = base + block_exclusive_sum<kBinBlock>(cnt, smem, tot);
-        base += tot;
+        uint32_t zb = 0;
+        const int64_t cnt = g < n ? pair_count(view, records, sat, g, x0, x1, y0, y1, zb) : 0;
+        int64_t pos = 0;
+        if (LAYOUT == 0) {
+            int64_t tot;
+            pos = base + block_exclusive_sum<kBinBlock>(cnt, smem, tot);
+            base += tot;
+        }
         if (cnt == 0) continue;
-        const uint64_t zbits =
-            (uint64_t)__float_as_uint(reinterpret_cast<const float4*>(records + view.rec_base + g)[2].z);
-        const uint32_t val = (uint32_t)(view.rec_base + g);
+        const uint32_t rec = (uint32_t)(view.rec_base + g);
+        const int bin = LAYOUT == 1 ? depth_bin(zb, lo, hi) : 0;
+        const int area = (x1 - x0 + 1) * (y1 - y0 + 1);
+        if (area > kBigArea) {
+            const int slot = atomicAdd(big_count, 1);
+            big_list[slot] = make_uint4(rec, (uint32_t)blockIdx.y, (uint32_t)(pos & 0xffffffff),
+                                        (uint32_t)(pos >> 32));
+            continue;
+        }
         for (int ty = y0; ty <= y1; ++ty) {
             const int64_t row = (int64_t)view.tile_base + (int64_t)ty * view.tiles_x;
             for (int tx = x0; tx <= x1; ++tx) {
                 if (!tile_active[row + tx]) continue;
-                if (pos < capacity) {
-                    keys[pos] = ((uint64_t)(row + tx) << 32) | zbits;
-                    vals[pos] = val;
+                if (LAYOUT == 0) {
+                    if (pos < capacity) {
+                        keys[pos] = ((uint64_t)(row + tx) << 32) | zb;
+                        vals[pos] = rec;
+                    }
+                    ++pos;
+                } else {
+                    const int64_t sub = (int64_t)tile_rank[row + tx] * kDepthBins + bin;
+                    const int64_t p = (int64_t)bin_offsets[sub] + atomicAdd(cursor + sub, 1);
+                    if (p < capacity) keys[p] = ((uint64_t)zb << 32) | rec;
                 }
-                ++pos;
+            }
+        }
+    }
+}
+
+// One warp per large rectangle; lanes walk its tiles in row-major order. The
+// flat layout keeps that order with a ballot prefix.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256)
+emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
+                const uint8_t* __restrict__ tile_active, const int32_t* __restrict__ tile_rank,
+                const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
+                const uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
+                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
+                const uint4* __restrict__ big_list, const int32_t* __restrict__ big_count) {
+    const int lane = threadIdx.x & 31;
+    const int nbig = *big_count;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nbig;
+         w += (gridDim.x * blockDim.x) >> 5) {
+        const uint4 item = big_list[w];
+        const ClsView& view = views[item.y];
+        int x0, x1, y0, y1;
+        uint32_t zb;
+        record_rect(view, records, item.x, x0, x1, y0, y1, zb);
+        const int wdt = x1 - x0 + 1;
+        const int area = wdt * (y1 - y0 + 1);
+        int64_t pos = ((int64_t)item.w << 32) | item.z;
+        const int bin = LAYOUT == 1 ? depth_bin(zb, zmin[item.y], zmax[item.y]) : 0;
+        for (int k0 = 0; k0 < area; k0 += 32) {
+            const int k = k0 + lane;
+            int64_t tile = 0;
+            bool on = false;
+            if (k < area) {
+                const int ty = y0 + k / wdt, tx = x0 + k % wdt;
+                tile = (int64_t)view.tile_base + (int64_t)ty * view.tiles_x + tx;
+                on = tile_active[tile] != 0;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, on);
+            if (LAYOUT == 0) {
+                const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
+                if (on && p < capacity) {
+                    keys[p] = ((uint64_t)tile << 32) | zb;
+                    vals[p] = item.x;
+                }
+                pos += __popc(m);
+            } else if (on) {
+                const int64_t sub = (int64_t)tile_rank[tile] * kDepthBins + bin;
+                const int64_t p = (int64_t)bin_offsets[sub] + atomicAdd(cursor + sub, 1);
+                if (p < capacity) keys[p] = ((uint64_t)zb << 32) | item.x;
             }
         }
     }
@@ -213,30 +456,62 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
 
 using namespace cls;
 
-static int64_t bin_chunks_per_view(const ClsBatchInfo* info) {
+namespace {
+
+struct ProjLayout {
+    size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
+        bins, total;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+int64_t bin_chunks_per_view(const ClsBatchInfo* info) {
     return (info->max_n + kBinChunk - 1) / kBinChunk;
 }
 
+ProjLayout proj_layout(const ClsBatchInfo* info) {
+    ProjLayout L;
+    const int64_t V = info->n_views;
+    const int64_t subs = info->total_tiles * kDepthBins;
+    size_t o = 0;
+    L.partials = o; o = align256(o + (size_t)(bin_chunks_per_view(info) * V + 1) * 8);
+    L.sat = o; o = align256(o + (size_t)info->total_sat * 4);
+    L.diff = o; o = align256(o + (size_t)info->total_sat * 4);
+    L.zmin = o; o = align256(o + (size_t)V * 4);
+    L.zmax = o; o = align256(o + (size_t)V * 4);
+    L.tile_rank = o; o = align256(o + (size_t)info->total_tiles * 4);
+    L.cursor = o; o = align256(o + (size_t)subs * 4);
+    L.sub_partials = o; o = align256(o + (size_t)((subs + kBinChunk - 1) / kBinChunk + 1) * 8);
+    L.big_list = o; o = align256(o + (size_t)info->total_records * 16);
+    L.big_count = o; o = align256(o + 4);
+    L.bins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
 extern "C" size_t cls_project_workspace_size(const ClsBatchInfo* info) {
-    if (!info) return 0;
-    const int64_t parts = bin_chunks_per_view(info) * info->n_views + 1;
-    size_t bytes = (size_t)parts * sizeof(int64_t);
-    bytes = (bytes + 255) / 256 * 256;
-    bytes += (size_t)info->total_sat * sizeof(int32_t);
-    return (bytes + 255) / 256 * 256;
+    return info ? proj_layout(info).total : 0;
+}
+
+extern "C" size_t cls_bin_offsets_size(const ClsBatchInfo* info) {
+    return info ? (size_t)(info->total_tiles * kDepthBins + 1) : 0;
 }
 
 extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
-                                   const ClsBatchInfo* info, int32_t project_mode,
+                                   const ClsBatchInfo* info, int32_t project_mode, int32_t layout,
                                    ClsProjected* records, uint8_t* tile_active,
                                    int32_t* active_tiles, int32_t* n_active_tiles_dev,
                                    uint64_t* keys, uint32_t* vals, int64_t capacity,
-                                   int64_t* n_pairs_dev, int32_t* status_dev, void* workspace,
-                                   size_t workspace_bytes, cls_stream_t stream) {
+                                   int64_t* n_pairs_dev, uint32_t* ranges, uint32_t* bin_offsets,
+                                   int32_t* status_dev, void* workspace, size_t workspace_bytes,
+                                   cls_stream_t stream) {
     if (!info || !scenes_dev || !views_dev || !records || !tile_active || !active_tiles ||
-        !n_active_tiles_dev || !n_pairs_dev || !status_dev || !workspace ||
-        (capacity > 0 && (!keys || !vals)) || capacity < 0 ||
-        (project_mode != 0 && project_mode != 1))
+        !n_active_tiles_dev || !n_pairs_dev || !status_dev || !workspace || capacity < 0 ||
+        (project_mode != 0 && project_mode != 1) || (layout != 0 && layout != 1) ||
+        (capacity > 0 && !keys) || (layout == 0 && capacity > 0 && !vals) ||
+        (layout == 1 && (!ranges || !bin_offsets)))
         return CLS_ERR_INVALID_ARG;
     if (info->n_views <= 0 || info->n_views > 65535 || info->total_tiles <= 0 ||
         workspace_bytes < cls_project_workspace_size(info) || capacity >= ((int64_t)1 << 32))
@@ -244,35 +519,81 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     cudaStream_t s = as_stream(stream);
     const unsigned V = (unsigned)info->n_views;
     const int64_t cpv = bin_chunks_per_view(info);
-    int64_t* partials = static_cast<int64_t*>(workspace);
-    size_t off = ((size_t)(cpv * V + 1) * sizeof(int64_t) + 255) / 256 * 256;
-    int32_t* sat = reinterpret_cast<int32_t*>(static_cast<char*>(workspace) + off);
+    const ProjLayout L = proj_layout(info);
+    char* ws = static_cast<char*>(workspace);
+    int64_t* partials = reinterpret_cast<int64_t*>(ws + L.partials);
+    int32_t* sat = reinterpret_cast<int32_t*>(ws + L.sat);
+    int32_t* diff = reinterpret_cast<int32_t*>(ws + L.diff);
+    uint32_t* zmin = reinterpret_cast<uint32_t*>(ws + L.zmin);
+    uint32_t* zmax = reinterpret_cast<uint32_t*>(ws + L.zmax);
+    int32_t* tile_rank = reinterpret_cast<int32_t*>(ws + L.tile_rank);
+    int32_t* cursor = reinterpret_cast<int32_t*>(ws + L.cursor);
+    int64_t* sub_partials = reinterpret_cast<int64_t*>(ws + L.sub_partials);
+    uint4* big_list = reinterpret_cast<uint4*>(ws + L.big_list);
+    int32_t* big_count = reinterpret_cast<int32_t*>(ws + L.big_count);
+    int32_t* bins = reinterpret_cast<int32_t*>(ws + L.bins);
+    const int64_t subs = info->total_tiles * kDepthBins;
 
-    if (project_mode == 0) {
-        if (info->max_n > 0)
-            project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock,
-                                 0, s>>>(scenes_dev, views_dev, records);
-    }
+    if (project_mode == 0 && info->max_n > 0)
+        project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
+                             s>>>(scenes_dev, views_dev, records);
     if (info->max_active > 0)
         project_kernel<1><<<dim3((info->max_active + kProjBlock - 1) / kProjBlock, V), kProjBlock,
                              0, s>>>(scenes_dev, views_dev, records);
-    cudaMemsetAsync(tile_active, 0, (size_t)info->total_tiles, s);
+    cudaMemsetAsync(diff, 0, (size_t)info->total_sat * 4, s);
+    cudaMemsetAsync(big_count, 0, 4, s);
     if (info->max_active > 0)
-        mark_tiles_kernel<<<dim3((info->max_active + 255) / 256, V), 256, 0, s>>>(
-            scenes_dev, views_dev, records, tile_active);
+        stamp_active_kernel<<<dim3((info->max_active + 255) / 256, V), 256, 0, s>>>(
+            scenes_dev, views_dev, records, diff);
+    tile_mask_kernel<<<V, 256, 0, s>>>(views_dev, diff, tile_active, sat);
     compact_tiles_kernel<<<1, 1024, 0, s>>>(tile_active, info->total_tiles, active_tiles,
-                                            n_active_tiles_dev);
-    tile_sat_kernel<<<V, 256, 0, s>>>(views_dev, tile_active, sat);
-    if (cpv > 0) {
-        count_pairs_kernel<<<dim3((unsigned)cpv, V), kBinBlock, 0, s>>>(
-            scenes_dev, views_dev, records, sat, (int)cpv, partials);
+                                            n_active_tiles_dev, tile_rank);
+    if (cpv == 0) {
+        cudaMemsetAsync(n_pairs_dev, 0, sizeof(int64_t), s);
+        if (layout == 1) cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
+        CLS_CHECK_LAUNCH();
+        return CLS_OK;
+    }
+    const dim3 rec_grid((unsigned)cpv, V);
+    if (layout == 1) {
+        cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
+        cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
+    }
+    count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
+                                                      (int)cpv, partials,
+                                                      layout == 1 ? zmin : nullptr,
+                                                      layout == 1 ? zmax : nullptr);
+    if (layout == 0) {
         scan_partials_kernel<<<1, 1024, 0, s>>>(partials, cpv * V, n_pairs_dev, nullptr, capacity,
                                                 status_dev);
-        emit_pairs_kernel<<<dim3((unsigned)cpv, V), kBinBlock, 0, s>>>(
-            scenes_dev, views_dev, records, sat, tile_active, (int)cpv, partials, keys, vals,
-            capacity);
+        emit_pairs_kernel<0><<<rec_grid, kBinBlock, 0, s>>>(
+            scenes_dev, views_dev, records, sat, tile_active, tile_rank, (int)cpv, partials,
+            nullptr, nullptr, nullptr, nullptr, keys, vals, capacity, big_list, big_count);
+        emit_big_kernel<0><<<1024, 256, 0, s>>>(views_dev, records, tile_active, tile_rank,
+                                                nullptr, nullptr, nullptr, nullptr, keys, vals,
+                                                capacity, big_list, big_count);
     } else {
-        cudaMemsetAsync(n_pairs_dev, 0, sizeof(int64_t), s);
+        const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
+        cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
+        cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
+        cudaMemsetAsync(cursor, 0, (size_t)subs * 4, s);
+        stamp_bins_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
+                                                         zmin, zmax, bins, info->total_sat);
+        bins_prefix_kernel<<<dim3(kDepthBins, V), 256, 0, s>>>(views_dev, bins, info->total_sat);
+        sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
+            views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
+            sub_partials);
+        scan_partials_kernel<<<1, 1024, 0, s>>>(sub_partials, sub_chunks, n_pairs_dev, nullptr,
+                                                capacity, status_dev);
+        sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
+            views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
+            sub_partials, capacity, bin_offsets, ranges);
+        emit_pairs_kernel<1><<<rec_grid, kBinBlock, 0, s>>>(
+            scenes_dev, views_dev, records, sat, tile_active, tile_rank, (int)cpv, nullptr, zmin,
+            zmax, bin_offsets, cursor, keys, nullptr, capacity, big_list, big_count);
+        emit_big_kernel<1><<<1024, 256, 0, s>>>(views_dev, records, tile_active, tile_rank, zmin,
+                                                zmax, bin_offsets, cursor, keys, nullptr,
+                                                capacity, big_list, big_count);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;

@@ -24,7 +24,7 @@ constexpr int kG2Stride = 12;
 __global__ void __launch_bounds__(kTilePixels)
 render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
-                  const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
+                  int vals_stride, const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
                   const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
                   const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib,
                   const float* __restrict__ dL_dimage, float* __restrict__ grad2d,
@@ -79,7 +79,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
             const int nb = hi - lo;
             if ((int)threadIdx.x < nb) {
                 const float4* rec =
-                    reinterpret_cast<const float4*>(records + vals[start + lo + threadIdx.x]);
+                    reinterpret_cast<const float4*>(records + vals[(int64_t)(start + lo + threadIdx.x) * vals_stride]);
                 s_a[threadIdx.x] = rec[0];
                 s_b[threadIdx.x] = rec[1];
                 const float4 c = rec[2];
@@ -391,12 +391,14 @@ using namespace cls;
 
 extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
                                    const ClsBatchInfo* info, const ClsProjected* records,
-                                   const uint32_t* vals, const uint32_t* ranges,
+                                   const uint32_t* vals, int32_t vals_stride,
+                                   const uint32_t* ranges,
                                    const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
                                    const float* bg, const float* T_final, const int32_t* n_contrib,
                                    const float* dL_dimage, float* grad2d, float* grads,
                                    int32_t* work_counter, cls_stream_t stream) {
-    if (!scenes_dev || !views_dev || !info || !records || !ranges || !active_tiles ||
+    if (!scenes_dev || !views_dev || !info || !records || !vals ||
+        (vals_stride != 1 && vals_stride != 2) || !ranges || !active_tiles ||
         !n_active_tiles_dev || !bg || !T_final || !n_contrib || !dL_dimage || !work_counter ||
         info->n_views <= 0 || info->total_tiles <= 0 || info->n_scenes > 65535 ||
         (info->total_g2 > 0 && !grad2d) || (info->total_grad_rows > 0 && !grads))
@@ -414,7 +416,7 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
     const int blocks = (int)hmin64(info->total_tiles, g_bwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_bwd_kernel<<<blocks, kTilePixels, 0, s>>>(
-        views_dev, info->n_views, records, vals, ranges, active_tiles, n_active_tiles_dev, bg[0],
+        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, bg[0],
         bg[1], bg[2], T_final, n_contrib, dL_dimage, grad2d, work_counter);
     if (info->max_active > 0 && info->total_grad_rows > 0) {
         backward_gaussian_kernel<<<dim3((info->max_active + 127) / 128, info->n_scenes), 128, 0,

@@ -10,7 +10,7 @@ namespace cls {
 __global__ void __launch_bounds__(kTilePixels)
 render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
-                  const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
+                  int vals_stride, const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
                   const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
                   const float* __restrict__ target, int loss_mode, float* __restrict__ image,
                   float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
@@ -46,7 +46,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             if (__syncthreads_count(done) == kTilePixels) break;
             const uint32_t idx = b + threadIdx.x;
             if (idx < end) {
-                const float4* rec = reinterpret_cast<const float4*>(records + vals[idx]);
+                const float4* rec = reinterpret_cast<const float4*>(records + vals[(int64_t)idx * vals_stride]);
                 s_a[threadIdx.x] = rec[0];
                 s_b[threadIdx.x] = rec[1];
                 s_c[threadIdx.x] = rec[2].x;
@@ -131,13 +131,13 @@ using namespace cls;
 
 extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
                                   const ClsProjected* records, const uint32_t* vals,
-                                  const uint32_t* ranges, const int32_t* active_tiles,
+                                  int32_t vals_stride, const uint32_t* ranges, const int32_t* active_tiles,
                                   const int32_t* n_active_tiles_dev, const float* bg,
                                   const float* target, int32_t loss_mode, float* image,
                                   float* T_final, int32_t* n_contrib, float* dL_dimage,
                                   float* loss_per_scene, int32_t* work_counter,
                                   cls_stream_t stream) {
-    if (!views_dev || !info || !records || !ranges || !active_tiles || !n_active_tiles_dev ||
+    if (!views_dev || !info || !records || !vals || (vals_stride != 1 && vals_stride != 2) || !ranges || !active_tiles || !n_active_tiles_dev ||
         !bg || !T_final || !n_contrib || !work_counter || loss_mode < 0 || loss_mode > 2 ||
         (loss_mode != 0 && (!target || !dL_dimage)) || info->n_views <= 0 ||
         info->total_tiles <= 0)
@@ -153,7 +153,7 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
     const int blocks = (int)hmin64(info->total_tiles, g_fwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_fwd_kernel<<<blocks, kTilePixels, 0, s>>>(
-        views_dev, info->n_views, records, vals, ranges, active_tiles, n_active_tiles_dev, bg[0],
+        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, bg[0],
         bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
         work_counter);
     CLS_CHECK_LAUNCH();

@@ -102,8 +102,12 @@ class Batch:
     """Scene/view tables of one launch batch and every buffer the hot path uses."""
 
     def __init__(self, scenes: Sequence[SceneState], cams_per_scene: Sequence[Sequence],
-                 device="cuda"):
+                 device="cuda", layout: int = 1):
+        """layout 1: pairs bucketed by (tile, depth bin), sorted per tile in
+        shared memory (cls_sort_tiles); layout 0: flat (tile, depth) keys sorted
+        by the global onesweep radix sort (cls_sort_keys)."""
         self.device = device
+        self.layout = layout
         self.scenes = list(scenes)
         S = len(scenes)
         views = []
@@ -148,7 +152,9 @@ class Batch:
                                   device=dev)
         self.grads = torch.zeros(max(info.total_grad_rows, 1) * info.max_row_stride,
                                  dtype=torch.float32, device=dev)
-        self.counter = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.counter = torch.zeros(4, dtype=torch.int32, device=dev)
+        self.bin_offsets = torch.zeros(abi.cls_bin_offsets_size(info), dtype=torch.int32,
+                                       device=dev)
         self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
                                    device=dev)
         self.adam_ws = torch.zeros(max(abi.cls_adam_workspace_size(S), 256), dtype=torch.uint8,
@@ -186,10 +192,11 @@ class Batch:
     def project_and_bin(self, mode: int):
         b = self
         abi.check(abi.cls_project_and_bin(
-            _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, mode, _ptr(b.records),
+            _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, mode, b.layout, _ptr(b.records),
             _ptr(b.tile_active), _ptr(b.active_tiles), _ptr(b.n_active_tiles),
-            _ptr(b.keys), _ptr(b.vals), b.capacity, _ptr(b.n_pairs), _ptr(b.status),
-            _ptr(b.proj_ws), b.proj_ws.numel(), b.stream()), "cls_project_and_bin")
+            _ptr(b.keys), _ptr(b.vals), b.capacity, _ptr(b.n_pairs), _ptr(b.ranges),
+            _ptr(b.bin_offsets), _ptr(b.status), _ptr(b.proj_ws), b.proj_ws.numel(),
+            b.stream()), "cls_project_and_bin")
 
     def plan_capacity(self, slack: float = 1.5, extra: int = 1 << 16):
         """Count the pairs once (mode 0 projection, no keys) and size the key
@@ -208,13 +215,19 @@ class Batch:
         self.capacity = capacity
         self.keys = torch.empty(capacity, dtype=torch.int64, device=dev)
         self.keys_alt = torch.empty(capacity, dtype=torch.int64, device=dev)
-        self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
-        self.vals_alt = torch.empty(capacity, dtype=torch.int32, device=dev)
-        self.sort_ws = torch.empty(abi.cls_sort_workspace_size(capacity, self.info.key_bits),
-                                   dtype=torch.uint8, device=dev)
+        if self.layout == 0:
+            self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
+            self.vals_alt = torch.empty(capacity, dtype=torch.int32, device=dev)
+            self.sort_ws = torch.empty(abi.cls_sort_workspace_size(capacity, self.info.key_bits),
+                                       dtype=torch.uint8, device=dev)
 
     def sort(self):
         b = self
+        if b.layout == 1:
+            abi.check(abi.cls_sort_tiles(_ptr(b.keys), _ptr(b.keys_alt), _ptr(b.bin_offsets),
+                                         _ptr(b.n_active_tiles), b.info.total_tiles,
+                                         _ptr(b.counter) + 8, b.stream()), "cls_sort_tiles")
+            return
         abi.check(abi.cls_sort_keys(
             _ptr(b.keys), _ptr(b.vals), _ptr(b.keys_alt), _ptr(b.vals_alt), _ptr(b.n_pairs),
             b.capacity, b.info.key_bits, _ptr(b.ranges), b.info.total_tiles, _ptr(b.status),
@@ -225,17 +238,31 @@ class Batch:
         if loss_mode:
             b.loss.zero_()
         abi.check(abi.cls_render_forward(
-            _ptr(b.views_dev), b.info, _ptr(b.records), _ptr(b.vals), _ptr(b.ranges),
+            _ptr(b.views_dev), b.info, _ptr(b.records), *b._sorted_vals(), _ptr(b.ranges),
             _ptr(b.active_tiles), _ptr(b.n_active_tiles), bg,
             _ptr(b.target) if loss_mode else None, loss_mode,
             _ptr(b.image) if write_image else None, _ptr(b.T_final), _ptr(b.n_contrib),
             _ptr(b.dL_dimage) if loss_mode else None, _ptr(b.loss) if loss_mode else None,
             _ptr(b.counter), b.stream()), "cls_render_forward")
 
+    def _sorted_vals(self):
+        """Record index of sorted pair i: vals[i] (flat) or the low word of
+        keys[i] (bucketed)."""
+        if self.layout == 1:
+            return _ptr(self.keys), 2
+        return _ptr(self.vals), 1
+
+    def sorted_records(self) -> np.ndarray:
+        """Record index of every sorted pair (host copy, for checks)."""
+        n = min(int(self.n_pairs.item()), self.capacity)
+        if self.layout == 1:
+            return self.keys[:n].cpu().numpy().view(np.uint32)[0::2].copy()
+        return self.vals[:n].cpu().numpy().view(np.uint32).copy()
+
     def backward(self, bg=(0.0, 0.0, 0.0)):
         b = self
         abi.check(abi.cls_render_backward(
-            _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, _ptr(b.records), _ptr(b.vals),
+            _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, _ptr(b.records), *b._sorted_vals(),
             _ptr(b.ranges), _ptr(b.active_tiles), _ptr(b.n_active_tiles), bg, _ptr(b.T_final),
             _ptr(b.n_contrib), _ptr(b.dL_dimage), _ptr(b.grad2d), _ptr(b.grads),
             _ptr(b.counter) + 4, b.stream()), "cls_render_backward")
@@ -247,11 +274,20 @@ class Batch:
             _ptr(b.adam_ws), b.adam_ws.numel(), b.stream()), "cls_adam_step_active")
 
     def launches_per_step(self) -> int:
-        """Kernels of one iteration: project_and_bin 7, sort 3 + passes (+1
-        copy if the pass count is odd), forward 1, backward 2, Adam 2."""
-        passes = -(-self.info.key_bits // 8)
-        active = 1 if self.info.max_active > 0 else 0
-        return (5 + 2 * active) + (3 + passes + passes % 2) + 1 + (1 + active) + (1 + active)
+        """Kernels of one iteration. project_and_bin (mode 1): project and
+        stamp (2 if any Gaussian is active), tile mask, compaction, count,
+        then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
+        prefix, bucket counts, scan, offsets, emit, emit-big (7). Sort: flat
+        hist + scan + passes (+ copy if odd) + ranges; bucketed 1. Forward 1,
+        backward 2, Adam 2."""
+        active = 2 if self.info.max_active > 0 else 0
+        proj = active + 3 + (7 if self.layout == 1 else 3)
+        if self.layout == 1:
+            sort = 1
+        else:
+            passes = -(-self.info.key_bits // 8)
+            sort = 3 + passes + passes % 2
+        return proj + sort + 1 + (1 + active // 2) + (1 + active // 2)
 
     def check_status(self):
         code = int(self.status.item())
@@ -305,7 +341,8 @@ class LocalUpdate:
 
     def __init__(self, scene, cams, sh_degree: int, targets=None, masks=None, active=None,
                  vote_mode: int = 0, loss: str = "l1", lr: float = 1e-3,
-                 bg=(0.0, 0.0, 0.0), device="cuda", capacity_slack: float = 1.5):
+                 bg=(0.0, 0.0, 0.0), device="cuda", capacity_slack: float = 1.5,
+                 layout: int = 1):
         self.cams = list(cams)
         self.loss_mode = LOSS_MODES[loss]
         self.lr = lr
@@ -317,7 +354,7 @@ class LocalUpdate:
             lift(self.state, self.cams, masks, vote_mode, device)
         else:
             raise ValueError("give either an active set or change masks")
-        self.batch = Batch([self.state], [self.cams], device)
+        self.batch = Batch([self.state], [self.cams], device, layout)
         if targets is not None:
             self.batch.set_targets(targets)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
@@ -326,7 +363,7 @@ class LocalUpdate:
     @classmethod
     def from_resident(cls, state: SceneState, cams, targets, masks, vote_mode: int = 0,
                       loss: str = "l1", lr: float = 1e-3, bg=(0.0, 0.0, 0.0),
-                      capacity_slack: float = 1.5):
+                      capacity_slack: float = 1.5, layout: int = 1):
         """A new update of a scene already resident on the device. `targets`
         (float32, [3][H][W] per view, concatenated) and `masks` (uint8, [H][W]
         per view, concatenated) are flat tensors, typically pinned host memory;
@@ -339,7 +376,7 @@ class LocalUpdate:
         self.state = state
         dev = state.params.device
         lift(state, self.cams, masks, vote_mode, dev)
-        self.batch = Batch([state], [self.cams], dev)
+        self.batch = Batch([state], [self.cams], dev, layout)
         self.batch.target = targets.to(dev, non_blocking=True)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
         return self

@@ -35,9 +35,10 @@ def _built():
     build.build()
 
 
-def _update(scene, cams, deg, targets=None, active=None, loss="l1", masks=None):
+def _update(scene, cams, deg, targets=None, active=None, loss="l1", masks=None, layout=1):
     from paper_2506_21117_gb300.update import LocalUpdate
-    lu = LocalUpdate(scene, cams, deg, targets=targets, active=active, loss=loss, masks=masks)
+    lu = LocalUpdate(scene, cams, deg, targets=targets, active=active, loss=loss, masks=masks,
+                     layout=layout)
     lu.render_pass(with_backward=targets is not None, with_adam=False)
     torch.cuda.synchronize()
     lu.batch.check_status()
@@ -50,11 +51,19 @@ def _records(lu):
 
 
 def _gpu_pairs(lu):
+    """Sorted pairs as (tile<<32 | depth bits) keys and record values, from
+    either layout, plus the tile ranges."""
     b = lu.batch
     n = int(b.n_pairs.item())
-    keys = b.keys[:n].cpu().numpy().view(np.uint64)
-    vals = b.vals[:n].cpu().numpy().view(np.uint32)
     ranges = b.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+    raw = b.keys[:n].cpu().numpy().view(np.uint64)
+    if b.layout == 0:
+        return raw, b.vals[:n].cpu().numpy().view(np.uint32), ranges
+    tile = np.zeros(n, np.uint64)
+    for t, (a, e) in enumerate(ranges):
+        tile[a:e] = t
+    keys = (tile << np.uint64(32)) | (raw >> np.uint64(32))
+    vals = (raw & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     return keys, vals, ranges
 
 
@@ -98,17 +107,26 @@ def _compare_grads(lu, ref, active, deg, exclude=()):
 
 # ---------------------------------------------------------------- indexing --
 
-@pytest.mark.parametrize("case", ["plain", "local"])
-def test_projection_and_tile_lists_bit_exact(case):
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("case", ["plain", "local", "large_radii"])
+def test_projection_and_tile_lists_bit_exact(case, layout):
     if case == "plain":
         scene, cams, targets = S.workload_plain()
         deg, active = 0, np.ones(2000, bool)
-    else:
+    elif case == "local":
         scene, cams, masks, targets = _small_local()
         deg = 3
         active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
         assert 0 < active.sum() < 0.5 * active.size
-    lu = _update(scene, cams, deg, active=active)
+    else:
+        # big splats on a 300x200 view: rectangles above the warp-emission
+        # threshold, tiles with more pairs than one shared-memory window
+        scene = S.uniform_scene(20000, 1, 21)
+        scene["log_scales"] += np.float32(1.6)
+        cams = S.ring_cameras(2, 4.0, 300, 200, angles=[0.3, 2.0])
+        deg = 1
+        active = np.random.default_rng(21).uniform(size=20000) < 0.02
+    lu = _update(scene, cams, deg, active=active, layout=layout)
     rec, reci = _records(lu)
     projs, masks_o, sk, sv, rng = _oracle_index(scene, cams, active)
     n = scene["means"].shape[0]
@@ -147,11 +165,12 @@ def test_votes_bit_exact():
     assert np.array_equal(act1.astype(bool), c == len(cams))
 
 
-@pytest.mark.parametrize("n", [0, 1, 3839, 3840, 3841, 100_000, 777_777])
-def test_sort_random_keys_bit_exact(n):
+@pytest.mark.parametrize("n,bits", [(0, 44), (1, 44), (3839, 44), (3840, 44), (3841, 44),
+                                    (100_000, 44), (777_777, 44), (50_000, 40)])
+def test_sort_random_keys_bit_exact(n, bits):
     from paper_2506_21117_gb300 import _abi
     rng = np.random.default_rng(n)
-    tiles = rng.integers(0, 3000, n).astype(np.uint64)
+    tiles = rng.integers(0, min(3000, 1 << (bits - 32)), n).astype(np.uint64)
     depth = rng.integers(0, 64, n).astype(np.uint64) + np.uint64(0x3F000000)  # many ties
     keys = (tiles << np.uint64(32)) | depth
     vals = np.arange(n, dtype=np.uint32)
@@ -163,7 +182,6 @@ def test_sort_random_keys_bit_exact(n):
     ka, va = torch.empty_like(kd), torch.empty_like(vd)
     nd = torch.tensor([n], dtype=torch.int64, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    bits = 32 + 12
     ws = torch.zeros(_abi.cls_sort_workspace_size(cap, bits), dtype=torch.uint8, device="cuda")
     ranges = torch.zeros(2 * 3000, dtype=torch.int32, device="cuda")
     code = _abi.cls_sort_keys(kd.data_ptr(), vd.data_ptr(), ka.data_ptr(), va.data_ptr(),
