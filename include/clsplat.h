@@ -116,6 +116,7 @@ typedef struct ClsBatchInfo {
     int64_t total_pixels;  /* sum over views of W * H */
     int64_t total_g2;      /* sum over views of n_active(scene) */
     int64_t total_grad_rows; /* sum over scenes of n_active */
+    int64_t max_view_tiles;  /* largest tiles_x * tiles_y of a view */
 } ClsBatchInfo;
 
 /* Projected 2D record of one Gaussian in one view (48 bytes), written by
@@ -221,7 +222,7 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  * Tile rectangle: radius r = ceil(3 sqrt(lambda_max(Sigma'))), tiles
  * floor((u - r)/16) .. floor((u + r)/16) clamped to the grid (same for v).
  * records [total_records] ClsProjected. */
-#define CLS_DEPTH_BINS 64
+#define CLS_DEPTH_BINS 256
 size_t cls_project_workspace_size(const ClsBatchInfo* info);
 size_t cls_bin_offsets_size(const ClsBatchInfo* info); /* uint32 entries */
 int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
@@ -235,15 +236,21 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
 /* ------------------------------------------------------------------------
  * Per-tile depth sort of the bucketed layout (Supp. "Local Optimization
  * Kernel", item 1: per-tile depth order). Binning already did the most
- * significant radix pass (tile, then depth bin); this sorts every bucket by
- * its key, i.e. by depth, equal depths by record index, in shared memory, so
- * each tile's pairs end in (depth, index) order.
+ * significant radix pass (tile, then depth bin); this sorts every bucket with
+ * at least `min_bin` keys by its key, i.e. by depth, equal depths by record
+ * index, in shared memory. min_bin <= 1 sorts every bucket, so each tile's
+ * pairs end in (depth, index) order. A larger min_bin leaves the small buckets
+ * to cls_render_forward, which sorts them lazily (pass CLS_LAZY_MAX_BIN + 1).
  *   keys        [capacity] in/out, layout 1 of cls_project_and_bin
- *   keys_alt    [capacity] scratch (used only for bins above 4096 pairs)
+ *   keys_alt    [capacity] scratch (used only for buckets above 4096 pairs)
  *   bin_offsets as written by cls_project_and_bin
- *   work_counter device int32 scratch (reset by the call) */
+ *   work_counter device int32 scratch (reset by the call)
+ *   workspace   cls_sort_tiles_workspace_size(capacity, min_bin) bytes */
+#define CLS_LAZY_MAX_BIN 1024
+size_t cls_sort_tiles_workspace_size(int64_t capacity, int32_t min_bin);
 int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offsets,
-                   const int32_t* n_active_tiles_dev, int64_t total_tiles, int32_t* work_counter,
+                   const int32_t* n_active_tiles_dev, int64_t total_tiles, int64_t capacity,
+                   int32_t min_bin, int32_t* work_counter, void* workspace, size_t workspace_bytes,
                    cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
@@ -273,6 +280,13 @@ int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* 
  * T (1 - alpha) < 1e-4; C += colour alpha T; T *= 1 - alpha; C += T bg.
  * The record index of sorted pair i is vals[i * vals_stride]: vals_stride 1
  * with the flat layout's vals, 2 with the bucketed layout's keys (low words).
+ * Lazy sorting (bucketed layout, bin_offsets != NULL): the tile's depth bins
+ * are walked front to back; bins of at most CLS_LAZY_MAX_BIN keys are sorted
+ * here in shared memory (consecutive bins gathered up to 256 keys) and written
+ * back to lazy_keys, larger bins must already be sorted (cls_sort_tiles with
+ * min_bin = CLS_LAZY_MAX_BIN + 1); bins behind the depth at which every pixel
+ * of the tile stopped are left unsorted (the backward pass never reads them).
+ * vals/vals_stride are ignored in that mode.
  * Outputs at the view's pix_base (pixels of inactive tiles are not written):
  *   image      [3][H][W] per view (planar), may be NULL
  *   T_final    [H][W], n_contrib [H][W] (one past the last list position
@@ -286,11 +300,12 @@ int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* 
  * bg is a host array of 3 floats. */
 int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
                        const ClsProjected* records, const uint32_t* vals, int32_t vals_stride,
-                       const uint32_t* ranges,
-                       const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
-                       const float* bg, const float* target, int32_t loss_mode, float* image,
-                       float* T_final, int32_t* n_contrib, float* dL_dimage,
-                       float* loss_per_scene, int32_t* work_counter, cls_stream_t stream);
+                       const uint32_t* ranges, const int32_t* active_tiles,
+                       const int32_t* n_active_tiles_dev, uint64_t* lazy_keys,
+                       const uint32_t* bin_offsets, const float* bg, const float* target,
+                       int32_t loss_mode, float* image, float* T_final, int32_t* n_contrib,
+                       float* dL_dimage, float* loss_per_scene, int32_t* work_counter,
+                       cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Backward pass (Supp. "Local Optimization Kernel", items 2 and 3). Pixel

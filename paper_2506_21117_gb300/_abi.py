@@ -46,7 +46,8 @@ class ClsBatchInfo(C.Structure):
                 ("max_active", C.c_int32), ("max_row_stride", C.c_int32),
                 ("key_bits", C.c_int32), ("total_tiles", C.c_int64), ("total_sat", C.c_int64),
                 ("total_records", C.c_int64), ("total_pixels", C.c_int64),
-                ("total_g2", C.c_int64), ("total_grad_rows", C.c_int64)]
+                ("total_g2", C.c_int64), ("total_grad_rows", C.c_int64),
+                ("max_view_tiles", C.c_int64)]
 
 
 class ClsProjected(C.Structure):
@@ -74,10 +75,12 @@ SIGNATURES = {
     "cls_bin_offsets_size": (SZ, [P]),
     "cls_project_and_bin": (C.c_int, [P, P, P, I32, I32, P, P, P, P, P, P, I64, P, P, P, P, P,
                                       SZ, P]),
-    "cls_sort_tiles": (C.c_int, [P, P, P, P, I64, P, P]),
+    "cls_sort_tiles_workspace_size": (SZ, [I64, I32]),
+    "cls_sort_tiles": (C.c_int, [P, P, P, P, I64, I64, I32, P, P, SZ, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
     "cls_sort_keys": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, P]),
-    "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, I32, P, P, P, P, P, P, P]),
+    "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, I32, P, P, P, P, P,
+                                     P, P]),
     "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P]),
     "cls_adam_workspace_size": (SZ, [I32]),
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
@@ -177,10 +180,18 @@ def cls_project_and_bin(scenes_dev, views_dev, info, project_mode, layout, recor
                                       status_dev, workspace, workspace_bytes, stream)
 
 
-def cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles, work_counter,
-                   stream) -> int:
+LAZY_MAX_BIN = 1024
+
+
+def cls_sort_tiles_workspace_size(capacity, min_bin) -> int:
+    return load().cls_sort_tiles_workspace_size(capacity, min_bin)
+
+
+def cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles, capacity, min_bin,
+                   work_counter, workspace, workspace_bytes, stream) -> int:
     return load().cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles,
-                                 work_counter, stream)
+                                 capacity, min_bin, work_counter, workspace, workspace_bytes,
+                                 stream)
 
 
 def cls_sort_workspace_size(capacity, key_bits) -> int:
@@ -194,11 +205,13 @@ def cls_sort_keys(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bit
 
 
 def cls_render_forward(views_dev, info, records, vals, vals_stride, ranges, active_tiles,
-                       n_active_tiles_dev, bg, target, loss_mode, image, T_final, n_contrib,
-                       dL_dimage, loss_per_scene, work_counter, stream) -> int:
+                       n_active_tiles_dev, lazy_keys, bin_offsets, bg, target, loss_mode, image,
+                       T_final, n_contrib, dL_dimage, loss_per_scene, work_counter,
+                       stream) -> int:
     bg3 = (C.c_float * 3)(*bg)
     return load().cls_render_forward(views_dev, C.byref(info), records, vals, vals_stride, ranges,
-                                     active_tiles, n_active_tiles_dev, bg3, target, loss_mode,
+                                     active_tiles, n_active_tiles_dev, lazy_keys, bin_offsets,
+                                     bg3, target, loss_mode,
                                      image, T_final, n_contrib, dL_dimage, loss_per_scene,
                                      work_counter, stream)
 

@@ -56,6 +56,8 @@ extern "C" int cls_batch_prepare(ClsScene* scenes, int32_t n_scenes, ClsView* vi
         v.loss_scale = (float)(1.0 / (3.0 * (double)v.cam.width * (double)v.cam.height *
                                       (double)sc.n_views));
         tiles += (int64_t)v.tiles_x * v.tiles_y;
+        if ((int64_t)v.tiles_x * v.tiles_y > info->max_view_tiles)
+            info->max_view_tiles = (int64_t)v.tiles_x * v.tiles_y;
         sat += (int64_t)(v.tiles_x + 1) * (v.tiles_y + 1);
         recs += sc.n;
         pix += (int64_t)v.cam.width * v.cam.height;

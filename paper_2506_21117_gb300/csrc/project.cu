@@ -316,7 +316,8 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
                    const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
                    const int32_t* __restrict__ bins, int64_t total_sat,
                    const int64_t* __restrict__ partials, int64_t capacity,
-                   uint32_t* __restrict__ bin_offsets, uint32_t* __restrict__ ranges) {
+                   uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
+                   uint32_t* __restrict__ ranges) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     const int64_t ne = (int64_t)(*n_active) * kDepthBins;
     int64_t base = partials[blockIdx.x];
@@ -330,6 +331,7 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
             const uint32_t o = (uint32_t)(off < capacity ? off : capacity);
             const uint32_t o_end = (uint32_t)(off + c < capacity ? off + c : capacity);
             bin_offsets[e] = o;
+            cursor[e] = (int32_t)o;
             const int t = (int)(e / kDepthBins), b = (int)(e - (int64_t)t * kDepthBins);
             const int64_t tile = active_tiles[t];
             if (b == 0) ranges[2 * tile] = o;
@@ -357,9 +359,15 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
                   uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
                   uint4* __restrict__ big_list, int32_t* __restrict__ big_count) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
+    extern __shared__ int32_t s_rank[];  // bucketed: this view's tile ranks
     const ClsView& view = views[blockIdx.y];
     const int n = scenes[view.scene].n;
     int64_t base = LAYOUT == 0 ? offsets[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] : 0;
+    if (LAYOUT == 1) {
+        for (int i = threadIdx.x; i < view.tiles_x * view.tiles_y; i += kBinBlock)
+            s_rank[i] = tile_rank[view.tile_base + i];
+        __syncthreads();
+    }
     const uint32_t lo = LAYOUT == 1 ? zmin[blockIdx.y] : 0u;
     const uint32_t hi = LAYOUT == 1 ? zmax[blockIdx.y] : 0u;
     for (int it = 0; it < kBinItems; ++it) {
@@ -383,20 +391,27 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
                                         (uint32_t)(pos >> 32));
             continue;
         }
-        for (int ty = y0; ty <= y1; ++ty) {
-            const int64_t row = (int64_t)view.tile_base + (int64_t)ty * view.tiles_x;
-            for (int tx = x0; tx <= x1; ++tx) {
-                if (!tile_active[row + tx]) continue;
-                if (LAYOUT == 0) {
+        if (LAYOUT == 0) {
+            for (int ty = y0; ty <= y1; ++ty) {
+                const int64_t row = (int64_t)view.tile_base + (int64_t)ty * view.tiles_x;
+                for (int tx = x0; tx <= x1; ++tx) {
+                    if (!tile_active[row + tx]) continue;
                     if (pos < capacity) {
                         keys[pos] = ((uint64_t)(row + tx) << 32) | zb;
                         vals[pos] = rec;
                     }
                     ++pos;
-                } else {
-                    const int64_t sub = (int64_t)tile_rank[row + tx] * kDepthBins + bin;
-                    const int64_t p = (int64_t)bin_offsets[sub] + atomicAdd(cursor + sub, 1);
-                    if (p < capacity) keys[p] = ((uint64_t)zb << 32) | rec;
+                }
+            }
+        } else {
+            const uint64_t key = ((uint64_t)zb << 32) | rec;
+            for (int ty = y0; ty <= y1; ++ty) {
+                const int* rrow = s_rank + ty * view.tiles_x;
+                for (int tx = x0; tx <= x1; ++tx) {
+                    const int r = rrow[tx];
+                    if (r < 0) continue;
+                    const int64_t p = atomicAdd(cursor + (int64_t)r * kDepthBins + bin, 1);
+                    if (p < capacity) keys[p] = key;
                 }
             }
         }
@@ -445,7 +460,7 @@ emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restric
                 pos += __popc(m);
             } else if (on) {
                 const int64_t sub = (int64_t)tile_rank[tile] * kDepthBins + bin;
-                const int64_t p = (int64_t)bin_offsets[sub] + atomicAdd(cursor + sub, 1);
+                const int64_t p = atomicAdd(cursor + sub, 1);
                 if (p < capacity) keys[p] = ((uint64_t)zb << 32) | item.x;
             }
         }
@@ -491,6 +506,8 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
 
 }  // namespace
 
+static int g_max_view_tiles_checked = 0;
+
 extern "C" size_t cls_project_workspace_size(const ClsBatchInfo* info) {
     return info ? proj_layout(info).total : 0;
 }
@@ -533,6 +550,13 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     int32_t* big_count = reinterpret_cast<int32_t*>(ws + L.big_count);
     int32_t* bins = reinterpret_cast<int32_t*>(ws + L.bins);
     const int64_t subs = info->total_tiles * kDepthBins;
+    const int64_t max_view_tiles = info->max_view_tiles;
+    if (layout == 1 && g_max_view_tiles_checked == 0) {
+        cudaFuncSetAttribute(emit_pairs_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        g_max_view_tiles_checked = 1;
+    }
+    if (layout == 1 && max_view_tiles * 4 > 200 * 1024) return CLS_ERR_INVALID_ARG;
 
     if (project_mode == 0 && info->max_n > 0)
         project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
@@ -576,7 +600,6 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
         cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
         cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
-        cudaMemsetAsync(cursor, 0, (size_t)subs * 4, s);
         stamp_bins_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
                                                          zmin, zmax, bins, info->total_sat);
         bins_prefix_kernel<<<dim3(kDepthBins, V), 256, 0, s>>>(views_dev, bins, info->total_sat);
@@ -587,8 +610,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                 capacity, status_dev);
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
-            sub_partials, capacity, bin_offsets, ranges);
-        emit_pairs_kernel<1><<<rec_grid, kBinBlock, 0, s>>>(
+            sub_partials, capacity, bin_offsets, cursor, ranges);
+        emit_pairs_kernel<1><<<rec_grid, kBinBlock, (size_t)max_view_tiles * 4, s>>>(
             scenes_dev, views_dev, records, sat, tile_active, tile_rank, (int)cpv, nullptr, zmin,
             zmax, bin_offsets, cursor, keys, nullptr, capacity, big_list, big_count);
         emit_big_kernel<1><<<1024, 256, 0, s>>>(views_dev, records, tile_active, tile_rank, zmin,

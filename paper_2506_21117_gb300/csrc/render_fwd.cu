@@ -7,26 +7,79 @@
 
 namespace cls {
 
+constexpr int kLazyWin = kTilePixels;  // keys per rank-sorted window
+constexpr int kLazyMax = 1024;         // largest bin the renderer sorts itself
+constexpr int kBins = CLS_DEPTH_BINS;
+
+struct FwdSmem {
+    float4 a[kTilePixels];
+    float4 b[kTilePixels];
+    float c[kTilePixels];
+    uint64_t key[kLazyMax];
+    uint64_t sorted[kLazyMax];
+    uint32_t off[kBins + 1];
+    float red[kTilePixels / 32];
+    int tile;
+};
+
+// Per-thread compositing state of one pixel.
+struct PixelState {
+    float T, c0, c1, c2;
+    uint32_t last;
+    bool done;
+};
+
+__device__ __forceinline__ void stage_record(FwdSmem& sm, const ClsProjected* records, uint32_t rec) {
+    const float4* r = reinterpret_cast<const float4*>(records + rec);
+    sm.a[threadIdx.x] = r[0];
+    sm.b[threadIdx.x] = r[1];
+    sm.c[threadIdx.x] = r[2].x;
+}
+
+// Composite the nb staged records (list positions pos0 ..) into one pixel.
+__device__ __forceinline__ void composite_batch(const FwdSmem& sm, int nb, uint32_t pos0, float fx,
+                                                float fy, PixelState& ps) {
+    for (int k = 0; k < nb && !ps.done; ++k) {
+        const float4 a = sm.a[k];
+        const float4 bb = sm.b[k];
+        const float power = pair_power(fx - a.x, fy - a.y, a.z, a.w, bb.x);
+        if (power > 0.0f) continue;
+        const float alpha = fminf(kAlphaMax, bb.y * __expf(power));
+        if (alpha < kAlphaMin) continue;
+        const float test_T = ps.T * (1.0f - alpha);
+        if (test_T < kTMin) {
+            ps.done = true;
+            break;
+        }
+        const float w = alpha * ps.T;
+        ps.c0 += bb.z * w;
+        ps.c1 += bb.w * w;
+        ps.c2 += sm.c[k] * w;
+        ps.T = test_T;
+        ps.last = pos0 + k + 1;
+    }
+}
+
 __global__ void __launch_bounds__(kTilePixels)
 render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
-                  int vals_stride, const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
-                  const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
+                  int vals_stride, const uint32_t* __restrict__ ranges,
+                  const int32_t* __restrict__ active_tiles,
+                  const int32_t* __restrict__ n_active_tiles, uint64_t* __restrict__ lazy_keys,
+                  const uint32_t* __restrict__ bin_offsets, float bg0, float bg1, float bg2,
                   const float* __restrict__ target, int loss_mode, float* __restrict__ image,
                   float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
                   float* __restrict__ dL_dimage, float* __restrict__ loss_per_scene,
                   int* __restrict__ work_counter) {
-    __shared__ float4 s_a[kTilePixels];
-    __shared__ float4 s_b[kTilePixels];
-    __shared__ float s_c[kTilePixels];
-    __shared__ int s_tile;
-    __shared__ float s_red[kTilePixels / 32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smem_raw);
     const int n_tiles = *n_active_tiles;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const bool lazy = bin_offsets != nullptr;
     for (;;) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(work_counter, 1);
+        if (threadIdx.x == 0) sm.tile = atomicAdd(work_counter, 1);
         __syncthreads();
-        const int t = s_tile;
+        const int t = sm.tile;
         if (t >= n_tiles) break;
         const int tile = active_tiles[t];
         const int vi = view_of_tile(views, n_views, tile);
@@ -39,51 +92,67 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
         const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
         const uint32_t start = ranges[2 * (int64_t)tile], end = ranges[2 * (int64_t)tile + 1];
 
-        float T = 1.0f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-        uint32_t last = 0;
-        bool done = !inside;
-        for (uint32_t b = start; b < end; b += kTilePixels) {
-            if (__syncthreads_count(done) == kTilePixels) break;
-            const uint32_t idx = b + threadIdx.x;
-            if (idx < end) {
-                const float4* rec = reinterpret_cast<const float4*>(records + vals[(int64_t)idx * vals_stride]);
-                s_a[threadIdx.x] = rec[0];
-                s_b[threadIdx.x] = rec[1];
-                s_c[threadIdx.x] = rec[2].x;
+        PixelState ps{1.0f, 0.f, 0.f, 0.f, 0u, !inside};
+        if (!lazy) {
+            for (uint32_t b = start; b < end; b += kTilePixels) {
+                if (__syncthreads_count(ps.done) == kTilePixels) break;
+                const uint32_t idx = b + threadIdx.x;
+                if (idx < end) stage_record(sm, records, vals[(int64_t)idx * vals_stride]);
+                __syncthreads();
+                composite_batch(sm, (int)min((uint32_t)kTilePixels, end - b), b - start, fx, fy, ps);
             }
+        } else {
+            // Walk the tile's depth bins front to back. Consecutive bins up to
+            // kLazyWin keys (or one bin up to kLazyMax) are sorted here by rank
+            // counting on the unique (depth, index) keys, written back for the
+            // backward pass, and composited; bins behind the point where every
+            // pixel saturated are never sorted. Larger bins were sorted before.
+            for (int i = threadIdx.x; i <= kBins; i += kTilePixels)
+                sm.off[i] = bin_offsets[(int64_t)t * kBins + i];
             __syncthreads();
-            const int nb = (int)min((uint32_t)kTilePixels, end - b);
-            for (int k = 0; k < nb && !done; ++k) {
-                const float4 a = s_a[k];
-                const float4 bb = s_b[k];
-                const float power = pair_power(fx - a.x, fy - a.y, a.z, a.w, bb.x);
-                if (power > 0.0f) continue;
-                const float alpha = fminf(kAlphaMax, bb.y * __expf(power));
-                if (alpha < kAlphaMin) continue;
-                const float test_T = T * (1.0f - alpha);
-                if (test_T < kTMin) {
-                    done = true;
-                    break;
+            int bin = 0;
+            while (bin < kBins) {
+                if (__syncthreads_count(ps.done) == kTilePixels) break;
+                const uint32_t w0 = sm.off[bin];
+                int e = bin + 1;
+                while (e < kBins && sm.off[e + 1] - w0 <= (uint32_t)kLazyWin) ++e;
+                const int n = (int)(sm.off[e] - w0);
+                bin = e;
+                if (n == 0) continue;
+                const bool here = n <= kLazyMax;
+                if (here) {
+                    for (int i = threadIdx.x; i < n; i += kTilePixels) sm.key[i] = lazy_keys[w0 + i];
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < n; i += kTilePixels) {
+                        const uint64_t k = sm.key[i];
+                        int r = 0;
+                        for (int j = 0; j < n; ++j) r += sm.key[j] < k;
+                        sm.sorted[r] = k;
+                    }
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < n; i += kTilePixels) lazy_keys[w0 + i] = sm.sorted[i];
                 }
-                const float w = alpha * T;
-                c0 += bb.z * w;
-                c1 += bb.w * w;
-                c2 += s_c[k] * w;
-                T = test_T;
-                last = b - start + k + 1;
+                for (int c0 = 0; c0 < n; c0 += kTilePixels) {
+                    if (c0 > 0 && __syncthreads_count(ps.done) == kTilePixels) break;
+                    const int idx = c0 + threadIdx.x;
+                    if (idx < n)
+                        stage_record(sm, records,
+                                     (uint32_t)(here ? sm.sorted[idx] : lazy_keys[w0 + idx]));
+                    __syncthreads();
+                    composite_batch(sm, min(kTilePixels, n - c0), w0 - start + c0, fx, fy, ps);
+                    __syncthreads();
+                }
             }
         }
 
         float lsum = 0.0f;
         if (inside) {
-            c0 += T * bg0;
-            c1 += T * bg1;
-            c2 += T * bg2;
+            const float c0 = ps.c0 + ps.T * bg0, c1 = ps.c1 + ps.T * bg1, c2 = ps.c2 + ps.T * bg2;
             const int64_t pix = view.pix_base + (int64_t)py * W + px;
             const int64_t plane = (int64_t)W * H;
             const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
-            T_final[pix] = T;
-            n_contrib[pix] = (int32_t)last;
+            T_final[pix] = ps.T;
+            n_contrib[pix] = (int32_t)ps.last;
             if (image) {
                 image[p3] = c0;
                 image[p3 + plane] = c1;
@@ -111,11 +180,11 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
         }
         if (loss_mode != 0 && loss_per_scene) {
             for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-            if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = lsum;
+            if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = lsum;
             __syncthreads();
             if (threadIdx.x == 0) {
                 float tot = 0.f;
-                for (int w = 0; w < kTilePixels / 32; ++w) tot += s_red[w];
+                for (int w = 0; w < kTilePixels / 32; ++w) tot += sm.red[w];
                 atomicAdd(loss_per_scene + view.scene, tot);
             }
         }
@@ -132,12 +201,15 @@ using namespace cls;
 extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
                                   const ClsProjected* records, const uint32_t* vals,
                                   int32_t vals_stride, const uint32_t* ranges, const int32_t* active_tiles,
-                                  const int32_t* n_active_tiles_dev, const float* bg,
+                                  const int32_t* n_active_tiles_dev, uint64_t* lazy_keys,
+                                  const uint32_t* bin_offsets, const float* bg,
                                   const float* target, int32_t loss_mode, float* image,
                                   float* T_final, int32_t* n_contrib, float* dL_dimage,
                                   float* loss_per_scene, int32_t* work_counter,
                                   cls_stream_t stream) {
-    if (!views_dev || !info || !records || !vals || (vals_stride != 1 && vals_stride != 2) || !ranges || !active_tiles || !n_active_tiles_dev ||
+    if (!views_dev || !info || !records ||
+        (bin_offsets ? !lazy_keys : (!vals || (vals_stride != 1 && vals_stride != 2))) ||
+        !ranges || !active_tiles || !n_active_tiles_dev ||
         !bg || !T_final || !n_contrib || !work_counter || loss_mode < 0 || loss_mode > 2 ||
         (loss_mode != 0 && (!target || !dL_dimage)) || info->n_views <= 0 ||
         info->total_tiles <= 0)
@@ -147,13 +219,17 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel, kTilePixels, 0);
+        cudaFuncSetAttribute(render_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(FwdSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel, kTilePixels,
+                                                      sizeof(FwdSmem));
         g_fwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     const int blocks = (int)hmin64(info->total_tiles, g_fwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
-    render_fwd_kernel<<<blocks, kTilePixels, 0, s>>>(
-        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, bg[0],
+    render_fwd_kernel<<<blocks, kTilePixels, sizeof(FwdSmem), s>>>(
+        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
+        n_active_tiles_dev, lazy_keys, bin_offsets, bg[0],
         bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
         work_counter);
     CLS_CHECK_LAUNCH();

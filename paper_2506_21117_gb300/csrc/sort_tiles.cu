@@ -234,17 +234,62 @@ sort_tiles_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
     }
 }
 
+// Bins holding at least `min_bin` keys (the renderer sorts smaller ones).
+__global__ void collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
+                                    const int32_t* __restrict__ n_active, int min_bin,
+                                    uint2* __restrict__ list, int32_t* __restrict__ count,
+                                    int64_t list_cap) {
+    const int64_t ne = (int64_t)(*n_active) * kBinsPerTile;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = bin_offsets[e], n = bin_offsets[e + 1] - a;
+        if (n >= (uint32_t)min_bin) {
+            const int slot = atomicAdd(count, 1);
+            if (slot < list_cap) list[slot] = make_uint2(a, n);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTB)
+sort_bins_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
+                 const uint2* __restrict__ list, const int32_t* __restrict__ count,
+                 int64_t list_cap, int* __restrict__ work_counter) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSortSmem& sm = *reinterpret_cast<TileSortSmem*>(smem_raw);
+    const int64_t n_items = min((int64_t)*count, list_cap);
+    for (;;) {
+        if (threadIdx.x == 0) sm.tile = atomicAdd(work_counter, 1);
+        __syncthreads();
+        const int t = sm.tile;
+        if (t >= n_items) break;
+        const uint2 it = list[t];
+        if (it.y > (uint32_t)kCap) sort_big(sm, keys, alt, it.x, it.y);
+        else sort_window(sm, keys, it.x, (int)it.y);
+        __syncthreads();
+    }
+}
+
 static int g_tiles_blocks = 0;
 
 }  // namespace cls
 
 using namespace cls;
 
+static int64_t list_cap_for(int64_t capacity, int32_t min_bin) {
+    return min_bin <= 1 ? 0 : capacity / min_bin + 1;
+}
+
+extern "C" size_t cls_sort_tiles_workspace_size(int64_t capacity, int32_t min_bin) {
+    return (size_t)(256 + list_cap_for(capacity, min_bin) * sizeof(uint2) + 255) / 256 * 256;
+}
+
 extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offsets,
                               const int32_t* n_active_tiles_dev, int64_t total_tiles,
-                              int32_t* work_counter, cls_stream_t stream) {
+                              int64_t capacity, int32_t min_bin, int32_t* work_counter,
+                              void* workspace, size_t workspace_bytes, cls_stream_t stream) {
     if (!keys || !keys_alt || !bin_offsets || !n_active_tiles_dev || !work_counter ||
-        total_tiles <= 0)
+        total_tiles <= 0 || capacity < 0 || !workspace ||
+        workspace_bytes < cls_sort_tiles_workspace_size(capacity, min_bin))
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     if (g_tiles_blocks == 0) {
@@ -253,13 +298,26 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(sort_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSortSmem));
+        cudaFuncSetAttribute(sort_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(TileSortSmem));
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_tiles_kernel, kTB,
                                                       sizeof(TileSortSmem));
         g_tiles_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
-    sort_tiles_kernel<<<(int)hmin64(total_tiles, g_tiles_blocks), kTB, sizeof(TileSortSmem), s>>>(
-        keys, keys_alt, bin_offsets, n_active_tiles_dev, work_counter);
+    if (min_bin <= 1) {
+        sort_tiles_kernel<<<(int)hmin64(total_tiles, g_tiles_blocks), kTB, sizeof(TileSortSmem),
+                            s>>>(keys, keys_alt, bin_offsets, n_active_tiles_dev, work_counter);
+    } else {
+        int32_t* count = static_cast<int32_t*>(workspace);
+        uint2* list = reinterpret_cast<uint2*>(static_cast<char*>(workspace) + 256);
+        const int64_t cap = list_cap_for(capacity, min_bin);
+        cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+        collect_bins_kernel<<<1024, 256, 0, s>>>(bin_offsets, n_active_tiles_dev, min_bin, list,
+                                                 count, cap);
+        sort_bins_kernel<<<g_tiles_blocks, kTB, sizeof(TileSortSmem), s>>>(keys, keys_alt, list,
+                                                                          count, cap, work_counter);
+    }
     CLS_CHECK_LAUNCH();
     return CLS_OK;
 }

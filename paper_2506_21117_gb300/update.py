@@ -102,12 +102,15 @@ class Batch:
     """Scene/view tables of one launch batch and every buffer the hot path uses."""
 
     def __init__(self, scenes: Sequence[SceneState], cams_per_scene: Sequence[Sequence],
-                 device="cuda", layout: int = 1):
-        """layout 1: pairs bucketed by (tile, depth bin), sorted per tile in
-        shared memory (cls_sort_tiles); layout 0: flat (tile, depth) keys sorted
-        by the global onesweep radix sort (cls_sort_keys)."""
+                 device="cuda", layout: int = 1, lazy: bool = True):
+        """layout 1: pairs bucketed by (tile, depth bin); with `lazy` the
+        renderer sorts the depth bins it reaches (cls_sort_tiles only pre-sorts
+        bins above CLS_LAZY_MAX_BIN keys), otherwise cls_sort_tiles sorts every
+        bin. layout 0: flat (tile, depth) keys sorted by the global onesweep
+        radix sort (cls_sort_keys)."""
         self.device = device
         self.layout = layout
+        self.lazy = lazy and layout == 1
         self.scenes = list(scenes)
         S = len(scenes)
         views = []
@@ -215,18 +218,25 @@ class Batch:
         self.capacity = capacity
         self.keys = torch.empty(capacity, dtype=torch.int64, device=dev)
         self.keys_alt = torch.empty(capacity, dtype=torch.int64, device=dev)
+        self.tiles_ws = torch.empty(
+            max(abi.cls_sort_tiles_workspace_size(capacity, self.min_bin()), 256),
+            dtype=torch.uint8, device=dev)
         if self.layout == 0:
             self.vals = torch.empty(capacity, dtype=torch.int32, device=dev)
             self.vals_alt = torch.empty(capacity, dtype=torch.int32, device=dev)
             self.sort_ws = torch.empty(abi.cls_sort_workspace_size(capacity, self.info.key_bits),
                                        dtype=torch.uint8, device=dev)
 
+    def min_bin(self) -> int:
+        return abi.LAZY_MAX_BIN + 1 if self.lazy else 1
+
     def sort(self):
         b = self
         if b.layout == 1:
             abi.check(abi.cls_sort_tiles(_ptr(b.keys), _ptr(b.keys_alt), _ptr(b.bin_offsets),
-                                         _ptr(b.n_active_tiles), b.info.total_tiles,
-                                         _ptr(b.counter) + 8, b.stream()), "cls_sort_tiles")
+                                         _ptr(b.n_active_tiles), b.info.total_tiles, b.capacity,
+                                         b.min_bin(), _ptr(b.counter) + 8, _ptr(b.tiles_ws),
+                                         b.tiles_ws.numel(), b.stream()), "cls_sort_tiles")
             return
         abi.check(abi.cls_sort_keys(
             _ptr(b.keys), _ptr(b.vals), _ptr(b.keys_alt), _ptr(b.vals_alt), _ptr(b.n_pairs),
@@ -239,7 +249,8 @@ class Batch:
             b.loss.zero_()
         abi.check(abi.cls_render_forward(
             _ptr(b.views_dev), b.info, _ptr(b.records), *b._sorted_vals(), _ptr(b.ranges),
-            _ptr(b.active_tiles), _ptr(b.n_active_tiles), bg,
+            _ptr(b.active_tiles), _ptr(b.n_active_tiles),
+            _ptr(b.keys) if b.lazy else None, _ptr(b.bin_offsets) if b.lazy else None, bg,
             _ptr(b.target) if loss_mode else None, loss_mode,
             _ptr(b.image) if write_image else None, _ptr(b.T_final), _ptr(b.n_contrib),
             _ptr(b.dL_dimage) if loss_mode else None, _ptr(b.loss) if loss_mode else None,
@@ -283,7 +294,7 @@ class Batch:
         active = 2 if self.info.max_active > 0 else 0
         proj = active + 3 + (7 if self.layout == 1 else 3)
         if self.layout == 1:
-            sort = 1
+            sort = 2 if self.lazy else 1
         else:
             passes = -(-self.info.key_bits // 8)
             sort = 3 + passes + passes % 2
@@ -342,7 +353,7 @@ class LocalUpdate:
     def __init__(self, scene, cams, sh_degree: int, targets=None, masks=None, active=None,
                  vote_mode: int = 0, loss: str = "l1", lr: float = 1e-3,
                  bg=(0.0, 0.0, 0.0), device="cuda", capacity_slack: float = 1.5,
-                 layout: int = 1):
+                 layout: int = 1, lazy: bool = True):
         self.cams = list(cams)
         self.loss_mode = LOSS_MODES[loss]
         self.lr = lr
@@ -354,7 +365,7 @@ class LocalUpdate:
             lift(self.state, self.cams, masks, vote_mode, device)
         else:
             raise ValueError("give either an active set or change masks")
-        self.batch = Batch([self.state], [self.cams], device, layout)
+        self.batch = Batch([self.state], [self.cams], device, layout, lazy)
         if targets is not None:
             self.batch.set_targets(targets)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
@@ -363,7 +374,7 @@ class LocalUpdate:
     @classmethod
     def from_resident(cls, state: SceneState, cams, targets, masks, vote_mode: int = 0,
                       loss: str = "l1", lr: float = 1e-3, bg=(0.0, 0.0, 0.0),
-                      capacity_slack: float = 1.5, layout: int = 1):
+                      capacity_slack: float = 1.5, layout: int = 1, lazy: bool = True):
         """A new update of a scene already resident on the device. `targets`
         (float32, [3][H][W] per view, concatenated) and `masks` (uint8, [H][W]
         per view, concatenated) are flat tensors, typically pinned host memory;
@@ -376,7 +387,7 @@ class LocalUpdate:
         self.state = state
         dev = state.params.device
         lift(state, self.cams, masks, vote_mode, dev)
-        self.batch = Batch([state], [self.cams], dev, layout)
+        self.batch = Batch([state], [self.cams], dev, layout, lazy)
         self.batch.target = targets.to(dev, non_blocking=True)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
         return self

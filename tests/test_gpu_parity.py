@@ -35,10 +35,11 @@ def _built():
     build.build()
 
 
-def _update(scene, cams, deg, targets=None, active=None, loss="l1", masks=None, layout=1):
+def _update(scene, cams, deg, targets=None, active=None, loss="l1", masks=None, layout=1,
+            lazy=True):
     from paper_2506_21117_gb300.update import LocalUpdate
     lu = LocalUpdate(scene, cams, deg, targets=targets, active=active, loss=loss, masks=masks,
-                     layout=layout)
+                     layout=layout, lazy=lazy)
     lu.render_pass(with_backward=targets is not None, with_adam=False)
     torch.cuda.synchronize()
     lu.batch.check_status()
@@ -107,9 +108,21 @@ def _compare_grads(lu, ref, active, deg, exclude=()):
 
 # ---------------------------------------------------------------- indexing --
 
-@pytest.mark.parametrize("layout", [0, 1])
+def _tile_max_contrib(lu, cams):
+    """Per global tile id, the largest n_contrib of its pixels."""
+    out = []
+    for (base, H, W), cam in zip(lu.batch.view_slices(), cams):
+        nc = lu.batch.n_contrib[base:base + H * W].view(H, W).cpu().numpy()
+        Tx, Ty = fx.tiles_of(cam)
+        pad = np.zeros((Ty * 16, Tx * 16), np.int64)
+        pad[:H, :W] = nc
+        out.append(pad.reshape(Ty, 16, Tx, 16).max(axis=(1, 3)).ravel())
+    return np.concatenate(out)
+
+
+@pytest.mark.parametrize("layout,lazy", [(0, False), (1, False), (1, True)])
 @pytest.mark.parametrize("case", ["plain", "local", "large_radii"])
-def test_projection_and_tile_lists_bit_exact(case, layout):
+def test_projection_and_tile_lists_bit_exact(case, layout, lazy):
     if case == "plain":
         scene, cams, targets = S.workload_plain()
         deg, active = 0, np.ones(2000, bool)
@@ -126,7 +139,7 @@ def test_projection_and_tile_lists_bit_exact(case, layout):
         cams = S.ring_cameras(2, 4.0, 300, 200, angles=[0.3, 2.0])
         deg = 1
         active = np.random.default_rng(21).uniform(size=20000) < 0.02
-    lu = _update(scene, cams, deg, active=active, layout=layout)
+    lu = _update(scene, cams, deg, active=active, layout=layout, lazy=lazy)
     rec, reci = _records(lu)
     projs, masks_o, sk, sv, rng = _oracle_index(scene, cams, active)
     n = scene["means"].shape[0]
@@ -145,9 +158,22 @@ def test_projection_and_tile_lists_bit_exact(case, layout):
     assert np.array_equal(lu.batch.active_tiles[:nt].cpu().numpy(), np.flatnonzero(tile_mask))
     keys, vals, ranges = _gpu_pairs(lu)
     assert keys.size == sk.size > 0
-    assert np.array_equal(keys, sk)
-    assert np.array_equal(vals, sv)
     assert np.array_equal(ranges, rng)
+    if not lazy:
+        assert np.array_equal(keys, sk)
+        assert np.array_equal(vals, sv)
+        return
+    # lazy sorting: every tile is sorted up to the deepest position a pixel used
+    used = _tile_max_contrib(lu, cams)
+    checked = 0
+    for t in np.flatnonzero(tile_mask):
+        a, e = rng[t]
+        m = a + used[t]
+        assert np.array_equal(keys[a:m], sk[a:m]) and np.array_equal(vals[a:m], sv[a:m]), t
+        # the rest of the tile holds the same pairs, possibly unsorted
+        assert np.array_equal(np.sort(keys[m:e]), sk[m:e])
+        checked += used[t]
+    assert checked > 0
 
 
 def test_votes_bit_exact():
