@@ -20,11 +20,80 @@ namespace cls {
 constexpr int kSub = 32;      // list entries reduced per shared-memory flush
 constexpr int kGradComps = 9; // du dv dA dB dC dopacity dr dg db
 constexpr int kG2Stride = 12;
+constexpr int kBwdThreads = kTilePixels / 2;  // two pixels per thread: rows ly and ly + 8
+constexpr int kBwdWarps = kBwdThreads / 32;
 
-__global__ void __launch_bounds__(kTilePixels)
+// Reverse-walk state of one pixel.
+struct BwdPixel {
+    float fx, fy;
+    float T, g0, g1, g2, S0, S1, S2;
+    int last;
+    bool inside;
+};
+
+// One list entry at one pixel: recover T in front of the entry, update the
+// colour behind, and (if `active`) add the entry's 2D gradient to gr[].
+__device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, const float4& a, const float4& bb,
+                                          float cb, bool active, float* gr) {
+    if (!(p.inside && pos < p.last)) return false;
+    const float dx = p.fx - a.x, dy = p.fy - a.y;
+    const float power = pair_power(dx, dy, a.z, a.w, bb.x);
+    if (power > 0.0f) return false;
+    const float G = __expf(power);
+    const float alpha = fminf(kAlphaMax, bb.y * G);
+    if (alpha < kAlphaMin) return false;
+    const float inv_om = __fdividef(1.0f, 1.0f - alpha);
+    p.T *= inv_om;
+    const float w = alpha * p.T;
+    if (active) {
+        const float dLda = p.g0 * (bb.z * p.T - p.S0 * inv_om) +
+                           p.g1 * (bb.w * p.T - p.S1 * inv_om) +
+                           p.g2 * (cb * p.T - p.S2 * inv_om);
+        const bool clamped = bb.y * G > kAlphaMax;
+        const float dpow = clamped ? 0.f : dLda * alpha;
+        gr[0] += dpow * (a.z * dx + a.w * dy);
+        gr[1] += dpow * (bb.x * dy + a.w * dx);
+        gr[2] += -0.5f * dx * dx * dpow;
+        gr[3] += -dx * dy * dpow;
+        gr[4] += -0.5f * dy * dy * dpow;
+        gr[5] += clamped ? 0.f : dLda * G;
+        gr[6] += w * p.g0;
+        gr[7] += w * p.g1;
+        gr[8] += w * p.g2;
+    }
+    p.S0 += bb.z * w;
+    p.S1 += bb.w * w;
+    p.S2 += cb * w;
+    return true;
+}
+
+__device__ __forceinline__ void bwd_load_pixel(BwdPixel& p, const ClsView& view, int px, int py,
+                                               float bg0, float bg1, float bg2,
+                                               const float* T_final, const int32_t* n_contrib,
+                                               const float* dL_dimage) {
+    const int W = view.cam.width, H = view.cam.height;
+    p.inside = px < W && py < H;
+    p.fx = (float)px + 0.5f;
+    p.fy = (float)py + 0.5f;
+    p.T = 1.0f; p.g0 = p.g1 = p.g2 = 0.f; p.last = 0;
+    if (p.inside) {
+        const int64_t pix = view.pix_base + (int64_t)py * W + px;
+        const int64_t plane = (int64_t)W * H;
+        const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
+        p.T = T_final[pix];
+        p.last = n_contrib[pix];
+        p.g0 = dL_dimage[p3];
+        p.g1 = dL_dimage[p3 + plane];
+        p.g2 = dL_dimage[p3 + 2 * plane];
+    }
+    p.S0 = p.T * bg0; p.S1 = p.T * bg1; p.S2 = p.T * bg2;
+}
+
+__global__ void __launch_bounds__(kBwdThreads)
 render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
-                  int vals_stride, const uint32_t* __restrict__ ranges, const int32_t* __restrict__ active_tiles,
+                  int vals_stride, const uint32_t* __restrict__ ranges,
+                  const int32_t* __restrict__ active_tiles,
                   const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
                   const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib,
                   const float* __restrict__ dL_dimage, float* __restrict__ grad2d,
@@ -33,12 +102,12 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
     __shared__ float4 s_b[kTilePixels];
     __shared__ float s_c[kTilePixels];
     __shared__ int s_slot[kTilePixels];
-    __shared__ float s_g[kSub][kTilePixels / 32][kGradComps + 1];
+    __shared__ float s_g[kSub][kBwdWarps][kGradComps + 1];
     __shared__ int s_tile;
     __shared__ int s_maxlast;
     const int n_tiles = *n_active_tiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, 8)
     for (;;) {
         if (threadIdx.x == 0) {
             s_tile = atomicAdd(work_counter, 1);
@@ -51,96 +120,46 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
         const ClsView& view = views[view_of_tile(views, n_views, tile)];
         const int local = tile - view.tile_base;
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
-        const int W = view.cam.width, H = view.cam.height;
-        const int px = tx * kTile + lx, py = ty * kTile + ly;
-        const bool inside = px < W && py < H;
-        const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
         const uint32_t start = ranges[2 * (int64_t)tile];
-
-        float T = 1.0f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-        int last = 0;
-        if (inside) {
-            const int64_t pix = view.pix_base + (int64_t)py * W + px;
-            const int64_t plane = (int64_t)W * H;
-            const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
-            T = T_final[pix];
-            last = n_contrib[pix];
-            g0 = dL_dimage[p3];
-            g1 = dL_dimage[p3 + plane];
-            g2 = dL_dimage[p3 + 2 * plane];
-            atomicMax(&s_maxlast, last);
-        }
-        float S0 = T * bg0, S1 = T * bg1, S2 = T * bg2;  // colour behind
+        BwdPixel p0, p1;
+        bwd_load_pixel(p0, view, tx * kTile + lx, ty * kTile + ly, bg0, bg1, bg2, T_final,
+                       n_contrib, dL_dimage);
+        bwd_load_pixel(p1, view, tx * kTile + lx, ty * kTile + ly + 8, bg0, bg1, bg2, T_final,
+                       n_contrib, dL_dimage);
+        const int my_last = max(p0.last, p1.last);
+        if (my_last > 0) atomicMax(&s_maxlast, my_last);
         __syncthreads();
         const int max_last = s_maxlast;
 
         for (int hi = max_last; hi > 0; hi -= kTilePixels) {
             const int lo = hi > kTilePixels ? hi - kTilePixels : 0;
             const int nb = hi - lo;
-            if ((int)threadIdx.x < nb) {
-                const float4* rec =
-                    reinterpret_cast<const float4*>(records + vals[(int64_t)(start + lo + threadIdx.x) * vals_stride]);
-                s_a[threadIdx.x] = rec[0];
-                s_b[threadIdx.x] = rec[1];
+            for (int i = threadIdx.x; i < nb; i += kBwdThreads) {
+                const float4* rec = reinterpret_cast<const float4*>(
+                    records + vals[(int64_t)(start + lo + i) * vals_stride]);
+                s_a[i] = rec[0];
+                s_b[i] = rec[1];
                 const float4 c = rec[2];
-                s_c[threadIdx.x] = c.x;
-                s_slot[threadIdx.x] = __float_as_int(c.y);
+                s_c[i] = c.x;
+                s_slot[i] = __float_as_int(c.y);
             }
             __syncthreads();
             for (int kk = nb - 1; kk >= 0; kk -= kSub) {
                 const int sub_lo = kk >= kSub - 1 ? kk - (kSub - 1) : 0;
                 bool any_active = false;
                 for (int k = kk; k >= sub_lo; --k) {
-                    const int pos = lo + k;
                     const float4 a = s_a[k];
                     const float4 bb = s_b[k];
-                    const float dx = fx - a.x, dy = fy - a.y;
-                    bool contrib = inside && pos < last;
-                    float alpha = 0.f, G = 0.f, power = 0.f;
-                    if (contrib) {
-                        power = pair_power(dx, dy, a.z, a.w, bb.x);
-                        contrib = power <= 0.0f;
-                        if (contrib) {
-                            G = __expf(power);
-                            alpha = fminf(kAlphaMax, bb.y * G);
-                            contrib = alpha >= kAlphaMin;
-                        }
-                    }
-                    const float cr = bb.z, cg = bb.w, cb = s_c[k];
-                    const bool active = s_slot[k] >= 0;
+                    const float cb = s_c[k];
+                    const bool active = s_slot[k] >= 0;  // uniform over the block
                     float gr[kGradComps];
-                    if (contrib) {
-                        const float om = 1.0f - alpha;
-                        T = T / om;
-                        const float w = alpha * T;
-                        if (active) {
-                            const float inv_om = 1.0f / om;
-                            const float dLda = g0 * (cr * T - S0 * inv_om) +
-                                               g1 * (cg * T - S1 * inv_om) +
-                                               g2 * (cb * T - S2 * inv_om);
-                            const bool clamped = bb.y * G > kAlphaMax;
-                            const float dpow = clamped ? 0.f : dLda * alpha;
-                            gr[0] = dpow * (a.z * dx + a.w * dy);
-                            gr[1] = dpow * (bb.x * dy + a.w * dx);
-                            gr[2] = -0.5f * dx * dx * dpow;
-                            gr[3] = -dx * dy * dpow;
-                            gr[4] = -0.5f * dy * dy * dpow;
-                            gr[5] = clamped ? 0.f : dLda * G;
-                            gr[6] = w * g0;
-                            gr[7] = w * g1;
-                            gr[8] = w * g2;
-                        }
-                        S0 += cr * w;
-                        S1 += cg * w;
-                        S2 += cb * w;
-                    }
-                    if (active) {  // uniform over the block
-                        any_active = true;
-                        if (!(contrib)) {
 #pragma unroll
-                            for (int c = 0; c < kGradComps; ++c) gr[c] = 0.f;
-                        }
-                        if (__any_sync(0xffffffffu, contrib)) {
+                    for (int c = 0; c < kGradComps; ++c) gr[c] = 0.f;
+                    const bool c0 = bwd_entry(p0, lo + k, a, bb, cb, active, gr);
+                    const bool c1 = bwd_entry(p1, lo + k, a, bb, cb, active, gr);
+                    if (active) {
+                        any_active = true;
+                        if (__any_sync(0xffffffffu, c0 || c1)) {
 #pragma unroll
                             for (int c = 0; c < kGradComps; ++c) {
                                 float x = gr[c];
@@ -159,13 +178,13 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                 if (any_active) {  // uniform over the block
                     __syncthreads();
                     const int cnt = kk - sub_lo + 1;
-                    for (int e = threadIdx.x; e < cnt * kGradComps; e += kTilePixels) {
+                    for (int e = threadIdx.x; e < cnt * kGradComps; e += kBwdThreads) {
                         const int ent = e / kGradComps, comp = e - ent * kGradComps;
                         const int slot = s_slot[sub_lo + ent];
                         if (slot < 0) continue;
                         float sum = 0.f;
 #pragma unroll
-                        for (int w = 0; w < kTilePixels / 32; ++w) sum += s_g[ent][w][comp];
+                        for (int w = 0; w < kBwdWarps; ++w) sum += s_g[ent][w][comp];
                         if (sum != 0.f) atomicAdd(grad2d + (int64_t)slot * kG2Stride + comp, sum);
                     }
                     __syncthreads();
@@ -410,12 +429,12 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel, kTilePixels, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel, kBwdThreads, 0);
         g_bwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     const int blocks = (int)hmin64(info->total_tiles, g_bwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
-    render_bwd_kernel<<<blocks, kTilePixels, 0, s>>>(
+    render_bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(
         views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, bg[0],
         bg[1], bg[2], T_final, n_contrib, dL_dimage, grad2d, work_counter);
     if (info->max_active > 0 && info->total_grad_rows > 0) {

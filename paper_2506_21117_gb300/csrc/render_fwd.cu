@@ -7,6 +7,7 @@
 
 namespace cls {
 
+constexpr int kFwdThreads = kTilePixels / 2;  // two pixels per thread: rows ly and ly + 8
 constexpr int kLazyWin = kTilePixels;  // keys per rank-sorted window
 constexpr int kLazyMax = 1024;         // largest bin the renderer sorts itself
 constexpr int kBins = CLS_DEPTH_BINS;
@@ -18,7 +19,7 @@ struct FwdSmem {
     uint64_t key[kLazyMax];
     uint64_t sorted[kLazyMax];
     uint32_t off[kBins + 1];
-    float red[kTilePixels / 32];
+    float red[kFwdThreads / 32];
     int tile;
 };
 
@@ -29,38 +30,87 @@ struct PixelState {
     bool done;
 };
 
-__device__ __forceinline__ void stage_record(FwdSmem& sm, const ClsProjected* records, uint32_t rec) {
+__device__ __forceinline__ void stage_record(FwdSmem& sm, int i, const ClsProjected* records,
+                                             uint32_t rec) {
     const float4* r = reinterpret_cast<const float4*>(records + rec);
-    sm.a[threadIdx.x] = r[0];
-    sm.b[threadIdx.x] = r[1];
-    sm.c[threadIdx.x] = r[2].x;
+    sm.a[i] = r[0];
+    sm.b[i] = r[1];
+    sm.c[i] = r[2].x;
 }
 
-// Composite the nb staged records (list positions pos0 ..) into one pixel.
+__device__ __forceinline__ void composite_one(const float4& a, const float4& bb, float cb,
+                                              uint32_t pos, float fx, float fy, PixelState& ps) {
+    if (ps.done) return;
+    const float power = pair_power(fx - a.x, fy - a.y, a.z, a.w, bb.x);
+    if (power > 0.0f) return;
+    const float alpha = fminf(kAlphaMax, bb.y * __expf(power));
+    if (alpha < kAlphaMin) return;
+    const float test_T = ps.T * (1.0f - alpha);
+    if (test_T < kTMin) {
+        ps.done = true;
+        return;
+    }
+    const float w = alpha * ps.T;
+    ps.c0 += bb.z * w;
+    ps.c1 += bb.w * w;
+    ps.c2 += cb * w;
+    ps.T = test_T;
+    ps.last = pos + 1;
+}
+
+// Composite the nb staged records (list positions pos0 ..) into two pixels.
 __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int nb, uint32_t pos0, float fx,
-                                                float fy, PixelState& ps) {
-    for (int k = 0; k < nb && !ps.done; ++k) {
+                                                float fy0, float fy1, PixelState& p0,
+                                                PixelState& p1) {
+    for (int k = 0; k < nb && !(p0.done && p1.done); ++k) {
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
-        const float power = pair_power(fx - a.x, fy - a.y, a.z, a.w, bb.x);
-        if (power > 0.0f) continue;
-        const float alpha = fminf(kAlphaMax, bb.y * __expf(power));
-        if (alpha < kAlphaMin) continue;
-        const float test_T = ps.T * (1.0f - alpha);
-        if (test_T < kTMin) {
-            ps.done = true;
-            break;
-        }
-        const float w = alpha * ps.T;
-        ps.c0 += bb.z * w;
-        ps.c1 += bb.w * w;
-        ps.c2 += sm.c[k] * w;
-        ps.T = test_T;
-        ps.last = pos0 + k + 1;
+        const float cb = sm.c[k];
+        composite_one(a, bb, cb, pos0 + k, fx, fy0, p0);
+        composite_one(a, bb, cb, pos0 + k, fx, fy1, p1);
     }
 }
 
-__global__ void __launch_bounds__(kTilePixels)
+__device__ __forceinline__ void finish_pixel(const PixelState& ps, const ClsView& view, int px,
+                                             int py, float bg0, float bg1, float bg2,
+                                             const float* target, int loss_mode, float* image,
+                                             float* T_final, int32_t* n_contrib, float* dL_dimage,
+                                             float& lsum) {
+    const int W = view.cam.width, H = view.cam.height;
+    if (!(px < W && py < H)) return;
+    const float c0 = ps.c0 + ps.T * bg0, c1 = ps.c1 + ps.T * bg1, c2 = ps.c2 + ps.T * bg2;
+    const int64_t pix = view.pix_base + (int64_t)py * W + px;
+    const int64_t plane = (int64_t)W * H;
+    const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
+    T_final[pix] = ps.T;
+    n_contrib[pix] = (int32_t)ps.last;
+    if (image) {
+        image[p3] = c0;
+        image[p3 + plane] = c1;
+        image[p3 + 2 * plane] = c2;
+    }
+    if (loss_mode != 0) {
+        const float d0 = c0 - target[p3], d1 = c1 - target[p3 + plane],
+                    d2 = c2 - target[p3 + 2 * plane];
+        const float sc = view.loss_scale;
+        float g0, g1, g2, l;
+        if (loss_mode == 1) {
+            g0 = (d0 > 0.f) - (d0 < 0.f);
+            g1 = (d1 > 0.f) - (d1 < 0.f);
+            g2 = (d2 > 0.f) - (d2 < 0.f);
+            l = fabsf(d0) + fabsf(d1) + fabsf(d2);
+        } else {
+            g0 = 2.f * d0; g1 = 2.f * d1; g2 = 2.f * d2;
+            l = d0 * d0 + d1 * d1 + d2 * d2;
+        }
+        dL_dimage[p3] = g0 * sc;
+        dL_dimage[p3 + plane] = g1 * sc;
+        dL_dimage[p3 + 2 * plane] = g2 * sc;
+        lsum += l * sc;
+    }
+}
+
+__global__ void __launch_bounds__(kFwdThreads)
 render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
                   int vals_stride, const uint32_t* __restrict__ ranges,
@@ -74,7 +124,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smem_raw);
     const int n_tiles = *n_active_tiles;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, 8)
     const bool lazy = bin_offsets != nullptr;
     for (;;) {
         if (threadIdx.x == 0) sm.tile = atomicAdd(work_counter, 1);
@@ -87,19 +137,20 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
         const int local = tile - view.tile_base;
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const int W = view.cam.width, H = view.cam.height;
-        const int px = tx * kTile + lx, py = ty * kTile + ly;
-        const bool inside = px < W && py < H;
-        const float fx = (float)px + 0.5f, fy = (float)py + 0.5f;
+        const int px = tx * kTile + lx, py0 = ty * kTile + ly, py1 = py0 + 8;
+        const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
         const uint32_t start = ranges[2 * (int64_t)tile], end = ranges[2 * (int64_t)tile + 1];
 
-        PixelState ps{1.0f, 0.f, 0.f, 0.f, 0u, !inside};
+        PixelState p0{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py0 < H)};
+        PixelState p1{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py1 < H)};
         if (!lazy) {
             for (uint32_t b = start; b < end; b += kTilePixels) {
-                if (__syncthreads_count(ps.done) == kTilePixels) break;
-                const uint32_t idx = b + threadIdx.x;
-                if (idx < end) stage_record(sm, records, vals[(int64_t)idx * vals_stride]);
+                if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
+                for (int i = threadIdx.x; i < kTilePixels && b + i < end; i += kFwdThreads)
+                    stage_record(sm, i, records, vals[(int64_t)(b + i) * vals_stride]);
                 __syncthreads();
-                composite_batch(sm, (int)min((uint32_t)kTilePixels, end - b), b - start, fx, fy, ps);
+                composite_batch(sm, (int)min((uint32_t)kTilePixels, end - b), b - start, fx, fy0,
+                                fy1, p0, p1);
             }
         } else {
             // Walk the tile's depth bins front to back. Consecutive bins up to
@@ -107,12 +158,12 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             // counting on the unique (depth, index) keys, written back for the
             // backward pass, and composited; bins behind the point where every
             // pixel saturated are never sorted. Larger bins were sorted before.
-            for (int i = threadIdx.x; i <= kBins; i += kTilePixels)
+            for (int i = threadIdx.x; i <= kBins; i += kFwdThreads)
                 sm.off[i] = bin_offsets[(int64_t)t * kBins + i];
             __syncthreads();
             int bin = 0;
             while (bin < kBins) {
-                if (__syncthreads_count(ps.done) == kTilePixels) break;
+                if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
                 const uint32_t w0 = sm.off[bin];
                 int e = bin + 1;
                 while (e < kBins && sm.off[e + 1] - w0 <= (uint32_t)kLazyWin) ++e;
@@ -121,70 +172,42 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                 if (n == 0) continue;
                 const bool here = n <= kLazyMax;
                 if (here) {
-                    for (int i = threadIdx.x; i < n; i += kTilePixels) sm.key[i] = lazy_keys[w0 + i];
+                    for (int i = threadIdx.x; i < n; i += kFwdThreads) sm.key[i] = lazy_keys[w0 + i];
                     __syncthreads();
-                    for (int i = threadIdx.x; i < n; i += kTilePixels) {
+                    for (int i = threadIdx.x; i < n; i += kFwdThreads) {
                         const uint64_t k = sm.key[i];
                         int r = 0;
                         for (int j = 0; j < n; ++j) r += sm.key[j] < k;
                         sm.sorted[r] = k;
                     }
                     __syncthreads();
-                    for (int i = threadIdx.x; i < n; i += kTilePixels) lazy_keys[w0 + i] = sm.sorted[i];
+                    for (int i = threadIdx.x; i < n; i += kFwdThreads) lazy_keys[w0 + i] = sm.sorted[i];
                 }
                 for (int c0 = 0; c0 < n; c0 += kTilePixels) {
-                    if (c0 > 0 && __syncthreads_count(ps.done) == kTilePixels) break;
-                    const int idx = c0 + threadIdx.x;
-                    if (idx < n)
-                        stage_record(sm, records,
-                                     (uint32_t)(here ? sm.sorted[idx] : lazy_keys[w0 + idx]));
+                    if (c0 > 0 && __syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
+                    for (int i = threadIdx.x; i < kTilePixels && c0 + i < n; i += kFwdThreads)
+                        stage_record(sm, i, records,
+                                     (uint32_t)(here ? sm.sorted[c0 + i] : lazy_keys[w0 + c0 + i]));
                     __syncthreads();
-                    composite_batch(sm, min(kTilePixels, n - c0), w0 - start + c0, fx, fy, ps);
+                    composite_batch(sm, min(kTilePixels, n - c0), w0 - start + c0, fx, fy0, fy1,
+                                    p0, p1);
                     __syncthreads();
                 }
             }
         }
 
         float lsum = 0.0f;
-        if (inside) {
-            const float c0 = ps.c0 + ps.T * bg0, c1 = ps.c1 + ps.T * bg1, c2 = ps.c2 + ps.T * bg2;
-            const int64_t pix = view.pix_base + (int64_t)py * W + px;
-            const int64_t plane = (int64_t)W * H;
-            const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
-            T_final[pix] = ps.T;
-            n_contrib[pix] = (int32_t)ps.last;
-            if (image) {
-                image[p3] = c0;
-                image[p3 + plane] = c1;
-                image[p3 + 2 * plane] = c2;
-            }
-            if (loss_mode != 0) {
-                const float d0 = c0 - target[p3], d1 = c1 - target[p3 + plane],
-                            d2 = c2 - target[p3 + 2 * plane];
-                const float sc = view.loss_scale;
-                float g0, g1, g2;
-                if (loss_mode == 1) {
-                    g0 = (d0 > 0.f) - (d0 < 0.f);
-                    g1 = (d1 > 0.f) - (d1 < 0.f);
-                    g2 = (d2 > 0.f) - (d2 < 0.f);
-                    lsum = fabsf(d0) + fabsf(d1) + fabsf(d2);
-                } else {
-                    g0 = 2.f * d0; g1 = 2.f * d1; g2 = 2.f * d2;
-                    lsum = d0 * d0 + d1 * d1 + d2 * d2;
-                }
-                dL_dimage[p3] = g0 * sc;
-                dL_dimage[p3 + plane] = g1 * sc;
-                dL_dimage[p3 + 2 * plane] = g2 * sc;
-                lsum *= sc;
-            }
-        }
+        finish_pixel(p0, view, px, py0, bg0, bg1, bg2, target, loss_mode, image, T_final,
+                     n_contrib, dL_dimage, lsum);
+        finish_pixel(p1, view, px, py1, bg0, bg1, bg2, target, loss_mode, image, T_final,
+                     n_contrib, dL_dimage, lsum);
         if (loss_mode != 0 && loss_per_scene) {
             for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
             if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = lsum;
             __syncthreads();
             if (threadIdx.x == 0) {
                 float tot = 0.f;
-                for (int w = 0; w < kTilePixels / 32; ++w) tot += sm.red[w];
+                for (int w = 0; w < kFwdThreads / 32; ++w) tot += sm.red[w];
                 atomicAdd(loss_per_scene + view.scene, tot);
             }
         }
@@ -221,13 +244,13 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(render_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(FwdSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel, kTilePixels,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel, kFwdThreads,
                                                       sizeof(FwdSmem));
         g_fwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
     }
     const int blocks = (int)hmin64(info->total_tiles, g_fwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
-    render_fwd_kernel<<<blocks, kTilePixels, sizeof(FwdSmem), s>>>(
+    render_fwd_kernel<<<blocks, kFwdThreads, sizeof(FwdSmem), s>>>(
         views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
         n_active_tiles_dev, lazy_keys, bin_offsets, bg[0],
         bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
