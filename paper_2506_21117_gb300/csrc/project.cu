@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(kBinBlock)
 count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                    const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
                    int chunks_per_view, int64_t* __restrict__ partials,
-                   uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax) {
+                   uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
+                   uint32_t* __restrict__ work_list, int32_t* __restrict__ work_count) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     __shared__ uint32_t s_lo, s_hi;
     const ClsView& view = views[blockIdx.y];
@@ -221,6 +222,15 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
                 cnt += c;
                 lo = min(lo, zb);
                 hi = max(hi, zb);
+            }
+            if (work_list) {  // compact the pair-producing records of this view
+                const uint32_t m = __ballot_sync(__activemask(), c > 0);
+                const int lane = threadIdx.x & 31;
+                int base = 0;
+                const int leader = __ffs(m) - 1;
+                if (m && lane == leader) base = atomicAdd(work_count + blockIdx.y, __popc(m));
+                base = __shfl_sync(__activemask(), base, leader < 0 ? 0 : leader);
+                if (c > 0) work_list[view.rec_base + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)g;
             }
         }
     }
@@ -418,6 +428,79 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
     }
 }
 
+// Bucketed emission, load-balanced: a warp takes 32 pair-producing Gaussians of
+// one view, prefix-sums their rectangle areas, and spreads the rectangle cells
+// over its lanes (each lane finds the owner of its cell by a binary search over
+// the prefix); an active cell claims a slot in its (tile, depth bin) bucket.
+__global__ void __launch_bounds__(kBinBlock)
+emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
+                     const int32_t* __restrict__ tile_rank, const uint32_t* __restrict__ zmin,
+                     const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
+                     uint64_t* __restrict__ keys, int64_t capacity,
+                     const uint32_t* __restrict__ work_list,
+                     const int32_t* __restrict__ work_count) {
+    extern __shared__ int32_t s_rank[];
+    const ClsView& view = views[blockIdx.y];
+    const int Tx = view.tiles_x;
+    for (int i = threadIdx.x; i < Tx * view.tiles_y; i += kBinBlock)
+        s_rank[i] = tile_rank[view.tile_base + i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int n = work_count[blockIdx.y];
+    const uint32_t lo = zmin[blockIdx.y], hi = zmax[blockIdx.y];
+    const int warps_total = gridDim.x * (kBinBlock / 32);
+    for (int w = blockIdx.x * (kBinBlock / 32) + (threadIdx.x >> 5); w * 32 < n; w += warps_total) {
+        const int item = w * 32 + lane;
+        int x0 = 0, x1 = -1, y0 = 0, y1 = -1, area = 0, bin = 0;
+        uint32_t zb = 0, rec = 0;
+        if (item < n) {
+            const uint32_t g = work_list[view.rec_base + item];
+            rec = (uint32_t)(view.rec_base + g);
+            if (record_rect(view, records, rec, x0, x1, y0, y1, zb)) {
+                area = (x1 - x0 + 1) * (y1 - y0 + 1);
+                bin = depth_bin(zb, lo, hi);
+            }
+        }
+        int incl = area;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int wdt = x1 - x0 + 1;
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            const int c = c0 + lane;
+            // owner = first lane whose inclusive prefix exceeds c
+            int l = 0, h = 31;
+#pragma unroll
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (l + h) >> 1;
+                const int pm = __shfl_sync(0xffffffffu, incl, mid);
+                if (pm > c) h = mid; else l = mid + 1;
+            }
+            const int own = l;
+            const int o_incl = __shfl_sync(0xffffffffu, incl, own);
+            const int o_area = __shfl_sync(0xffffffffu, area, own);
+            const int o_x0 = __shfl_sync(0xffffffffu, x0, own);
+            const int o_y0 = __shfl_sync(0xffffffffu, y0, own);
+            const int o_w = __shfl_sync(0xffffffffu, wdt, own);
+            const int o_bin = __shfl_sync(0xffffffffu, bin, own);
+            const uint32_t o_zb = __shfl_sync(0xffffffffu, zb, own);
+            const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, own);
+            if (c < total) {
+                const int k = c - (o_incl - o_area);
+                const int ty = o_y0 + k / o_w, tx = o_x0 + k - (k / o_w) * o_w;
+                const int r = s_rank[ty * Tx + tx];
+                if (r >= 0) {
+                    const int64_t p = atomicAdd(cursor + (int64_t)r * kDepthBins + o_bin, 1);
+                    if (p < capacity) keys[p] = ((uint64_t)o_zb << 32) | o_rec;
+                }
+            }
+        }
+    }
+}
+
 // One warp per large rectangle; lanes walk its tiles in row-major order. The
 // flat layout keeps that order with a ballot prefix.
 template <int LAYOUT>
@@ -475,7 +558,7 @@ namespace {
 
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, total;
+        bins, work_list, work_count, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -500,6 +583,8 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.big_list = o; o = align256(o + (size_t)info->total_records * 16);
     L.big_count = o; o = align256(o + 4);
     L.bins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
+    L.work_list = o; o = align256(o + (size_t)info->total_records * 4);
+    L.work_count = o; o = align256(o + (size_t)V * 4);
     L.total = o;
     return L;
 }
@@ -549,10 +634,12 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     uint4* big_list = reinterpret_cast<uint4*>(ws + L.big_list);
     int32_t* big_count = reinterpret_cast<int32_t*>(ws + L.big_count);
     int32_t* bins = reinterpret_cast<int32_t*>(ws + L.bins);
+    uint32_t* work_list = reinterpret_cast<uint32_t*>(ws + L.work_list);
+    int32_t* work_count = reinterpret_cast<int32_t*>(ws + L.work_count);
     const int64_t subs = info->total_tiles * kDepthBins;
     const int64_t max_view_tiles = info->max_view_tiles;
     if (layout == 1 && g_max_view_tiles_checked == 0) {
-        cudaFuncSetAttribute(emit_pairs_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(emit_bucketed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
         g_max_view_tiles_checked = 1;
     }
@@ -582,11 +669,14 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     if (layout == 1) {
         cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
         cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
+        cudaMemsetAsync(work_count, 0, (size_t)V * 4, s);
     }
     count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
                                                       (int)cpv, partials,
                                                       layout == 1 ? zmin : nullptr,
-                                                      layout == 1 ? zmax : nullptr);
+                                                      layout == 1 ? zmax : nullptr,
+                                                      layout == 1 ? work_list : nullptr,
+                                                      work_count);
     if (layout == 0) {
         scan_partials_kernel<<<1, 1024, 0, s>>>(partials, cpv * V, n_pairs_dev, nullptr, capacity,
                                                 status_dev);
@@ -611,12 +701,11 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
             sub_partials, capacity, bin_offsets, cursor, ranges);
-        emit_pairs_kernel<1><<<rec_grid, kBinBlock, (size_t)max_view_tiles * 4, s>>>(
-            scenes_dev, views_dev, records, sat, tile_active, tile_rank, (int)cpv, nullptr, zmin,
-            zmax, bin_offsets, cursor, keys, nullptr, capacity, big_list, big_count);
-        emit_big_kernel<1><<<1024, 256, 0, s>>>(views_dev, records, tile_active, tile_rank, zmin,
-                                                zmax, bin_offsets, cursor, keys, nullptr,
-                                                capacity, big_list, big_count);
+        const unsigned emit_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
+                                                      2048);
+        emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 4, s>>>(
+            views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
+            work_count);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;

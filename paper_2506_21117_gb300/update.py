@@ -288,11 +288,11 @@ class Batch:
         """Kernels of one iteration. project_and_bin (mode 1): project and
         stamp (2 if any Gaussian is active), tile mask, compaction, count,
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
-        prefix, bucket counts, scan, offsets, emit, emit-big (7). Sort: flat
+        prefix, bucket counts, scan, offsets, emit (6). Sort: flat
         hist + scan + passes (+ copy if odd) + ranges; bucketed 1. Forward 1,
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
-        proj = active + 3 + (7 if self.layout == 1 else 3)
+        proj = active + 3 + (6 if self.layout == 1 else 3)
         if self.layout == 1:
             sort = 2 if self.lazy else 1
         else:
