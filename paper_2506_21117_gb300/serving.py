@@ -1,0 +1,291 @@
+"""Serving loop for scene updates: continuous batching of local optimisations.
+
+Each request is one CL-Splats update of a resident scene (Sec. 3): a few new
+posed views with their change masks and target images, lifted to an active set
+and optimised for a fixed number of local iterations. The paper applies the
+method "in parallel to each change" (Sec. 5, "Concurrent Updates"); here the
+updates of different scenes share the GPU:
+
+* every scene's Gaussians and Adam state stay resident on the device;
+* requests wait in a FIFO queue and are admitted at iteration boundaries when a
+  slot is free, their scene is not already being updated, and their estimated
+  HBM footprint fits the budget (continuous batching: requests that arrive
+  while others run join the next iteration);
+* one engine step runs one iteration of every in-flight request in the same
+  launches (one scene table and one view table spanning all requests, views of
+  different resolutions side by side), captured once per batch composition in
+  a CUDA graph and replayed while the composition is unchanged;
+* a request completes after its iterations; its latency is arrival to
+  completion, read back with its loss.
+
+The plain baseline runs the same requests one at a time on the same kernels.
+`Scheduler` holds the host-side policy and runs without a GPU.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Callable, Dict, List, Optional, Sequence
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    scene: int
+    cams: list
+    masks: object          # flat uint8 tensor, views concatenated (pinned host memory)
+    targets: object        # flat float32 tensor, [3][H][W] per view (pinned host memory)
+    iters: int = 10
+    arrival: float = 0.0
+    footprint: int = 0     # estimated device bytes while in flight
+    # filled while serving
+    admitted: float = -1.0
+    done: float = -1.0
+    it: int = 0
+    loss: float = float("nan")
+    n_active: int = 0
+
+
+def estimate_footprint(n_gauss: int, cams: Sequence, pairs_per_tile: int = 1024) -> int:
+    """Device bytes one in-flight request needs beyond its resident scene:
+    projected records (48 B per Gaussian and view), per-pixel buffers (image,
+    target, dL/dimage, final T, last contributor: 44 B), per-tile tables and a
+    key allowance of `pairs_per_tile` pairs of 16 B (key + scratch) per tile."""
+    total = 0
+    for c in cams:
+        W, H = int(c["width"]), int(c["height"])
+        tiles = ((W + 15) // 16) * ((H + 15) // 16)
+        total += n_gauss * 48 + W * H * 44 + tiles * (256 * 8 + 64) + tiles * pairs_per_tile * 16
+    return total
+
+
+class Scheduler:
+    """Admission policy: FIFO queue, `max_slots` concurrent requests, at most
+    one in-flight request per scene, and the sum of in-flight footprints within
+    `budget` bytes. A request that alone exceeds the budget is rejected."""
+
+    def __init__(self, max_slots: int, budget: int):
+        self.max_slots = max_slots
+        self.budget = budget
+        self.queue: collections.deque = collections.deque()
+        self.inflight: List[Request] = []
+        self.rejected: List[Request] = []
+        self.finished: List[Request] = []
+        self.used = 0
+
+    def submit(self, req: Request) -> None:
+        if req.footprint > self.budget:
+            self.rejected.append(req)
+            return
+        self.queue.append(req)
+
+    def admit(self, now: float) -> List[Request]:
+        """Move every queued request that fits into the in-flight set, in
+        arrival order, skipping (not reordering) requests whose scene is busy
+        or that do not fit yet."""
+        admitted = []
+        busy = {r.scene for r in self.inflight}
+        keep = collections.deque()
+        while self.queue:
+            r = self.queue.popleft()
+            if (len(self.inflight) < self.max_slots and r.scene not in busy
+                    and self.used + r.footprint <= self.budget):
+                r.admitted = now
+                self.inflight.append(r)
+                busy.add(r.scene)
+                self.used += r.footprint
+                admitted.append(r)
+            else:
+                keep.append(r)
+        self.queue = keep
+        return admitted
+
+    def advance(self, now: float) -> List[Request]:
+        """One iteration of every in-flight request has run; retire finished
+        ones and free their memory."""
+        done = []
+        for r in self.inflight:
+            r.it += 1
+            if r.it >= r.iters:
+                r.done = now
+                done.append(r)
+        if done:
+            self.inflight = [r for r in self.inflight if r.done < 0]
+            for r in done:
+                self.used -= r.footprint
+            self.finished.extend(done)
+        return done
+
+    def idle(self) -> bool:
+        return not self.queue and not self.inflight
+
+
+def latency_stats(reqs: Sequence[Request], wall: float) -> Dict[str, float]:
+    lat = np.array([r.done - r.arrival for r in reqs if r.done >= 0])
+    if lat.size == 0:
+        return {"completed": 0}
+    return {"completed": int(lat.size), "updates_per_s": lat.size / wall,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}
+
+
+class Server:
+    """GPU engine. `states` are resident SceneStates (index = scene id)."""
+
+    def __init__(self, states, max_slots: int = 8, budget: Optional[int] = None,
+                 graphs: bool = True, loss: str = "l1", lr: float = 1e-3, vote_mode: int = 0,
+                 clock: Callable[[], float] = time.perf_counter):
+        import torch
+        self.torch = torch
+        self.states = states
+        self.graphs = graphs
+        self.loss_mode = {"l1": 1, "l2": 2}[loss]
+        self.lr = lr
+        self.vote_mode = vote_mode
+        self.clock = clock
+        if budget is None:
+            free, _ = torch.cuda.mem_get_info()
+            budget = int(free * 0.6)
+        self.sched = Scheduler(max_slots, budget)
+        self.batch = None
+        self.graph = None
+        self.composition = None
+        self.device_targets: Dict[int, object] = {}
+        self.stats = {"steps": 0, "graph_captures": 0, "graph_replays": 0, "rebuilds": 0}
+
+    # -- request life cycle ----------------------------------------------------
+    def submit(self, req: Request) -> None:
+        if req.footprint == 0:
+            req.footprint = estimate_footprint(self.states[req.scene].n, req.cams)
+        self.sched.submit(req)
+
+    def _start(self, req: Request) -> None:
+        """Admission on the device: reset the scene's optimiser, copy the
+        request's masks and targets from pinned host memory, lift."""
+        from .update import lift
+        torch = self.torch
+        st = self.states[req.scene]
+        st.adam_m.zero_()
+        st.adam_v.zero_()
+        st.adam_step.zero_()
+        masks = req.masks.to(st.params.device, non_blocking=True)
+        self.device_targets[req.rid] = req.targets.to(st.params.device, non_blocking=True)
+        lift(st, req.cams, masks, self.vote_mode, st.params.device)
+        req.n_active = st.n_active
+
+    def _rebuild(self) -> None:
+        from .update import Batch
+        torch = self.torch
+        reqs = self.sched.inflight
+        self.batch = Batch([self.states[r.scene] for r in reqs], [r.cams for r in reqs],
+                           self.states[reqs[0].scene].params.device)
+        self.batch.target = torch.cat([self.device_targets[r.rid] for r in reqs])
+        self.batch.plan_capacity()
+        self.composition = tuple(r.rid for r in reqs)
+        self.graph = None
+        self.stats["rebuilds"] += 1
+
+    def _iteration(self) -> None:
+        b = self.batch
+        b.project_and_bin(1)
+        b.sort()
+        b.forward(self.loss_mode, write_image=False)
+        b.backward()
+        b.adam(self.lr)
+
+    def _step(self) -> None:
+        torch = self.torch
+        if not self.graphs:
+            self._iteration()
+        elif self.graph is None:
+            self._iteration()  # eager first iteration of a composition (warm-up)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._iteration()
+            self.graph = g
+            self.stats["graph_captures"] += 1
+            # the captured iteration did not run; the eager one stands for this step
+        else:
+            self.graph.replay()
+            self.stats["graph_replays"] += 1
+        self.stats["steps"] += 1
+
+    def _finish(self, done: Sequence[Request]) -> None:
+        order = {r.rid: i for i, r in enumerate(self.batch_requests)}
+        self.pending_losses.append((self.batch.loss.clone(), [(r, order[r.rid]) for r in done]))
+        for r in done:
+            self.device_targets.pop(r.rid, None)
+
+    # -- driving loops -----------------------------------------------------------
+    def serve(self, schedule: Sequence[Request], realtime: bool = True,
+              run_ahead: int = 2) -> Dict[str, float]:
+        """Serve `schedule` (requests with arrival offsets in seconds). With
+        `realtime` a request becomes visible at its arrival time; otherwise all
+        are queued at once (closed loop, saturation). The host does not wait
+        for each step: a CUDA event marks the end of every step, completion
+        times are read from those events, and the host runs at most
+        `run_ahead` steps ahead of the device."""
+        torch = self.torch
+        pending = collections.deque(sorted(schedule, key=lambda r: r.arrival))
+        self.pending_losses = []
+        marks = []  # (event, requests finished by that step)
+        torch.cuda.synchronize()
+        ref = torch.cuda.Event(enable_timing=True)
+        ref.record()
+        t0 = self.clock()
+        for r in pending:
+            r.arrival = t0 + (r.arrival if realtime else 0.0)
+        recent = collections.deque()
+        while pending or not self.sched.idle():
+            now = self.clock()
+            while pending and pending[0].arrival <= now:
+                self.submit(pending.popleft())
+            started = self.sched.admit(now)
+            for r in started:
+                self._start(r)
+            if not self.sched.inflight:
+                if pending:
+                    time.sleep(max(0.0, min(pending[0].arrival - self.clock(), 0.002)))
+                continue
+            if self.composition != tuple(r.rid for r in self.sched.inflight):
+                self._rebuild()
+            self.batch_requests = list(self.sched.inflight)
+            self._step()
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record()
+            recent.append(ev)
+            if len(recent) > run_ahead:
+                recent.popleft().synchronize()
+            done = self.sched.advance(self.clock())
+            if done:
+                self._finish(done)
+                marks.append((ev, done))
+        torch.cuda.synchronize()
+        for ev, done in marks:
+            t = t0 + ref.elapsed_time(ev) / 1e3
+            for r in done:
+                r.done = t
+        for loss, items in self.pending_losses:
+            vals = loss.cpu().numpy()
+            for r, i in items:
+                r.loss = float(vals[i])
+        if self.batch is not None:
+            self.batch.check_status()
+        wall = max(r.done for r in self.sched.finished) - t0 if self.sched.finished else 0.0
+        out = latency_stats(self.sched.finished, max(wall, 1e-9))
+        out.update(self.stats)
+        out["rejected"] = len(self.sched.rejected)
+        return out
+
+
+def run_plain(states, schedule: Sequence[Request], loss: str = "l1", lr: float = 1e-3,
+              realtime: bool = True, graphs: bool = True,
+              clock: Callable[[], float] = time.perf_counter) -> Dict[str, float]:
+    """The plain loop: one request at a time, FIFO, same kernels."""
+    srv = Server(states, max_slots=1, graphs=graphs, loss=loss, lr=lr, clock=clock)
+    return srv.serve(schedule, realtime)

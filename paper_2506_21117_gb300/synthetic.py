@@ -283,3 +283,54 @@ def workload_fd(seed: int = 0):
     cams = ring_cameras(2, 4.0, 32, 32, angles=[0.0, 0.5 * math.pi])
     targets = [random_image(c, seed + i) for i, c in enumerate(cams)]
     return scene, cams, targets
+
+
+def serving_scenes(n_scenes: int = 64, n_lo: int = 50_000, n_hi: int = 500_000,
+                   sh_degree: int = 3, seed: int = 0):
+    """Resident scenes of the serving workload: Gaussian counts log-uniform in
+    [n_lo, n_hi], each a clustered room like the large workload with the
+    cluster count scaled to its size. Returns (scenes, centres)."""
+    rng = np.random.default_rng(seed + 10)
+    ns = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_scenes)).astype(int)
+    scenes, centres = [], []
+    for i, n in enumerate(ns):
+        k = max(2, int(round(20 * n / 1_000_000)))
+        sc, c = cluster_scene(int(n), k, 0.3, 4.0, 5.0, sh_degree, seed + 100 + i)
+        scenes.append(sc)
+        centres.append(c)
+    return scenes, centres
+
+
+SERVING_RESOLUTIONS = [(640, 480), (800, 800), (1280, 720)]
+
+
+def serving_templates(scenes, centres, n_templates: int = 32, seed: int = 0):
+    """Update requests of the serving workload: a scene drawn uniformly, 2-8
+    views on a ring of radius 4 (random phase), one of three resolutions, and a
+    change box around the scene's best-seen cluster holding 1-10% of its
+    Gaussians. Returns dicts with scene, cams, masks (list of H x W uint8)."""
+    rng = np.random.default_rng(seed + 20)
+    out = []
+    for _ in range(n_templates):
+        s = int(rng.integers(0, len(scenes)))
+        V = int(rng.integers(2, 9))
+        W, H = SERVING_RESOLUTIONS[int(rng.integers(0, len(SERVING_RESOLUTIONS)))]
+        phase = float(rng.uniform(0, 2 * math.pi))
+        angles = [phase + 2 * math.pi * k / V for k in range(V)]
+        cams = ring_cameras(V, 4.0, W, H, angles=angles)
+        frac = float(rng.uniform(0.01, 0.10))
+        box = box_holding_fraction(scenes[s]["means"], change_cluster(centres[s], cams), frac)
+        masks = [box_change_mask(c, box) for c in cams]
+        out.append({"scene": s, "cams": cams, "masks": masks, "fraction": frac})
+    return out
+
+
+def poisson_arrivals(rate: float, duration: float, n_templates: int, seed: int = 0):
+    """Arrival offsets (seconds) of a Poisson stream and the template of each."""
+    rng = np.random.default_rng(seed + 30)
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > duration:
+            return out
+        out.append((t, int(rng.integers(0, n_templates))))

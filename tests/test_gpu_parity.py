@@ -85,10 +85,13 @@ def _small_local(seed=0, n=6000, deg=3, size=(100, 75), views=3, frac=0.05):
     return scene, cams, masks, targets
 
 
-def _compare_grads(lu, ref, active, deg, exclude=()):
+def _compare_grads(lu, ref, active, deg, exclude=(), rows=None):
+    """GPU gradient rows of the active set (from the update's buffer, or the
+    given [A][stride] array) against the oracle's."""
     from paper_2506_21117_gb300.update import unpack_rows
     A = int(active.sum())
-    rows = lu.batch.grads[: A * lu.state.stride].view(A, lu.state.stride).cpu().numpy()
+    if rows is None:
+        rows = lu.batch.grads[: A * lu.state.stride].view(A, lu.state.stride).cpu().numpy()
     got = unpack_rows(rows.astype(np.float64), deg)
     idx = np.flatnonzero(active)
     keep = ~np.isin(idx, np.array(sorted(exclude), dtype=np.int64))
@@ -306,6 +309,31 @@ def test_gradients_local_active_set_equal_full_image_gradients():
     worst, excl = _compare_grads(lu, ref, active, 3, exclude=ref["near_ids"])
     print(f"local SH3 gradients: {int(active.sum())} active, worst {worst:.3f}, {excl} excluded")
     assert excl <= 0.1 * active.sum()
+
+
+def test_autograd_function_matches_oracle_gradient():
+    """The hand-written adjoint behind torch.autograd.Function: an L2 loss
+    written in torch over the rendered images back-propagates through
+    cls_render_backward to the oracle's float64 gradient (which is itself
+    pinned by central finite differences)."""
+    from paper_2506_21117_gb300.autograd import ActiveRasterizer
+    from paper_2506_21117_gb300.update import SceneState
+    scene, cams, targets = S.workload_fd()
+    active = np.ones(500, bool)
+    st = SceneState(scene, 1)
+    st.set_active(active)
+    rast = ActiveRasterizer(st, cams)
+    params = st.params.requires_grad_(True)
+    imgs = rast(params)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    loss = sum(((im - t) ** 2).sum() / (3 * im.shape[1] * im.shape[2])
+               for im, t in zip(imgs, tg)) / len(imgs)
+    loss.backward()
+    ref = ostep.local_step_reference(scene, cams, 1, targets, active, "l2")
+    assert abs(float(loss) - ref["loss"]) <= 1e-5 * ref["loss"]
+    rows = params.grad.detach().cpu().numpy()
+    worst, excl = _compare_grads(None, ref, active, 1, exclude=ref["near_ids"], rows=rows)
+    print(f"autograd.Function L2 gradients: worst error/bound {worst:.3f}, {excl} excluded")
 
 
 # -------------------------------------------------------------------- Adam --
