@@ -49,6 +49,11 @@ def parse():
     p.add_argument("--iters-per-update", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-tiles", type=int, default=4)
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serving-scenes", type=int, default=64)
+    p.add_argument("--serving-seconds", type=float, default=10.0)
+    p.add_argument("--serving-rate", type=float, default=200.0)
+    p.add_argument("--serving-slots", type=int, default=8)
     return p.parse_args()
 
 
@@ -291,6 +296,7 @@ def run_ours(args, rank, world):
                       "frac_of_hbm": B_iter * value / world / 1e9 / hbm_peak}
 
     e2e = run_e2e(args, lu, targets, masks, cams)
+    active_np = lu.state.active.cpu().numpy().astype(bool)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -309,13 +315,73 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "gpu_launches": int(bt.launches_per_step() * args.steps),
     }
+    if not args.no_serving:
+        del lu, bt
+        torch.cuda.empty_cache()
+        line["serving"] = run_serving(args, seed=rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import torch as _t
-        sec, desc = oracle_sample(scene, cams, targets, lu.state.active.cpu().numpy().astype(bool),
-                                  tiles_on, args.cpu_tiles, proj_frac=0.05)
+        sec, desc = oracle_sample(scene, cams, targets, active_np, tiles_on, args.cpu_tiles,
+                                  proj_frac=0.05)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": _t.get_num_threads(),
                                 "kind": "oracle", "sample": desc}
     return line
+
+
+def run_serving(args, seed=0):
+    """Serving workload: resident scenes with log-uniform sizes, Poisson update
+    requests (2-8 views at 640x480, 800x800 or 1280x720, a change box holding
+    1-10% of the scene, 10 local iterations each), continuous batching against
+    the plain one-at-a-time loop on the same kernels. Saturation first (all
+    requests queued at once); then the open-loop stream at the configured rate,
+    or at 50% and 90% of the batched saturation rate if the rate exceeds it."""
+    import torch
+    from paper_2506_21117_gb300 import synthetic as S
+    from paper_2506_21117_gb300.serving import Request, Server, run_plain
+    from paper_2506_21117_gb300.update import SceneState
+    t_setup = time.perf_counter()
+    scenes, centres = S.serving_scenes(args.serving_scenes, seed=seed)
+    templates = S.serving_templates(scenes, centres, 32, seed=seed)
+    states = [SceneState(sc, 3) for sc in scenes]
+    del scenes
+    rng = np.random.default_rng(seed + 40)
+    tgt = {}
+    for (W, H) in S.SERVING_RESOLUTIONS:
+        img = rng.uniform(0, 1, size=(8, 3, H, W)).astype(np.float32)
+        tgt[(W, H)] = torch.from_numpy(img.reshape(-1)).pin_memory()
+    packed = []
+    for tp in templates:
+        W, H = int(tp["cams"][0]["width"]), int(tp["cams"][0]["height"])
+        V = len(tp["cams"])
+        m = torch.from_numpy(np.concatenate([x.reshape(-1) for x in tp["masks"]])).pin_memory()
+        packed.append((tp["scene"], tp["cams"], m, tgt[(W, H)][: V * 3 * H * W]))
+    setup_s = time.perf_counter() - t_setup
+
+    def requests(schedule):
+        return [Request(rid=i, scene=packed[k][0], cams=packed[k][1], masks=packed[k][2],
+                        targets=packed[k][3], iters=10, arrival=t) for i, (t, k) in enumerate(schedule)]
+
+    n_sat = 96
+    sat_sched = [(0.0, int(rng.integers(0, len(packed)))) for _ in range(n_sat)]
+    warm = requests(sat_sched[:8])
+    Server(states, max_slots=args.serving_slots).serve(warm, realtime=False)
+    sat_b = Server(states, max_slots=args.serving_slots).serve(requests(sat_sched), realtime=False)
+    sat_p = run_plain(states, requests(sat_sched[: n_sat // 2]), realtime=False)
+    rates = [args.serving_rate] if args.serving_rate < sat_b["updates_per_s"] else \
+        [0.5 * sat_b["updates_per_s"], 0.9 * sat_b["updates_per_s"]]
+    open_loop = []
+    for rate in rates:
+        sched = S.poisson_arrivals(rate, args.serving_seconds, len(packed), seed=seed + int(rate))
+        cut = 2.0 * args.serving_seconds
+        b = Server(states, max_slots=args.serving_slots).serve(requests(sched), realtime=True,
+                                                              deadline=cut)
+        p = run_plain(states, requests(sched), realtime=True, deadline=cut)
+        open_loop.append({"rate_per_s": rate, "requests": len(sched), "batched": b, "plain": p})
+    return {"scenes": len(states), "setup_s": setup_s, "templates": len(packed),
+            "deadline_s": 2.0 * args.serving_seconds,
+            "iters_per_update": 10, "slots": args.serving_slots,
+            "saturation": {"batched": sat_b, "plain": sat_p},
+            "open_loop": open_loop}
 
 
 def run_e2e(args, lu, targets, masks, cams):

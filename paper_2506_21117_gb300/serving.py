@@ -223,13 +223,15 @@ class Server:
 
     # -- driving loops -----------------------------------------------------------
     def serve(self, schedule: Sequence[Request], realtime: bool = True,
-              run_ahead: int = 2) -> Dict[str, float]:
+              run_ahead: int = 2, deadline: Optional[float] = None) -> Dict[str, float]:
         """Serve `schedule` (requests with arrival offsets in seconds). With
         `realtime` a request becomes visible at its arrival time; otherwise all
         are queued at once (closed loop, saturation). The host does not wait
         for each step: a CUDA event marks the end of every step, completion
         times are read from those events, and the host runs at most
-        `run_ahead` steps ahead of the device."""
+        `run_ahead` steps ahead of the device. With a `deadline` (seconds
+        after the start) no request is admitted after it; requests not
+        finished are counted as `unfinished`."""
         torch = self.torch
         pending = collections.deque(sorted(schedule, key=lambda r: r.arrival))
         self.pending_losses = []
@@ -241,8 +243,15 @@ class Server:
         for r in pending:
             r.arrival = t0 + (r.arrival if realtime else 0.0)
         recent = collections.deque()
+        unfinished = 0
         while pending or not self.sched.idle():
             now = self.clock()
+            if deadline is not None and now - t0 > deadline:
+                unfinished = len(pending) + len(self.sched.queue)
+                pending.clear()
+                self.sched.queue.clear()
+                if not self.sched.inflight:
+                    break
             while pending and pending[0].arrival <= now:
                 self.submit(pending.popleft())
             started = self.sched.admit(now)
@@ -280,12 +289,13 @@ class Server:
         out = latency_stats(self.sched.finished, max(wall, 1e-9))
         out.update(self.stats)
         out["rejected"] = len(self.sched.rejected)
+        out["unfinished"] = unfinished
         return out
 
 
 def run_plain(states, schedule: Sequence[Request], loss: str = "l1", lr: float = 1e-3,
-              realtime: bool = True, graphs: bool = True,
+              realtime: bool = True, graphs: bool = True, deadline: Optional[float] = None,
               clock: Callable[[], float] = time.perf_counter) -> Dict[str, float]:
     """The plain loop: one request at a time, FIFO, same kernels."""
     srv = Server(states, max_slots=1, graphs=graphs, loss=loss, lr=lr, clock=clock)
-    return srv.serve(schedule, realtime)
+    return srv.serve(schedule, realtime, deadline=deadline)
