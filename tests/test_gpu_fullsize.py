@@ -1,0 +1,163 @@
+"""Parity at the benchmark's full size (1,000,000 Gaussians, four 1920x1080
+views, 5% change box), in the launch configuration the benchmark times (bucketed
+pairs, render-fused lazy depth sort). Bit-exact on every vote, projection and
+tile-mask entry; on sampled tiles, pixels and Gaussians the oracle computes one
+by one."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fp32_index as fx
+from oracle import step as ostep
+from paper_2506_21117_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    from paper_2506_21117_gb300 import build
+    from paper_2506_21117_gb300.update import LocalUpdate
+    build.build()
+    scene, _, cams, masks, _ = S.workload_large(n=1_000_000, fraction=0.05)
+    targets = [S.random_image(c, 60 + j) for j, c in enumerate(cams)]
+    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
+    lu.render_pass(with_backward=True, with_adam=False)
+    torch.cuda.synchronize()
+    lu.batch.check_status()
+    c, o = fx.votes(scene["means"], cams, masks)
+    active = fx.vote_rule(c, o, len(cams))
+    projs = [fx.project_index(scene, cam) for cam in cams]
+    tmask = [fx.tile_mask(p, active, cam) for p, cam in zip(projs, cams)]
+    return {"lu": lu, "scene": scene, "cams": cams, "targets": targets, "active": active,
+            "projs": projs, "tmask": tmask}
+
+
+def test_votes_projection_and_tile_mask_bit_exact(run):
+    lu, active = run["lu"], run["active"]
+    assert np.array_equal(lu.state.active.cpu().numpy().astype(bool), active)
+    A = lu.state.n_active
+    assert A == active.sum() > 10000
+    assert np.array_equal(lu.state.active_idx[:A].cpu().numpy(), np.flatnonzero(active))
+    rec = lu.batch.records.view(-1, 12).cpu().numpy()
+    reci = rec.view(np.int32)
+    n = run["scene"]["means"].shape[0]
+    for j, p in enumerate(run["projs"]):
+        ri, r = reci[j * n:(j + 1) * n], rec[j * n:(j + 1) * n]
+        valid = ri[:, 11] > 0
+        assert np.array_equal(valid, p["valid"])
+        assert np.array_equal(ri[valid, 11], p["radius"][valid].astype(np.int32))
+        assert np.array_equal(r[valid, 0].view(np.uint32), p["u"][valid].view(np.uint32))
+        assert np.array_equal(r[valid, 1].view(np.uint32), p["v"][valid].view(np.uint32))
+        assert np.array_equal(r[valid, 10].view(np.uint32), p["zbits"][valid])
+    assert np.array_equal(lu.batch.tile_active.cpu().numpy(),
+                          np.concatenate([m.ravel() for m in run["tmask"]]))
+
+
+def _tile_lists(run, samples):
+    """GPU (lazy-sorted prefix, whole bucket) and oracle lists of sampled tiles."""
+    lu = run["lu"]
+    ranges = lu.batch.ranges.view(-1, 2).cpu().numpy().astype(np.int64)
+    keys = lu.batch.keys.cpu().numpy().view(np.uint64)
+    bases = [int(v.tile_base) for v in lu.batch.view_tab]
+    out = []
+    for (j, tx, ty) in samples:
+        Tx = fx.tiles_of(run["cams"][j])[0]
+        t = bases[j] + ty * Tx + tx
+        a, e = ranges[t]
+        got = keys[a:e]
+        want = ostep.tile_list(run["projs"][j], tx, ty)
+        out.append((j, tx, ty, got, want))
+    return out
+
+
+def _sample_tiles(run, k, seed):
+    rng = np.random.default_rng(seed)
+    picks = []
+    for j, m in enumerate(run["tmask"]):
+        ys, xs = np.nonzero(m)
+        sel = rng.choice(ys.size, size=min(k, ys.size), replace=False)
+        picks += [(j, int(xs[i]), int(ys[i])) for i in sel]
+    return picks
+
+
+def test_sampled_tile_lists_and_pixels(run):
+    lu, cams = run["lu"], run["cams"]
+    samples = _sample_tiles(run, 4, seed=3)
+    n_contrib = lu.batch.per_view(lu.batch.n_contrib, 1)
+    image = lu.batch.per_view(lu.batch.image, 3)
+    checked_px = near_px = 0
+    for (j, tx, ty, got, want) in _tile_lists(run, samples):
+        rec = (got & np.uint64(0xFFFFFFFF)).astype(np.int64) - j * run["scene"]["means"].shape[0]
+        assert got.size == want.size
+        nc = n_contrib[j][ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16].cpu().numpy()
+        m = int(nc.max())
+        assert np.array_equal(rec[:m], want[:m]), (j, tx, ty)
+        assert np.array_equal(np.sort(rec), np.sort(want))
+        # pixels of the tile from the oracle, over the Gaussians reaching it
+        sub = {k2: v[want] for k2, v in run["scene"].items()}
+        ref = ostep.render(sub, [cams[j]], 3, tiles=[[(tx, ty)]])
+        r_img = ref["image"][0][:, ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
+        g_img = image[j][:, ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16].cpu().numpy()
+        near = ref["near"][0][ty * 16:(ty + 1) * 16, tx * 16:(tx + 1) * 16]
+        ok = ~near & np.isfinite(r_img[0])
+        assert np.abs(g_img - r_img)[:, ok].max() <= 1e-4
+        checked_px += int(ok.sum())
+        near_px += int((~ok).sum())
+    print(f"full size: {len(samples)} sampled tiles, {checked_px} pixels within 1e-4, "
+          f"{near_px} near-threshold excluded")
+    assert near_px <= 0.01 * (checked_px + near_px)
+
+
+def test_sampled_gradients(run):
+    """Gradients of a few small active Gaussians: the oracle renders every tile
+    their rectangles reach, in every view, over the Gaussians reaching those
+    tiles, and differentiates the full-image-normalised L1 loss."""
+    from paper_2506_21117_gb300.update import unpack_rows
+    lu, cams, scene = run["lu"], run["cams"], run["scene"]
+    active = run["active"]
+    idx = np.flatnonzero(active)
+    area = np.zeros(idx.size, np.int64)
+    seen = np.zeros(idx.size, np.int64)
+    for p in run["projs"]:
+        a = (p["tx1"] - p["tx0"] + 1) * (p["ty1"] - p["ty0"] + 1)
+        area = np.maximum(area, np.where(p["valid"][idx], a[idx], 0))
+        seen += p["valid"][idx]
+    order = np.lexsort((area, seen < 2))  # seen in two or more views first, then smallest
+    pick = idx[order[:3]]
+    print("sampled active Gaussians: max tiles per view", area[order[:3]].tolist())
+    tiles = []
+    for j, p in enumerate(run["projs"]):
+        tl = set()
+        for g in pick:
+            if p["valid"][g]:
+                tl |= {(x, y) for x in range(p["tx0"][g], p["tx1"][g] + 1)
+                       for y in range(p["ty0"][g], p["ty1"][g] + 1)}
+        tiles.append(sorted(tl))
+    # Gaussians reaching any of those tiles (in any view), in index order
+    keep = np.zeros(scene["means"].shape[0], bool)
+    for j, p in enumerate(run["projs"]):
+        for (tx, ty) in tiles[j]:
+            keep |= p["valid"] & (p["tx0"] <= tx) & (p["tx1"] >= tx) & (p["ty0"] <= ty) & \
+                (p["ty1"] >= ty)
+    ids = np.flatnonzero(keep)
+    sub = {k: v[ids] for k, v in scene.items()}
+    ref = ostep.render(sub, cams, 3, targets=run["targets"], loss="l1", need_grad=True,
+                       tiles=tiles)
+    A = lu.state.n_active
+    rows = lu.batch.grads[: A * lu.state.stride].view(A, lu.state.stride).cpu().numpy()
+    got = unpack_rows(rows.astype(np.float64), 3)
+    rank = {int(g): i for i, g in enumerate(idx)}
+    near = set(int(ids[i]) for i in ref["near_ids"])
+    checked = 0
+    sel = [int(g) for g in pick if int(g) not in near]
+    print(f"{len(pick) - len(sel)} of {len(pick)} sampled Gaussians have a threshold decision")
+    pos = [int(np.searchsorted(ids, g)) for g in sel]
+    for k in ostep.PARAM_KEYS:
+        r = np.stack([np.asarray(ref["grads"][k][s_], np.float64).ravel() for s_ in pos])
+        v = np.stack([np.asarray(got[k][rank[g]], np.float64).ravel() for g in sel])
+        floor = 5e-2 * np.sqrt(np.mean(r * r))  # of the sampled group, from the oracle
+        assert np.all(np.abs(v - r) <= 1e-3 * np.maximum(np.abs(r), floor)), (k, v, r)
+    checked = len(sel)
+    print(f"full size: gradients of {checked} sampled active Gaussians match the oracle")
+    assert checked >= 1
