@@ -469,34 +469,48 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         const int wdt = x1 - x0 + 1;
-        for (int c0 = 0; c0 < total; c0 += 32) {
-            const int c = c0 + lane;
-            // owner = first lane whose inclusive prefix exceeds c
-            int l = 0, h = 31;
+        // four cells per lane per round, so four slot claims are in flight
+        // before the first key is stored
+        constexpr int kU = 4;
+        for (int c0 = 0; c0 < total; c0 += 32 * kU) {
+            int64_t sub[kU];
+            uint64_t key[kU];
 #pragma unroll
-            for (int step = 0; step < 5; ++step) {
-                const int mid = (l + h) >> 1;
-                const int pm = __shfl_sync(0xffffffffu, incl, mid);
-                if (pm > c) h = mid; else l = mid + 1;
-            }
-            const int own = l;
-            const int o_incl = __shfl_sync(0xffffffffu, incl, own);
-            const int o_area = __shfl_sync(0xffffffffu, area, own);
-            const int o_x0 = __shfl_sync(0xffffffffu, x0, own);
-            const int o_y0 = __shfl_sync(0xffffffffu, y0, own);
-            const int o_w = __shfl_sync(0xffffffffu, wdt, own);
-            const int o_bin = __shfl_sync(0xffffffffu, bin, own);
-            const uint32_t o_zb = __shfl_sync(0xffffffffu, zb, own);
-            const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, own);
-            if (c < total) {
-                const int k = c - (o_incl - o_area);
-                const int ty = o_y0 + k / o_w, tx = o_x0 + k - (k / o_w) * o_w;
-                const int r = s_rank[ty * Tx + tx];
-                if (r >= 0) {
-                    const int64_t p = atomicAdd(cursor + (int64_t)r * kDepthBins + o_bin, 1);
-                    if (p < capacity) keys[p] = ((uint64_t)o_zb << 32) | o_rec;
+            for (int u = 0; u < kU; ++u) {
+                const int c = c0 + u * 32 + lane;
+                int l = 0, h = 31;
+#pragma unroll
+                for (int step = 0; step < 5; ++step) {
+                    const int mid = (l + h) >> 1;
+                    const int pm = __shfl_sync(0xffffffffu, incl, mid);
+                    if (pm > c) h = mid; else l = mid + 1;
+                }
+                const int own = l;
+                const int o_incl = __shfl_sync(0xffffffffu, incl, own);
+                const int o_area = __shfl_sync(0xffffffffu, area, own);
+                const int o_x0 = __shfl_sync(0xffffffffu, x0, own);
+                const int o_y0 = __shfl_sync(0xffffffffu, y0, own);
+                const int o_w = __shfl_sync(0xffffffffu, wdt, own);
+                const int o_bin = __shfl_sync(0xffffffffu, bin, own);
+                const uint32_t o_zb = __shfl_sync(0xffffffffu, zb, own);
+                const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, own);
+                sub[u] = -1;
+                if (c < total) {
+                    const int k = c - (o_incl - o_area);
+                    const int q = k / o_w;
+                    const int r = s_rank[(o_y0 + q) * Tx + o_x0 + (k - q * o_w)];
+                    if (r >= 0) {
+                        sub[u] = (int64_t)r * kDepthBins + o_bin;
+                        key[u] = ((uint64_t)o_zb << 32) | o_rec;
+                    }
                 }
             }
+            int64_t p[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = key[u];
         }
     }
 }
