@@ -130,8 +130,12 @@ def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-FWD_FLOP_PER_EVAL = 24   # power (11), exp (2), alpha (2), test (2), weight and colour (7)
-BWD_FLOP_PER_EVAL = 24   # the same recomputation, T recovery, colour behind
+# Algorithmic FP32 work per (pixel, list entry) evaluation: offsets (2), exponent
+# (9), exp (1), alpha and clamp (2), then forward: transmittance test (2), weight
+# (1), colour (6) = 21; backward (static entry): 1 - alpha and T recovery (2),
+# weight (1), colour behind (6) = 23 (an active entry adds 32 for its gradient).
+FWD_FLOP_PER_EVAL = 21
+BWD_FLOP_PER_EVAL = 23
 
 
 def setup_workload(args, seed):
