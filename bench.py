@@ -138,6 +138,23 @@ FWD_FLOP_PER_EVAL = 21
 BWD_FLOP_PER_EVAL = 23
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of `x` over all ranks (the whole job's time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, max_ms: float) -> float:
+    """Iterations of all ranks per second of the slowest rank (weak scaling:
+    every rank runs its own update)."""
+    return world * steps / (max_ms / 1e3)
+
+
 def setup_workload(args, seed):
     from paper_2506_21117_gb300 import synthetic as S
     return S.workload_large(n=args.n, n_views=args.views, width=args.width, height=args.height,
@@ -250,11 +267,7 @@ def run_ours(args, rank, world):
     end.record()
     torch.cuda.synchronize()
     clk = clocks.stop(t_wall0, time.time())
-    total_ms = start.elapsed_time(end)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(start.elapsed_time(end), dev)
     bt.check_status()
     stage_ms = {s: sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
                 for i, s in enumerate(stages)}
@@ -271,7 +284,7 @@ def run_ours(args, rank, world):
     P_act = tiles_on * 256
 
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, args.steps, total_ms)
     hbm_peak, peak_kind, sm_max = load_peaks()
     # algorithmic bytes per stage launch (design notes give the derivation)
     bytes_stage = {
