@@ -138,6 +138,35 @@ FWD_FLOP_PER_EVAL = 21
 BWD_FLOP_PER_EVAL = 23
 
 
+PROFILE_OF_STAGE = {"render_backward": ("render_bwd_1M_4x1080p.md", "csrc/render_bwd.cu"),
+                    "render_forward": ("render_fwd_1M_4x1080p.md", "csrc/render_fwd.cu")}
+
+
+def profiled_traffic(stage: str, args):
+    """DRAM bytes per launch of a stage's kernel from the committed ncu summary,
+    only if the summary was taken on this workload and on the current kernel
+    source (else None)."""
+    import hashlib
+    default = (args.n, args.width, args.height, args.views, args.fraction) == \
+        (1_000_000, 1920, 1080, 4, 0.05)
+    if stage not in PROFILE_OF_STAGE or not default:
+        return None
+    md, src = PROFILE_OF_STAGE[stage]
+    try:
+        text = open(os.path.join(ROOT, "profiles", md)).read()
+        m = hashlib.sha256()
+        for f in (src, "csrc/common.cuh"):
+            m.update(open(os.path.join(ROOT, "paper_2506_21117_gb300", f), "rb").read())
+        if f"source_sha256_16: {m.hexdigest()[:16]}" not in text:
+            return None
+        for line in text.splitlines():
+            if line.startswith("dram_bytes_per_launch:"):
+                return int(line.split(":")[1])
+    except OSError:
+        return None
+    return None
+
+
 def max_over_ranks(x: float, device=None) -> float:
     """The largest value of `x` over all ranks (the whole job's time)."""
     import torch
@@ -298,7 +327,8 @@ def run_ours(args, rank, world):
         flops = evals * (FWD_FLOP_PER_EVAL if dominant == "render_forward" else BWD_FLOP_PER_EVAL)
         ach = flops / (stage_ms[dominant] * 1e-3) / 1e12
         roof = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": ach / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": ach / alu_peak,
+                "traffic": profiled_traffic(dominant, args),
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock",
                 "units_per_launch": evals, "unit_work": "(pixel, list entry) evaluations"}
     else:
