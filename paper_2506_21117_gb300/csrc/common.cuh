@@ -216,13 +216,29 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int degree, 
     Y[15] = -0.5900435899266435f * x * (xx - 3.0f * yy);
 }
 
-// Alpha of one (pixel, Gaussian) pair. The forward and backward kernels call
-// this one function so both take identical skip decisions. Returns the
-// exponent; alpha is min(0.99, opacity * G).
-__device__ __forceinline__ float pair_power(float dx, float dy, float A, float B, float C) {
-    // -1/2 (A dx^2 + C dy^2) - B dx dy with an explicit rounding order.
-    const float q = __fmaf_rn(C * dy, dy, A * dx * dx);
-    return __fmaf_rn(-B * dx, dy, -0.5f * q);
+// Alpha of one (pixel, Gaussian) pair, as the forward and backward kernels
+// both compute it (so they take identical skip decisions). The conic of a
+// staged record is pre-scaled so the exponent comes out in base 2:
+//   a2 = -A/2 log2(e),  b2 = -B log2(e),  c2 = -C/2 log2(e),
+//   power2 = a2 dx^2 + b2 dx dy + c2 dy^2 = power * log2(e),  G = 2^power2,
+// evaluated as dx (a2 dx + b2 dy) + c2 dy^2, with t = a2 dx shared by the two
+// pixels of a thread (they lie in the same column).
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float4 stage_conic_a(float4 r0) {  // (u, v, A, B) -> (u, v, a2, b2)
+    return make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
+}
+__device__ __forceinline__ float4 stage_conic_b(float4 r1) {  // (C, o, r, g) -> (c2, o, r, g)
+    return make_float4(-0.5f * kLog2e * r1.x, r1.y, r1.z, r1.w);
+}
+__device__ __forceinline__ float pair_power2(float dx, float t, float dy, float b2, float c2) {
+    return __fmaf_rn(c2 * dy, dy, dx * __fmaf_rn(b2, dy, t));
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
 constexpr float kAlphaMin = 1.0f / 255.0f;

@@ -33,26 +33,29 @@ struct BwdPixel {
 
 // One list entry at one pixel: recover T in front of the entry, update the
 // colour behind, and (if `active`) add the entry's 2D gradient to gr[].
-__device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, const float4& a, const float4& bb,
-                                          float cb, bool active, float* gr) {
+// a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
+__device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float t,
+                                          const float4& a, const float4& bb, float cb, bool active,
+                                          float* gr) {
     if (!(p.inside && pos < p.last)) return false;
-    const float dx = p.fx - a.x, dy = p.fy - a.y;
-    const float power = pair_power(dx, dy, a.z, a.w, bb.x);
-    if (power > 0.0f) return false;
-    const float G = __expf(power);
+    const float dy = p.fy - a.y;
+    const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
+    if (power2 > 0.0f) return false;
+    const float G = ex2_approx(power2);
     const float alpha = fminf(kAlphaMax, bb.y * G);
     if (alpha < kAlphaMin) return false;
     const float inv_om = __fdividef(1.0f, 1.0f - alpha);
     p.T *= inv_om;
     const float w = alpha * p.T;
     if (active) {
+        const float A = -2.0f * kLn2 * a.z, B = -kLn2 * a.w, C = -2.0f * kLn2 * bb.x;
         const float dLda = p.g0 * (bb.z * p.T - p.S0 * inv_om) +
                            p.g1 * (bb.w * p.T - p.S1 * inv_om) +
                            p.g2 * (cb * p.T - p.S2 * inv_om);
         const bool clamped = bb.y * G > kAlphaMax;
         const float dpow = clamped ? 0.f : dLda * alpha;
-        gr[0] += dpow * (a.z * dx + a.w * dy);
-        gr[1] += dpow * (bb.x * dy + a.w * dx);
+        gr[0] += dpow * (A * dx + B * dy);
+        gr[1] += dpow * (C * dy + B * dx);
         gr[2] += -0.5f * dx * dx * dpow;
         gr[3] += -dx * dy * dpow;
         gr[4] += -0.5f * dy * dy * dpow;
@@ -137,8 +140,8 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
             for (int i = threadIdx.x; i < nb; i += kBwdThreads) {
                 const float4* rec = reinterpret_cast<const float4*>(
                     records + vals[(int64_t)(start + lo + i) * vals_stride]);
-                s_a[i] = rec[0];
-                s_b[i] = rec[1];
+                s_a[i] = stage_conic_a(rec[0]);
+                s_b[i] = stage_conic_b(rec[1]);
                 const float4 c = rec[2];
                 s_c[i] = c.x;
                 s_slot[i] = __float_as_int(c.y);
@@ -155,8 +158,10 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     float gr[kGradComps];
 #pragma unroll
                     for (int c = 0; c < kGradComps; ++c) gr[c] = 0.f;
-                    const bool c0 = bwd_entry(p0, lo + k, a, bb, cb, active, gr);
-                    const bool c1 = bwd_entry(p1, lo + k, a, bb, cb, active, gr);
+                    const float dx = p0.fx - a.x;
+                    const float t = a.z * dx;
+                    const bool c0 = bwd_entry(p0, lo + k, dx, t, a, bb, cb, active, gr);
+                    const bool c1 = bwd_entry(p1, lo + k, dx, t, a, bb, cb, active, gr);
                     if (active) {
                         any_active = true;
                         if (__any_sync(0xffffffffu, c0 || c1)) {

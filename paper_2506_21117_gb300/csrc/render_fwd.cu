@@ -33,17 +33,18 @@ struct PixelState {
 __device__ __forceinline__ void stage_record(FwdSmem& sm, int i, const ClsProjected* records,
                                              uint32_t rec) {
     const float4* r = reinterpret_cast<const float4*>(records + rec);
-    sm.a[i] = r[0];
-    sm.b[i] = r[1];
+    sm.a[i] = stage_conic_a(r[0]);
+    sm.b[i] = stage_conic_b(r[1]);
     sm.c[i] = r[2].x;
 }
 
-__device__ __forceinline__ void composite_one(const float4& a, const float4& bb, float cb,
-                                              uint32_t pos, float fx, float fy, PixelState& ps) {
+__device__ __forceinline__ void composite_one(float dx, float t, float dy, const float4& a,
+                                              const float4& bb, float cb, uint32_t pos,
+                                              PixelState& ps) {
     if (ps.done) return;
-    const float power = pair_power(fx - a.x, fy - a.y, a.z, a.w, bb.x);
-    if (power > 0.0f) return;
-    const float alpha = fminf(kAlphaMax, bb.y * __expf(power));
+    const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
+    if (power2 > 0.0f) return;
+    const float alpha = fminf(kAlphaMax, bb.y * ex2_approx(power2));
     if (alpha < kAlphaMin) return;
     const float test_T = ps.T * (1.0f - alpha);
     if (test_T < kTMin) {
@@ -58,7 +59,8 @@ __device__ __forceinline__ void composite_one(const float4& a, const float4& bb,
     ps.last = pos + 1;
 }
 
-// Composite the nb staged records (list positions pos0 ..) into two pixels.
+// Composite the nb staged records (list positions pos0 ..) into two pixels of
+// one column.
 __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int nb, uint32_t pos0, float fx,
                                                 float fy0, float fy1, PixelState& p0,
                                                 PixelState& p1) {
@@ -66,8 +68,10 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int nb, uint3
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
-        composite_one(a, bb, cb, pos0 + k, fx, fy0, p0);
-        composite_one(a, bb, cb, pos0 + k, fx, fy1, p1);
+        const float dx = fx - a.x;
+        const float t = a.z * dx;
+        composite_one(dx, t, fy0 - a.y, a, bb, cb, pos0 + k, p0);
+        composite_one(dx, t, fy1 - a.y, a, bb, cb, pos0 + k, p1);
     }
 }
 
