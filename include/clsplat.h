@@ -230,8 +230,28 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
                         ClsProjected* records, uint8_t* tile_active, int32_t* active_tiles,
                         int32_t* n_active_tiles_dev, uint64_t* keys, uint32_t* vals,
                         int64_t capacity, int64_t* n_pairs_dev, uint32_t* ranges,
-                        uint32_t* bin_offsets, int32_t* status_dev, void* workspace,
-                        size_t workspace_bytes, cls_stream_t stream);
+                        uint32_t* bin_offsets, const uint8_t* bin_cut, int32_t* status_dev,
+                        void* workspace, size_t workspace_bytes, cls_stream_t stream);
+
+/* Speculative depth cut (bucketed layout). With bin_cut != NULL (uint8
+ * [total_tiles], the last depth bin to emit per global tile id), pairs of
+ * deeper bins are counted and given their slots in bin_offsets but not
+ * written. cls_render_forward with cut_in = bin_cut stops each tile at its
+ * cut, records in cut_out the last bin the tile needed plus a margin (the cut
+ * of the next iteration), and lists in `trunc` every tile that ran out of
+ * emitted bins before all its pixels saturated (its outputs are not written).
+ * cls_complete_truncated then writes the missing pairs of those tiles (same
+ * workspace as the preceding cls_project_and_bin call, unchanged), and a
+ * second cls_render_forward over the listed tiles (active_tiles = trunc,
+ * n_active_tiles_dev = trunc_count, list_ranks = trunc + trunc_cap, cut_in =
+ * NULL) renders them completely. The result equals rendering without a cut.
+ *   trunc  int32 [3 * trunc_cap]: tile ids, their active-tile ranks, old cuts
+ *   trunc_cap >= total_tiles; trunc_count device int32 (caller zeroes it) */
+int cls_complete_truncated(const ClsView* views_dev, const ClsBatchInfo* info,
+                           const ClsProjected* records, uint64_t* keys, int64_t capacity,
+                           const int32_t* trunc, const int32_t* trunc_count, int64_t trunc_cap,
+                           int32_t* work_counter, void* workspace, size_t workspace_bytes,
+                           cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Per-tile depth sort of the bucketed layout (Supp. "Local Optimization
@@ -286,7 +306,9 @@ int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* 
  * back to lazy_keys, larger bins must already be sorted (cls_sort_tiles with
  * min_bin = CLS_LAZY_MAX_BIN + 1); bins behind the depth at which every pixel
  * of the tile stopped are left unsorted (the backward pass never reads them).
- * vals/vals_stride are ignored in that mode.
+ * vals/vals_stride are ignored in that mode. list_ranks (optional) gives the
+ * active-tile rank of each listed tile (default: its position in the list);
+ * cut_in/cut_out/trunc: see cls_complete_truncated (all may be NULL).
  * Outputs at the view's pix_base (pixels of inactive tiles are not written):
  *   image      [3][H][W] per view (planar), may be NULL
  *   T_final    [H][W], n_contrib [H][W] (one past the last list position
@@ -302,7 +324,10 @@ int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
                        const ClsProjected* records, const uint32_t* vals, int32_t vals_stride,
                        const uint32_t* ranges, const int32_t* active_tiles,
                        const int32_t* n_active_tiles_dev, uint64_t* lazy_keys,
-                       const uint32_t* bin_offsets, const float* bg, const float* target,
+                       const uint32_t* bin_offsets, const int32_t* list_ranks,
+                       const uint8_t* cut_in, uint8_t* cut_out, int32_t* trunc,
+                       int32_t* trunc_count, int64_t trunc_cap, const float* bg,
+                       const float* target,
                        int32_t loss_mode, float* image, float* T_final, int32_t* n_contrib,
                        float* dL_dimage, float* loss_per_scene, int32_t* work_counter,
                        cls_stream_t stream);

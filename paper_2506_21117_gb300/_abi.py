@@ -74,13 +74,14 @@ SIGNATURES = {
     "cls_project_workspace_size": (SZ, [P]),
     "cls_bin_offsets_size": (SZ, [P]),
     "cls_project_and_bin": (C.c_int, [P, P, P, I32, I32, P, P, P, P, P, P, I64, P, P, P, P, P,
-                                      SZ, P]),
+                                      P, SZ, P]),
+    "cls_complete_truncated": (C.c_int, [P, P, P, P, I64, P, P, I64, P, P, SZ, P]),
     "cls_sort_tiles_workspace_size": (SZ, [I64, I32]),
     "cls_sort_tiles": (C.c_int, [P, P, P, P, I64, I64, I32, P, P, SZ, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
     "cls_sort_keys": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, P]),
-    "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, I32, P, P, P, P, P,
-                                     P, P]),
+    "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, I64, P, P,
+                                     I32, P, P, P, P, P, P, P]),
     "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P]),
     "cls_adam_workspace_size": (SZ, [I32]),
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
@@ -172,12 +173,19 @@ def cls_bin_offsets_size(info) -> int:
 
 def cls_project_and_bin(scenes_dev, views_dev, info, project_mode, layout, records, tile_active,
                         active_tiles, n_active_tiles_dev, keys, vals, capacity, n_pairs_dev,
-                        ranges, bin_offsets, status_dev, workspace, workspace_bytes,
+                        ranges, bin_offsets, bin_cut, status_dev, workspace, workspace_bytes,
                         stream) -> int:
     return load().cls_project_and_bin(scenes_dev, views_dev, C.byref(info), project_mode, layout,
                                       records, tile_active, active_tiles, n_active_tiles_dev,
                                       keys, vals, capacity, n_pairs_dev, ranges, bin_offsets,
-                                      status_dev, workspace, workspace_bytes, stream)
+                                      bin_cut, status_dev, workspace, workspace_bytes, stream)
+
+
+def cls_complete_truncated(views_dev, info, records, keys, capacity, trunc, trunc_count,
+                           trunc_cap, work_counter, workspace, workspace_bytes, stream) -> int:
+    return load().cls_complete_truncated(views_dev, C.byref(info), records, keys, capacity, trunc,
+                                         trunc_count, trunc_cap, work_counter, workspace,
+                                         workspace_bytes, stream)
 
 
 LAZY_MAX_BIN = 1024
@@ -205,12 +213,13 @@ def cls_sort_keys(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bit
 
 
 def cls_render_forward(views_dev, info, records, vals, vals_stride, ranges, active_tiles,
-                       n_active_tiles_dev, lazy_keys, bin_offsets, bg, target, loss_mode, image,
-                       T_final, n_contrib, dL_dimage, loss_per_scene, work_counter,
-                       stream) -> int:
+                       n_active_tiles_dev, lazy_keys, bin_offsets, list_ranks, cut_in, cut_out,
+                       trunc, trunc_count, trunc_cap, bg, target, loss_mode, image, T_final,
+                       n_contrib, dL_dimage, loss_per_scene, work_counter, stream) -> int:
     bg3 = (C.c_float * 3)(*bg)
     return load().cls_render_forward(views_dev, C.byref(info), records, vals, vals_stride, ranges,
                                      active_tiles, n_active_tiles_dev, lazy_keys, bin_offsets,
+                                     list_ranks, cut_in, cut_out, trunc, trunc_count, trunc_cap,
                                      bg3, target, loss_mode,
                                      image, T_final, n_contrib, dL_dimage, loss_per_scene,
                                      work_counter, stream)

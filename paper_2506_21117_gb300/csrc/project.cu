@@ -438,12 +438,16 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                      uint64_t* __restrict__ keys, int64_t capacity,
                      const uint32_t* __restrict__ work_list,
-                     const int32_t* __restrict__ work_count) {
-    extern __shared__ int32_t s_rank[];
+                     const int32_t* __restrict__ work_count, const uint8_t* __restrict__ cut) {
+    extern __shared__ int32_t s_rank[];  // rank of each tile of the view; then its depth cut
     const ClsView& view = views[blockIdx.y];
     const int Tx = view.tiles_x;
-    for (int i = threadIdx.x; i < Tx * view.tiles_y; i += kBinBlock)
+    const int nt = Tx * view.tiles_y;
+    uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_rank + nt);
+    for (int i = threadIdx.x; i < nt; i += kBinBlock) {
         s_rank[i] = tile_rank[view.tile_base + i];
+        s_cut[i] = cut ? cut[view.tile_base + i] : (uint8_t)(kDepthBins - 1);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int n = work_count[blockIdx.y];
@@ -498,8 +502,9 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                 if (c < total) {
                     const int k = c - (o_incl - o_area);
                     const int q = k / o_w;
-                    const int r = s_rank[(o_y0 + q) * Tx + o_x0 + (k - q * o_w)];
-                    if (r >= 0) {
+                    const int cell = (o_y0 + q) * Tx + o_x0 + (k - q * o_w);
+                    const int r = s_rank[cell];
+                    if (r >= 0 && o_bin <= (int)s_cut[cell]) {
                         sub[u] = (int64_t)r * kDepthBins + o_bin;
                         key[u] = ((uint64_t)o_zb << 32) | o_rec;
                     }
@@ -511,6 +516,52 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
 #pragma unroll
             for (int u = 0; u < kU; ++u)
                 if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = key[u];
+        }
+    }
+}
+
+// Completion of tiles whose depth cut was too shallow: every pair-producing
+// Gaussian of the tile's view is tested against the tile and, if its depth bin
+// lies beyond the old cut, claims a slot in its bucket. Work items are (tile,
+// chunk of the view's list), taken from a counter.
+constexpr int kCompleteChunks = 64;
+
+__global__ void __launch_bounds__(256)
+complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
+                      const ClsProjected* __restrict__ records, const uint32_t* __restrict__ zmin,
+                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
+                      uint64_t* __restrict__ keys, int64_t capacity,
+                      const uint32_t* __restrict__ work_list,
+                      const int32_t* __restrict__ work_count, const int32_t* __restrict__ trunc,
+                      const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
+                      int* __restrict__ item_counter) {
+    __shared__ int s_item;
+    const int n_items = (int)min((int64_t)*trunc_count, trunc_cap) * kCompleteChunks;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int e = item / kCompleteChunks, chunk = item - e * kCompleteChunks;
+        const int tile = trunc[e], rank = trunc[trunc_cap + e], old_cut = trunc[2 * trunc_cap + e];
+        const int v = view_of_tile(views, n_views, tile);
+        const ClsView& view = views[v];
+        const int local = tile - view.tile_base;
+        const int ty = local / view.tiles_x, tx = local - ty * view.tiles_x;
+        const int n = work_count[v];
+        const int per = (n + kCompleteChunks - 1) / kCompleteChunks;
+        const int a = chunk * per, b = min(n, a + per);
+        for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
+            const uint32_t rec = (uint32_t)(view.rec_base + work_list[view.rec_base + i]);
+            int x0, x1, y0, y1;
+            uint32_t zb;
+            if (!record_rect(view, records, rec, x0, x1, y0, y1, zb)) continue;
+            if (tx < x0 || tx > x1 || ty < y0 || ty > y1) continue;
+            const int bin = depth_bin(zb, zmin[v], zmax[v]);
+            if (bin <= old_cut) continue;
+            const int64_t p = atomicAdd(cursor + (int64_t)rank * kDepthBins + bin, 1);
+            if (p < capacity) keys[p] = ((uint64_t)zb << 32) | rec;
         }
     }
 }
@@ -621,8 +672,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                    int32_t* active_tiles, int32_t* n_active_tiles_dev,
                                    uint64_t* keys, uint32_t* vals, int64_t capacity,
                                    int64_t* n_pairs_dev, uint32_t* ranges, uint32_t* bin_offsets,
-                                   int32_t* status_dev, void* workspace, size_t workspace_bytes,
-                                   cls_stream_t stream) {
+                                   const uint8_t* bin_cut, int32_t* status_dev, void* workspace,
+                                   size_t workspace_bytes, cls_stream_t stream) {
     if (!info || !scenes_dev || !views_dev || !records || !tile_active || !active_tiles ||
         !n_active_tiles_dev || !n_pairs_dev || !status_dev || !workspace || capacity < 0 ||
         (project_mode != 0 && project_mode != 1) || (layout != 0 && layout != 1) ||
@@ -657,7 +708,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                              200 * 1024);
         g_max_view_tiles_checked = 1;
     }
-    if (layout == 1 && max_view_tiles * 4 > 200 * 1024) return CLS_ERR_INVALID_ARG;
+    if (layout == 1 && max_view_tiles * 5 > 200 * 1024) return CLS_ERR_INVALID_ARG;
 
     if (project_mode == 0 && info->max_n > 0)
         project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
@@ -717,10 +768,33 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             sub_partials, capacity, bin_offsets, cursor, ranges);
         const unsigned emit_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
                                                       2048);
-        emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 4, s>>>(
+        emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 5, s>>>(
             views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count);
+            work_count, bin_cut);
     }
+    CLS_CHECK_LAUNCH();
+    return CLS_OK;
+}
+
+extern "C" int cls_complete_truncated(const ClsView* views_dev, const ClsBatchInfo* info,
+                                      const ClsProjected* records, uint64_t* keys,
+                                      int64_t capacity, const int32_t* trunc,
+                                      const int32_t* trunc_count, int64_t trunc_cap,
+                                      int32_t* work_counter, void* workspace,
+                                      size_t workspace_bytes, cls_stream_t stream) {
+    if (!views_dev || !info || !records || !keys || !trunc || !trunc_count || !work_counter ||
+        !workspace || workspace_bytes < cls_project_workspace_size(info) || trunc_cap <= 0)
+        return CLS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    const ProjLayout L = proj_layout(info);
+    char* ws = static_cast<char*>(workspace);
+    cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
+    complete_tiles_kernel<<<1024, 256, 0, s>>>(
+        views_dev, info->n_views, records, reinterpret_cast<uint32_t*>(ws + L.zmin),
+        reinterpret_cast<uint32_t*>(ws + L.zmax), reinterpret_cast<int32_t*>(ws + L.cursor), keys,
+        capacity, reinterpret_cast<uint32_t*>(ws + L.work_list),
+        reinterpret_cast<int32_t*>(ws + L.work_count), trunc, trunc_count, trunc_cap,
+        work_counter);
     CLS_CHECK_LAUNCH();
     return CLS_OK;
 }

@@ -11,6 +11,7 @@ constexpr int kFwdThreads = kTilePixels / 2;  // two pixels per thread: rows ly 
 constexpr int kLazyWin = kTilePixels;  // keys per rank-sorted window
 constexpr int kLazyMax = 1024;         // largest bin the renderer sorts itself
 constexpr int kBins = CLS_DEPTH_BINS;
+constexpr int kCutMargin = 4;          // depth bins emitted beyond last iteration's need
 
 struct FwdSmem {
     float4 a[kTilePixels];
@@ -21,6 +22,7 @@ struct FwdSmem {
     uint32_t off[kBins + 1];
     float red[kFwdThreads / 32];
     int tile;
+    int last_bin;
 };
 
 // Per-thread compositing state of one pixel.
@@ -120,7 +122,10 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                   int vals_stride, const uint32_t* __restrict__ ranges,
                   const int32_t* __restrict__ active_tiles,
                   const int32_t* __restrict__ n_active_tiles, uint64_t* __restrict__ lazy_keys,
-                  const uint32_t* __restrict__ bin_offsets, float bg0, float bg1, float bg2,
+                  const uint32_t* __restrict__ bin_offsets, const int32_t* __restrict__ list_ranks,
+                  const uint8_t* __restrict__ cut_in, uint8_t* __restrict__ cut_out,
+                  int32_t* __restrict__ trunc, int32_t* __restrict__ trunc_count,
+                  int64_t trunc_cap, float bg0, float bg1, float bg2,
                   const float* __restrict__ target, int loss_mode, float* __restrict__ image,
                   float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
                   float* __restrict__ dL_dimage, float* __restrict__ loss_per_scene,
@@ -147,6 +152,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
 
         PixelState p0{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py0 < H)};
         PixelState p1{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py1 < H)};
+        bool truncated = false;
         if (!lazy) {
             for (uint32_t b = start; b < end; b += kTilePixels) {
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
@@ -162,18 +168,24 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             // counting on the unique (depth, index) keys, written back for the
             // backward pass, and composited; bins behind the point where every
             // pixel saturated are never sorted. Larger bins were sorted before.
+            // Only bins up to cut_in[tile] were emitted; if the tile needs more,
+            // it is queued for completion and its outputs are left to the rerun.
+            const int rank = list_ranks ? list_ranks[t] : t;
+            const int limit = cut_in ? (int)cut_in[tile] : kBins - 1;
             for (int i = threadIdx.x; i <= kBins; i += kFwdThreads)
-                sm.off[i] = bin_offsets[(int64_t)t * kBins + i];
+                sm.off[i] = bin_offsets[(int64_t)rank * kBins + i];
+            if (threadIdx.x == 0) sm.last_bin = -1;
             __syncthreads();
             int bin = 0;
-            while (bin < kBins) {
+            while (bin <= limit) {
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
                 const uint32_t w0 = sm.off[bin];
                 int e = bin + 1;
-                while (e < kBins && sm.off[e + 1] - w0 <= (uint32_t)kLazyWin) ++e;
+                while (e <= limit && sm.off[e + 1] - w0 <= (uint32_t)kLazyWin) ++e;
                 const int n = (int)(sm.off[e] - w0);
                 bin = e;
                 if (n == 0) continue;
+                if (threadIdx.x == 0) sm.last_bin = e - 1;
                 const bool here = n <= kLazyMax;
                 if (here) {
                     for (int i = threadIdx.x; i < n; i += kFwdThreads) sm.key[i] = lazy_keys[w0 + i];
@@ -198,6 +210,24 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                     __syncthreads();
                 }
             }
+            const bool all_done = __syncthreads_count(p0.done && p1.done) == kFwdThreads;
+            truncated = !all_done && limit < kBins - 1 && sm.off[limit + 1] < sm.off[kBins];
+            if (threadIdx.x == 0) {
+                if (truncated) {
+                    const int slot = atomicAdd(trunc_count, 1);
+                    if (slot < trunc_cap) {
+                        trunc[slot] = tile;
+                        trunc[trunc_cap + slot] = rank;
+                        trunc[2 * trunc_cap + slot] = limit;
+                    }
+                } else if (cut_out) {
+                    cut_out[tile] = (uint8_t)min(kBins - 1, max(sm.last_bin, 0) + kCutMargin);
+                }
+            }
+        }
+        if (truncated) {  // uniform over the block; the completion rerun writes this tile
+            __syncthreads();
+            continue;
         }
 
         float lsum = 0.0f;
@@ -229,13 +259,16 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
                                   const ClsProjected* records, const uint32_t* vals,
                                   int32_t vals_stride, const uint32_t* ranges, const int32_t* active_tiles,
                                   const int32_t* n_active_tiles_dev, uint64_t* lazy_keys,
-                                  const uint32_t* bin_offsets, const float* bg,
+                                  const uint32_t* bin_offsets, const int32_t* list_ranks,
+                                  const uint8_t* cut_in, uint8_t* cut_out, int32_t* trunc,
+                                  int32_t* trunc_count, int64_t trunc_cap, const float* bg,
                                   const float* target, int32_t loss_mode, float* image,
                                   float* T_final, int32_t* n_contrib, float* dL_dimage,
                                   float* loss_per_scene, int32_t* work_counter,
                                   cls_stream_t stream) {
     if (!views_dev || !info || !records ||
         (bin_offsets ? !lazy_keys : (!vals || (vals_stride != 1 && vals_stride != 2))) ||
+        (cut_in && (!bin_offsets || !trunc || !trunc_count || trunc_cap < info->total_tiles)) ||
         !ranges || !active_tiles || !n_active_tiles_dev ||
         !bg || !T_final || !n_contrib || !work_counter || loss_mode < 0 || loss_mode > 2 ||
         (loss_mode != 0 && (!target || !dL_dimage)) || info->n_views <= 0 ||
@@ -256,7 +289,8 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_fwd_kernel<<<blocks, kFwdThreads, sizeof(FwdSmem), s>>>(
         views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
-        n_active_tiles_dev, lazy_keys, bin_offsets, bg[0],
+        n_active_tiles_dev, lazy_keys, bin_offsets, list_ranks, cut_in, cut_out, trunc,
+        trunc_count, trunc_cap, bg[0],
         bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
         work_counter);
     CLS_CHECK_LAUNCH();

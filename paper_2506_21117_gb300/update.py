@@ -158,6 +158,11 @@ class Batch:
         self.counter = torch.zeros(4, dtype=torch.int32, device=dev)
         self.bin_offsets = torch.zeros(abi.cls_bin_offsets_size(info), dtype=torch.int32,
                                        device=dev)
+        # speculative depth cut per tile (bucketed + lazy): every bin at first
+        self.use_cut = self.lazy
+        self.cut = torch.full((info.total_tiles,), 255, dtype=torch.uint8, device=dev)
+        self.trunc = torch.zeros(3 * info.total_tiles, dtype=torch.int32, device=dev)
+        self.trunc_count = torch.zeros(1, dtype=torch.int32, device=dev)
         self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
                                    device=dev)
         self.adam_ws = torch.zeros(max(abi.cls_adam_workspace_size(S), 256), dtype=torch.uint8,
@@ -198,8 +203,8 @@ class Batch:
             _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, mode, b.layout, _ptr(b.records),
             _ptr(b.tile_active), _ptr(b.active_tiles), _ptr(b.n_active_tiles),
             _ptr(b.keys), _ptr(b.vals), b.capacity, _ptr(b.n_pairs), _ptr(b.ranges),
-            _ptr(b.bin_offsets), _ptr(b.status), _ptr(b.proj_ws), b.proj_ws.numel(),
-            b.stream()), "cls_project_and_bin")
+            _ptr(b.bin_offsets), _ptr(b.cut) if b.use_cut else None, _ptr(b.status),
+            _ptr(b.proj_ws), b.proj_ws.numel(), b.stream()), "cls_project_and_bin")
 
     def plan_capacity(self, slack: float = 1.5, extra: int = 1 << 16):
         """Count the pairs once (mode 0 projection, no keys) and size the key
@@ -247,10 +252,31 @@ class Batch:
         b = self
         if loss_mode:
             b.loss.zero_()
+        cut = b.use_cut
+        if cut:
+            b.trunc_count.zero_()
+        b._forward_call(loss_mode, bg, write_image, _ptr(b.active_tiles), _ptr(b.n_active_tiles),
+                        None, _ptr(b.cut) if cut else None, _ptr(b.cut) if cut else None)
+        if cut:
+            # tiles whose cut was too shallow: write their missing pairs, render again
+            cap = b.info.total_tiles
+            abi.check(abi.cls_complete_truncated(
+                _ptr(b.views_dev), b.info, _ptr(b.records), _ptr(b.keys), b.capacity,
+                _ptr(b.trunc), _ptr(b.trunc_count), cap, _ptr(b.counter) + 12, _ptr(b.proj_ws),
+                b.proj_ws.numel(), b.stream()), "cls_complete_truncated")
+            b._forward_call(loss_mode, bg, write_image, _ptr(b.trunc), _ptr(b.trunc_count),
+                            _ptr(b.trunc) + 4 * cap, None, _ptr(b.cut), rerun=True)
+
+    def _forward_call(self, loss_mode, bg, write_image, tiles, n_tiles, list_ranks, cut_in,
+                      cut_out, rerun=False):
+        b = self
+        cap = b.info.total_tiles
         abi.check(abi.cls_render_forward(
             _ptr(b.views_dev), b.info, _ptr(b.records), *b._sorted_vals(), _ptr(b.ranges),
-            _ptr(b.active_tiles), _ptr(b.n_active_tiles),
-            _ptr(b.keys) if b.lazy else None, _ptr(b.bin_offsets) if b.lazy else None, bg,
+            tiles, n_tiles, _ptr(b.keys) if b.lazy else None,
+            _ptr(b.bin_offsets) if b.lazy else None, list_ranks, cut_in, cut_out,
+            None if rerun or cut_in is None else _ptr(b.trunc),
+            None if rerun or cut_in is None else _ptr(b.trunc_count), cap, bg,
             _ptr(b.target) if loss_mode else None, loss_mode,
             _ptr(b.image) if write_image else None, _ptr(b.T_final), _ptr(b.n_contrib),
             _ptr(b.dL_dimage) if loss_mode else None, _ptr(b.loss) if loss_mode else None,
@@ -289,7 +315,8 @@ class Batch:
         stamp (2 if any Gaussian is active), tile mask, compaction, count,
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
         prefix, bucket counts, scan, offsets, emit (6). Sort: flat
-        hist + scan + passes (+ copy if odd) + ranges; bucketed 1. Forward 1,
+        hist + scan + passes (+ copy if odd) + ranges; bucketed 1 or 2.
+        Forward 1, or 3 with the depth cut (forward, completion, rerun);
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
         proj = active + 3 + (6 if self.layout == 1 else 3)
@@ -298,7 +325,8 @@ class Batch:
         else:
             passes = -(-self.info.key_bits // 8)
             sort = 3 + passes + passes % 2
-        return proj + sort + 1 + (1 + active // 2) + (1 + active // 2)
+        fwd = 3 if self.use_cut else 1
+        return proj + sort + fwd + (1 + active // 2) + (1 + active // 2)
 
     def check_status(self):
         code = int(self.status.item())

@@ -336,6 +336,45 @@ def test_autograd_function_matches_oracle_gradient():
     print(f"autograd.Function L2 gradients: worst error/bound {worst:.3f}, {excl} excluded")
 
 
+def test_depth_cut_and_completion_reproduce_full_emission():
+    """The speculative per-tile depth cut: forcing every cut to bin 0 makes
+    tiles run out of emitted pairs; completion and the rerun must give the same
+    image, transmittance, last contributors and loss as full emission, and the
+    same gradients up to float32 summation order."""
+    scene = S.uniform_scene(20000, 1, 31)
+    scene["log_scales"] += np.float32(1.0)
+    cams = S.ring_cameras(2, 4.0, 240, 160, angles=[0.3, 2.0])
+    targets = [S.random_image(c, 70 + j) for j, c in enumerate(cams)]
+    active = np.random.default_rng(31).uniform(size=20000) < 0.03
+    lu = _update(scene, cams, 1, targets=targets, active=active, loss="l1")
+    b = lu.batch
+
+    def snapshot():
+        A = lu.state.n_active
+        return (b.image.clone(), b.T_final.clone(), b.n_contrib.clone(), float(b.loss[0]),
+                b.grads[: A * lu.state.stride].clone())
+
+    full = snapshot()
+    b.cut.fill_(0)
+    lu.render_pass(with_backward=True, with_adam=False)
+    torch.cuda.synchronize()
+    b.check_status()
+    n_trunc = int(b.trunc_count.item())
+    cut = snapshot()
+    assert n_trunc > 10
+    for x, y in zip(full[:3], cut[:3]):
+        assert torch.equal(x, y)
+    assert cut[3] == pytest.approx(full[3], rel=1e-6)
+    torch.testing.assert_close(cut[4], full[4], rtol=1e-4, atol=1e-9)
+    # the learnt cuts are used on the next pass
+    assert int(b.cut.max()) > 0
+    lu.render_pass(with_backward=True, with_adam=False)
+    torch.cuda.synchronize()
+    again = snapshot()
+    assert torch.equal(again[0], full[0]) and torch.equal(again[2], full[2])
+    print(f"depth cut: {n_trunc} tiles completed after a forced cut of 0")
+
+
 # -------------------------------------------------------------------- Adam --
 
 def test_adam_step_matches_oracle_and_freezes_static_rows():
