@@ -265,12 +265,18 @@ int cls_complete_truncated(const ClsView* views_dev, const ClsBatchInfo* info,
  *   keys_alt    [capacity] scratch (used only for buckets above 4096 pairs)
  *   bin_offsets as written by cls_project_and_bin
  *   work_counter device int32 scratch (reset by the call)
- *   workspace   cls_sort_tiles_workspace_size(capacity, min_bin) bytes */
+ *   workspace   cls_sort_tiles_workspace_size(capacity, min_bin) bytes
+ * With the speculative depth cut (min_bin > 1 only): `cut` (with
+ * active_tiles) skips bins beyond each tile's cut, which are not emitted yet;
+ * `trunc` (see cls_complete_truncated) restricts the call to the completed
+ * tiles' bins beyond their old cut, to be run after cls_complete_truncated. */
 #define CLS_LAZY_MAX_BIN 1024
 size_t cls_sort_tiles_workspace_size(int64_t capacity, int32_t min_bin);
 int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offsets,
-                   const int32_t* n_active_tiles_dev, int64_t total_tiles, int64_t capacity,
-                   int32_t min_bin, int32_t* work_counter, void* workspace, size_t workspace_bytes,
+                   const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
+                   int64_t total_tiles, int64_t capacity, int32_t min_bin, const uint8_t* cut,
+                   const int32_t* trunc, const int32_t* trunc_count, int64_t trunc_cap,
+                   int32_t* work_counter, void* workspace, size_t workspace_bytes,
                    cls_stream_t stream);
 
 /* ------------------------------------------------------------------------

@@ -77,7 +77,7 @@ SIGNATURES = {
                                       P, SZ, P]),
     "cls_complete_truncated": (C.c_int, [P, P, P, P, I64, P, P, I64, P, P, SZ, P]),
     "cls_sort_tiles_workspace_size": (SZ, [I64, I32]),
-    "cls_sort_tiles": (C.c_int, [P, P, P, P, I64, I64, I32, P, P, SZ, P]),
+    "cls_sort_tiles": (C.c_int, [P, P, P, P, P, I64, I64, I32, P, P, P, I64, P, P, SZ, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
     "cls_sort_keys": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, P]),
     "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, I64, P, P,
@@ -195,11 +195,12 @@ def cls_sort_tiles_workspace_size(capacity, min_bin) -> int:
     return load().cls_sort_tiles_workspace_size(capacity, min_bin)
 
 
-def cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles, capacity, min_bin,
-                   work_counter, workspace, workspace_bytes, stream) -> int:
-    return load().cls_sort_tiles(keys, keys_alt, bin_offsets, n_active_tiles_dev, total_tiles,
-                                 capacity, min_bin, work_counter, workspace, workspace_bytes,
-                                 stream)
+def cls_sort_tiles(keys, keys_alt, bin_offsets, active_tiles, n_active_tiles_dev, total_tiles,
+                   capacity, min_bin, cut, trunc, trunc_count, trunc_cap, work_counter, workspace,
+                   workspace_bytes, stream) -> int:
+    return load().cls_sort_tiles(keys, keys_alt, bin_offsets, active_tiles, n_active_tiles_dev,
+                                 total_tiles, capacity, min_bin, cut, trunc, trunc_count,
+                                 trunc_cap, work_counter, workspace, workspace_bytes, stream)
 
 
 def cls_sort_workspace_size(capacity, key_bits) -> int:

@@ -235,14 +235,32 @@ sort_tiles_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
 }
 
 // Bins holding at least `min_bin` keys (the renderer sorts smaller ones).
+// With `cut`, bins beyond a tile's cut (not emitted yet) are skipped. With a
+// list of completed tiles (`trunc`), only their bins beyond the old cut are
+// taken.
 __global__ void collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
-                                    const int32_t* __restrict__ n_active, int min_bin,
-                                    uint2* __restrict__ list, int32_t* __restrict__ count,
-                                    int64_t list_cap) {
-    const int64_t ne = (int64_t)(*n_active) * kBinsPerTile;
+                                    const int32_t* __restrict__ n_active,
+                                    const int32_t* __restrict__ active_tiles,
+                                    const uint8_t* __restrict__ cut,
+                                    const int32_t* __restrict__ trunc,
+                                    const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
+                                    int min_bin, uint2* __restrict__ list,
+                                    int32_t* __restrict__ count, int64_t list_cap) {
+    const int64_t nt = trunc ? min((int64_t)*trunc_count, trunc_cap) : (int64_t)(*n_active);
+    const int64_t ne = nt * kBinsPerTile;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t a = bin_offsets[e], n = bin_offsets[e + 1] - a;
+        const int64_t t = e / kBinsPerTile;
+        const int b = (int)(e - t * kBinsPerTile);
+        int64_t rank = t;
+        if (trunc) {
+            rank = trunc[trunc_cap + t];
+            if (b <= trunc[2 * trunc_cap + t]) continue;
+        } else if (cut && b > (int)cut[active_tiles[t]]) {
+            continue;
+        }
+        const int64_t idx = rank * kBinsPerTile + b;
+        const uint32_t a = bin_offsets[idx], n = bin_offsets[idx + 1] - a;
         if (n >= (uint32_t)min_bin) {
             const int slot = atomicAdd(count, 1);
             if (slot < list_cap) list[slot] = make_uint2(a, n);
@@ -284,12 +302,17 @@ extern "C" size_t cls_sort_tiles_workspace_size(int64_t capacity, int32_t min_bi
 }
 
 extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offsets,
-                              const int32_t* n_active_tiles_dev, int64_t total_tiles,
-                              int64_t capacity, int32_t min_bin, int32_t* work_counter,
-                              void* workspace, size_t workspace_bytes, cls_stream_t stream) {
+                              const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
+                              int64_t total_tiles, int64_t capacity, int32_t min_bin,
+                              const uint8_t* cut, const int32_t* trunc,
+                              const int32_t* trunc_count, int64_t trunc_cap,
+                              int32_t* work_counter, void* workspace, size_t workspace_bytes,
+                              cls_stream_t stream) {
     if (!keys || !keys_alt || !bin_offsets || !n_active_tiles_dev || !work_counter ||
         total_tiles <= 0 || capacity < 0 || !workspace ||
-        workspace_bytes < cls_sort_tiles_workspace_size(capacity, min_bin))
+        workspace_bytes < cls_sort_tiles_workspace_size(capacity, min_bin) ||
+        (cut && !active_tiles) || (trunc && (!trunc_count || trunc_cap < total_tiles)) ||
+        ((cut || trunc) && min_bin <= 1))
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     if (g_tiles_blocks == 0) {
@@ -313,8 +336,9 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
         uint2* list = reinterpret_cast<uint2*>(static_cast<char*>(workspace) + 256);
         const int64_t cap = list_cap_for(capacity, min_bin);
         cudaMemsetAsync(count, 0, sizeof(int32_t), s);
-        collect_bins_kernel<<<1024, 256, 0, s>>>(bin_offsets, n_active_tiles_dev, min_bin, list,
-                                                 count, cap);
+        collect_bins_kernel<<<1024, 256, 0, s>>>(bin_offsets, n_active_tiles_dev, active_tiles,
+                                                 cut, trunc, trunc_count, trunc_cap, min_bin,
+                                                 list, count, cap);
         sort_bins_kernel<<<g_tiles_blocks, kTB, sizeof(TileSortSmem), s>>>(keys, keys_alt, list,
                                                                           count, cap, work_counter);
     }

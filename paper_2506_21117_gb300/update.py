@@ -232,16 +232,24 @@ class Batch:
             self.sort_ws = torch.empty(abi.cls_sort_workspace_size(capacity, self.info.key_bits),
                                        dtype=torch.uint8, device=dev)
 
+    def _sort_tiles(self, cut=False, after_completion=False):
+        b = self
+        cap = b.info.total_tiles
+        abi.check(abi.cls_sort_tiles(
+            _ptr(b.keys), _ptr(b.keys_alt), _ptr(b.bin_offsets), _ptr(b.active_tiles),
+            _ptr(b.n_active_tiles), cap, b.capacity, b.min_bin(),
+            _ptr(b.cut) if cut and not after_completion else None,
+            _ptr(b.trunc) if after_completion else None,
+            _ptr(b.trunc_count) if after_completion else None, cap, _ptr(b.counter) + 8,
+            _ptr(b.tiles_ws), b.tiles_ws.numel(), b.stream()), "cls_sort_tiles")
+
     def min_bin(self) -> int:
         return abi.LAZY_MAX_BIN + 1 if self.lazy else 1
 
     def sort(self):
         b = self
         if b.layout == 1:
-            abi.check(abi.cls_sort_tiles(_ptr(b.keys), _ptr(b.keys_alt), _ptr(b.bin_offsets),
-                                         _ptr(b.n_active_tiles), b.info.total_tiles, b.capacity,
-                                         b.min_bin(), _ptr(b.counter) + 8, _ptr(b.tiles_ws),
-                                         b.tiles_ws.numel(), b.stream()), "cls_sort_tiles")
+            b._sort_tiles(cut=b.use_cut)
             return
         abi.check(abi.cls_sort_keys(
             _ptr(b.keys), _ptr(b.vals), _ptr(b.keys_alt), _ptr(b.vals_alt), _ptr(b.n_pairs),
@@ -264,6 +272,7 @@ class Batch:
                 _ptr(b.views_dev), b.info, _ptr(b.records), _ptr(b.keys), b.capacity,
                 _ptr(b.trunc), _ptr(b.trunc_count), cap, _ptr(b.counter) + 12, _ptr(b.proj_ws),
                 b.proj_ws.numel(), b.stream()), "cls_complete_truncated")
+            b._sort_tiles(after_completion=True)  # large bins the completion filled
             b._forward_call(loss_mode, bg, write_image, _ptr(b.trunc), _ptr(b.trunc_count),
                             _ptr(b.trunc) + 4 * cap, None, _ptr(b.cut), rerun=True)
 
@@ -316,7 +325,8 @@ class Batch:
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
         prefix, bucket counts, scan, offsets, emit (6). Sort: flat
         hist + scan + passes (+ copy if odd) + ranges; bucketed 1 or 2.
-        Forward 1, or 3 with the depth cut (forward, completion, rerun);
+        Forward 1, or 5 with the depth cut (forward, completion, large-bin
+        collection and sort, rerun);
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
         proj = active + 3 + (6 if self.layout == 1 else 3)
@@ -325,7 +335,7 @@ class Batch:
         else:
             passes = -(-self.info.key_bits // 8)
             sort = 3 + passes + passes % 2
-        fwd = 3 if self.use_cut else 1
+        fwd = 5 if self.use_cut else 1
         return proj + sort + fwd + (1 + active // 2) + (1 + active // 2)
 
     def check_status(self):

@@ -336,16 +336,39 @@ def test_autograd_function_matches_oracle_gradient():
     print(f"autograd.Function L2 gradients: worst error/bound {worst:.3f}, {excl} excluded")
 
 
-def test_depth_cut_and_completion_reproduce_full_emission():
+def _slab_scene():
+    """A dense thin slab facing the camera (thousands of pairs per depth bin)
+    plus a few Gaussians spread in depth so the view's depth range is wide."""
+    slab = S.uniform_scene(30000, 1, 33)
+    rng = np.random.default_rng(33)
+    m = slab["means"].astype(np.float64)
+    m[:, 0] *= 0.3
+    m[:, 1] *= 0.3
+    m[:, 2] = rng.uniform(-1e-3, 1e-3, m.shape[0])
+    m[:500] = np.stack([rng.uniform(-2, 2, 500), rng.uniform(-1, 1, 500),
+                        rng.uniform(-3.0, 20.0, 500)], 1)
+    slab["means"] = m.astype(np.float32)
+    return slab
+
+
+@pytest.mark.parametrize("case", ["spread", "slab"])
+def test_depth_cut_and_completion_reproduce_full_emission(case):
     """The speculative per-tile depth cut: forcing every cut to bin 0 makes
-    tiles run out of emitted pairs; completion and the rerun must give the same
-    image, transmittance, last contributors and loss as full emission, and the
-    same gradients up to float32 summation order."""
-    scene = S.uniform_scene(20000, 1, 31)
-    scene["log_scales"] += np.float32(1.0)
-    cams = S.ring_cameras(2, 4.0, 240, 160, angles=[0.3, 2.0])
+    tiles run out of emitted pairs; completion (including bins above the
+    renderer's 1,024-key sorting limit, sorted after completion) and the rerun
+    must give the same image, transmittance, last contributors and loss as full
+    emission, and the same gradients up to float32 summation order."""
+    if case == "spread":
+        scene = S.uniform_scene(20000, 1, 31)
+        scene["log_scales"] += np.float32(1.0)
+        cams = S.ring_cameras(2, 4.0, 240, 160, angles=[0.3, 2.0])
+        active = np.random.default_rng(31).uniform(size=20000) < 0.03
+    else:
+        scene = _slab_scene()
+        cams = S.ring_cameras(1, 4.0, 160, 120, angles=[0.0])
+        active = np.zeros(30000, bool)
+        active[500::97] = True
     targets = [S.random_image(c, 70 + j) for j, c in enumerate(cams)]
-    active = np.random.default_rng(31).uniform(size=20000) < 0.03
     lu = _update(scene, cams, 1, targets=targets, active=active, loss="l1")
     b = lu.batch
 
@@ -355,6 +378,9 @@ def test_depth_cut_and_completion_reproduce_full_emission():
                 b.grads[: A * lu.state.stride].clone())
 
     full = snapshot()
+    if case == "slab":
+        sizes = np.diff(b.bin_offsets[: int(b.n_active_tiles.item()) * 256 + 1].cpu().numpy())
+        assert sizes.max() > 1024  # bins the renderer does not sort itself
     b.cut.fill_(0)
     lu.render_pass(with_backward=True, with_adam=False)
     torch.cuda.synchronize()
