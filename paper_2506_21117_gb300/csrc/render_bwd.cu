@@ -32,11 +32,11 @@ struct BwdPixel {
 };
 
 // One list entry at one pixel: recover T in front of the entry, update the
-// colour behind, and (if `active`) add the entry's 2D gradient to gr[].
-// a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
+// colour behind, and (for an active Gaussian) add the entry's 2D gradient to
+// gr[]. a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
+template <bool ACTIVE>
 __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float t,
-                                          const float4& a, const float4& bb, float cb, bool active,
-                                          float* gr) {
+                                          const float4& a, const float4& bb, float cb, float* gr) {
     if (!(p.inside && pos < p.last)) return false;
     const float dy = p.fy - a.y;
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
@@ -47,7 +47,7 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float 
     const float inv_om = __fdividef(1.0f, 1.0f - alpha);
     p.T *= inv_om;
     const float w = alpha * p.T;
-    if (active) {
+    if (ACTIVE) {
         const float A = -2.0f * kLn2 * a.z, B = -kLn2 * a.w, C = -2.0f * kLn2 * bb.x;
         const float dLda = p.g0 * (bb.z * p.T - p.S0 * inv_om) +
                            p.g1 * (bb.w * p.T - p.S1 * inv_om) +
@@ -68,6 +68,31 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float 
     p.S1 += bb.w * w;
     p.S2 += cb * w;
     return true;
+}
+
+// Warp reduce-scatter of eight values: after it, lane L holds the warp sum of
+// value (L >> 2) & 7 (butterfly halving: 4 + 2 + 1 exchanges, then two more to
+// finish the sum), 9 shuffles instead of 40.
+__device__ __forceinline__ float reduce8_scatter(const float* v, int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b4 ? v[i] : v[i + 4];
+        const float keep = b4 ? v[i + 4] : v[i];
+        w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b3 ? w[i] : w[i + 2];
+        const float keep = b3 ? w[i + 2] : w[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float y = (b2 ? x[1] : x[0]) + __shfl_xor_sync(0xffffffffu, b2 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(0xffffffffu, y, 2);
+    y += __shfl_xor_sync(0xffffffffu, y, 1);
+    return y;
 }
 
 __device__ __forceinline__ void bwd_load_pixel(BwdPixel& p, const ClsView& view, int px, int py,
@@ -155,29 +180,30 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const float4 bb = s_b[k];
                     const float cb = s_c[k];
                     const bool active = s_slot[k] >= 0;  // uniform over the block
+                    const float dx = p0.fx - a.x;
+                    const float t = a.z * dx;
+                    if (!active) {
+                        bwd_entry<false>(p0, lo + k, dx, t, a, bb, cb, nullptr);
+                        bwd_entry<false>(p1, lo + k, dx, t, a, bb, cb, nullptr);
+                        continue;
+                    }
+                    any_active = true;
                     float gr[kGradComps];
 #pragma unroll
                     for (int c = 0; c < kGradComps; ++c) gr[c] = 0.f;
-                    const float dx = p0.fx - a.x;
-                    const float t = a.z * dx;
-                    const bool c0 = bwd_entry(p0, lo + k, dx, t, a, bb, cb, active, gr);
-                    const bool c1 = bwd_entry(p1, lo + k, dx, t, a, bb, cb, active, gr);
-                    if (active) {
-                        any_active = true;
-                        if (__any_sync(0xffffffffu, c0 || c1)) {
+                    const bool c0 = bwd_entry<true>(p0, lo + k, dx, t, a, bb, cb, gr);
+                    const bool c1 = bwd_entry<true>(p1, lo + k, dx, t, a, bb, cb, gr);
+                    float* dst = &s_g[k - sub_lo][warp][0];
+                    if (__any_sync(0xffffffffu, c0 || c1)) {
+                        const float y = reduce8_scatter(gr, lane);
+                        float z = gr[8];
 #pragma unroll
-                            for (int c = 0; c < kGradComps; ++c) {
-                                float x = gr[c];
-#pragma unroll
-                                for (int o = 16; o > 0; o >>= 1)
-                                    x += __shfl_xor_sync(0xffffffffu, x, o);
-                                gr[c] = x;
-                            }
-                        }
-                        if (lane == 0) {
-#pragma unroll
-                            for (int c = 0; c < kGradComps; ++c) s_g[k - sub_lo][warp][c] = gr[c];
-                        }
+                        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+                        if ((lane & 3) == 0) dst[lane >> 2] = y;
+                        if (lane == 0) dst[8] = z;
+                    } else {
+                        if ((lane & 3) == 0) dst[lane >> 2] = 0.f;
+                        if (lane == 0) dst[8] = 0.f;
                     }
                 }
                 if (any_active) {  // uniform over the block
