@@ -287,9 +287,9 @@ def run_ours(args, rank, world):
         e[1].record()
         bt.sort()
         e[2].record()
-        bt.forward(lu.loss_mode, lu.bg, write_image=False)
+        bt.forward(lu.loss_mode, lu.bg)
         e[3].record()
-        bt.backward(lu.bg)
+        bt.backward()
         e[4].record()
         bt.adam(lu.lr)
         e[5].record()

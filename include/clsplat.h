@@ -132,6 +132,27 @@ typedef struct ClsProjected {
     int32_t radius;
 } ClsProjected;
 
+/* Static-prefix cache of one tile (16 bytes), kept by the caller across the
+ * iterations of one update (ClsTileCache [total_tiles], every byte 0xff at the
+ * start of an update, i.e. no tile cached). Static Gaussians are frozen during
+ * an update, so the compositing state of a pixel after the static Gaussians in
+ * front of every active Gaussian of its tile does not change between
+ * iterations. The prefix of a tile is the entries of its sorted list with
+ * bits(z) < zb; the pixel state after the prefix is kept in prefix_state /
+ * prefix_last (see cls_render_forward). cls_project_and_bin decides per active
+ * tile whether the cache still holds (every active Gaussian of the tile has
+ * bits(z) >= zb) or must be rebuilt (zb is then set a margin of 2^17 float
+ * ulps, about 1.6%, in front of the tile's nearest active Gaussian, and
+ * n_prefix to CLS_PREFIX_UNKNOWN); the forward pass writes the state and
+ * n_prefix of rebuilt tiles and last_active of every tile it renders. */
+typedef struct ClsTileCache {
+    uint32_t zb;          /* prefix boundary, bits of a positive float depth */
+    uint32_t n_prefix;    /* list entries in the prefix, or CLS_PREFIX_UNKNOWN */
+    uint32_t zmin_active; /* smallest bits(z) of the tile's active Gaussians */
+    int32_t last_active;  /* last list position of an active entry, -1 if none */
+} ClsTileCache;
+#define CLS_PREFIX_UNKNOWN 0xffffffffu
+
 /* Floats per parameter row for an SH degree (0..3); -1 if out of range. */
 int32_t cls_row_stride(int32_t sh_degree);
 
@@ -221,7 +242,13 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  *                             (offsets and ranges are clamped to capacity).
  * Tile rectangle: radius r = ceil(3 sqrt(lambda_max(Sigma'))), tiles
  * floor((u - r)/16) .. floor((u + r)/16) clamped to the grid (same for v).
- * records [total_records] ClsProjected. */
+ * records [total_records] ClsProjected.
+ * tile_cache [total_tiles] (required): the static-prefix decision of every
+ * active tile (see ClsTileCache). prefix_mode 0 rebuilds every active tile's
+ * prefix (for callers whose static Gaussians may change between calls);
+ * prefix_mode 1 keeps a tile's cached prefix while it holds, and the bucketed
+ * layout then does not write the pairs of depth bins that lie entirely in
+ * front of the tile's boundary (their slots stay in bin_offsets). */
 #define CLS_DEPTH_BINS 256
 size_t cls_project_workspace_size(const ClsBatchInfo* info);
 size_t cls_bin_offsets_size(const ClsBatchInfo* info); /* uint32 entries */
@@ -230,7 +257,8 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
                         ClsProjected* records, uint8_t* tile_active, int32_t* active_tiles,
                         int32_t* n_active_tiles_dev, uint64_t* keys, uint32_t* vals,
                         int64_t capacity, int64_t* n_pairs_dev, uint32_t* ranges,
-                        uint32_t* bin_offsets, const uint8_t* bin_cut, int32_t* status_dev,
+                        uint32_t* bin_offsets, const uint8_t* bin_cut,
+                        ClsTileCache* tile_cache, int32_t prefix_mode, int32_t* status_dev,
                         void* workspace, size_t workspace_bytes, cls_stream_t stream);
 
 /* Speculative depth cut (bucketed layout). With bin_cut != NULL (uint8
@@ -246,7 +274,8 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
  * n_active_tiles_dev = trunc_count, list_ranks = trunc + trunc_cap, cut_in =
  * NULL) renders them completely. The result equals rendering without a cut.
  *   trunc  int32 [3 * trunc_cap]: tile ids, their active-tile ranks, old cuts
- *   trunc_cap >= total_tiles; trunc_count device int32 (caller zeroes it) */
+ *   trunc_cap >= total_tiles; trunc_count device int32 (caller zeroes it)
+ * Bins in front of a cached prefix boundary stay unwritten here too. */
 int cls_complete_truncated(const ClsView* views_dev, const ClsBatchInfo* info,
                            const ClsProjected* records, uint64_t* keys, int64_t capacity,
                            const int32_t* trunc, const int32_t* trunc_count, int64_t trunc_cap,
@@ -269,15 +298,17 @@ int cls_complete_truncated(const ClsView* views_dev, const ClsBatchInfo* info,
  * With the speculative depth cut (min_bin > 1 only): `cut` (with
  * active_tiles) skips bins beyond each tile's cut, which are not emitted yet;
  * `trunc` (see cls_complete_truncated) restricts the call to the completed
- * tiles' bins beyond their old cut, to be run after cls_complete_truncated. */
+ * tiles' bins beyond their old cut, to be run after cls_complete_truncated.
+ * `tile_cache` (optional) skips bins that lie entirely in a tile's cached
+ * prefix, which are not emitted. */
 #define CLS_LAZY_MAX_BIN 1024
 size_t cls_sort_tiles_workspace_size(int64_t capacity, int32_t min_bin);
 int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offsets,
                    const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
                    int64_t total_tiles, int64_t capacity, int32_t min_bin, const uint8_t* cut,
                    const int32_t* trunc, const int32_t* trunc_count, int64_t trunc_cap,
-                   int32_t* work_counter, void* workspace, size_t workspace_bytes,
-                   cls_stream_t stream);
+                   const ClsTileCache* tile_cache, int32_t* work_counter, void* workspace,
+                   size_t workspace_bytes, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Stable LSD radix sort of the flat layout's (tile, depth) keys with their
@@ -315,8 +346,17 @@ int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* 
  * vals/vals_stride are ignored in that mode. list_ranks (optional) gives the
  * active-tile rank of each listed tile (default: its position in the list);
  * cut_in/cut_out/trunc: see cls_complete_truncated (all may be NULL).
+ * Static prefix (tile_cache, as decided by cls_project_and_bin): a tile whose
+ * cache holds starts from the kept pixel state at list position n_prefix; a
+ * tile to rebuild is composited from the front, and the state of each pixel on
+ * reaching the first entry with bits(z) >= zb (or at the end, if every pixel
+ * saturated before it) is written to
+ *   prefix_state [total_pixels][4] float: (T, C_r, C_g, C_b) after the
+ *                prefix, T negated if the pixel stopped inside the prefix
+ *   prefix_last  [total_pixels] int32: n_contrib after the prefix
+ * and n_prefix to the tile's cache. Both paths give the same result.
  * Outputs at the view's pix_base (pixels of inactive tiles are not written):
- *   image      [3][H][W] per view (planar), may be NULL
+ *   image      [3][H][W] per view (planar; required, read by the backward)
  *   T_final    [H][W], n_contrib [H][W] (one past the last list position
  *              composited, counted from the tile's range start)
  *   loss_mode  0 none, 1 L1, 2 L2 against `target` ([3][H][W] per view):
@@ -332,7 +372,8 @@ int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
                        const int32_t* n_active_tiles_dev, uint64_t* lazy_keys,
                        const uint32_t* bin_offsets, const int32_t* list_ranks,
                        const uint8_t* cut_in, uint8_t* cut_out, int32_t* trunc,
-                       int32_t* trunc_count, int64_t trunc_cap, const float* bg,
+                       int32_t* trunc_count, int64_t trunc_cap, ClsTileCache* tile_cache,
+                       float* prefix_state, int32_t* prefix_last, const float* bg,
                        const float* target,
                        int32_t loss_mode, float* image, float* T_final, int32_t* n_contrib,
                        float* dL_dimage, float* loss_per_scene, int32_t* work_counter,
@@ -340,22 +381,28 @@ int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* info,
 
 /* ------------------------------------------------------------------------
  * Backward pass (Supp. "Local Optimization Kernel", items 2 and 3). Pixel
- * part: per active-tile pixel, walk its list from the last contributor back
- * to the front, recovering T before each Gaussian as T_after / (1 - alpha)
- * (no per-Gaussian-per-pixel state is stored); static Gaussians update T and
- * the colour behind but produce no gradient; the 2D gradients of each active
+ * part: per active-tile pixel, start from the state the forward pass kept
+ * after the tile's static prefix (tile_cache, prefix_state) and walk the list
+ * front to back up to the earlier of the pixel's last contributor and the
+ * tile's last active entry, recomputing T before each Gaussian exactly as the
+ * forward pass did; the colour behind a Gaussian is the final colour (image)
+ * minus the colour composited up to and including it, so no
+ * per-Gaussian-per-pixel state is stored. Static Gaussians update T and that
+ * colour but produce no gradient; the 2D gradients of each active
  * Gaussian are reduced over the tile's pixels and added into
  *   grad2d [total_g2][12]: du, dv, dA, dB, dC, d opacity, d r, d g, d b, 0, 0, 0
  * (zeroed by the call). Gaussian part (active Gaussians only): chain rule to
  * every parameter of the row, summed over the scene's views, written to
  *   grads [total_grad_rows][row_stride] at row scene.grad_base + rank
  * (every float of the row is written). dL_dimage as written by the forward
- * call or supplied by the caller ([3][H][W] per view). */
+ * call or supplied by the caller ([3][H][W] per view); image, prefix_state
+ * and n_contrib as the forward call left them. */
 int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
                         const ClsBatchInfo* info, const ClsProjected* records,
                         const uint32_t* vals, int32_t vals_stride, const uint32_t* ranges,
                         const int32_t* active_tiles,
-                        const int32_t* n_active_tiles_dev, const float* bg, const float* T_final,
+                        const int32_t* n_active_tiles_dev, const ClsTileCache* tile_cache,
+                        const float* prefix_state, const float* image,
                         const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
                         float* grads, int32_t* work_counter, cls_stream_t stream);
 

@@ -57,7 +57,16 @@ class ClsProjected(C.Structure):
                 ("z", C.c_float), ("radius", C.c_int32)]
 
 
+class ClsTileCache(C.Structure):
+    _fields_ = [("zb", C.c_uint32), ("n_prefix", C.c_uint32), ("zmin_active", C.c_uint32),
+                ("last_active", C.c_int32)]
+
+
+PREFIX_UNKNOWN = 0xFFFFFFFF
+TILE_CACHE_BYTES = 16
+
 assert C.sizeof(ClsCamera) == 88 and C.sizeof(ClsScene) == 72
+assert C.sizeof(ClsTileCache) == TILE_CACHE_BYTES
 assert C.sizeof(ClsView) == 144 and C.sizeof(ClsProjected) == 48
 
 P = C.c_void_p
@@ -74,15 +83,15 @@ SIGNATURES = {
     "cls_project_workspace_size": (SZ, [P]),
     "cls_bin_offsets_size": (SZ, [P]),
     "cls_project_and_bin": (C.c_int, [P, P, P, I32, I32, P, P, P, P, P, P, I64, P, P, P, P, P,
-                                      P, SZ, P]),
+                                      I32, P, P, SZ, P]),
     "cls_complete_truncated": (C.c_int, [P, P, P, P, I64, P, P, I64, P, P, SZ, P]),
     "cls_sort_tiles_workspace_size": (SZ, [I64, I32]),
-    "cls_sort_tiles": (C.c_int, [P, P, P, P, P, I64, I64, I32, P, P, P, I64, P, P, SZ, P]),
+    "cls_sort_tiles": (C.c_int, [P, P, P, P, P, I64, I64, I32, P, P, P, I64, P, P, P, SZ, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
     "cls_sort_keys": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, P]),
     "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, I64, P, P,
-                                     I32, P, P, P, P, P, P, P]),
-    "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P]),
+                                     P, P, P, I32, P, P, P, P, P, P, P]),
+    "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P, P]),
     "cls_adam_workspace_size": (SZ, [I32]),
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
 }
@@ -173,12 +182,13 @@ def cls_bin_offsets_size(info) -> int:
 
 def cls_project_and_bin(scenes_dev, views_dev, info, project_mode, layout, records, tile_active,
                         active_tiles, n_active_tiles_dev, keys, vals, capacity, n_pairs_dev,
-                        ranges, bin_offsets, bin_cut, status_dev, workspace, workspace_bytes,
-                        stream) -> int:
+                        ranges, bin_offsets, bin_cut, tile_cache, prefix_mode, status_dev,
+                        workspace, workspace_bytes, stream) -> int:
     return load().cls_project_and_bin(scenes_dev, views_dev, C.byref(info), project_mode, layout,
                                       records, tile_active, active_tiles, n_active_tiles_dev,
                                       keys, vals, capacity, n_pairs_dev, ranges, bin_offsets,
-                                      bin_cut, status_dev, workspace, workspace_bytes, stream)
+                                      bin_cut, tile_cache, prefix_mode, status_dev, workspace,
+                                      workspace_bytes, stream)
 
 
 def cls_complete_truncated(views_dev, info, records, keys, capacity, trunc, trunc_count,
@@ -196,11 +206,12 @@ def cls_sort_tiles_workspace_size(capacity, min_bin) -> int:
 
 
 def cls_sort_tiles(keys, keys_alt, bin_offsets, active_tiles, n_active_tiles_dev, total_tiles,
-                   capacity, min_bin, cut, trunc, trunc_count, trunc_cap, work_counter, workspace,
-                   workspace_bytes, stream) -> int:
+                   capacity, min_bin, cut, trunc, trunc_count, trunc_cap, tile_cache,
+                   work_counter, workspace, workspace_bytes, stream) -> int:
     return load().cls_sort_tiles(keys, keys_alt, bin_offsets, active_tiles, n_active_tiles_dev,
                                  total_tiles, capacity, min_bin, cut, trunc, trunc_count,
-                                 trunc_cap, work_counter, workspace, workspace_bytes, stream)
+                                 trunc_cap, tile_cache, work_counter, workspace, workspace_bytes,
+                                 stream)
 
 
 def cls_sort_workspace_size(capacity, key_bits) -> int:
@@ -215,24 +226,25 @@ def cls_sort_keys(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bit
 
 def cls_render_forward(views_dev, info, records, vals, vals_stride, ranges, active_tiles,
                        n_active_tiles_dev, lazy_keys, bin_offsets, list_ranks, cut_in, cut_out,
-                       trunc, trunc_count, trunc_cap, bg, target, loss_mode, image, T_final,
-                       n_contrib, dL_dimage, loss_per_scene, work_counter, stream) -> int:
+                       trunc, trunc_count, trunc_cap, tile_cache, prefix_state, prefix_last, bg,
+                       target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
+                       work_counter, stream) -> int:
     bg3 = (C.c_float * 3)(*bg)
     return load().cls_render_forward(views_dev, C.byref(info), records, vals, vals_stride, ranges,
                                      active_tiles, n_active_tiles_dev, lazy_keys, bin_offsets,
                                      list_ranks, cut_in, cut_out, trunc, trunc_count, trunc_cap,
-                                     bg3, target, loss_mode,
+                                     tile_cache, prefix_state, prefix_last, bg3, target, loss_mode,
                                      image, T_final, n_contrib, dL_dimage, loss_per_scene,
                                      work_counter, stream)
 
 
 def cls_render_backward(scenes_dev, views_dev, info, records, vals, vals_stride, ranges,
-                        active_tiles, n_active_tiles_dev, bg, T_final, n_contrib, dL_dimage,
-                        grad2d, grads, work_counter, stream) -> int:
-    bg3 = (C.c_float * 3)(*bg)
+                        active_tiles, n_active_tiles_dev, tile_cache, prefix_state, image,
+                        n_contrib, dL_dimage, grad2d, grads, work_counter, stream) -> int:
     return load().cls_render_backward(scenes_dev, views_dev, C.byref(info), records, vals,
-                                      vals_stride, ranges, active_tiles, n_active_tiles_dev, bg3, T_final,
-                                      n_contrib, dL_dimage, grad2d, grads, work_counter, stream)
+                                      vals_stride, ranges, active_tiles, n_active_tiles_dev,
+                                      tile_cache, prefix_state, image, n_contrib, dL_dimage,
+                                      grad2d, grads, work_counter, stream)
 
 
 def cls_adam_workspace_size(n_scenes) -> int:

@@ -26,7 +26,10 @@ class ActiveRasterizer:
         self.state = state
         self.cams = list(cams)
         self.bg = tuple(float(x) for x in bg)
-        self.batch = Batch([state], [self.cams], state.params.device, layout)
+        # the caller's optimiser may move any row, so the static prefix is
+        # rebuilt on every call
+        self.batch = Batch([state], [self.cams], state.params.device, layout,
+                           prefix_cache=False)
         self.batch.plan_capacity()
 
     def __call__(self, params: torch.Tensor) -> List[torch.Tensor]:
@@ -47,7 +50,7 @@ class _RasterizeActive(torch.autograd.Function):
         b.project_and_bin(1)
         b.sort()
         b.image.zero_()
-        b.forward(0, rast.bg, write_image=True)
+        b.forward(0, rast.bg)
         ctx.rast = rast
         return b.image.clone()
 
@@ -57,7 +60,7 @@ class _RasterizeActive(torch.autograd.Function):
         b = rast.batch
         st = rast.state
         b.dL_dimage.copy_(grad_image.contiguous().view(-1))
-        b.backward(rast.bg)
+        b.backward()
         grad = torch.zeros_like(st.params)
         A = st.n_active
         if A:

@@ -10,6 +10,8 @@ constexpr int kBinItems = 8;
 constexpr int kBinChunk = kBinBlock * kBinItems;
 constexpr int kDepthBins = CLS_DEPTH_BINS;  // depth buckets per tile (bucketed layout)
 constexpr int kBigArea = 128;               // rectangles above this many tiles: one warp each
+constexpr uint32_t kPrefixMargin = 1u << 17; // float ulps between a prefix boundary and the
+                                             // nearest active Gaussian (about 1.6% of depth)
 
 // ---------------------------------------------------------------------------
 // Projection. mode 0: every Gaussian of the view's scene (slot -1); mode 1:
@@ -129,22 +131,90 @@ __device__ __forceinline__ void prefix2d(int32_t* G, int rows, int cols, int Wd)
     __syncthreads();
 }
 
+__device__ __forceinline__ int32_t warp_inclusive_sum(int32_t v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// The same in shared memory, by warp scans: rows, then columns. An odd pitch
+// keeps the column pass free of bank conflicts.
+__device__ __forceinline__ void prefix2d_smem(int32_t* S, int rows, int cols, int p) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int y = warp; y < rows; y += nw) {
+        int32_t carry = 0;
+        for (int x0 = 0; x0 < cols; x0 += 32) {
+            const int x = x0 + lane;
+            int32_t v = x < cols ? S[y * p + x] : 0;
+            v = warp_inclusive_sum(v, lane) + carry;
+            if (x < cols) S[y * p + x] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    for (int x = warp; x < cols; x += nw) {
+        int32_t carry = 0;
+        for (int y0 = 0; y0 < rows; y0 += 32) {
+            const int y = y0 + lane;
+            int32_t v = y < rows ? S[y * p + x] : 0;
+            v = warp_inclusive_sum(v, lane) + carry;
+            if (y < rows) S[y * p + x] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+}
+
+// Odd shared-memory pitch for a grid of `cols` columns.
+__host__ __device__ __forceinline__ int smem_pitch(int cols) { return cols | 1; }
+
 // Per view: coverage of the active stamps -> tile mask -> summed-area table
-// S[y][x] = number of active tiles with ty < y and tx < x.
-__global__ void __launch_bounds__(256)
+// S[y][x] = number of active tiles with ty < y and tx < x. Also clears every
+// tile's nearest-active depth for active_zmin_kernel. The grids go through
+// shared memory when they fit in `smem_cap` bytes.
+__global__ void __launch_bounds__(512)
 tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
-                 uint8_t* __restrict__ tile_active, int32_t* __restrict__ sat) {
+                 uint8_t* __restrict__ tile_active, int32_t* __restrict__ sat,
+                 ClsTileCache* __restrict__ tile_cache, int smem_cap) {
+    extern __shared__ int32_t s_grid[];
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
     int32_t* D = diff + view.sat_base;
-    prefix2d(D, Ty, Tx, Wd);
     uint8_t* act = tile_active + view.tile_base;
+    int32_t* S = sat + view.sat_base;
+    const int p = smem_pitch(Tx);
+    if ((int64_t)Ty * p * 4 <= smem_cap) {
+        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+            const int y = t / Tx, x = t - y * Tx;
+            s_grid[y * p + x] = D[(int64_t)y * Wd + x];
+        }
+        __syncthreads();
+        prefix2d_smem(s_grid, Ty, Tx, p);
+        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+            const int y = t / Tx, x = t - y * Tx;
+            const int32_t a = s_grid[y * p + x] > 0 ? 1 : 0;
+            act[t] = (uint8_t)a;
+            s_grid[y * p + x] = a;
+            tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
+        }
+        __syncthreads();
+        prefix2d_smem(s_grid, Ty, Tx, p);
+        for (int t = threadIdx.x; t < (Tx + 1) * (Ty + 1); t += blockDim.x) {
+            const int y = t / Wd, x = t - y * Wd;
+            S[t] = (x == 0 || y == 0) ? 0 : s_grid[(y - 1) * p + x - 1];
+        }
+        return;
+    }
+    prefix2d(D, Ty, Tx, Wd);
     for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
         const int y = t / Tx, x = t - y * Tx;
         act[t] = D[(int64_t)y * Wd + x] > 0 ? 1 : 0;
+        tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
     }
     __syncthreads();
-    int32_t* S = sat + view.sat_base;
     for (int y = threadIdx.x; y <= Ty; y += blockDim.x) {
         int32_t run = 0;
         S[(int64_t)y * Wd] = 0;
@@ -163,16 +233,72 @@ tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
     }
 }
 
-// Ascending list of active tiles and each tile's rank in it (-1 if inactive).
+// Nearest active Gaussian of every tile: the depth bits of each non-culled
+// active record are min-reduced over the tiles of its rectangle. One warp per
+// active Gaussian, its lanes over the rectangle's cells; each block reduces
+// into a private copy of its view's tile grid in shared memory and merges it
+// into the global grid once.
+constexpr int kZminThreads = 1024;
+
+__global__ void __launch_bounds__(kZminThreads)
+active_zmin_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
+                   const ClsProjected* __restrict__ records,
+                   ClsTileCache* __restrict__ tile_cache) {
+    extern __shared__ uint32_t s_z[];
+    const ClsView& view = views[blockIdx.y];
+    const ClsScene& sc = scenes[view.scene];
+    const int nt = view.tiles_x * view.tiles_y;
+    if (sc.n_active == 0) return;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) s_z[i] = 0xffffffffu;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = blockDim.x >> 5;
+    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < sc.n_active;
+         i += gridDim.x * warps) {
+        int x0, x1, y0, y1;
+        uint32_t zb;
+        if (!record_rect(view, records, view.rec_base + sc.active_idx[i], x0, x1, y0, y1, zb))
+            continue;  // uniform over the warp
+        const int w = x1 - x0 + 1;
+        const int area = w * (y1 - y0 + 1);
+        for (int k = lane; k < area; k += 32) {
+            const int q = k / w;
+            const int cell = (y0 + q) * view.tiles_x + x0 + (k - q * w);
+            if (zb < s_z[cell]) atomicMin(&s_z[cell], zb);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const uint32_t z = s_z[i];
+        if (z != 0xffffffffu) atomicMin(&tile_cache[view.tile_base + i].zmin_active, z);
+    }
+}
+
+// Ascending list of active tiles and each tile's rank in it (-1 if inactive),
+// and the static-prefix decision of every active tile: its cache holds while
+// no active Gaussian of the tile lies in front of the boundary; otherwise the
+// boundary moves a margin in front of the nearest active Gaussian and the
+// prefix is rebuilt by the next forward pass.
 __global__ void __launch_bounds__(1024)
 compact_tiles_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
                      int32_t* __restrict__ active_tiles, int32_t* __restrict__ n_active_tiles,
-                     int32_t* __restrict__ tile_rank) {
+                     int32_t* __restrict__ tile_rank, ClsTileCache* __restrict__ tile_cache,
+                     int prefix_mode) {
     __shared__ int32_t smem[1024 / 32 + 1];
     int32_t carry = 0;
     for (int64_t base = 0; base < n_tiles; base += 1024) {
         const int64_t t = base + threadIdx.x;
         const int32_t f = (t < n_tiles && tile_active[t]) ? 1 : 0;
+        if (f) {
+            const ClsTileCache c = tile_cache[t];
+            const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
+                              c.zmin_active >= c.zb;
+            if (!keep) {
+                tile_cache[t].zb = c.zmin_active > kPrefixMargin ? c.zmin_active - kPrefixMargin
+                                                                 : 0u;
+                tile_cache[t].n_prefix = CLS_PREFIX_UNKNOWN;
+            }
+        }
         int32_t tot;
         const int32_t ex = block_exclusive_sum<1024>(f, smem, tot);
         if (f) active_tiles[carry + ex] = (int32_t)t;
@@ -284,10 +410,26 @@ stamp_bins_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
 
 __global__ void __launch_bounds__(256)
 bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins,
-                   int64_t total_sat) {
+                   int64_t total_sat, int smem_cap) {
+    extern __shared__ int32_t s_grid[];
     const ClsView& view = views[blockIdx.y];
-    prefix2d(bins + blockIdx.x * total_sat + view.sat_base, view.tiles_y, view.tiles_x,
-             view.tiles_x + 1);
+    const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
+    int32_t* G = bins + blockIdx.x * total_sat + view.sat_base;
+    const int p = smem_pitch(Tx);
+    if ((int64_t)Ty * p * 4 > smem_cap) {
+        prefix2d(G, Ty, Tx, Wd);
+        return;
+    }
+    for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+        const int y = t / Tx, x = t - y * Tx;
+        s_grid[y * p + x] = G[(int64_t)y * Wd + x];
+    }
+    __syncthreads();
+    prefix2d_smem(s_grid, Ty, Tx, p);
+    for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+        const int y = t / Tx, x = t - y * Tx;
+        G[(int64_t)y * Wd + x] = s_grid[y * p + x];
+    }
 }
 
 // Pairs per (active tile rank, depth bin), entry e = rank * kDepthBins + bin.
@@ -320,14 +462,18 @@ sub_count_kernel(const ClsView* __restrict__ views, int n_views,
 }
 
 // Offsets of every (tile, bin) bucket and the per-tile ranges, clamped to the
-// key capacity so every later access stays inside the key buffer.
+// key capacity so every later access stays inside the key buffer; the first
+// depth bin each tile emits (bins entirely in front of a cached prefix
+// boundary hold only prefix pairs and are not written).
 __global__ void __launch_bounds__(kBinBlock)
 sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
                    const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
                    const int32_t* __restrict__ bins, int64_t total_sat,
                    const int64_t* __restrict__ partials, int64_t capacity,
                    uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
-                   uint32_t* __restrict__ ranges) {
+                   uint32_t* __restrict__ ranges, const ClsTileCache* __restrict__ tile_cache,
+                   const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
+                   uint8_t* __restrict__ front) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     const int64_t ne = (int64_t)(*n_active) * kDepthBins;
     int64_t base = partials[blockIdx.x];
@@ -344,7 +490,13 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
             cursor[e] = (int32_t)o;
             const int t = (int)(e / kDepthBins), b = (int)(e - (int64_t)t * kDepthBins);
             const int64_t tile = active_tiles[t];
-            if (b == 0) ranges[2 * tile] = o;
+            if (b == 0) {
+                ranges[2 * tile] = o;
+                const ClsTileCache c = tile_cache[tile];
+                const int v = view_of_tile(views, n_views, (int)tile);
+                front[tile] = c.n_prefix != CLS_PREFIX_UNKNOWN
+                                  ? (uint8_t)depth_bin(c.zb, zmin[v], zmax[v]) : (uint8_t)0;
+            }
             if (b == kDepthBins - 1) {
                 ranges[2 * tile + 1] = o_end;
                 bin_offsets[e + 1] = o_end;  // sentinel: end of the tile's last bin
@@ -438,15 +590,20 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                      uint64_t* __restrict__ keys, int64_t capacity,
                      const uint32_t* __restrict__ work_list,
-                     const int32_t* __restrict__ work_count, const uint8_t* __restrict__ cut) {
-    extern __shared__ int32_t s_rank[];  // rank of each tile of the view; then its depth cut
+                     const int32_t* __restrict__ work_count, const uint8_t* __restrict__ cut,
+                     const uint8_t* __restrict__ front) {
+    // rank of each tile of the view, then its last and first emitted depth bin
+    extern __shared__ int32_t s_rank[];
     const ClsView& view = views[blockIdx.y];
     const int Tx = view.tiles_x;
     const int nt = Tx * view.tiles_y;
     uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_rank + nt);
+    uint8_t* s_front = s_cut + nt;
     for (int i = threadIdx.x; i < nt; i += kBinBlock) {
-        s_rank[i] = tile_rank[view.tile_base + i];
+        const int r = tile_rank[view.tile_base + i];
+        s_rank[i] = r;
         s_cut[i] = cut ? cut[view.tile_base + i] : (uint8_t)(kDepthBins - 1);
+        s_front[i] = r >= 0 ? front[view.tile_base + i] : (uint8_t)0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -504,7 +661,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                     const int q = k / o_w;
                     const int cell = (o_y0 + q) * Tx + o_x0 + (k - q * o_w);
                     const int r = s_rank[cell];
-                    if (r >= 0 && o_bin <= (int)s_cut[cell]) {
+                    if (r >= 0 && o_bin <= (int)s_cut[cell] && o_bin >= (int)s_front[cell]) {
                         sub[u] = (int64_t)r * kDepthBins + o_bin;
                         key[u] = ((uint64_t)o_zb << 32) | o_rec;
                     }
@@ -534,7 +691,7 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
                       const uint32_t* __restrict__ work_list,
                       const int32_t* __restrict__ work_count, const int32_t* __restrict__ trunc,
                       const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
-                      int* __restrict__ item_counter) {
+                      const uint8_t* __restrict__ front, int* __restrict__ item_counter) {
     __shared__ int s_item;
     const int n_items = (int)min((int64_t)*trunc_count, trunc_cap) * kCompleteChunks;
     for (;;) {
@@ -550,6 +707,7 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
         const int local = tile - view.tile_base;
         const int ty = local / view.tiles_x, tx = local - ty * view.tiles_x;
         const int n = work_count[v];
+        const int first_bin = front[tile];
         const int per = (n + kCompleteChunks - 1) / kCompleteChunks;
         const int a = chunk * per, b = min(n, a + per);
         for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
@@ -559,7 +717,7 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
             if (!record_rect(view, records, rec, x0, x1, y0, y1, zb)) continue;
             if (tx < x0 || tx > x1 || ty < y0 || ty > y1) continue;
             const int bin = depth_bin(zb, zmin[v], zmax[v]);
-            if (bin <= old_cut) continue;
+            if (bin <= old_cut || bin < first_bin) continue;
             const int64_t p = atomicAdd(cursor + (int64_t)rank * kDepthBins + bin, 1);
             if (p < capacity) keys[p] = ((uint64_t)zb << 32) | rec;
         }
@@ -623,7 +781,7 @@ namespace {
 
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, work_list, work_count, total;
+        bins, work_list, work_count, front, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -650,6 +808,7 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.bins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
     L.work_list = o; o = align256(o + (size_t)info->total_records * 4);
     L.work_count = o; o = align256(o + (size_t)V * 4);
+    L.front = o; o = align256(o + (size_t)info->total_tiles);
     L.total = o;
     return L;
 }
@@ -657,6 +816,7 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
 }  // namespace
 
 static int g_max_view_tiles_checked = 0;
+static int g_grid_cap_set = 0;
 
 extern "C" size_t cls_project_workspace_size(const ClsBatchInfo* info) {
     return info ? proj_layout(info).total : 0;
@@ -672,10 +832,12 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                    int32_t* active_tiles, int32_t* n_active_tiles_dev,
                                    uint64_t* keys, uint32_t* vals, int64_t capacity,
                                    int64_t* n_pairs_dev, uint32_t* ranges, uint32_t* bin_offsets,
-                                   const uint8_t* bin_cut, int32_t* status_dev, void* workspace,
+                                   const uint8_t* bin_cut, ClsTileCache* tile_cache,
+                                   int32_t prefix_mode, int32_t* status_dev, void* workspace,
                                    size_t workspace_bytes, cls_stream_t stream) {
     if (!info || !scenes_dev || !views_dev || !records || !tile_active || !active_tiles ||
         !n_active_tiles_dev || !n_pairs_dev || !status_dev || !workspace || capacity < 0 ||
+        !tile_cache || (prefix_mode != 0 && prefix_mode != 1) ||
         (project_mode != 0 && project_mode != 1) || (layout != 0 && layout != 1) ||
         (capacity > 0 && !keys) || (layout == 0 && capacity > 0 && !vals) ||
         (layout == 1 && (!ranges || !bin_offsets)))
@@ -701,6 +863,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     int32_t* bins = reinterpret_cast<int32_t*>(ws + L.bins);
     uint32_t* work_list = reinterpret_cast<uint32_t*>(ws + L.work_list);
     int32_t* work_count = reinterpret_cast<int32_t*>(ws + L.work_count);
+    uint8_t* front = reinterpret_cast<uint8_t*>(ws + L.front);
     const int64_t subs = info->total_tiles * kDepthBins;
     const int64_t max_view_tiles = info->max_view_tiles;
     if (layout == 1 && g_max_view_tiles_checked == 0) {
@@ -708,7 +871,19 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                              200 * 1024);
         g_max_view_tiles_checked = 1;
     }
-    if (layout == 1 && max_view_tiles * 5 > 200 * 1024) return CLS_ERR_INVALID_ARG;
+    if (layout == 1 && max_view_tiles * 6 > 200 * 1024) return CLS_ERR_INVALID_ARG;
+    if (max_view_tiles * 4 > 200 * 1024) return CLS_ERR_INVALID_ARG;  // nearest-active grid
+    // shared-memory grids of the prefix sums (larger views use global memory)
+    const int grid_cap = (int)hmin64(max_view_tiles * 4 + 16 * 1024, 200 * 1024);
+    if (g_grid_cap_set < grid_cap) {
+        cudaFuncSetAttribute(tile_mask_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(bins_prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        cudaFuncSetAttribute(active_zmin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             200 * 1024);
+        g_grid_cap_set = grid_cap;
+    }
 
     if (project_mode == 0 && info->max_n > 0)
         project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
@@ -721,9 +896,16 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     if (info->max_active > 0)
         stamp_active_kernel<<<dim3((info->max_active + 255) / 256, V), 256, 0, s>>>(
             scenes_dev, views_dev, records, diff);
-    tile_mask_kernel<<<V, 256, 0, s>>>(views_dev, diff, tile_active, sat);
+    tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
+                                              grid_cap);
+    if (info->max_active > 0)
+        active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads - 1) /
+                                                       kZminThreads, 38), V),
+                             kZminThreads, (size_t)max_view_tiles * 4, s>>>(
+            scenes_dev, views_dev, records, tile_cache);
     compact_tiles_kernel<<<1, 1024, 0, s>>>(tile_active, info->total_tiles, active_tiles,
-                                            n_active_tiles_dev, tile_rank);
+                                            n_active_tiles_dev, tile_rank, tile_cache,
+                                            prefix_mode);
     if (cpv == 0) {
         cudaMemsetAsync(n_pairs_dev, 0, sizeof(int64_t), s);
         if (layout == 1) cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
@@ -757,7 +939,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
         stamp_bins_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
                                                          zmin, zmax, bins, info->total_sat);
-        bins_prefix_kernel<<<dim3(kDepthBins, V), 256, 0, s>>>(views_dev, bins, info->total_sat);
+        bins_prefix_kernel<<<dim3(kDepthBins, V), 256, grid_cap, s>>>(views_dev, bins,
+                                                                      info->total_sat, grid_cap);
         sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
             sub_partials);
@@ -765,12 +948,12 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                 capacity, status_dev);
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
-            sub_partials, capacity, bin_offsets, cursor, ranges);
+            sub_partials, capacity, bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
         const unsigned emit_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
                                                       2048);
-        emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 5, s>>>(
+        emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 6, s>>>(
             views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, bin_cut);
+            work_count, bin_cut, front);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;
@@ -794,7 +977,7 @@ extern "C" int cls_complete_truncated(const ClsView* views_dev, const ClsBatchIn
         reinterpret_cast<uint32_t*>(ws + L.zmax), reinterpret_cast<int32_t*>(ws + L.cursor), keys,
         capacity, reinterpret_cast<uint32_t*>(ws + L.work_list),
         reinterpret_cast<int32_t*>(ws + L.work_count), trunc, trunc_count, trunc_cap,
-        work_counter);
+        reinterpret_cast<uint8_t*>(ws + L.front), work_counter);
     CLS_CHECK_LAUNCH();
     return CLS_OK;
 }

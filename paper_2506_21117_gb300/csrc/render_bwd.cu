@@ -1,15 +1,18 @@
 // Backward pass of the local optimisation (Supp. "Local Optimization Kernel",
 // items 2 and 3).
 //
-// Pixel part: one 256-thread block per active tile (persistent, queue of
-// tiles). Each pixel walks its list from its last contributor back to the
-// front, recovering the transmittance in front of each Gaussian as
-// T_after / (1 - alpha) and keeping the colour already composited behind it,
-// so nothing per (pixel, Gaussian) is stored by the forward pass. Static
-// Gaussians update T and the colour behind but skip all gradient work. The 2D
-// gradients of an active Gaussian are reduced over the tile with warp shuffles
-// and a shared-memory sum over warps, then added to global memory with one
-// atomic per component per tile.
+// Pixel part: one 128-thread block per active tile (persistent, queue of
+// tiles), two pixels per thread. Each pixel starts from the state the forward
+// pass kept after the tile's static prefix (nothing in front of it depends on
+// an active Gaussian) and walks its list front to back, up to the earlier of
+// its last contributor and the tile's last active entry (nothing behind both
+// reaches an active gradient). T in front of each Gaussian is recomputed with
+// the forward pass's own operations; the colour behind a Gaussian is the final
+// colour minus what has been composited up to and including it, so nothing
+// per (pixel, Gaussian) is stored. Static Gaussians update T and that colour
+// but skip all gradient work. The 2D gradients of an active Gaussian are
+// reduced over the tile with warp shuffles and a shared-memory sum over warps,
+// then added to global memory with one atomic per component per tile.
 //
 // Gaussian part: one thread per active Gaussian; the chain rule from the 2D
 // gradients of every view of its scene to every float of its parameter row.
@@ -23,35 +26,37 @@ constexpr int kG2Stride = 12;
 constexpr int kBwdThreads = kTilePixels / 2;  // two pixels per thread: rows ly and ly + 8
 constexpr int kBwdWarps = kBwdThreads / 32;
 
-// Reverse-walk state of one pixel.
+// Walk state of one pixel: T in front of the next entry, R = colour not yet
+// composited (final colour minus everything in front, background included).
 struct BwdPixel {
     float fx, fy;
-    float T, g0, g1, g2, S0, S1, S2;
-    int last;
-    bool inside;
+    float T, g0, g1, g2, R0, R1, R2;
+    int end;  // list positions before `end` are walked
 };
 
-// One list entry at one pixel: recover T in front of the entry, update the
-// colour behind, and (for an active Gaussian) add the entry's 2D gradient to
-// gr[]. a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
+// One list entry at one pixel: the forward pass's alpha and T, the colour
+// behind, and (for an active Gaussian) the entry's 2D gradient added to gr[].
+// a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
 template <bool ACTIVE>
 __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float t,
                                           const float4& a, const float4& bb, float cb, float* gr) {
-    if (!(p.inside && pos < p.last)) return false;
+    if (pos >= p.end) return false;
     const float dy = p.fy - a.y;
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
     if (power2 > 0.0f) return false;
     const float G = ex2_approx(power2);
     const float alpha = fminf(kAlphaMax, bb.y * G);
     if (alpha < kAlphaMin) return false;
-    const float inv_om = __fdividef(1.0f, 1.0f - alpha);
-    p.T *= inv_om;
     const float w = alpha * p.T;
+    p.R0 = __fmaf_rn(-bb.z, w, p.R0);
+    p.R1 = __fmaf_rn(-bb.w, w, p.R1);
+    p.R2 = __fmaf_rn(-cb, w, p.R2);
     if (ACTIVE) {
+        const float inv_om = __fdividef(1.0f, 1.0f - alpha);
         const float A = -2.0f * kLn2 * a.z, B = -kLn2 * a.w, C = -2.0f * kLn2 * bb.x;
-        const float dLda = p.g0 * (bb.z * p.T - p.S0 * inv_om) +
-                           p.g1 * (bb.w * p.T - p.S1 * inv_om) +
-                           p.g2 * (cb * p.T - p.S2 * inv_om);
+        const float cg = bb.z * p.g0 + bb.w * p.g1 + cb * p.g2;
+        const float gR = p.g0 * p.R0 + p.g1 * p.R1 + p.g2 * p.R2;
+        const float dLda = p.T * cg - gR * inv_om;
         const bool clamped = bb.y * G > kAlphaMax;
         const float dpow = clamped ? 0.f : dLda * alpha;
         gr[0] += dpow * (A * dx + B * dy);
@@ -64,9 +69,7 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float 
         gr[7] += w * p.g1;
         gr[8] += w * p.g2;
     }
-    p.S0 += bb.z * w;
-    p.S1 += bb.w * w;
-    p.S2 += cb * w;
+    p.T = p.T * (1.0f - alpha);
     return true;
 }
 
@@ -95,26 +98,35 @@ __device__ __forceinline__ float reduce8_scatter(const float* v, int lane) {
     return y;
 }
 
+// Pixel start state: after the tile's prefix (n_prefix entries), walking to
+// min(n_contrib, last active + 1). A pixel that stopped inside the prefix, or
+// lies outside the image, walks nothing.
 __device__ __forceinline__ void bwd_load_pixel(BwdPixel& p, const ClsView& view, int px, int py,
-                                               float bg0, float bg1, float bg2,
-                                               const float* T_final, const int32_t* n_contrib,
+                                               int n_prefix, int end_active,
+                                               const float* prefix_state, const float* image,
+                                               const int32_t* n_contrib,
                                                const float* dL_dimage) {
     const int W = view.cam.width, H = view.cam.height;
-    p.inside = px < W && py < H;
     p.fx = (float)px + 0.5f;
     p.fy = (float)py + 0.5f;
-    p.T = 1.0f; p.g0 = p.g1 = p.g2 = 0.f; p.last = 0;
-    if (p.inside) {
-        const int64_t pix = view.pix_base + (int64_t)py * W + px;
-        const int64_t plane = (int64_t)W * H;
-        const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
-        p.T = T_final[pix];
-        p.last = n_contrib[pix];
-        p.g0 = dL_dimage[p3];
-        p.g1 = dL_dimage[p3 + plane];
-        p.g2 = dL_dimage[p3 + 2 * plane];
-    }
-    p.S0 = p.T * bg0; p.S1 = p.T * bg1; p.S2 = p.T * bg2;
+    p.T = 1.0f; p.g0 = p.g1 = p.g2 = 0.f; p.R0 = p.R1 = p.R2 = 0.f;
+    p.end = 0;
+    if (!(px < W && py < H)) return;
+    const int64_t pix = view.pix_base + (int64_t)py * W + px;
+    const float4 st = reinterpret_cast<const float4*>(prefix_state)[pix];
+    if (st.x < 0.0f) return;
+    const int end = min(n_contrib[pix], end_active);
+    if (end <= n_prefix) return;
+    const int64_t plane = (int64_t)W * H;
+    const int64_t p3 = 3 * view.pix_base + (int64_t)py * W + px;
+    p.end = end;
+    p.T = st.x;
+    p.g0 = dL_dimage[p3];
+    p.g1 = dL_dimage[p3 + plane];
+    p.g2 = dL_dimage[p3 + 2 * plane];
+    p.R0 = image[p3] - st.y;
+    p.R1 = image[p3 + plane] - st.z;
+    p.R2 = image[p3 + 2 * plane] - st.w;
 }
 
 __global__ void __launch_bounds__(kBwdThreads)
@@ -122,60 +134,68 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
                   int vals_stride, const uint32_t* __restrict__ ranges,
                   const int32_t* __restrict__ active_tiles,
-                  const int32_t* __restrict__ n_active_tiles, float bg0, float bg1, float bg2,
-                  const float* __restrict__ T_final, const int32_t* __restrict__ n_contrib,
-                  const float* __restrict__ dL_dimage, float* __restrict__ grad2d,
-                  int* __restrict__ work_counter) {
+                  const int32_t* __restrict__ n_active_tiles,
+                  const ClsTileCache* __restrict__ tile_cache,
+                  const float* __restrict__ prefix_state, const float* __restrict__ image,
+                  const int32_t* __restrict__ n_contrib, const float* __restrict__ dL_dimage,
+                  float* __restrict__ grad2d, int* __restrict__ work_counter) {
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
     __shared__ float s_c[kTilePixels];
     __shared__ int s_slot[kTilePixels];
     __shared__ float s_g[kSub][kBwdWarps][kGradComps + 1];
     __shared__ int s_tile;
-    __shared__ int s_maxlast;
+    __shared__ int s_maxend;
     const int n_tiles = *n_active_tiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, 8)
     for (;;) {
         if (threadIdx.x == 0) {
             s_tile = atomicAdd(work_counter, 1);
-            s_maxlast = 0;
+            s_maxend = 0;
         }
         __syncthreads();
         const int t = s_tile;
         if (t >= n_tiles) break;
         const int tile = active_tiles[t];
+        const ClsTileCache c = tile_cache[tile];
+        const int n_prefix = (int)c.n_prefix;
+        // no active entry behind the prefix: no gradient (an unrendered tile
+        // has no prefix and is skipped too)
+        if (c.n_prefix == CLS_PREFIX_UNKNOWN || c.last_active < n_prefix) {
+            __syncthreads();
+            continue;
+        }
         const ClsView& view = views[view_of_tile(views, n_views, tile)];
         const int local = tile - view.tile_base;
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const uint32_t start = ranges[2 * (int64_t)tile];
         BwdPixel p0, p1;
-        bwd_load_pixel(p0, view, tx * kTile + lx, ty * kTile + ly, bg0, bg1, bg2, T_final,
-                       n_contrib, dL_dimage);
-        bwd_load_pixel(p1, view, tx * kTile + lx, ty * kTile + ly + 8, bg0, bg1, bg2, T_final,
-                       n_contrib, dL_dimage);
-        const int my_last = max(p0.last, p1.last);
-        if (my_last > 0) atomicMax(&s_maxlast, my_last);
+        bwd_load_pixel(p0, view, tx * kTile + lx, ty * kTile + ly, n_prefix, c.last_active + 1,
+                       prefix_state, image, n_contrib, dL_dimage);
+        bwd_load_pixel(p1, view, tx * kTile + lx, ty * kTile + ly + 8, n_prefix,
+                       c.last_active + 1, prefix_state, image, n_contrib, dL_dimage);
+        const int my_end = max(p0.end, p1.end);
+        if (my_end > n_prefix) atomicMax(&s_maxend, my_end);
         __syncthreads();
-        const int max_last = s_maxlast;
+        const int max_end = s_maxend;
 
-        for (int hi = max_last; hi > 0; hi -= kTilePixels) {
-            const int lo = hi > kTilePixels ? hi - kTilePixels : 0;
-            const int nb = hi - lo;
+        for (int lo = n_prefix; lo < max_end; lo += kTilePixels) {
+            const int nb = min(kTilePixels, max_end - lo);
             for (int i = threadIdx.x; i < nb; i += kBwdThreads) {
                 const float4* rec = reinterpret_cast<const float4*>(
                     records + vals[(int64_t)(start + lo + i) * vals_stride]);
                 s_a[i] = stage_conic_a(rec[0]);
                 s_b[i] = stage_conic_b(rec[1]);
-                const float4 c = rec[2];
-                s_c[i] = c.x;
-                s_slot[i] = __float_as_int(c.y);
+                const float4 cc = rec[2];
+                s_c[i] = cc.x;
+                s_slot[i] = __float_as_int(cc.y);
             }
             __syncthreads();
-            for (int kk = nb - 1; kk >= 0; kk -= kSub) {
-                const int sub_lo = kk >= kSub - 1 ? kk - (kSub - 1) : 0;
+            for (int k0 = 0; k0 < nb; k0 += kSub) {
+                const int k1 = min(nb, k0 + kSub);
                 bool any_active = false;
-                for (int k = kk; k >= sub_lo; --k) {
+                for (int k = k0; k < k1; ++k) {
                     const float4 a = s_a[k];
                     const float4 bb = s_b[k];
                     const float cb = s_c[k];
@@ -190,10 +210,10 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     any_active = true;
                     float gr[kGradComps];
 #pragma unroll
-                    for (int c = 0; c < kGradComps; ++c) gr[c] = 0.f;
+                    for (int q = 0; q < kGradComps; ++q) gr[q] = 0.f;
                     const bool c0 = bwd_entry<true>(p0, lo + k, dx, t, a, bb, cb, gr);
                     const bool c1 = bwd_entry<true>(p1, lo + k, dx, t, a, bb, cb, gr);
-                    float* dst = &s_g[k - sub_lo][warp][0];
+                    float* dst = &s_g[k - k0][warp][0];
                     if (__any_sync(0xffffffffu, c0 || c1)) {
                         const float y = reduce8_scatter(gr, lane);
                         float z = gr[8];
@@ -208,10 +228,10 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                 }
                 if (any_active) {  // uniform over the block
                     __syncthreads();
-                    const int cnt = kk - sub_lo + 1;
+                    const int cnt = k1 - k0;
                     for (int e = threadIdx.x; e < cnt * kGradComps; e += kBwdThreads) {
                         const int ent = e / kGradComps, comp = e - ent * kGradComps;
-                        const int slot = s_slot[sub_lo + ent];
+                        const int slot = s_slot[k0 + ent];
                         if (slot < 0) continue;
                         float sum = 0.f;
 #pragma unroll
@@ -223,7 +243,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
             }
             __syncthreads();
         }
-        __syncthreads();  // s_tile / s_maxlast are rewritten for the next tile
+        __syncthreads();  // s_tile / s_maxend are rewritten for the next tile
     }
 }
 
@@ -444,12 +464,14 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
                                    const uint32_t* vals, int32_t vals_stride,
                                    const uint32_t* ranges,
                                    const int32_t* active_tiles, const int32_t* n_active_tiles_dev,
-                                   const float* bg, const float* T_final, const int32_t* n_contrib,
+                                   const ClsTileCache* tile_cache, const float* prefix_state,
+                                   const float* image, const int32_t* n_contrib,
                                    const float* dL_dimage, float* grad2d, float* grads,
                                    int32_t* work_counter, cls_stream_t stream) {
     if (!scenes_dev || !views_dev || !info || !records || !vals ||
         (vals_stride != 1 && vals_stride != 2) || !ranges || !active_tiles ||
-        !n_active_tiles_dev || !bg || !T_final || !n_contrib || !dL_dimage || !work_counter ||
+        !n_active_tiles_dev || !tile_cache || !prefix_state || !image || !n_contrib ||
+        !dL_dimage || !work_counter ||
         info->n_views <= 0 || info->total_tiles <= 0 || info->n_scenes > 65535 ||
         (info->total_g2 > 0 && !grad2d) || (info->total_grad_rows > 0 && !grads))
         return CLS_ERR_INVALID_ARG;
@@ -466,8 +488,9 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
     const int blocks = (int)hmin64(info->total_tiles, g_bwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(
-        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, bg[0],
-        bg[1], bg[2], T_final, n_contrib, dL_dimage, grad2d, work_counter);
+        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
+        n_active_tiles_dev, tile_cache, prefix_state, image, n_contrib, dL_dimage, grad2d,
+        work_counter);
     if (info->max_active > 0 && info->total_grad_rows > 0) {
         backward_gaussian_kernel<<<dim3((info->max_active + 127) / 128, info->n_scenes), 128, 0,
                                    s>>>(scenes_dev, views_dev, grad2d, grads);

@@ -1,8 +1,16 @@
 // Forward rendering of the active tiles (Supp. "Local Optimization Kernel",
-// item 2): one 256-thread block per 16x16 tile, one pixel per thread, the
+// item 2): a 128-thread block per 16x16 tile, two pixels per thread, the
 // tile's depth-sorted list staged through shared memory in batches of 256
 // records; blocks are persistent and take tiles from a queue. The photometric
 // loss and its pixel gradient are fused into the epilogue.
+//
+// Static prefix: static Gaussians are frozen during an update, so the state of
+// a pixel after the static entries in front of every active Gaussian of its
+// tile repeats from one iteration to the next. A tile whose cache holds starts
+// from that state at list position n_prefix; a tile to rebuild composites from
+// the front and writes the state when it reaches the first entry at or behind
+// the boundary depth. The same floating-point operations run on the same
+// entries in the same order either way, so both give identical results.
 #include "common.cuh"
 
 namespace cls {
@@ -23,6 +31,9 @@ struct FwdSmem {
     float red[kFwdThreads / 32];
     int tile;
     int last_bin;
+    int first_bin;
+    int last_active;  // last list position of a staged active entry
+    int n_below;      // entries of the staged batch in front of the prefix boundary
 };
 
 // Per-thread compositing state of one pixel.
@@ -32,12 +43,31 @@ struct PixelState {
     bool done;
 };
 
+// Tile-uniform state of the static prefix while a tile is rendered.
+struct PrefixWalk {
+    uint32_t zb;        // boundary depth bits
+    uint32_t skip_to;   // first list position to composite (cached prefix)
+    bool rebuild;       // the state after the prefix is written this pass
+    bool crossed;       // ... and has been
+    uint32_t n_prefix;  // entries in front of the boundary (rebuild)
+};
+
 __device__ __forceinline__ void stage_record(FwdSmem& sm, int i, const ClsProjected* records,
-                                             uint32_t rec) {
+                                             uint32_t rec, int pos, uint32_t zb, bool count,
+                                             int& below) {
     const float4* r = reinterpret_cast<const float4*>(records + rec);
     sm.a[i] = stage_conic_a(r[0]);
     sm.b[i] = stage_conic_b(r[1]);
-    sm.c[i] = r[2].x;
+    const float4 r2 = r[2];
+    sm.c[i] = r2.x;
+    if (__float_as_int(r2.y) >= 0) atomicMax(&sm.last_active, pos);
+    below += (count && __float_as_uint(r2.z) < zb) ? 1 : 0;
+}
+
+// Warp-aggregated count of the staged entries in front of the boundary.
+__device__ __forceinline__ void add_below(FwdSmem& sm, int below) {
+    below = __reduce_add_sync(0xffffffffu, (unsigned)below);
+    if ((threadIdx.x & 31) == 0 && below) atomicAdd(&sm.n_below, below);
 }
 
 __device__ __forceinline__ void composite_one(float dx, float t, float dy, const float4& a,
@@ -61,12 +91,12 @@ __device__ __forceinline__ void composite_one(float dx, float t, float dy, const
     ps.last = pos + 1;
 }
 
-// Composite the nb staged records (list positions pos0 ..) into two pixels of
-// one column.
-__device__ __forceinline__ void composite_batch(const FwdSmem& sm, int nb, uint32_t pos0, float fx,
-                                                float fy0, float fy1, PixelState& p0,
+// Composite staged records k0 .. k1 - 1 (list positions pos0 + k) into two
+// pixels of one column.
+__device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k1, uint32_t pos0,
+                                                float fx, float fy0, float fy1, PixelState& p0,
                                                 PixelState& p1) {
-    for (int k = 0; k < nb && !(p0.done && p1.done); ++k) {
+    for (int k = k0; k < k1 && !(p0.done && p1.done); ++k) {
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
@@ -77,6 +107,50 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int nb, uint3
     }
 }
 
+__device__ __forceinline__ void save_prefix(const PixelState& ps, const ClsView& view, int px,
+                                            int py, float* prefix_state, int32_t* prefix_last) {
+    if (!(px < view.cam.width && py < view.cam.height)) return;
+    const int64_t pix = view.pix_base + (int64_t)py * view.cam.width + px;
+    reinterpret_cast<float4*>(prefix_state)[pix] =
+        make_float4(ps.done ? -ps.T : ps.T, ps.c0, ps.c1, ps.c2);
+    prefix_last[pix] = (int32_t)ps.last;
+}
+
+__device__ __forceinline__ void load_prefix(PixelState& ps, const ClsView& view, int px, int py,
+                                            const float* prefix_state,
+                                            const int32_t* prefix_last) {
+    if (ps.done) return;  // outside the image
+    const int64_t pix = view.pix_base + (int64_t)py * view.cam.width + px;
+    const float4 st = reinterpret_cast<const float4*>(prefix_state)[pix];
+    ps.T = fabsf(st.x);
+    ps.done = st.x < 0.0f;
+    ps.c0 = st.y; ps.c1 = st.z; ps.c2 = st.w;
+    ps.last = (uint32_t)prefix_last[pix];
+}
+
+// Composite one staged batch of nb entries at list positions pos0 ..: skip
+// the cached prefix, and when rebuilding, save the pixel state at the first
+// entry at or behind the boundary. Uniform over the block.
+__device__ __forceinline__ void composite_staged(const FwdSmem& sm, int nb, uint32_t pos0,
+                                                 PrefixWalk& pw, const ClsView& view, int px,
+                                                 int py0, int py1, float fx, float fy0, float fy1,
+                                                 PixelState& p0, PixelState& p1,
+                                                 float* prefix_state, int32_t* prefix_last) {
+    const int k0 = pw.skip_to > pos0 ? (int)min((uint32_t)nb, pw.skip_to - pos0) : 0;
+    if (pw.rebuild && !pw.crossed) {
+        const int ci = sm.n_below;
+        if (ci < nb) {
+            composite_batch(sm, k0, ci, pos0, fx, fy0, fy1, p0, p1);
+            save_prefix(p0, view, px, py0, prefix_state, prefix_last);
+            save_prefix(p1, view, px, py1, prefix_state, prefix_last);
+            pw.crossed = true;
+            pw.n_prefix = pos0 + ci;
+            composite_batch(sm, ci, nb, pos0, fx, fy0, fy1, p0, p1);
+            return;
+        }
+    }
+    composite_batch(sm, k0, nb, pos0, fx, fy0, fy1, p0, p1);
+}
 __device__ __forceinline__ void finish_pixel(const PixelState& ps, const ClsView& view, int px,
                                              int py, float bg0, float bg1, float bg2,
                                              const float* target, int loss_mode, float* image,
@@ -125,18 +199,23 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const uint32_t* __restrict__ bin_offsets, const int32_t* __restrict__ list_ranks,
                   const uint8_t* __restrict__ cut_in, uint8_t* __restrict__ cut_out,
                   int32_t* __restrict__ trunc, int32_t* __restrict__ trunc_count,
-                  int64_t trunc_cap, float bg0, float bg1, float bg2,
-                  const float* __restrict__ target, int loss_mode, float* __restrict__ image,
-                  float* __restrict__ T_final, int32_t* __restrict__ n_contrib,
-                  float* __restrict__ dL_dimage, float* __restrict__ loss_per_scene,
-                  int* __restrict__ work_counter) {
+                  int64_t trunc_cap, ClsTileCache* __restrict__ tile_cache,
+                  float* __restrict__ prefix_state, int32_t* __restrict__ prefix_last, float bg0,
+                  float bg1, float bg2, const float* __restrict__ target, int loss_mode,
+                  float* __restrict__ image, float* __restrict__ T_final,
+                  int32_t* __restrict__ n_contrib, float* __restrict__ dL_dimage,
+                  float* __restrict__ loss_per_scene, int* __restrict__ work_counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smem_raw);
     const int n_tiles = *n_active_tiles;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, 8)
     const bool lazy = bin_offsets != nullptr;
     for (;;) {
-        if (threadIdx.x == 0) sm.tile = atomicAdd(work_counter, 1);
+        if (threadIdx.x == 0) {
+            sm.tile = atomicAdd(work_counter, 1);
+            sm.last_active = -1;
+            sm.n_below = 0;
+        }
         __syncthreads();
         const int t = sm.tile;
         if (t >= n_tiles) break;
@@ -152,15 +231,34 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
 
         PixelState p0{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py0 < H)};
         PixelState p1{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py1 < H)};
+        PrefixWalk pw;
+        {
+            const ClsTileCache c = tile_cache[tile];
+            pw.zb = c.zb;
+            pw.rebuild = c.n_prefix == CLS_PREFIX_UNKNOWN;
+            pw.crossed = false;
+            pw.skip_to = pw.rebuild ? 0u : c.n_prefix;
+            pw.n_prefix = 0u;
+        }
+        if (!pw.rebuild) {
+            load_prefix(p0, view, px, py0, prefix_state, prefix_last);
+            load_prefix(p1, view, px, py1, prefix_state, prefix_last);
+        }
         bool truncated = false;
         if (!lazy) {
-            for (uint32_t b = start; b < end; b += kTilePixels) {
+            for (uint32_t b = start + min(pw.skip_to, end - start); b < end; b += kTilePixels) {
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
-                for (int i = threadIdx.x; i < kTilePixels && b + i < end; i += kFwdThreads)
-                    stage_record(sm, i, records, vals[(int64_t)(b + i) * vals_stride]);
+                const int nb = (int)min((uint32_t)kTilePixels, end - b);
+                int below = 0;
+                for (int i = threadIdx.x; i < nb; i += kFwdThreads)
+                    stage_record(sm, i, records, vals[(int64_t)(b + i) * vals_stride],
+                                 (int)(b - start) + i, pw.zb, pw.rebuild && !pw.crossed, below);
+                if (pw.rebuild && !pw.crossed) add_below(sm, below);
                 __syncthreads();
-                composite_batch(sm, (int)min((uint32_t)kTilePixels, end - b), b - start, fx, fy0,
-                                fy1, p0, p1);
+                composite_staged(sm, nb, b - start, pw, view, px, py0, py1, fx, fy0, fy1, p0, p1,
+                                 prefix_state, prefix_last);
+                __syncthreads();
+                if (threadIdx.x == 0) sm.n_below = 0;
             }
         } else {
             // Walk the tile's depth bins front to back. Consecutive bins up to
@@ -170,13 +268,26 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             // pixel saturated are never sorted. Larger bins were sorted before.
             // Only bins up to cut_in[tile] were emitted; if the tile needs more,
             // it is queued for completion and its outputs are left to the rerun.
+            // A cached prefix starts the walk at the bin holding its end.
             const int rank = list_ranks ? list_ranks[t] : t;
             const int limit = cut_in ? (int)cut_in[tile] : kBins - 1;
             for (int i = threadIdx.x; i <= kBins; i += kFwdThreads)
                 sm.off[i] = bin_offsets[(int64_t)rank * kBins + i];
-            if (threadIdx.x == 0) sm.last_bin = -1;
             __syncthreads();
-            int bin = 0;
+            if (threadIdx.x == 0) {
+                sm.last_bin = -1;
+                int lo = 0;  // last bin starting at or before skip_to
+                if (!pw.rebuild) {
+                    int hi = kBins - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sm.off[mid] - sm.off[0] <= pw.skip_to) lo = mid; else hi = mid - 1;
+                    }
+                }
+                sm.first_bin = lo;
+            }
+            __syncthreads();
+            int bin = sm.first_bin;
             while (bin <= limit) {
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
                 const uint32_t w0 = sm.off[bin];
@@ -200,14 +311,21 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                     for (int i = threadIdx.x; i < n; i += kFwdThreads) lazy_keys[w0 + i] = sm.sorted[i];
                 }
                 for (int c0 = 0; c0 < n; c0 += kTilePixels) {
+                    const uint32_t pos0 = w0 - start + c0;
+                    const int nb = min(kTilePixels, n - c0);
+                    if (pos0 + nb <= pw.skip_to) continue;  // inside the cached prefix
                     if (c0 > 0 && __syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
-                    for (int i = threadIdx.x; i < kTilePixels && c0 + i < n; i += kFwdThreads)
+                    int below = 0;
+                    for (int i = threadIdx.x; i < nb; i += kFwdThreads)
                         stage_record(sm, i, records,
-                                     (uint32_t)(here ? sm.sorted[c0 + i] : lazy_keys[w0 + c0 + i]));
+                                     (uint32_t)(here ? sm.sorted[c0 + i] : lazy_keys[w0 + c0 + i]),
+                                     (int)pos0 + i, pw.zb, pw.rebuild && !pw.crossed, below);
+                    if (pw.rebuild && !pw.crossed) add_below(sm, below);
                     __syncthreads();
-                    composite_batch(sm, min(kTilePixels, n - c0), w0 - start + c0, fx, fy0, fy1,
-                                    p0, p1);
+                    composite_staged(sm, nb, pos0, pw, view, px, py0, py1, fx, fy0, fy1, p0, p1,
+                                     prefix_state, prefix_last);
                     __syncthreads();
+                    if (threadIdx.x == 0) sm.n_below = 0;
                 }
             }
             const bool all_done = __syncthreads_count(p0.done && p1.done) == kFwdThreads;
@@ -221,7 +339,9 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                         trunc[2 * trunc_cap + slot] = limit;
                     }
                 } else if (cut_out) {
-                    cut_out[tile] = (uint8_t)min(kBins - 1, max(sm.last_bin, 0) + kCutMargin);
+                    cut_out[tile] =
+                        sm.last_bin < 0 ? (uint8_t)0
+                                        : (uint8_t)min(kBins - 1, sm.last_bin + kCutMargin);
                 }
             }
         }
@@ -229,6 +349,15 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             __syncthreads();
             continue;
         }
+        if (pw.rebuild) {
+            if (!pw.crossed) {  // every pixel stopped (or the list ended) in front of it
+                save_prefix(p0, view, px, py0, prefix_state, prefix_last);
+                save_prefix(p1, view, px, py1, prefix_state, prefix_last);
+                pw.n_prefix = end - start;
+            }
+            if (threadIdx.x == 0) tile_cache[tile].n_prefix = pw.n_prefix;
+        }
+        if (threadIdx.x == 0) tile_cache[tile].last_active = sm.last_active;
 
         float lsum = 0.0f;
         finish_pixel(p0, view, px, py0, bg0, bg1, bg2, target, loss_mode, image, T_final,
@@ -261,7 +390,9 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
                                   const int32_t* n_active_tiles_dev, uint64_t* lazy_keys,
                                   const uint32_t* bin_offsets, const int32_t* list_ranks,
                                   const uint8_t* cut_in, uint8_t* cut_out, int32_t* trunc,
-                                  int32_t* trunc_count, int64_t trunc_cap, const float* bg,
+                                  int32_t* trunc_count, int64_t trunc_cap,
+                                  ClsTileCache* tile_cache, float* prefix_state,
+                                  int32_t* prefix_last, const float* bg,
                                   const float* target, int32_t loss_mode, float* image,
                                   float* T_final, int32_t* n_contrib, float* dL_dimage,
                                   float* loss_per_scene, int32_t* work_counter,
@@ -269,7 +400,8 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
     if (!views_dev || !info || !records ||
         (bin_offsets ? !lazy_keys : (!vals || (vals_stride != 1 && vals_stride != 2))) ||
         (cut_in && (!bin_offsets || !trunc || !trunc_count || trunc_cap < info->total_tiles)) ||
-        !ranges || !active_tiles || !n_active_tiles_dev ||
+        !ranges || !active_tiles || !n_active_tiles_dev || !tile_cache || !prefix_state ||
+        !prefix_last || !image ||
         !bg || !T_final || !n_contrib || !work_counter || loss_mode < 0 || loss_mode > 2 ||
         (loss_mode != 0 && (!target || !dL_dimage)) || info->n_views <= 0 ||
         info->total_tiles <= 0)
@@ -290,7 +422,7 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
     render_fwd_kernel<<<blocks, kFwdThreads, sizeof(FwdSmem), s>>>(
         views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
         n_active_tiles_dev, lazy_keys, bin_offsets, list_ranks, cut_in, cut_out, trunc,
-        trunc_count, trunc_cap, bg[0],
+        trunc_count, trunc_cap, tile_cache, prefix_state, prefix_last, bg[0],
         bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
         work_counter);
     CLS_CHECK_LAUNCH();

@@ -205,7 +205,8 @@ __device__ void sort_big(TileSortSmem& sm, uint64_t* keys, uint64_t* alt, int64_
 __global__ void __launch_bounds__(kTB)
 sort_tiles_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
                   const uint32_t* __restrict__ bin_offsets, const int32_t* __restrict__ n_active,
-                  int* __restrict__ work_counter) {
+                  const int32_t* __restrict__ active_tiles,
+                  const ClsTileCache* __restrict__ tile_cache, int* __restrict__ work_counter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSortSmem& sm = *reinterpret_cast<TileSortSmem*>(smem_raw);
     const int n_tiles = *n_active;
@@ -218,6 +219,11 @@ sort_tiles_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
             sm.off[threadIdx.x] = bin_offsets[(int64_t)t * kBinsPerTile + threadIdx.x];
         __syncthreads();
         int b = 0;
+        if (tile_cache) {  // bins that end inside a cached prefix are not emitted
+            const uint32_t np = tile_cache[active_tiles[t]].n_prefix;
+            if (np != CLS_PREFIX_UNKNOWN)
+                while (b < kBinsPerTile && sm.off[b + 1] - sm.off[0] <= np) ++b;
+        }
         while (b < kBinsPerTile) {  // uniform over the block
             const uint32_t w0 = sm.off[b];
             int e = b + 1;
@@ -244,6 +250,7 @@ __global__ void collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
                                     const uint8_t* __restrict__ cut,
                                     const int32_t* __restrict__ trunc,
                                     const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
+                                    const ClsTileCache* __restrict__ tile_cache,
                                     int min_bin, uint2* __restrict__ list,
                                     int32_t* __restrict__ count, int64_t list_cap) {
     const int64_t nt = trunc ? min((int64_t)*trunc_count, trunc_cap) : (int64_t)(*n_active);
@@ -261,6 +268,12 @@ __global__ void collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
         }
         const int64_t idx = rank * kBinsPerTile + b;
         const uint32_t a = bin_offsets[idx], n = bin_offsets[idx + 1] - a;
+        if (n >= (uint32_t)min_bin && tile_cache) {
+            // a bin that ends inside the tile's cached prefix is never read
+            const uint32_t np = tile_cache[trunc ? trunc[t] : active_tiles[t]].n_prefix;
+            if (np != CLS_PREFIX_UNKNOWN && a + n - bin_offsets[rank * kBinsPerTile] <= np)
+                continue;
+        }
         if (n >= (uint32_t)min_bin) {
             const int slot = atomicAdd(count, 1);
             if (slot < list_cap) list[slot] = make_uint2(a, n);
@@ -306,12 +319,13 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
                               int64_t total_tiles, int64_t capacity, int32_t min_bin,
                               const uint8_t* cut, const int32_t* trunc,
                               const int32_t* trunc_count, int64_t trunc_cap,
-                              int32_t* work_counter, void* workspace, size_t workspace_bytes,
-                              cls_stream_t stream) {
+                              const ClsTileCache* tile_cache, int32_t* work_counter,
+                              void* workspace, size_t workspace_bytes, cls_stream_t stream) {
     if (!keys || !keys_alt || !bin_offsets || !n_active_tiles_dev || !work_counter ||
         total_tiles <= 0 || capacity < 0 || !workspace ||
         workspace_bytes < cls_sort_tiles_workspace_size(capacity, min_bin) ||
-        (cut && !active_tiles) || (trunc && (!trunc_count || trunc_cap < total_tiles)) ||
+        ((cut || tile_cache) && !active_tiles) ||
+        (trunc && (!trunc_count || trunc_cap < total_tiles)) ||
         ((cut || trunc) && min_bin <= 1))
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
@@ -330,15 +344,16 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     if (min_bin <= 1) {
         sort_tiles_kernel<<<(int)hmin64(total_tiles, g_tiles_blocks), kTB, sizeof(TileSortSmem),
-                            s>>>(keys, keys_alt, bin_offsets, n_active_tiles_dev, work_counter);
+                            s>>>(keys, keys_alt, bin_offsets, n_active_tiles_dev, active_tiles,
+                                 tile_cache, work_counter);
     } else {
         int32_t* count = static_cast<int32_t*>(workspace);
         uint2* list = reinterpret_cast<uint2*>(static_cast<char*>(workspace) + 256);
         const int64_t cap = list_cap_for(capacity, min_bin);
         cudaMemsetAsync(count, 0, sizeof(int32_t), s);
         collect_bins_kernel<<<1024, 256, 0, s>>>(bin_offsets, n_active_tiles_dev, active_tiles,
-                                                 cut, trunc, trunc_count, trunc_cap, min_bin,
-                                                 list, count, cap);
+                                                 cut, trunc, trunc_count, trunc_cap, tile_cache,
+                                                 min_bin, list, count, cap);
         sort_bins_kernel<<<g_tiles_blocks, kTB, sizeof(TileSortSmem), s>>>(keys, keys_alt, list,
                                                                           count, cap, work_counter);
     }

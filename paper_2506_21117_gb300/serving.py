@@ -52,13 +52,14 @@ class Request:
 def estimate_footprint(n_gauss: int, cams: Sequence, pairs_per_tile: int = 1024) -> int:
     """Device bytes one in-flight request needs beyond its resident scene:
     projected records (48 B per Gaussian and view), per-pixel buffers (image,
-    target, dL/dimage, final T, last contributor: 44 B), per-tile tables and a
+    target, dL/dimage, final T, last contributor, state after the static
+    prefix: 64 B), per-tile tables and a
     key allowance of `pairs_per_tile` pairs of 16 B (key + scratch) per tile."""
     total = 0
     for c in cams:
         W, H = int(c["width"]), int(c["height"])
         tiles = ((W + 15) // 16) * ((H + 15) // 16)
-        total += n_gauss * 48 + W * H * 44 + tiles * (256 * 8 + 64) + tiles * pairs_per_tile * 16
+        total += n_gauss * 48 + W * H * 64 + tiles * (256 * 8 + 80) + tiles * pairs_per_tile * 16
     return total
 
 
@@ -193,7 +194,7 @@ class Server:
         b = self.batch
         b.project_and_bin(1)
         b.sort()
-        b.forward(self.loss_mode, write_image=False)
+        b.forward(self.loss_mode)
         b.backward()
         b.adam(self.lr)
 

@@ -86,6 +86,7 @@ class SceneState:
         self.active = torch.zeros(self.n, dtype=torch.uint8, device=device)
         self.active_idx = torch.zeros(max(self.n, 1), dtype=torch.int32, device=device)
         self.n_active = 0
+        self.epoch = 0  # bumped whenever the active set changes
 
     def set_active(self, active: np.ndarray):
         a = np.asarray(active, bool)
@@ -93,6 +94,7 @@ class SceneState:
         self.active.copy_(torch.from_numpy(a.astype(np.uint8)))
         self.active_idx[: idx.size].copy_(torch.from_numpy(idx))
         self.n_active = int(idx.size)
+        self.epoch += 1
 
     def bytes_resident(self) -> int:
         return 3 * self.params.numel() * 4 + self.active.numel() * 5
@@ -102,15 +104,19 @@ class Batch:
     """Scene/view tables of one launch batch and every buffer the hot path uses."""
 
     def __init__(self, scenes: Sequence[SceneState], cams_per_scene: Sequence[Sequence],
-                 device="cuda", layout: int = 1, lazy: bool = True):
+                 device="cuda", layout: int = 1, lazy: bool = True, prefix_cache: bool = True):
         """layout 1: pairs bucketed by (tile, depth bin); with `lazy` the
         renderer sorts the depth bins it reaches (cls_sort_tiles only pre-sorts
         bins above CLS_LAZY_MAX_BIN keys), otherwise cls_sort_tiles sorts every
         bin. layout 0: flat (tile, depth) keys sorted by the global onesweep
-        radix sort (cls_sort_keys)."""
+        radix sort (cls_sort_keys). `prefix_cache` keeps each tile's static
+        prefix across iterations (valid while the static rows of the scenes do
+        not change, which masked Adam guarantees); off, every iteration
+        rebuilds it."""
         self.device = device
         self.layout = layout
         self.lazy = lazy and layout == 1
+        self.prefix_mode = 1 if prefix_cache else 0
         self.scenes = list(scenes)
         S = len(scenes)
         views = []
@@ -163,6 +169,13 @@ class Batch:
         self.cut = torch.full((info.total_tiles,), 255, dtype=torch.uint8, device=dev)
         self.trunc = torch.zeros(3 * info.total_tiles, dtype=torch.int32, device=dev)
         self.trunc_count = torch.zeros(1, dtype=torch.int32, device=dev)
+        # static-prefix cache: per tile (ClsTileCache), per pixel state after the prefix
+        self.tile_cache = torch.empty(info.total_tiles * abi.TILE_CACHE_BYTES // 4,
+                                      dtype=torch.int32, device=dev)
+        self.prefix_state = torch.zeros(info.total_pixels * 4, dtype=torch.float32, device=dev)
+        self.prefix_last = torch.zeros(info.total_pixels, dtype=torch.int32, device=dev)
+        self._epochs = [st.epoch for st in self.scenes]
+        self.reset_prefix()
         self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
                                    device=dev)
         self.adam_ws = torch.zeros(max(abi.cls_adam_workspace_size(S), 256), dtype=torch.uint8,
@@ -197,14 +210,23 @@ class Batch:
     def stream(self):
         return torch.cuda.current_stream().cuda_stream
 
+    def reset_prefix(self):
+        """Forget every tile's static prefix (the next iteration rebuilds it)."""
+        self.tile_cache.fill_(-1)
+
     def project_and_bin(self, mode: int):
         b = self
+        epochs = [st.epoch for st in b.scenes]
+        if epochs != b._epochs:  # an active set changed: the frozen rows did too
+            b._epochs = epochs
+            b.reset_prefix()
         abi.check(abi.cls_project_and_bin(
             _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, mode, b.layout, _ptr(b.records),
             _ptr(b.tile_active), _ptr(b.active_tiles), _ptr(b.n_active_tiles),
             _ptr(b.keys), _ptr(b.vals), b.capacity, _ptr(b.n_pairs), _ptr(b.ranges),
-            _ptr(b.bin_offsets), _ptr(b.cut) if b.use_cut else None, _ptr(b.status),
-            _ptr(b.proj_ws), b.proj_ws.numel(), b.stream()), "cls_project_and_bin")
+            _ptr(b.bin_offsets), _ptr(b.cut) if b.use_cut else None, _ptr(b.tile_cache),
+            b.prefix_mode, _ptr(b.status), _ptr(b.proj_ws), b.proj_ws.numel(), b.stream()),
+            "cls_project_and_bin")
 
     def plan_capacity(self, slack: float = 1.5, extra: int = 1 << 16):
         """Count the pairs once (mode 0 projection, no keys) and size the key
@@ -240,7 +262,8 @@ class Batch:
             _ptr(b.n_active_tiles), cap, b.capacity, b.min_bin(),
             _ptr(b.cut) if cut and not after_completion else None,
             _ptr(b.trunc) if after_completion else None,
-            _ptr(b.trunc_count) if after_completion else None, cap, _ptr(b.counter) + 8,
+            _ptr(b.trunc_count) if after_completion else None, cap, _ptr(b.tile_cache),
+            _ptr(b.counter) + 8,
             _ptr(b.tiles_ws), b.tiles_ws.numel(), b.stream()), "cls_sort_tiles")
 
     def min_bin(self) -> int:
@@ -256,14 +279,16 @@ class Batch:
             b.capacity, b.info.key_bits, _ptr(b.ranges), b.info.total_tiles, _ptr(b.status),
             _ptr(b.sort_ws), b.sort_ws.numel(), b.stream()), "cls_sort_keys")
 
-    def forward(self, loss_mode: int, bg=(0.0, 0.0, 0.0), write_image: bool = True):
+    def forward(self, loss_mode: int, bg=(0.0, 0.0, 0.0)):
+        """Render the active tiles into `image` (the backward pass reads it),
+        with the fused loss when loss_mode is 1 (L1) or 2 (L2)."""
         b = self
         if loss_mode:
             b.loss.zero_()
         cut = b.use_cut
         if cut:
             b.trunc_count.zero_()
-        b._forward_call(loss_mode, bg, write_image, _ptr(b.active_tiles), _ptr(b.n_active_tiles),
+        b._forward_call(loss_mode, bg, _ptr(b.active_tiles), _ptr(b.n_active_tiles),
                         None, _ptr(b.cut) if cut else None, _ptr(b.cut) if cut else None)
         if cut:
             # tiles whose cut was too shallow: write their missing pairs, render again
@@ -273,11 +298,11 @@ class Batch:
                 _ptr(b.trunc), _ptr(b.trunc_count), cap, _ptr(b.counter) + 12, _ptr(b.proj_ws),
                 b.proj_ws.numel(), b.stream()), "cls_complete_truncated")
             b._sort_tiles(after_completion=True)  # large bins the completion filled
-            b._forward_call(loss_mode, bg, write_image, _ptr(b.trunc), _ptr(b.trunc_count),
+            b._forward_call(loss_mode, bg, _ptr(b.trunc), _ptr(b.trunc_count),
                             _ptr(b.trunc) + 4 * cap, None, _ptr(b.cut), rerun=True)
 
-    def _forward_call(self, loss_mode, bg, write_image, tiles, n_tiles, list_ranks, cut_in,
-                      cut_out, rerun=False):
+    def _forward_call(self, loss_mode, bg, tiles, n_tiles, list_ranks, cut_in, cut_out,
+                      rerun=False):
         b = self
         cap = b.info.total_tiles
         abi.check(abi.cls_render_forward(
@@ -285,9 +310,10 @@ class Batch:
             tiles, n_tiles, _ptr(b.keys) if b.lazy else None,
             _ptr(b.bin_offsets) if b.lazy else None, list_ranks, cut_in, cut_out,
             None if rerun or cut_in is None else _ptr(b.trunc),
-            None if rerun or cut_in is None else _ptr(b.trunc_count), cap, bg,
+            None if rerun or cut_in is None else _ptr(b.trunc_count), cap, _ptr(b.tile_cache),
+            _ptr(b.prefix_state), _ptr(b.prefix_last), bg,
             _ptr(b.target) if loss_mode else None, loss_mode,
-            _ptr(b.image) if write_image else None, _ptr(b.T_final), _ptr(b.n_contrib),
+            _ptr(b.image), _ptr(b.T_final), _ptr(b.n_contrib),
             _ptr(b.dL_dimage) if loss_mode else None, _ptr(b.loss) if loss_mode else None,
             _ptr(b.counter), b.stream()), "cls_render_forward")
 
@@ -305,13 +331,16 @@ class Batch:
             return self.keys[:n].cpu().numpy().view(np.uint32)[0::2].copy()
         return self.vals[:n].cpu().numpy().view(np.uint32).copy()
 
-    def backward(self, bg=(0.0, 0.0, 0.0)):
+    def backward(self):
+        """Gradients of the active rows from dL_dimage (the background is in
+        the image the forward pass wrote)."""
         b = self
         abi.check(abi.cls_render_backward(
             _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, _ptr(b.records), *b._sorted_vals(),
-            _ptr(b.ranges), _ptr(b.active_tiles), _ptr(b.n_active_tiles), bg, _ptr(b.T_final),
-            _ptr(b.n_contrib), _ptr(b.dL_dimage), _ptr(b.grad2d), _ptr(b.grads),
-            _ptr(b.counter) + 4, b.stream()), "cls_render_backward")
+            _ptr(b.ranges), _ptr(b.active_tiles), _ptr(b.n_active_tiles), _ptr(b.tile_cache),
+            _ptr(b.prefix_state), _ptr(b.image), _ptr(b.n_contrib), _ptr(b.dL_dimage),
+            _ptr(b.grad2d), _ptr(b.grads), _ptr(b.counter) + 4, b.stream()),
+            "cls_render_backward")
 
     def adam(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-15):
         b = self
@@ -320,8 +349,9 @@ class Batch:
             _ptr(b.adam_ws), b.adam_ws.numel(), b.stream()), "cls_adam_step_active")
 
     def launches_per_step(self) -> int:
-        """Kernels of one iteration. project_and_bin (mode 1): project and
-        stamp (2 if any Gaussian is active), tile mask, compaction, count,
+        """Kernels of one iteration. project_and_bin (mode 1): project,
+        stamp and nearest-active depth (3 if any Gaussian is active), tile
+        mask, compaction, count,
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
         prefix, bucket counts, scan, offsets, emit (6). Sort: flat
         hist + scan + passes (+ copy if odd) + ranges; bucketed 1 or 2.
@@ -329,7 +359,7 @@ class Batch:
         collection and sort, rerun);
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
-        proj = active + 3 + (6 if self.layout == 1 else 3)
+        proj = (3 if active else 0) + 3 + (6 if self.layout == 1 else 3)
         if self.layout == 1:
             sort = 2 if self.lazy else 1
         else:
@@ -378,6 +408,7 @@ def lift(state: SceneState, cams: Sequence, masks, vote_mode: int = 0, device="c
         vote_mode, _ptr(state.active), _ptr(state.active_idx), _ptr(n_act), _ptr(votes),
         _ptr(ws), ws.numel(), stream), "cls_lift_change_masks")
     state.n_active = int(n_act.item())
+    state.epoch += 1
     if not want_votes:
         return None, None
     return state.active.cpu().numpy(), votes.view(-1, 2)[:n].cpu().numpy()
@@ -436,7 +467,7 @@ class LocalUpdate:
         b.sort()
         b.forward(self.loss_mode if b.target is not None else 0, self.bg)
         if with_backward:
-            b.backward(self.bg)
+            b.backward()
             if with_adam:
                 b.adam(self.lr)
 

@@ -161,3 +161,28 @@ def test_sampled_gradients(run):
     checked = len(sel)
     print(f"full size: gradients of {checked} sampled active Gaussians match the oracle")
     assert checked >= 1
+
+
+def test_cached_static_prefix_full_size(run):
+    """Two more passes with the parameters unchanged start every tile from its
+    cached static prefix and reproduce the first pass bit for bit (image,
+    final T, last contributors) and its gradients up to summation order."""
+    lu = run["lu"]
+    b = lu.batch
+    A = lu.state.n_active
+    first = (b.image.clone(), b.T_final.clone(), b.n_contrib.clone())
+    g_first = b.grads[: A * lu.state.stride].clone()
+    for _ in range(2):
+        b.project_and_bin(1)
+        decided = b.tile_cache.view(-1, 4)[:, 1].clone()
+        b.sort()
+        b.forward(lu.loss_mode)
+        b.backward()
+    torch.cuda.synchronize()
+    b.check_status()
+    tiles = b.active_tiles[: int(b.n_active_tiles.item())].long()
+    assert bool((decided[tiles] != -1).all())
+    for x, y in zip(first, (b.image, b.T_final, b.n_contrib)):
+        assert torch.equal(x, y)
+    torch.testing.assert_close(b.grads[: A * lu.state.stride], g_first, rtol=1e-4, atol=1e-9)
+    print(f"full size: {tiles.numel()} tiles rendered from their cached static prefix")

@@ -401,6 +401,100 @@ def test_depth_cut_and_completion_reproduce_full_emission(case):
     print(f"depth cut: {n_trunc} tiles completed after a forced cut of 0")
 
 
+# ----------------------------------------------------------- static prefix --
+
+def _iteration(b, loss_mode, lr):
+    """One iteration step by step; returns each tile's n_prefix as decided
+    before the forward pass (-1: the prefix is rebuilt this iteration)."""
+    b.project_and_bin(1)
+    decided = b.tile_cache.view(-1, 4)[:, 1].clone()
+    b.sort()
+    b.forward(loss_mode)
+    b.backward()
+    b.adam(lr)
+    return decided
+
+
+def _outputs(lu):
+    b = lu.batch
+    A = lu.state.n_active
+    return (b.image.clone(), b.T_final.clone(), b.n_contrib.clone(), float(b.loss[0]),
+            b.grads[: A * lu.state.stride].clone())
+
+
+@pytest.mark.parametrize("layout,lazy", [(1, True), (1, False), (0, False)])
+def test_static_prefix_cache_is_exact(layout, lazy):
+    """With the parameters held fixed (lr = 0), iterations that start from
+    every tile's cached static prefix give bit-identical images, final T and
+    last contributors, and the same gradients up to float32 summation order,
+    as the first iteration, which composites every tile from the front."""
+    from paper_2506_21117_gb300.update import LocalUpdate
+    scene, _, cams, masks, _ = S.workload_local(n=30000, n_views=4, size=160)
+    targets = [S.random_image(c, 80 + j) for j, c in enumerate(cams)]
+    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1", layout=layout,
+                     lazy=lazy)
+    b = lu.batch
+    outs, decided = [], []
+    for _ in range(3):
+        decided.append(_iteration(b, 1, 0.0))
+        torch.cuda.synchronize()
+        b.check_status()
+        outs.append(_outputs(lu))
+    tiles = b.active_tiles[: int(b.n_active_tiles.item())].long()
+    assert tiles.numel() > 20
+    assert bool((decided[0][tiles] == -1).all())
+    kept = float((decided[2][tiles] != -1).float().mean())
+    assert kept == 1.0, kept
+    for o in outs[1:]:
+        for x, y in zip(outs[0][:3], o[:3]):
+            assert torch.equal(x, y)
+        assert o[3] == pytest.approx(outs[0][3], rel=1e-6)
+        torch.testing.assert_close(o[4], outs[0][4], rtol=1e-4, atol=1e-9)
+    print(f"static prefix ({layout}, {lazy}): {tiles.numel()} tiles kept their prefix")
+
+
+def test_static_prefix_cache_after_active_gaussians_move():
+    """The active Gaussians move after the prefix was cached (every parameter
+    of theirs perturbed by N(0, 0.05), the static rows unchanged): tiles whose
+    nearest active Gaussian crossed the boundary rebuild, the others keep it,
+    and the result equals a fresh render of the moved scene bit for bit and
+    the oracle's within the pixel and gradient tolerances."""
+    from paper_2506_21117_gb300.update import LocalUpdate, pack_params
+    scene, cams, masks, targets = _small_local(seed=5, n=6000, deg=3, size=(128, 96))
+    active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
+    lu = LocalUpdate(scene, cams, 3, targets=targets, active=active, loss="l1")
+    b = lu.batch
+    _iteration(b, 1, 0.0)
+    moved = S.perturb_scene(scene, active, 0.05, seed=11)
+    idx = np.flatnonzero(active)
+    rows = torch.from_numpy(pack_params(moved, 3)[idx]).to(lu.state.params.device)
+    lu.state.params[torch.from_numpy(idx).long().cuda()] = rows
+    decided = _iteration(b, 1, 0.0)
+    torch.cuda.synchronize()
+    b.check_status()
+    tiles = b.active_tiles[: int(b.n_active_tiles.item())].long()
+    kept = int((decided[tiles] != -1).sum())
+    print(f"moved: {kept} of {tiles.numel()} tiles kept their static prefix")
+    assert 0 < kept < tiles.numel()
+    got = _outputs(lu)
+
+    fresh = LocalUpdate(moved, cams, 3, targets=targets, active=active, loss="l1")
+    _iteration(fresh.batch, 1, 0.0)
+    torch.cuda.synchronize()
+    want = _outputs(fresh)
+    for x, y in zip(got[:3], want[:3]):
+        assert torch.equal(x, y)
+    torch.testing.assert_close(got[4], want[4], rtol=1e-4, atol=1e-9)
+
+    tl = ostep.active_tiles(moved, cams, active)
+    ref = ostep.render(moved, cams, 3, targets=targets, tiles=tl)
+    _compare_pixels(lu, ref, cams)
+    gref = ostep.local_step_reference(moved, cams, 3, targets, active, "l1")
+    worst, excl = _compare_grads(lu, gref, active, 3, exclude=gref["near_ids"])
+    print(f"moved: gradients worst error/bound {worst:.3f}, {excl} excluded")
+    assert excl <= 0.05 * active.sum()
+
+
 # -------------------------------------------------------------------- Adam --
 
 def test_adam_step_matches_oracle_and_freezes_static_rows():
