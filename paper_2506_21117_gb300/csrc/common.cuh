@@ -245,6 +245,42 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
 
+// Conservative per-tile cull of a list entry: true only if no pixel centre of
+// the tile whose first pixel is (tx0, ty0) can reach alpha >= 1/255, so every
+// pixel would skip the entry and dropping it changes nothing. With
+// Q(d) = A dx^2 + 2 B dx dy + C dy^2 (the record's conic; power = -Q/2), the
+// minimum of Q over the rectangle of the tile's pixel offsets is 0 if the
+// centre lies inside, else it lies on an edge, at the stationary point along
+// that edge clamped to it. The offsets bound exactly the renderer's own
+// dx = (x + 0.5) - u (same rounding, monotone). The bound is lowered by
+// 1e-5 S + 1e-5, S >= |A| dx^2 + 2|B dx dy| + |C| dy^2 on the rectangle: both
+// this minimum and the renderer's exponent are float32 sums whose rounding is
+// near 1e-7 S. An entry is culled if even that lowered minimum leaves
+// o exp(-Q/2) below 0.999 / 255.
+__device__ __forceinline__ bool tile_culled(float4 r0, float4 r1, float tx0, float ty0) {
+    const float u = r0.x, v = r0.y, A = r0.z, B = r0.w, C = r1.x, o = r1.y;
+    if (o < kAlphaMin * 0.999f) return true;
+    const float X0 = (tx0 + 0.5f) - u, X1 = (tx0 + (float)kTile - 0.5f) - u;
+    const float Y0 = (ty0 + 0.5f) - v, Y1 = (ty0 + (float)kTile - 0.5f) - v;
+    if (X0 <= 0.f && X1 >= 0.f && Y0 <= 0.f && Y1 >= 0.f) return false;
+    const float iA = 1.0f / A, iC = 1.0f / C;
+    float q = 3.4e38f;
+    {
+        const float ya = fminf(fmaxf(-B * X0 * iC, Y0), Y1);
+        const float yb = fminf(fmaxf(-B * X1 * iC, Y0), Y1);
+        const float xa = fminf(fmaxf(-B * Y0 * iA, X0), X1);
+        const float xb = fminf(fmaxf(-B * Y1 * iA, X0), X1);
+        q = fminf(q, A * X0 * X0 + 2.0f * B * X0 * ya + C * ya * ya);
+        q = fminf(q, A * X1 * X1 + 2.0f * B * X1 * yb + C * yb * yb);
+        q = fminf(q, A * xa * xa + 2.0f * B * xa * Y0 + C * Y0 * Y0);
+        q = fminf(q, A * xb * xb + 2.0f * B * xb * Y1 + C * Y1 * Y1);
+    }
+    const float DX = fmaxf(fabsf(X0), fabsf(X1)), DY = fmaxf(fabsf(Y0), fabsf(Y1));
+    const float S = (fabsf(A) + fabsf(B)) * DX * DX + (fabsf(B) + fabsf(C)) * DY * DY;
+    const float q_lo = q - 1e-5f * S - 1e-5f;
+    return q_lo > 2.0f * logf(o * (255.0f / 0.999f));
+}
+
 // View index owning a global tile id (views sorted by tile_base).
 __device__ __forceinline__ int view_of_tile(const ClsView* views, int n_views, int tile) {
     int lo = 0, hi = n_views - 1;

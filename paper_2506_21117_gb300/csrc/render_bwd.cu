@@ -143,7 +143,9 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
     __shared__ float4 s_b[kTilePixels];
     __shared__ float s_c[kTilePixels];
     __shared__ int s_slot[kTilePixels];
+    __shared__ int s_pos[kTilePixels];
     __shared__ float s_g[kSub][kBwdWarps][kGradComps + 1];
+    __shared__ int s_cnt[2][kBwdWarps];
     __shared__ int s_tile;
     __shared__ int s_maxend;
     const int n_tiles = *n_active_tiles;
@@ -170,6 +172,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
         const int local = tile - view.tile_base;
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const uint32_t start = ranges[2 * (int64_t)tile];
+        const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
         BwdPixel p0, p1;
         bwd_load_pixel(p0, view, tx * kTile + lx, ty * kTile + ly, n_prefix, c.last_active + 1,
                        prefix_state, image, n_contrib, dL_dimage);
@@ -182,37 +185,69 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
 
         for (int lo = n_prefix; lo < max_end; lo += kTilePixels) {
             const int nb = min(kTilePixels, max_end - lo);
-            for (int i = threadIdx.x; i < nb; i += kBwdThreads) {
-                const float4* rec = reinterpret_cast<const float4*>(
-                    records + vals[(int64_t)(start + lo + i) * vals_stride]);
-                s_a[i] = stage_conic_a(rec[0]);
-                s_b[i] = stage_conic_b(rec[1]);
-                const float4 cc = rec[2];
-                s_c[i] = cc.x;
-                s_slot[i] = __float_as_int(cc.y);
+            // stage the batch, dropping entries the forward pass's tile cull
+            // drops (no pixel of the tile reaches alpha >= 1/255), in order
+            uint32_t rec[2];
+            unsigned mk[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int i = r * kBwdThreads + threadIdx.x;
+                bool keep = false;
+                rec[r] = 0;
+                if (i < nb) {
+                    rec[r] = vals[(int64_t)(start + lo + i) * vals_stride];
+                    const float4* q = reinterpret_cast<const float4*>(records + rec[r]);
+                    keep = !tile_culled(q[0], q[1], tx0, ty0);
+                }
+                mk[r] = __ballot_sync(0xffffffffu, keep);
+                if (lane == 0) s_cnt[r][warp] = __popc(mk[r]);
             }
             __syncthreads();
-            for (int k0 = 0; k0 < nb; k0 += kSub) {
-                const int k1 = min(nb, k0 + kSub);
+            int nk = 0, base[2] = {0, 0};
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                for (int w = 0; w < kBwdWarps; ++w) {
+                    if (w == warp) base[r] = nk;
+                    nk += s_cnt[r][w];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (mk[r] & (1u << lane)) {
+                    const int k = base[r] + __popc(mk[r] & ((1u << lane) - 1u));
+                    const float4* q = reinterpret_cast<const float4*>(records + rec[r]);
+                    s_a[k] = stage_conic_a(q[0]);
+                    s_b[k] = stage_conic_b(q[1]);
+                    const float4 cc = q[2];
+                    s_c[k] = cc.x;
+                    s_slot[k] = __float_as_int(cc.y);
+                    s_pos[k] = lo + r * kBwdThreads + threadIdx.x;
+                }
+            }
+            __syncthreads();
+            for (int k0 = 0; k0 < nk; k0 += kSub) {
+                const int k1 = min(nk, k0 + kSub);
                 bool any_active = false;
                 for (int k = k0; k < k1; ++k) {
                     const float4 a = s_a[k];
                     const float4 bb = s_b[k];
                     const float cb = s_c[k];
                     const bool active = s_slot[k] >= 0;  // uniform over the block
+                    const int pos = s_pos[k];
                     const float dx = p0.fx - a.x;
                     const float t = a.z * dx;
                     if (!active) {
-                        bwd_entry<false>(p0, lo + k, dx, t, a, bb, cb, nullptr);
-                        bwd_entry<false>(p1, lo + k, dx, t, a, bb, cb, nullptr);
+                        bwd_entry<false>(p0, pos, dx, t, a, bb, cb, nullptr);
+                        bwd_entry<false>(p1, pos, dx, t, a, bb, cb, nullptr);
                         continue;
                     }
                     any_active = true;
                     float gr[kGradComps];
 #pragma unroll
                     for (int q = 0; q < kGradComps; ++q) gr[q] = 0.f;
-                    const bool c0 = bwd_entry<true>(p0, lo + k, dx, t, a, bb, cb, gr);
-                    const bool c1 = bwd_entry<true>(p1, lo + k, dx, t, a, bb, cb, gr);
+                    const bool c0 = bwd_entry<true>(p0, pos, dx, t, a, bb, cb, gr);
+                    const bool c1 = bwd_entry<true>(p1, pos, dx, t, a, bb, cb, gr);
                     float* dst = &s_g[k - k0][warp][0];
                     if (__any_sync(0xffffffffu, c0 || c1)) {
                         const float y = reduce8_scatter(gr, lane);

@@ -21,19 +21,24 @@ constexpr int kLazyMax = 1024;         // largest bin the renderer sorts itself
 constexpr int kBins = CLS_DEPTH_BINS;
 constexpr int kCutMargin = 4;          // depth bins emitted beyond last iteration's need
 
+constexpr int kFwdWarps = kFwdThreads / 32;
+
 struct FwdSmem {
     float4 a[kTilePixels];
     float4 b[kTilePixels];
     float c[kTilePixels];
+    uint32_t pos[kTilePixels];  // list position of each staged entry
     uint64_t key[kLazyMax];
     uint64_t sorted[kLazyMax];
     uint32_t off[kBins + 1];
-    float red[kFwdThreads / 32];
+    float red[kFwdWarps];
+    // per staging round and warp: entries kept, kept in front of the prefix
+    // boundary, in front of the boundary
+    int cnt[3][2][kFwdWarps];
     int tile;
     int last_bin;
     int first_bin;
     int last_active;  // last list position of a staged active entry
-    int n_below;      // entries of the staged batch in front of the prefix boundary
 };
 
 // Per-thread compositing state of one pixel.
@@ -52,22 +57,77 @@ struct PrefixWalk {
     uint32_t n_prefix;  // entries in front of the boundary (rebuild)
 };
 
-__device__ __forceinline__ void stage_record(FwdSmem& sm, int i, const ClsProjected* records,
-                                             uint32_t rec, int pos, uint32_t zb, bool count,
-                                             int& below) {
-    const float4* r = reinterpret_cast<const float4*>(records + rec);
-    sm.a[i] = stage_conic_a(r[0]);
-    sm.b[i] = stage_conic_b(r[1]);
-    const float4 r2 = r[2];
-    sm.c[i] = r2.x;
-    if (__float_as_int(r2.y) >= 0) atomicMax(&sm.last_active, pos);
-    below += (count && __float_as_uint(r2.z) < zb) ? 1 : 0;
-}
+// Counts of one staged batch (uniform over the block).
+struct Staged {
+    int n;             // entries kept
+    int n_below_kept;  // kept entries in front of the prefix boundary (a prefix of them)
+    int n_below_all;   // batch entries in front of the boundary
+};
 
-// Warp-aggregated count of the staged entries in front of the boundary.
-__device__ __forceinline__ void add_below(FwdSmem& sm, int below) {
-    below = __reduce_add_sync(0xffffffffu, (unsigned)below);
-    if ((threadIdx.x & 31) == 0 && below) atomicAdd(&sm.n_below, below);
+// Stage batch entries i = 0 .. nb-1 (record rec_of(i), list position pos0 + i)
+// into shared memory in list order, keeping those at or behind skip_to that
+// tile_culled does not drop; counts the entries in front of the prefix
+// boundary while a rebuild has not crossed it. Two entries per thread; an
+// order-preserving compaction by ballots and per-warp counts.
+template <typename RecOf>
+__device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0, RecOf rec_of,
+                                              const ClsProjected* records, float tx0, float ty0,
+                                              const PrefixWalk& pw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool count = pw.rebuild && !pw.crossed;
+    uint32_t rec[2];
+    unsigned mk[2];
+    // pass 1: which entries stay (the records are read again in pass 2, from cache)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = r * kFwdThreads + threadIdx.x;
+        bool keep = false, below = false;
+        rec[r] = 0;
+        if (i < nb) {
+            rec[r] = rec_of(i);
+            const float4* p = reinterpret_cast<const float4*>(records + rec[r]);
+            below = count && __float_as_uint(p[2].z) < pw.zb;
+            keep = pos0 + (uint32_t)i >= pw.skip_to && !tile_culled(p[0], p[1], tx0, ty0);
+        }
+        mk[r] = __ballot_sync(0xffffffffu, keep);
+        const unsigned mkb = __ballot_sync(0xffffffffu, keep && below);
+        const unsigned mb = __ballot_sync(0xffffffffu, below);
+        if (lane == 0) {
+            sm.cnt[0][r][warp] = __popc(mk[r]);
+            sm.cnt[1][r][warp] = __popc(mkb);
+            sm.cnt[2][r][warp] = __popc(mb);
+        }
+    }
+    __syncthreads();
+    Staged st{0, 0, 0};
+    int base[2] = {0, 0};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int w = 0; w < kFwdWarps; ++w) {
+            if (w == warp) base[r] = st.n;
+            st.n += sm.cnt[0][r][w];
+            st.n_below_kept += sm.cnt[1][r][w];
+            st.n_below_all += sm.cnt[2][r][w];
+        }
+    }
+    // pass 2: the kept entries, compacted in list order
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (mk[r] & (1u << lane)) {
+            const int k = base[r] + __popc(mk[r] & lt);
+            const uint32_t pos = pos0 + (uint32_t)(r * kFwdThreads + threadIdx.x);
+            const float4* p = reinterpret_cast<const float4*>(records + rec[r]);
+            const float4 r2 = p[2];
+            sm.a[k] = stage_conic_a(p[0]);
+            sm.b[k] = stage_conic_b(p[1]);
+            sm.c[k] = r2.x;
+            sm.pos[k] = pos;
+            if (__float_as_int(r2.y) >= 0) atomicMax(&sm.last_active, (int)pos);
+        }
+    }
+    return st;
 }
 
 __device__ __forceinline__ void composite_one(float dx, float t, float dy, const float4& a,
@@ -91,19 +151,19 @@ __device__ __forceinline__ void composite_one(float dx, float t, float dy, const
     ps.last = pos + 1;
 }
 
-// Composite staged records k0 .. k1 - 1 (list positions pos0 + k) into two
-// pixels of one column.
-__device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k1, uint32_t pos0,
-                                                float fx, float fy0, float fy1, PixelState& p0,
+// Composite staged records k0 .. k1 - 1 into two pixels of one column.
+__device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k1, float fx,
+                                                float fy0, float fy1, PixelState& p0,
                                                 PixelState& p1) {
     for (int k = k0; k < k1 && !(p0.done && p1.done); ++k) {
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
+        const uint32_t pos = sm.pos[k];
         const float dx = fx - a.x;
         const float t = a.z * dx;
-        composite_one(dx, t, fy0 - a.y, a, bb, cb, pos0 + k, p0);
-        composite_one(dx, t, fy1 - a.y, a, bb, cb, pos0 + k, p1);
+        composite_one(dx, t, fy0 - a.y, a, bb, cb, pos, p0);
+        composite_one(dx, t, fy1 - a.y, a, bb, cb, pos, p1);
     }
 }
 
@@ -128,28 +188,25 @@ __device__ __forceinline__ void load_prefix(PixelState& ps, const ClsView& view,
     ps.last = (uint32_t)prefix_last[pix];
 }
 
-// Composite one staged batch of nb entries at list positions pos0 ..: skip
-// the cached prefix, and when rebuilding, save the pixel state at the first
-// entry at or behind the boundary. Uniform over the block.
-__device__ __forceinline__ void composite_staged(const FwdSmem& sm, int nb, uint32_t pos0,
-                                                 PrefixWalk& pw, const ClsView& view, int px,
-                                                 int py0, int py1, float fx, float fy0, float fy1,
-                                                 PixelState& p0, PixelState& p1,
-                                                 float* prefix_state, int32_t* prefix_last) {
-    const int k0 = pw.skip_to > pos0 ? (int)min((uint32_t)nb, pw.skip_to - pos0) : 0;
-    if (pw.rebuild && !pw.crossed) {
-        const int ci = sm.n_below;
-        if (ci < nb) {
-            composite_batch(sm, k0, ci, pos0, fx, fy0, fy1, p0, p1);
-            save_prefix(p0, view, px, py0, prefix_state, prefix_last);
-            save_prefix(p1, view, px, py1, prefix_state, prefix_last);
-            pw.crossed = true;
-            pw.n_prefix = pos0 + ci;
-            composite_batch(sm, ci, nb, pos0, fx, fy0, fy1, p0, p1);
-            return;
-        }
+// Composite one staged batch (nb list entries from position pos0, `st` as
+// staged); when rebuilding, save the pixel state at the first entry at or
+// behind the boundary. Uniform over the block.
+__device__ __forceinline__ void composite_staged(const FwdSmem& sm, const Staged& st, int nb,
+                                                 uint32_t pos0, PrefixWalk& pw,
+                                                 const ClsView& view, int px, int py0, int py1,
+                                                 float fx, float fy0, float fy1, PixelState& p0,
+                                                 PixelState& p1, float* prefix_state,
+                                                 int32_t* prefix_last) {
+    if (pw.rebuild && !pw.crossed && st.n_below_all < nb) {
+        composite_batch(sm, 0, st.n_below_kept, fx, fy0, fy1, p0, p1);
+        save_prefix(p0, view, px, py0, prefix_state, prefix_last);
+        save_prefix(p1, view, px, py1, prefix_state, prefix_last);
+        pw.crossed = true;
+        pw.n_prefix = pos0 + (uint32_t)st.n_below_all;
+        composite_batch(sm, st.n_below_kept, st.n, fx, fy0, fy1, p0, p1);
+        return;
     }
-    composite_batch(sm, k0, nb, pos0, fx, fy0, fy1, p0, p1);
+    composite_batch(sm, 0, st.n, fx, fy0, fy1, p0, p1);
 }
 __device__ __forceinline__ void finish_pixel(const PixelState& ps, const ClsView& view, int px,
                                              int py, float bg0, float bg1, float bg2,
@@ -190,7 +247,7 @@ __device__ __forceinline__ void finish_pixel(const PixelState& ps, const ClsView
     }
 }
 
-__global__ void __launch_bounds__(kFwdThreads)
+__global__ void __launch_bounds__(kFwdThreads, 8)
 render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
                   int vals_stride, const uint32_t* __restrict__ ranges,
@@ -214,7 +271,6 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
         if (threadIdx.x == 0) {
             sm.tile = atomicAdd(work_counter, 1);
             sm.last_active = -1;
-            sm.n_below = 0;
         }
         __syncthreads();
         const int t = sm.tile;
@@ -227,6 +283,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
         const int W = view.cam.width, H = view.cam.height;
         const int px = tx * kTile + lx, py0 = ty * kTile + ly, py1 = py0 + 8;
         const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
+        const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
         const uint32_t start = ranges[2 * (int64_t)tile], end = ranges[2 * (int64_t)tile + 1];
 
         PixelState p0{1.0f, 0.f, 0.f, 0.f, 0u, !(px < W && py0 < H)};
@@ -249,16 +306,14 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             for (uint32_t b = start + min(pw.skip_to, end - start); b < end; b += kTilePixels) {
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
                 const int nb = (int)min((uint32_t)kTilePixels, end - b);
-                int below = 0;
-                for (int i = threadIdx.x; i < nb; i += kFwdThreads)
-                    stage_record(sm, i, records, vals[(int64_t)(b + i) * vals_stride],
-                                 (int)(b - start) + i, pw.zb, pw.rebuild && !pw.crossed, below);
-                if (pw.rebuild && !pw.crossed) add_below(sm, below);
+                const Staged st = stage_batch(
+                    sm, nb, b - start,
+                    [&](int i) { return vals[(int64_t)(b + i) * vals_stride]; }, records, tx0,
+                    ty0, pw);
                 __syncthreads();
-                composite_staged(sm, nb, b - start, pw, view, px, py0, py1, fx, fy0, fy1, p0, p1,
-                                 prefix_state, prefix_last);
+                composite_staged(sm, st, nb, b - start, pw, view, px, py0, py1, fx, fy0, fy1, p0,
+                                 p1, prefix_state, prefix_last);
                 __syncthreads();
-                if (threadIdx.x == 0) sm.n_below = 0;
             }
         } else {
             // Walk the tile's depth bins front to back. Consecutive bins up to
@@ -315,17 +370,16 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const int nb = min(kTilePixels, n - c0);
                     if (pos0 + nb <= pw.skip_to) continue;  // inside the cached prefix
                     if (c0 > 0 && __syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
-                    int below = 0;
-                    for (int i = threadIdx.x; i < nb; i += kFwdThreads)
-                        stage_record(sm, i, records,
-                                     (uint32_t)(here ? sm.sorted[c0 + i] : lazy_keys[w0 + c0 + i]),
-                                     (int)pos0 + i, pw.zb, pw.rebuild && !pw.crossed, below);
-                    if (pw.rebuild && !pw.crossed) add_below(sm, below);
+                    const Staged st = stage_batch(
+                        sm, nb, pos0,
+                        [&](int i) {
+                            return (uint32_t)(here ? sm.sorted[c0 + i] : lazy_keys[w0 + c0 + i]);
+                        },
+                        records, tx0, ty0, pw);
                     __syncthreads();
-                    composite_staged(sm, nb, pos0, pw, view, px, py0, py1, fx, fy0, fy1, p0, p1,
-                                     prefix_state, prefix_last);
+                    composite_staged(sm, st, nb, pos0, pw, view, px, py0, py1, fx, fy0, fy1, p0,
+                                     p1, prefix_state, prefix_last);
                     __syncthreads();
-                    if (threadIdx.x == 0) sm.n_below = 0;
                 }
             }
             const bool all_done = __syncthreads_count(p0.done && p1.done) == kFwdThreads;
