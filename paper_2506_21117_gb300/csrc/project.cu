@@ -253,11 +253,29 @@ active_zmin_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warps = blockDim.x >> 5;
-    for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < sc.n_active;
-         i += gridDim.x * warps) {
+    const int stride = gridDim.x * warps;
+    int i = blockIdx.x * warps + (threadIdx.x >> 5);
+    // the next Gaussian's record is requested before this one is processed
+    float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c2 = c0;
+    if (i < sc.n_active) {
+        const float4* r = reinterpret_cast<const float4*>(records + view.rec_base +
+                                                          sc.active_idx[i]);
+        c0 = r[0];
+        c2 = r[2];
+    }
+    for (; i < sc.n_active; i += stride) {
+        const float4 cur0 = c0, cur2 = c2;
+        if (i + stride < sc.n_active) {
+            const float4* r = reinterpret_cast<const float4*>(records + view.rec_base +
+                                                              sc.active_idx[i + stride]);
+            c0 = r[0];
+            c2 = r[2];
+        }
+        const int radius = __float_as_int(cur2.w);
+        const uint32_t zb = __float_as_uint(cur2.z);
         int x0, x1, y0, y1;
-        uint32_t zb;
-        if (!record_rect(view, records, view.rec_base + sc.active_idx[i], x0, x1, y0, y1, zb))
+        if (radius <= 0 || !tile_rect(cur0.x, cur0.y, (float)radius, view.tiles_x, view.tiles_y,
+                                      x0, x1, y0, y1))
             continue;  // uniform over the warp
         const int w = x1 - x0 + 1;
         const int area = w * (y1 - y0 + 1);
@@ -284,25 +302,40 @@ compact_tiles_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
                      int32_t* __restrict__ active_tiles, int32_t* __restrict__ n_active_tiles,
                      int32_t* __restrict__ tile_rank, ClsTileCache* __restrict__ tile_cache,
                      int prefix_mode) {
+    constexpr int kPer = 4;  // consecutive tiles per thread
     __shared__ int32_t smem[1024 / 32 + 1];
     int32_t carry = 0;
-    for (int64_t base = 0; base < n_tiles; base += 1024) {
-        const int64_t t = base + threadIdx.x;
-        const int32_t f = (t < n_tiles && tile_active[t]) ? 1 : 0;
-        if (f) {
-            const ClsTileCache c = tile_cache[t];
-            const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
-                              c.zmin_active >= c.zb;
-            if (!keep) {
-                tile_cache[t].zb = c.zmin_active > kPrefixMargin ? c.zmin_active - kPrefixMargin
-                                                                 : 0u;
-                tile_cache[t].n_prefix = CLS_PREFIX_UNKNOWN;
+    for (int64_t base = 0; base < n_tiles; base += 1024 * kPer) {
+        const int64_t t0 = base + (int64_t)threadIdx.x * kPer;
+        unsigned f = 0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t t = t0 + j;
+            if (t < n_tiles && tile_active[t]) {
+                f |= 1u << j;
+                const ClsTileCache c = tile_cache[t];
+                const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
+                                  c.zmin_active >= c.zb;
+                if (!keep) {
+                    tile_cache[t].zb = c.zmin_active > kPrefixMargin
+                                           ? c.zmin_active - kPrefixMargin : 0u;
+                    tile_cache[t].n_prefix = CLS_PREFIX_UNKNOWN;
+                }
             }
         }
         int32_t tot;
-        const int32_t ex = block_exclusive_sum<1024>(f, smem, tot);
-        if (f) active_tiles[carry + ex] = (int32_t)t;
-        if (t < n_tiles) tile_rank[t] = f ? carry + ex : -1;
+        int32_t r = carry + block_exclusive_sum<1024>((int32_t)__popc(f), smem, tot);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t t = t0 + j;
+            if (t >= n_tiles) break;
+            if (f & (1u << j)) {
+                active_tiles[r] = (int32_t)t;
+                tile_rank[t] = r++;
+            } else {
+                tile_rank[t] = -1;
+            }
+        }
         carry += tot;
     }
     if (threadIdx.x == 0) *n_active_tiles = carry;
@@ -331,13 +364,16 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
                    uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
                    uint32_t* __restrict__ work_list, int32_t* __restrict__ work_count) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
+    __shared__ int32_t smem32[kBinBlock / 32 + 1];
     __shared__ uint32_t s_lo, s_hi;
+    __shared__ int32_t s_base;
     const ClsView& view = views[blockIdx.y];
     const int n = scenes[view.scene].n;
     if (threadIdx.x == 0) { s_lo = 0xffffffffu; s_hi = 0u; }
     __syncthreads();
     int64_t cnt = 0;
     uint32_t lo = 0xffffffffu, hi = 0u;
+    unsigned produces = 0;  // bit `it`: item `it` of this thread has pairs
     for (int it = 0; it < kBinItems; ++it) {
         const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
         if (g < n) {
@@ -348,21 +384,24 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
                 cnt += c;
                 lo = min(lo, zb);
                 hi = max(hi, zb);
-            }
-            if (work_list) {  // compact the pair-producing records of this view
-                const uint32_t m = __ballot_sync(__activemask(), c > 0);
-                const int lane = threadIdx.x & 31;
-                int base = 0;
-                const int leader = __ffs(m) - 1;
-                if (m && lane == leader) base = atomicAdd(work_count + blockIdx.y, __popc(m));
-                base = __shfl_sync(__activemask(), base, leader < 0 ? 0 : leader);
-                if (c > 0) work_list[view.rec_base + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)g;
+                produces |= 1u << it;
             }
         }
     }
     int64_t tot;
     block_exclusive_sum<kBinBlock>(cnt, smem, tot);
     if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] = tot;
+    if (work_list) {  // compact the pair-producing records: one atomic per block
+        int32_t nw;
+        int32_t k = block_exclusive_sum<kBinBlock>((int32_t)__popc(produces), smem32, nw);
+        if (threadIdx.x == 0) s_base = nw > 0 ? atomicAdd(work_count + blockIdx.y, nw) : 0;
+        __syncthreads();
+        k += s_base;
+        for (int it = 0; it < kBinItems; ++it)
+            if (produces & (1u << it))
+                work_list[view.rec_base + k++] =
+                    (uint32_t)(blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x);
+    }
     if (zmin) {
         for (int o = 16; o > 0; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -389,20 +428,21 @@ __device__ __forceinline__ int depth_bin(uint32_t zb, uint32_t lo, uint32_t hi) 
 
 // Bucketed layout: stamp every pair-producing rectangle into its depth bin's
 // difference grid; the prefix sums then give pairs per (tile, depth bin).
+// (the pair-producing records of each view are those of its work list)
 __global__ void __launch_bounds__(kBinBlock)
-stamp_bins_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-                  const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
+stamp_bins_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
                   const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
+                  const uint32_t* __restrict__ work_list, const int32_t* __restrict__ work_count,
                   int32_t* __restrict__ bins, int64_t total_sat) {
     const ClsView& view = views[blockIdx.y];
-    const int n = scenes[view.scene].n;
+    const int n = work_count[blockIdx.y];
     const uint32_t lo = zmin[blockIdx.y], hi = zmax[blockIdx.y];
-    for (int it = 0; it < kBinItems; ++it) {
-        const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
-        if (g >= n) break;
+    for (int i = blockIdx.x * kBinBlock + threadIdx.x; i < n; i += gridDim.x * kBinBlock) {
         int x0, x1, y0, y1;
         uint32_t zb;
-        if (pair_count(view, records, sat, g, x0, x1, y0, y1, zb) == 0) continue;
+        if (!record_rect(view, records, view.rec_base + work_list[view.rec_base + i], x0, x1, y0,
+                         y1, zb))
+            continue;
         const int b = depth_bin(zb, lo, hi);
         stamp_rect(bins + b * total_sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
     }
@@ -580,6 +620,85 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
     }
 }
 
+// Per tile row of every view: sparse tables of the first emitted depth bin
+// (minimum) and the depth cut (maximum) over runs of 2^l tiles, level l at
+// l * total_tiles + global tile id; inactive tiles are neutral (front 255,
+// cut 0). One block per view.
+constexpr int kRowLevels = 16;  // tiles per row < 2^16
+
+__global__ void __launch_bounds__(1024)
+bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ tile_rank,
+                         const uint8_t* __restrict__ front, const uint8_t* __restrict__ cut,
+                         uint8_t* __restrict__ t_front, uint8_t* __restrict__ t_cut,
+                         int64_t total_tiles, int smem_cap) {
+    extern __shared__ uint8_t s_tab[];
+    const ClsView& view = views[blockIdx.x];
+    const int Tx = view.tiles_x, nt = Tx * view.tiles_y;
+    const int64_t tb = view.tile_base;
+    const int levels = 32 - __clz(Tx);  // 2^(levels - 1) <= Tx
+    if ((int64_t)levels * nt * 2 <= smem_cap) {
+        uint8_t* sf = s_tab;
+        uint8_t* sc = s_tab + (int64_t)levels * nt;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const bool on = tile_rank[tb + i] >= 0;
+            sf[i] = on ? front[tb + i] : (uint8_t)255;
+            sc[i] = on ? (cut ? cut[tb + i] : (uint8_t)255) : (uint8_t)0;
+        }
+        for (int l = 1; l < levels; ++l) {
+            __syncthreads();
+            const int h = 1 << (l - 1);
+            const int prev = (l - 1) * nt, cur = l * nt;
+            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+                const int x = i % Tx;
+                if (x + 2 * h > Tx) continue;
+                sf[cur + i] = min(sf[prev + i], sf[prev + i + h]);
+                sc[cur + i] = max(sc[prev + i], sc[prev + i + h]);
+            }
+        }
+        __syncthreads();
+        for (int l = 0; l < levels; ++l)
+            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+                t_front[(int64_t)l * total_tiles + tb + i] = sf[l * nt + i];
+                t_cut[(int64_t)l * total_tiles + tb + i] = sc[l * nt + i];
+            }
+        return;
+    }
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+        const bool on = tile_rank[tb + i] >= 0;
+        t_front[tb + i] = on ? front[tb + i] : (uint8_t)255;
+        t_cut[tb + i] = on ? (cut ? cut[tb + i] : (uint8_t)255) : (uint8_t)0;
+    }
+    for (int l = 1; l < kRowLevels && (1 << l) <= Tx; ++l) {
+        __syncthreads();
+        const int h = 1 << (l - 1);
+        const int64_t prev = (int64_t)(l - 1) * total_tiles + tb, cur = prev + total_tiles;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int x = i % Tx;
+            if (x + 2 * h > Tx) continue;
+            t_front[cur + i] = min(t_front[prev + i], t_front[prev + i + h]);
+            t_cut[cur + i] = max(t_cut[prev + i], t_cut[prev + i + h]);
+        }
+    }
+}
+
+// Can depth bin `bin` be emitted into any tile of rectangle x0..x1, y0..y1?
+// False only if on every row the bin lies below the smallest first emitted
+// bin or above the largest cut (conservative: emission still tests each cell).
+__device__ __forceinline__ bool bin_window_possible(const uint8_t* t_front, const uint8_t* t_cut,
+                                                    int64_t total_tiles, const ClsView& view,
+                                                    int x0, int x1, int y0, int y1, int bin) {
+    const int w = x1 - x0 + 1;
+    const int l = 31 - __clz(w);
+    const int64_t lv = (int64_t)l * total_tiles + view.tile_base;
+    for (int y = y0; y <= y1; ++y) {
+        const int64_t a = lv + (int64_t)y * view.tiles_x + x0, b = a + w - (1 << l);
+        const int f = min(t_front[a], t_front[b]);
+        const int c = max(t_cut[a], t_cut[b]);
+        if (f <= bin && bin <= c) return true;
+    }
+    return false;
+}
+
 // Bucketed emission, load-balanced: a warp takes 32 pair-producing Gaussians of
 // one view, prefix-sums their rectangle areas, and spreads the rectangle cells
 // over its lanes (each lane finds the owner of its cell by a binary search over
@@ -591,7 +710,8 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                      uint64_t* __restrict__ keys, int64_t capacity,
                      const uint32_t* __restrict__ work_list,
                      const int32_t* __restrict__ work_count, const uint8_t* __restrict__ cut,
-                     const uint8_t* __restrict__ front) {
+                     const uint8_t* __restrict__ front, const uint8_t* __restrict__ t_front,
+                     const uint8_t* __restrict__ t_cut, int64_t total_tiles) {
     // rank of each tile of the view, then its last and first emitted depth bin
     extern __shared__ int32_t s_rank[];
     const ClsView& view = views[blockIdx.y];
@@ -618,8 +738,9 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
             const uint32_t g = work_list[view.rec_base + item];
             rec = (uint32_t)(view.rec_base + g);
             if (record_rect(view, records, rec, x0, x1, y0, y1, zb)) {
-                area = (x1 - x0 + 1) * (y1 - y0 + 1);
                 bin = depth_bin(zb, lo, hi);
+                if (bin_window_possible(t_front, t_cut, total_tiles, view, x0, x1, y0, y1, bin))
+                    area = (x1 - x0 + 1) * (y1 - y0 + 1);
             }
         }
         int incl = area;
@@ -781,7 +902,7 @@ namespace {
 
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, work_list, work_count, front, total;
+        bins, work_list, work_count, front, t_front, t_cut, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -809,6 +930,8 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.work_list = o; o = align256(o + (size_t)info->total_records * 4);
     L.work_count = o; o = align256(o + (size_t)V * 4);
     L.front = o; o = align256(o + (size_t)info->total_tiles);
+    L.t_front = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
+    L.t_cut = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
     L.total = o;
     return L;
 }
@@ -864,6 +987,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     uint32_t* work_list = reinterpret_cast<uint32_t*>(ws + L.work_list);
     int32_t* work_count = reinterpret_cast<int32_t*>(ws + L.work_count);
     uint8_t* front = reinterpret_cast<uint8_t*>(ws + L.front);
+    uint8_t* t_front = reinterpret_cast<uint8_t*>(ws + L.t_front);
+    uint8_t* t_cut = reinterpret_cast<uint8_t*>(ws + L.t_cut);
     const int64_t subs = info->total_tiles * kDepthBins;
     const int64_t max_view_tiles = info->max_view_tiles;
     if (layout == 1 && g_max_view_tiles_checked == 0) {
@@ -882,6 +1007,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                              200 * 1024);
         cudaFuncSetAttribute(active_zmin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              200 * 1024);
+        cudaFuncSetAttribute(bin_window_tables_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         g_grid_cap_set = grid_cap;
     }
 
@@ -937,8 +1064,10 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
         cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
         cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
-        stamp_bins_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
-                                                         zmin, zmax, bins, info->total_sat);
+        const unsigned work_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
+                                                      2048);
+        stamp_bins_kernel<<<dim3(work_blocks, V), kBinBlock, 0, s>>>(
+            views_dev, records, zmin, zmax, work_list, work_count, bins, info->total_sat);
         bins_prefix_kernel<<<dim3(kDepthBins, V), 256, grid_cap, s>>>(views_dev, bins,
                                                                       info->total_sat, grid_cap);
         sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
@@ -949,11 +1078,13 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
             sub_partials, capacity, bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
+        bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
+            views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
         const unsigned emit_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
                                                       2048);
         emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 6, s>>>(
             views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, bin_cut, front);
+            work_count, bin_cut, front, t_front, t_cut, info->total_tiles);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;

@@ -353,13 +353,13 @@ class Batch:
         stamp and nearest-active depth (3 if any Gaussian is active), tile
         mask, compaction, count,
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
-        prefix, bucket counts, scan, offsets, emit (6). Sort: flat
+        prefix, bucket counts, scan, offsets, emission window tables, emit (7). Sort: flat
         hist + scan + passes (+ copy if odd) + ranges; bucketed 1 or 2.
         Forward 1, or 5 with the depth cut (forward, completion, large-bin
         collection and sort, rerun);
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
-        proj = (3 if active else 0) + 3 + (6 if self.layout == 1 else 3)
+        proj = (3 if active else 0) + 3 + (7 if self.layout == 1 else 3)
         if self.layout == 1:
             sort = 2 if self.lazy else 1
         else:
