@@ -346,6 +346,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
             while (bin <= limit) {
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
                 const uint32_t w0 = sm.off[bin];
+                const int b0 = bin;
                 int e = bin + 1;
                 while (e <= limit && sm.off[e + 1] - w0 <= (uint32_t)kLazyWin) ++e;
                 const int n = (int)(sm.off[e] - w0);
@@ -356,10 +357,18 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                 if (here) {
                     for (int i = threadIdx.x; i < n; i += kFwdThreads) sm.key[i] = lazy_keys[w0 + i];
                     __syncthreads();
+                    // the bins are already in depth order: rank each key inside its own bin
                     for (int i = threadIdx.x; i < n; i += kFwdThreads) {
+                        const uint32_t p = w0 + (uint32_t)i;
+                        int lo = b0, hi = e - 1;  // last bin starting at or before p (non-empty)
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (sm.off[mid] <= p) lo = mid; else hi = mid - 1;
+                        }
+                        const int s0 = (int)(sm.off[lo] - w0), s1 = (int)(sm.off[lo + 1] - w0);
                         const uint64_t k = sm.key[i];
-                        int r = 0;
-                        for (int j = 0; j < n; ++j) r += sm.key[j] < k;
+                        int r = s0;
+                        for (int j = s0; j < s1; ++j) r += sm.key[j] < k;
                         sm.sorted[r] = k;
                     }
                     __syncthreads();
