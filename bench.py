@@ -346,6 +346,7 @@ def run_ours(args, rank, world):
 
     e2e = run_e2e(args, lu, targets, masks, cams)
     active_np = lu.state.active.cpu().numpy().astype(bool)
+    sphere = run_sphere_region(lu)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -363,6 +364,7 @@ def run_ours(args, rank, world):
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": int(bt.launches_per_step() * args.steps),
+        "sphere_region": sphere,
     }
     if not args.no_serving:
         del lu, bt
@@ -375,6 +377,29 @@ def run_ours(args, rank, world):
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": _t.get_num_threads(),
                                 "kind": "oracle", "sample": desc}
     return line
+
+
+def run_sphere_region(lu):
+    """Sphere region of the benchmark's O^t (K-Means, spheres) and one pruning
+    check, timed with CUDA events on the launching stream (after the timed
+    iterations; the pruning check removes the Gaussians that left it)."""
+    import torch
+    from paper_2506_21117_gb300.update import SphereRegion, prune_outside
+    st = lu.state
+    A = st.n_active
+    SphereRegion(st)  # warm-up (first launch of each kernel)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    region = SphereRegion(st)
+    e[1].record()
+    e[2].record()
+    removed = prune_outside(st, region)
+    e[3].record()
+    torch.cuda.synchronize()
+    return {"active_gaussians": A, "spheres": region.k, "kmeans_iters": 16,
+            "fit_ms": e[0].elapsed_time(e[1]), "prune_check_ms": e[2].elapsed_time(e[3]),
+            "removed": removed, "note": "prune_check_ms includes reading the removed count back"}
 
 
 def run_serving(args, seed=0):

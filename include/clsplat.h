@@ -407,6 +407,48 @@ int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
                         float* grads, int32_t* work_counter, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Sphere region and pruning (Sec. 3.3 "Sphere Pruning"; Supp. "Identifying
+ * Changed Gaussians": a sphere per cluster of O^t's centres, at the cluster
+ * mean, radius 1.1 x the 98th quantile of the members' distances to it; Supp.
+ * "3DGS Optimization in Changed Regions": every 15 iterations each Gaussian of
+ * O^t whose centre is in no sphere is removed).
+ * The clusters are K-Means ones (the paper uses HDBSCAN): farthest-point
+ * initial centres (first point of the list, then repeatedly the point
+ * farthest from its nearest chosen centre, ties to the lowest position), then
+ * `iters` Lloyd iterations (nearest centre, ties to the lowest cluster; an
+ * empty cluster keeps its centre). Distances are the float32 sequence
+ * ((dx*dx + dy*dy) + dz*dz) of rounded operations; cluster means are exact
+ * (coordinates summed as int64 multiples of 2^-24, rounded half to even; mean
+ * = float32(sum / count / 2^24) in float64), so the result does not depend on
+ * thread order. The quantile is NumPy's linear estimator in float64 over the
+ * members' float32 distances; radius = float32(1.1 q), -1 for an empty cluster.
+ *   params, row_stride  parameter rows (mean at floats 0..2)
+ *   idx [n_points]      device rows of the points (O^t's active_idx)
+ *   spheres [k]         device output; labels [n_points], counts [k] optional
+ *   workspace           cls_spheres_workspace_size(n_points) bytes
+ * Pruning: for each of the n_active Gaussians of active_idx, inside iff its
+ * float32 squared distance to some sphere's centre is <= radius * radius
+ * (float32); an outside one gets opacity logit -inf (it never contributes to
+ * a pixel again), active[g] = 0, its id in `removed` (optional, any order) and
+ * n_removed_dev; active_idx is compacted in order and n_active_dev written.
+ *   workspace  cls_prune_workspace_size(n_active) bytes */
+#define CLS_MAX_SPHERES 10
+typedef struct ClsSphere {
+    float cx, cy, cz, radius;
+} ClsSphere;
+size_t cls_spheres_workspace_size(int32_t n_points);
+int cls_fit_spheres(const float* params, int32_t row_stride, const int32_t* idx,
+                    int32_t n_points, int32_t k, int32_t iters, ClsSphere* spheres,
+                    int32_t* labels, int32_t* counts, void* workspace, size_t workspace_bytes,
+                    cls_stream_t stream);
+size_t cls_prune_workspace_size(int32_t n_active);
+int cls_prune_outside_spheres(float* params, int32_t row_stride, uint8_t* active,
+                              int32_t* active_idx, int32_t n_active, int32_t* n_active_dev,
+                              const ClsSphere* spheres, int32_t k, int32_t* removed,
+                              int32_t* n_removed_dev, void* workspace, size_t workspace_bytes,
+                              cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Masked Adam on the active set (Supp. "3DGS Optimization in Changed
  * Regions"): increments each scene's adam_step t, then for every active row
  * and every float of it: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;

@@ -63,10 +63,16 @@ class ClsTileCache(C.Structure):
 
 
 PREFIX_UNKNOWN = 0xFFFFFFFF
+MAX_SPHERES = 10
+
+
+class ClsSphere(C.Structure):
+    _fields_ = [("cx", C.c_float), ("cy", C.c_float), ("cz", C.c_float), ("radius", C.c_float)]
+
 TILE_CACHE_BYTES = 16
 
 assert C.sizeof(ClsCamera) == 88 and C.sizeof(ClsScene) == 72
-assert C.sizeof(ClsTileCache) == TILE_CACHE_BYTES
+assert C.sizeof(ClsTileCache) == TILE_CACHE_BYTES and C.sizeof(ClsSphere) == 16
 assert C.sizeof(ClsView) == 144 and C.sizeof(ClsProjected) == 48
 
 P = C.c_void_p
@@ -94,6 +100,10 @@ SIGNATURES = {
     "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P, P]),
     "cls_adam_workspace_size": (SZ, [I32]),
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
+    "cls_spheres_workspace_size": (SZ, [I32]),
+    "cls_fit_spheres": (C.c_int, [P, I32, P, I32, I32, I32, P, P, P, P, SZ, P]),
+    "cls_prune_workspace_size": (SZ, [I32]),
+    "cls_prune_outside_spheres": (C.c_int, [P, I32, P, P, I32, P, P, I32, P, P, P, SZ, P]),
 }
 
 _lib = None
@@ -260,3 +270,25 @@ def cls_adam_step_active(scenes_dev, info, grads, lr, beta1, beta2, eps, workspa
 def exported_symbols():
     """Names the header declares (for the export check)."""
     return list(SIGNATURES)
+
+
+def cls_spheres_workspace_size(n_points) -> int:
+    return load().cls_spheres_workspace_size(n_points)
+
+
+def cls_fit_spheres(params, row_stride, idx, n_points, k, iters, spheres, labels, counts,
+                    workspace, workspace_bytes, stream) -> int:
+    return load().cls_fit_spheres(params, row_stride, idx, n_points, k, iters, spheres, labels,
+                                  counts, workspace, workspace_bytes, stream)
+
+
+def cls_prune_workspace_size(n_active) -> int:
+    return load().cls_prune_workspace_size(n_active)
+
+
+def cls_prune_outside_spheres(params, row_stride, active, active_idx, n_active, n_active_dev,
+                              spheres, k, removed, n_removed_dev, workspace, workspace_bytes,
+                              stream) -> int:
+    return load().cls_prune_outside_spheres(params, row_stride, active, active_idx, n_active,
+                                            n_active_dev, spheres, k, removed, n_removed_dev,
+                                            workspace, workspace_bytes, stream)

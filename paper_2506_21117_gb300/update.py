@@ -176,6 +176,7 @@ class Batch:
         self.prefix_last = torch.zeros(info.total_pixels, dtype=torch.int32, device=dev)
         self._epochs = [st.epoch for st in self.scenes]
         self.reset_prefix()
+        self.reproject = False  # project every Gaussian on the next call (after pruning)
         self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
                                    device=dev)
         self.adam_ws = torch.zeros(max(abi.cls_adam_workspace_size(S), 256), dtype=torch.uint8,
@@ -210,12 +211,26 @@ class Batch:
     def stream(self):
         return torch.cuda.current_stream().cuda_stream
 
+    def refresh_active(self):
+        """Take the scenes' current active sets (after pruning shrank them):
+        rebuild the batch tables; the next projection covers every Gaussian so
+        no record keeps a gradient slot of a removed Gaussian."""
+        for s, st in enumerate(self.scenes):
+            self.scene_tab[s].n_active = st.n_active
+        abi.check(abi.cls_batch_prepare(self.scene_tab, self.view_tab, self.info),
+                  "cls_batch_prepare")
+        self.scenes_dev.copy_(_bytes(self.scene_tab))
+        self.views_dev.copy_(_bytes(self.view_tab))
+        self.reproject = True
+
     def reset_prefix(self):
         """Forget every tile's static prefix (the next iteration rebuilds it)."""
         self.tile_cache.fill_(-1)
 
     def project_and_bin(self, mode: int):
         b = self
+        if b.reproject:
+            mode, b.reproject = 0, False
         epochs = [st.epoch for st in b.scenes]
         if epochs != b._epochs:  # an active set changed: the frozen rows did too
             b._epochs = epochs
@@ -414,6 +429,59 @@ def lift(state: SceneState, cams: Sequence, masks, vote_mode: int = 0, device="c
     return state.active.cpu().numpy(), votes.view(-1, 2)[:n].cpu().numpy()
 
 
+class SphereRegion:
+    """The spheres bounding O^t (Sec. 3.3 "Sphere Pruning"; Supp. "Identifying
+    Changed Gaussians"): K-Means clusters of the active Gaussians' centres, a
+    sphere per cluster at its mean with radius 1.1 x the 98th quantile of the
+    members' distances. K defaults to min(10, max(1, A // 1000))."""
+
+    def __init__(self, state: "SceneState", k: Optional[int] = None, iters: int = 16):
+        A = state.n_active
+        if A <= 0:
+            raise ValueError("the sphere region needs a non-empty active set")
+        dev = state.params.device
+        self.k = int(k) if k is not None else int(min(abi.MAX_SPHERES, max(1, A // 1000)))
+        self.k = min(self.k, A)
+        self.spheres = torch.empty(self.k * 4, dtype=torch.float32, device=dev)
+        self.labels = torch.empty(A, dtype=torch.int32, device=dev)
+        self.counts = torch.empty(self.k, dtype=torch.int32, device=dev)
+        ws = torch.empty(abi.cls_spheres_workspace_size(A), dtype=torch.uint8, device=dev)
+        abi.check(abi.cls_fit_spheres(
+            _ptr(state.params), state.stride, _ptr(state.active_idx), A, self.k, iters,
+            _ptr(self.spheres), _ptr(self.labels), _ptr(self.counts), _ptr(ws), ws.numel(),
+            torch.cuda.current_stream().cuda_stream), "cls_fit_spheres")
+
+    def host(self) -> Dict[str, np.ndarray]:
+        s = self.spheres.view(self.k, 4).cpu().numpy()
+        return {"centers": s[:, :3].copy(), "radii": s[:, 3].copy(),
+                "counts": self.counts.cpu().numpy().astype(np.int64),
+                "labels": self.labels.cpu().numpy()}
+
+
+def prune_outside(state: "SceneState", region: SphereRegion, want_removed: bool = False):
+    """Supp. "3DGS Optimization in Changed Regions": remove every Gaussian of
+    O^t whose centre lies in no sphere (opacity logit -inf, out of the active
+    set). Returns the number removed (and their ids if asked)."""
+    dev = state.params.device
+    A = state.n_active
+    ws = torch.empty(max(abi.cls_prune_workspace_size(A), 256), dtype=torch.uint8, device=dev)
+    n_active = torch.zeros(1, dtype=torch.int32, device=dev)
+    n_removed = torch.zeros(1, dtype=torch.int32, device=dev)
+    removed = torch.empty(max(A, 1), dtype=torch.int32, device=dev) if want_removed else None
+    abi.check(abi.cls_prune_outside_spheres(
+        _ptr(state.params), state.stride, _ptr(state.active), _ptr(state.active_idx), A,
+        _ptr(n_active), _ptr(region.spheres), region.k, _ptr(removed), _ptr(n_removed),
+        _ptr(ws), ws.numel(), torch.cuda.current_stream().cuda_stream),
+        "cls_prune_outside_spheres")
+    k = int(n_removed.item())
+    if k:
+        state.n_active = int(n_active.item())
+        state.epoch += 1
+    if want_removed:
+        return k, np.sort(removed[:k].cpu().numpy())
+    return k
+
+
 class LocalUpdate:
     """One scene, a handful of posed views and their change masks: lift, then
     iterate project/bin -> sort -> render forward (+loss) -> render backward ->
@@ -422,7 +490,11 @@ class LocalUpdate:
     def __init__(self, scene, cams, sh_degree: int, targets=None, masks=None, active=None,
                  vote_mode: int = 0, loss: str = "l1", lr: float = 1e-3,
                  bg=(0.0, 0.0, 0.0), device="cuda", capacity_slack: float = 1.5,
-                 layout: int = 1, lazy: bool = True):
+                 layout: int = 1, lazy: bool = True, prune_every: int = 0,
+                 sphere_k: Optional[int] = None):
+        """prune_every > 0 fits the sphere region of the lifted O^t and removes
+        the Gaussians that leave it every `prune_every` iterations (the paper
+        uses 15)."""
         self.cams = list(cams)
         self.loss_mode = LOSS_MODES[loss]
         self.lr = lr
@@ -438,7 +510,14 @@ class LocalUpdate:
         if targets is not None:
             self.batch.set_targets(targets)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
+        self._init_region(prune_every, sphere_k)
         torch.cuda.synchronize()
+
+    def _init_region(self, prune_every: int, sphere_k: Optional[int]):
+        self.prune_every = int(prune_every)
+        self.iteration = 0
+        self.removed = 0
+        self.region = SphereRegion(self.state, sphere_k) if self.prune_every > 0 else None
 
     @classmethod
     def from_resident(cls, state: SceneState, cams, targets, masks, vote_mode: int = 0,
@@ -459,6 +538,7 @@ class LocalUpdate:
         self.batch = Batch([state], [self.cams], dev, layout, lazy)
         self.batch.target = targets.to(dev, non_blocking=True)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
+        self._init_region(0, None)
         return self
 
     def render_pass(self, with_backward: bool = True, with_adam: bool = True):
@@ -473,6 +553,12 @@ class LocalUpdate:
 
     def step(self):
         self.render_pass(True, True)
+        self.iteration += 1
+        if self.region is not None and self.iteration % self.prune_every == 0:
+            k = prune_outside(self.state, self.region)
+            if k:
+                self.removed += k
+                self.batch.refresh_active()
 
     def run(self, iters: int):
         for _ in range(iters):
