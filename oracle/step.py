@@ -54,6 +54,20 @@ def loss_terms(colour, target, kind: str):
     return d.abs() if kind == "l1" else d * d
 
 
+SSIM_LOSSES = ("ssim", "l1+ssim")
+
+
+def view_loss_ssim(image, target, kind: str):
+    """Per-view loss of the D-SSIM kinds over the whole image: "ssim" is
+    D-SSIM alone, "l1+ssim" the base optimiser's (1 - lambda) L1 + lambda
+    D-SSIM with the L1 mean over 3 H W values."""
+    from . import ssim as os_
+    d = os_.dssim(image, target)
+    if kind == "ssim":
+        return d
+    return (1.0 - os_.LAMBDA) * (image - target).abs().mean() + os_.LAMBDA * d
+
+
 def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
            bg=(0.0, 0.0, 0.0), targets: Optional[Sequence[np.ndarray]] = None,
            loss: str = "l1", need_grad: bool = False,
@@ -66,12 +80,16 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
     projections `pidx`, `near_ids` (set of Gaussian ids with a threshold
     decision), `loss` (float, over rendered pixels) and, if `need_grad`, the
     float64 gradient of every parameter array (`grads`, numpy, same shapes as
-    the scene)."""
+    the scene). The loss is the mean over views of the per-view loss; for the
+    D-SSIM kinds (`SSIM_LOSSES`, whole images only) `dL_dimage` holds the
+    float64 gradient of the loss with respect to each view's image."""
+    if loss in SSIM_LOSSES and tiles is not None:
+        raise ValueError("the D-SSIM losses are defined on whole images")
     V = len(cams)
     bg_t = torch.tensor(bg, dtype=T64)
     g = scene64(scene, requires_grad=need_grad)
     out = {"image": [], "T_final": [], "n_contrib": [], "n_incl": [], "near": [], "pidx": [],
-           "near_ids": set(), "loss": 0.0}
+           "near_ids": set(), "loss": 0.0, "dL_dimage": []}
     proj_outs, proj_grads = [], []
     for j, cam in enumerate(cams):
         W, H = int(cam["width"]), int(cam["height"])
@@ -90,6 +108,7 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
             np.asarray(targets[j], np.float64), dtype=T64)
         norm = 1.0 / (3.0 * H * W * V)
         todo = tiles[j] if tiles is not None else [(x, y) for y in range(Ty) for x in range(Tx)]
+        whole = torch.zeros(3, H * W, dtype=T64) if loss in SSIM_LOSSES else None
         for (tx, ty) in todo:
             ids_np = tile_list(pidx, tx, ty)
             ids = torch.tensor(ids_np, dtype=torch.int64)
@@ -104,11 +123,23 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
             ni[pyn, pxn] = cr["n_incl"].numpy()
             near[pyn, pxn] = cr["near"].numpy()
             out["near_ids"].update(ids_np[cr["near_ids"].numpy()].tolist())
-            if tgt is not None:
+            if whole is not None:
+                whole = whole.index_put((torch.arange(3)[:, None], (py * W + px)[None, :]),
+                                        col.T)
+            elif tgt is not None:
                 lt = loss_terms(col, tgt[:, py, px].T, loss).sum() * norm
                 out["loss"] += float(lt.detach())
                 if need_grad and lt.requires_grad:
                     lt.backward()
+        if whole is not None and tgt is not None:
+            image_t = whole.view(3, H, W)
+            if need_grad:
+                image_t.retain_grad()
+            lv = view_loss_ssim(image_t, tgt, loss) / V
+            out["loss"] += float(lv.detach())
+            if need_grad and lv.requires_grad:
+                lv.backward()
+                out["dL_dimage"].append(image_t.grad.numpy().copy())
         out["image"].append(img)
         out["T_final"].append(Tf)
         out["n_contrib"].append(nc)
