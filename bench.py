@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--width", type=int, default=1920)
     p.add_argument("--height", type=int, default=1080)
     p.add_argument("--views", type=int, default=4)
+    p.add_argument("--loss", default="l1", choices=["l1", "l1+ssim"],
+                   help="l1+ssim: the base optimiser's (1 - 0.2) L1 + 0.2 D-SSIM")
     p.add_argument("--e2e-updates", type=int, default=3)
     p.add_argument("--iters-per-update", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -261,7 +263,8 @@ def run_ours(args, rank, world):
     del tgt
     torch.cuda.empty_cache()
 
-    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
+    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss=args.loss)
+    ssim = args.loss == "l1+ssim"
     bt = lu.batch
     A = lu.state.n_active
     clocks = Clocks(dev.index)
@@ -270,9 +273,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     bt.check_status()
 
-    stages = ["project_and_bin", "sort_keys", "render_forward", "render_backward",
-              "adam_step_active"]
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    stages = ["project_and_bin", "sort_keys", "render_forward"] + (["ssim_loss"] if ssim else []) + \
+        ["render_backward", "adam_step_active"]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+          for _ in range(args.steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -287,12 +291,17 @@ def run_ours(args, rank, world):
         e[1].record()
         bt.sort()
         e[2].record()
-        bt.forward(lu.loss_mode, lu.bg)
-        e[3].record()
+        bt.render(lu.loss_mode, lu.bg)
+        i = 3
+        e[i].record()
+        if ssim:
+            bt.apply_ssim(lu.loss_mode)
+            i += 1
+            e[i].record()
         bt.backward()
-        e[4].record()
+        e[i + 1].record()
         bt.adam(lu.lr)
-        e[5].record()
+        e[i + 2].record()
     end.record()
     torch.cuda.synchronize()
     clk = clocks.stop(t_wall0, time.time())
@@ -311,6 +320,15 @@ def run_ours(args, rank, world):
     V = len(cams)
     passes = math.ceil(bt.info.key_bits / 8)
     P_act = tiles_on * 256
+    ssim_roof = None
+    if ssim:
+        # pass 1 reads x, y (24 B) and writes a, b, c (36 B) per rendered pixel;
+        # pass 2 reads a, b, c, x, y and dL/dC and writes dL/dC (84 B) per covered pixel
+        covered = int((bt.tile_active == 1).sum().item()) * 256
+        b_ssim = 60 * P_act + 84 * covered
+        ach = b_ssim / (stage_ms["ssim_loss"] * 1e-3) / 1e9
+        ssim_roof = {"bound": "hbm", "bytes_per_launch": b_ssim, "achieved": ach,
+                     "unit": "GB/s", "rendered_pixels": P_act, "covered_pixels": covered}
 
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, args.steps, total_ms)
@@ -366,6 +384,11 @@ def run_ours(args, rank, world):
         "gpu_launches": int(bt.launches_per_step() * args.steps),
         "sphere_region": sphere,
     }
+    if ssim_roof is not None:
+        ssim_roof["peak"] = hbm_peak
+        ssim_roof["frac"] = ssim_roof["achieved"] / hbm_peak
+        line["ssim_roofline"] = ssim_roof
+        line["config"]["workload"] = WORKLOAD.replace(", L1", ", L1 + D-SSIM (0.8/0.2)")
     if not args.no_serving:
         del lu, bt
         torch.cuda.empty_cache()

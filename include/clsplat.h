@@ -248,7 +248,11 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  * prefix (for callers whose static Gaussians may change between calls);
  * prefix_mode 1 keeps a tile's cached prefix while it holds, and the bucketed
  * layout then does not write the pairs of depth bins that lie entirely in
- * front of the tile's boundary (their slots stay in bin_offsets). */
+ * front of the tile's boundary (their slots stay in bin_offsets).
+ * tile_ring 1 also renders the ring of tiles around the covered ones
+ * (tile_active 2: uncovered, one of its eight neighbours covered), which the
+ * D-SSIM window needs (cls_ssim_loss); tile_active is 1 on covered tiles in
+ * both modes, and every tile with tile_active != 0 is in active_tiles. */
 #define CLS_DEPTH_BINS 256
 size_t cls_project_workspace_size(const ClsBatchInfo* info);
 size_t cls_bin_offsets_size(const ClsBatchInfo* info); /* uint32 entries */
@@ -258,8 +262,9 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
                         int32_t* n_active_tiles_dev, uint64_t* keys, uint32_t* vals,
                         int64_t capacity, int64_t* n_pairs_dev, uint32_t* ranges,
                         uint32_t* bin_offsets, const uint8_t* bin_cut,
-                        ClsTileCache* tile_cache, int32_t prefix_mode, int32_t* status_dev,
-                        void* workspace, size_t workspace_bytes, cls_stream_t stream);
+                        ClsTileCache* tile_cache, int32_t prefix_mode, int32_t tile_ring,
+                        int32_t* status_dev, void* workspace, size_t workspace_bytes,
+                        cls_stream_t stream);
 
 /* Speculative depth cut (bucketed layout). With bin_cut != NULL (uint8
  * [total_tiles], the last depth bin to emit per global tile id), pairs of
@@ -405,6 +410,27 @@ int cls_render_backward(const ClsScene* scenes_dev, const ClsView* views_dev,
                         const float* prefix_state, const float* image,
                         const int32_t* n_contrib, const float* dL_dimage, float* grad2d,
                         float* grads, int32_t* work_counter, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * D-SSIM term of the photometric loss (Supp. "Implementation Details": the
+ * base 3DGS optimiser's (1 - lambda) L1 + lambda (1 - SSIM), SSIM with an
+ * 11 x 11 Gaussian window of standard deviation 1.5, C1 = 0.01^2,
+ * C2 = 0.03^2, zero padding at the image border, mean over 3 H W per view).
+ * Call after cls_render_forward with loss_mode 1 (L1) and loss_per_scene NULL,
+ * on a batch binned with tile_ring 1: `tiles`/`n_tiles_dev` the rendered tile
+ * list (active_tiles), tile_active as cls_project_and_bin wrote it. On the
+ * pixels of covered tiles (tile_active 1) it replaces dL_dimage (the forward
+ * pass's L1 gradient sign(C - C*) * loss_scale) by the gradient of the
+ * combined loss with respect to the image — the D-SSIM part is that of the
+ * whole image: the ring supplies every pixel within 10 of a covered one — and
+ * adds to loss_per_scene the combined loss summed over the covered tiles'
+ * pixels (times loss_scale). abc: float [cls_ssim_buffer_size(info)] scratch
+ * (nine planes per view). */
+size_t cls_ssim_buffer_size(const ClsBatchInfo* info); /* float entries */
+int cls_ssim_loss(const ClsView* views_dev, const ClsBatchInfo* info, const int32_t* tiles,
+                  const int32_t* n_tiles_dev, const uint8_t* tile_active, const float* image,
+                  const float* target, float lambda, float* abc, float* dL_dimage,
+                  float* loss_per_scene, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Sphere region and pruning (Sec. 3.3 "Sphere Pruning"; Supp. "Identifying

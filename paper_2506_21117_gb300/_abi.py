@@ -89,7 +89,7 @@ SIGNATURES = {
     "cls_project_workspace_size": (SZ, [P]),
     "cls_bin_offsets_size": (SZ, [P]),
     "cls_project_and_bin": (C.c_int, [P, P, P, I32, I32, P, P, P, P, P, P, I64, P, P, P, P, P,
-                                      I32, P, P, SZ, P]),
+                                      I32, I32, P, P, SZ, P]),
     "cls_complete_truncated": (C.c_int, [P, P, P, P, I64, P, P, I64, P, P, SZ, P]),
     "cls_sort_tiles_workspace_size": (SZ, [I64, I32]),
     "cls_sort_tiles": (C.c_int, [P, P, P, P, P, I64, I64, I32, P, P, P, I64, P, P, P, SZ, P]),
@@ -100,6 +100,8 @@ SIGNATURES = {
     "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P, P]),
     "cls_adam_workspace_size": (SZ, [I32]),
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
+    "cls_ssim_buffer_size": (SZ, [P]),
+    "cls_ssim_loss": (C.c_int, [P, P, P, P, P, P, P, F32, P, P, P, P]),
     "cls_spheres_workspace_size": (SZ, [I32]),
     "cls_fit_spheres": (C.c_int, [P, I32, P, I32, I32, I32, P, P, P, P, SZ, P]),
     "cls_prune_workspace_size": (SZ, [I32]),
@@ -192,13 +194,13 @@ def cls_bin_offsets_size(info) -> int:
 
 def cls_project_and_bin(scenes_dev, views_dev, info, project_mode, layout, records, tile_active,
                         active_tiles, n_active_tiles_dev, keys, vals, capacity, n_pairs_dev,
-                        ranges, bin_offsets, bin_cut, tile_cache, prefix_mode, status_dev,
-                        workspace, workspace_bytes, stream) -> int:
+                        ranges, bin_offsets, bin_cut, tile_cache, prefix_mode, tile_ring,
+                        status_dev, workspace, workspace_bytes, stream) -> int:
     return load().cls_project_and_bin(scenes_dev, views_dev, C.byref(info), project_mode, layout,
                                       records, tile_active, active_tiles, n_active_tiles_dev,
                                       keys, vals, capacity, n_pairs_dev, ranges, bin_offsets,
-                                      bin_cut, tile_cache, prefix_mode, status_dev, workspace,
-                                      workspace_bytes, stream)
+                                      bin_cut, tile_cache, prefix_mode, tile_ring, status_dev,
+                                      workspace, workspace_bytes, stream)
 
 
 def cls_complete_truncated(views_dev, info, records, keys, capacity, trunc, trunc_count,
@@ -292,3 +294,13 @@ def cls_prune_outside_spheres(params, row_stride, active, active_idx, n_active, 
     return load().cls_prune_outside_spheres(params, row_stride, active, active_idx, n_active,
                                             n_active_dev, spheres, k, removed, n_removed_dev,
                                             workspace, workspace_bytes, stream)
+
+
+def cls_ssim_buffer_size(info) -> int:
+    return load().cls_ssim_buffer_size(C.byref(info))
+
+
+def cls_ssim_loss(views_dev, info, tiles, n_tiles_dev, tile_active, image, target, lam, abc,
+                  dL_dimage, loss_per_scene, stream) -> int:
+    return load().cls_ssim_loss(views_dev, C.byref(info), tiles, n_tiles_dev, tile_active, image,
+                                target, lam, abc, dL_dimage, loss_per_scene, stream)

@@ -171,14 +171,28 @@ __device__ __forceinline__ void prefix2d_smem(int32_t* S, int rows, int cols, in
 // Odd shared-memory pitch for a grid of `cols` columns.
 __host__ __device__ __forceinline__ int smem_pitch(int cols) { return cols | 1; }
 
-// Per view: coverage of the active stamps -> tile mask -> summed-area table
-// S[y][x] = number of active tiles with ty < y and tx < x. Also clears every
-// tile's nearest-active depth for active_zmin_kernel. The grids go through
-// shared memory when they fit in `smem_cap` bytes.
+// Ring around the covered tiles: 2 for an uncovered tile with a covered one
+// among its eight neighbours (cov: 1 covered, 0 not; row pitch `pitch`).
+__device__ __forceinline__ uint8_t ring_value(const int32_t* cov, int pitch, int Tx, int Ty,
+                                              int x, int y) {
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int xx = x + dx, yy = y + dy;
+            if (xx >= 0 && xx < Tx && yy >= 0 && yy < Ty && cov[yy * pitch + xx] > 0) return 2;
+        }
+    return 0;
+}
+
+// Per view: coverage of the active stamps -> tile mask (1: covered by an
+// active rectangle; with `ring`, 2: an uncovered tile next to a covered one,
+// rendered too) -> summed-area table S[y][x] = number of rendered tiles with
+// ty < y and tx < x. Also clears every tile's nearest-active depth for
+// active_zmin_kernel. The grids go through shared memory when they fit in
+// `smem_cap` bytes.
 __global__ void __launch_bounds__(512)
 tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
                  uint8_t* __restrict__ tile_active, int32_t* __restrict__ sat,
-                 ClsTileCache* __restrict__ tile_cache, int smem_cap) {
+                 ClsTileCache* __restrict__ tile_cache, int smem_cap, int ring) {
     extern __shared__ int32_t s_grid[];
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
@@ -196,9 +210,19 @@ tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
         for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
             const int y = t / Tx, x = t - y * Tx;
             const int32_t a = s_grid[y * p + x] > 0 ? 1 : 0;
-            act[t] = (uint8_t)a;
             s_grid[y * p + x] = a;
             tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+            const int y = t / Tx, x = t - y * Tx;
+            act[t] = s_grid[y * p + x] ? (uint8_t)1
+                                       : (ring ? ring_value(s_grid, p, Tx, Ty, x, y) : (uint8_t)0);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+            const int y = t / Tx, x = t - y * Tx;
+            s_grid[y * p + x] = act[t] ? 1 : 0;
         }
         __syncthreads();
         prefix2d_smem(s_grid, Ty, Tx, p);
@@ -215,11 +239,18 @@ tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
         tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
     }
     __syncthreads();
+    if (ring) {  // the coverage counts in D stay > 0 exactly on covered tiles
+        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+            const int y = t / Tx, x = t - y * Tx;
+            if (!act[t]) act[t] = ring_value(D, Wd, Tx, Ty, x, y);
+        }
+        __syncthreads();
+    }
     for (int y = threadIdx.x; y <= Ty; y += blockDim.x) {
         int32_t run = 0;
         S[(int64_t)y * Wd] = 0;
         for (int x = 0; x < Tx; ++x) {
-            if (y > 0) run += act[(int64_t)(y - 1) * Tx + x];
+            if (y > 0) run += act[(int64_t)(y - 1) * Tx + x] != 0;
             S[(int64_t)y * Wd + x + 1] = run;
         }
     }
@@ -956,11 +987,11 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                    uint64_t* keys, uint32_t* vals, int64_t capacity,
                                    int64_t* n_pairs_dev, uint32_t* ranges, uint32_t* bin_offsets,
                                    const uint8_t* bin_cut, ClsTileCache* tile_cache,
-                                   int32_t prefix_mode, int32_t* status_dev, void* workspace,
-                                   size_t workspace_bytes, cls_stream_t stream) {
+                                   int32_t prefix_mode, int32_t tile_ring, int32_t* status_dev,
+                                   void* workspace, size_t workspace_bytes, cls_stream_t stream) {
     if (!info || !scenes_dev || !views_dev || !records || !tile_active || !active_tiles ||
         !n_active_tiles_dev || !n_pairs_dev || !status_dev || !workspace || capacity < 0 ||
-        !tile_cache || (prefix_mode != 0 && prefix_mode != 1) ||
+        !tile_cache || (prefix_mode != 0 && prefix_mode != 1) || (tile_ring != 0 && tile_ring != 1) ||
         (project_mode != 0 && project_mode != 1) || (layout != 0 && layout != 1) ||
         (capacity > 0 && !keys) || (layout == 0 && capacity > 0 && !vals) ||
         (layout == 1 && (!ranges || !bin_offsets)))
@@ -1024,7 +1055,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         stamp_active_kernel<<<dim3((info->max_active + 255) / 256, V), 256, 0, s>>>(
             scenes_dev, views_dev, records, diff);
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
-                                              grid_cap);
+                                              grid_cap, tile_ring);
     if (info->max_active > 0)
         active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads - 1) /
                                                        kZminThreads, 38), V),

@@ -392,7 +392,9 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                 }
             }
             const bool all_done = __syncthreads_count(p0.done && p1.done) == kFwdThreads;
-            truncated = !all_done && limit < kBins - 1 && sm.off[limit + 1] < sm.off[kBins];
+            // entries the tile may still need: behind the cut and behind the cached prefix
+            const uint32_t needed_from = max(sm.off[limit + 1], start + pw.skip_to);
+            truncated = !all_done && limit < kBins - 1 && needed_from < sm.off[kBins];
             if (threadIdx.x == 0) {
                 if (truncated) {
                     const int slot = atomicAdd(trunc_count, 1);

@@ -1,0 +1,260 @@
+// D-SSIM term of the photometric loss over the rendered tiles (Supp.
+// "Implementation Details": the base 3DGS optimiser's loss,
+// (1 - lambda) L1 + lambda (1 - SSIM), SSIM with an 11 x 11 Gaussian window of
+// standard deviation 1.5, C1 = 0.01^2, C2 = 0.03^2, zero padding at the image
+// border).
+//
+// With mu = g * x, E[x^2] = g * x^2, E[xy] = g * (x y) per pixel p, the map
+// S(p) depends on x only through those window sums, so
+//   d/dx(q) sum_p S(p) = (g * a)(q) + 2 x(q) (g * b)(q) + y(q) (g * c)(q)
+// with a = dS/dmu_x - 2 mu_x dS/dsigma_x^2 - mu_y dS/dsigma_xy,
+// b = dS/dsigma_x^2, c = dS/dsigma_xy. Pass 1 computes S, a, b, c at every
+// pixel of every rendered tile (covered tiles and the ring around them, which
+// holds every pixel within 10 of a covered one); pass 2 blurs a, b, c at the
+// covered tiles' pixels and combines. A block handles one 16 x 16 tile: it
+// loads the 26 x 26 region (5-pixel halo) of every plane it needs at once,
+// then blurs one channel at a time with a separable 11-tap window.
+#include "common.cuh"
+
+namespace cls {
+
+constexpr int kSsimR = 5;                       // window radius
+constexpr int kSsimW = 2 * kSsimR + 1;          // 11 taps
+constexpr int kReg = kTile + 2 * kSsimR;        // 26 x 26 region
+constexpr float kSsimSigma = 1.5f;
+constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
+
+__device__ __forceinline__ void ssim_window(float* w) {
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int k = 0; k < kSsimW; ++k) {
+            const float d = (float)(k - kSsimR);
+            w[k] = expf(-(d * d) / (2.0f * kSsimSigma * kSsimSigma));
+            s += w[k];
+        }
+        for (int k = 0; k < kSsimW; ++k) w[k] /= s;
+    }
+}
+
+// Planar per-view images: channel c of pixel (x, y) of view v.
+__device__ __forceinline__ int64_t plane_index(const ClsView& v, int c, int x, int y) {
+    const int64_t plane = (int64_t)v.cam.width * v.cam.height;
+    return 3 * v.pix_base + c * plane + (int64_t)y * v.cam.width + x;
+}
+
+struct SsimSmem {
+    float w[kSsimW];
+    float r[9][kReg][kReg];   // region planes: x, y of each channel (pass 1); a, b, c (pass 2)
+    float h[5][kReg][kTile];  // horizontal sums of one channel
+    float red[8];
+};
+
+__device__ __forceinline__ float blur_col(const SsimSmem& sm, int q, int i, int j) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSsimW; ++k) s += sm.w[k] * sm.h[q][i + k][j];
+    return s;
+}
+
+__device__ __forceinline__ float block_sum(SsimSmem& sm, float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sm.red[k];
+    __syncthreads();
+    return t;
+}
+
+// Load `np` planes of the tile's 26 x 26 region (zero outside the image):
+// plane q is value(q, flat index of the pixel in its view's plane).
+template <typename Value>
+__device__ __forceinline__ void load_region(SsimSmem& sm, int np, int x0, int y0, int W, int H,
+                                            Value value) {
+    for (int e = threadIdx.x; e < kReg * kReg; e += blockDim.x) {
+        const int row = e / kReg, col = e - row * kReg;
+        const int gx = x0 + col, gy = y0 + row;
+        const bool in = gx >= 0 && gx < W && gy >= 0 && gy < H;
+        const int64_t off = (int64_t)gy * W + gx;
+        for (int q = 0; q < np; ++q) sm.r[q][row][col] = in ? value(q, off) : 0.f;
+    }
+}
+
+// Pass 1: S, a, b, c at every pixel of every rendered tile; lambda (1 - S)
+// summed into the loss over the covered tiles' pixels.
+__global__ void __launch_bounds__(kTilePixels)
+ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* __restrict__ tiles,
+                 const int32_t* __restrict__ n_tiles, const uint8_t* __restrict__ tile_active,
+                 const float* __restrict__ image, const float* __restrict__ target, float lambda,
+                 float* __restrict__ abc, float* __restrict__ loss_per_scene) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SsimSmem& sm = *reinterpret_cast<SsimSmem*>(smem_raw);
+    ssim_window(sm.w);
+    const int n = *n_tiles;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int tile = tiles[t];
+        const ClsView& view = views[view_of_tile(views, n_views, tile)];
+        const int local = tile - view.tile_base;
+        const int tx = local % view.tiles_x, ty = local / view.tiles_x;
+        const int W = view.cam.width, H = view.cam.height;
+        const int64_t plane = (int64_t)W * H;
+        const float* xi = image + 3 * view.pix_base;
+        const float* yi = target + 3 * view.pix_base;
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        __syncthreads();
+        load_region(sm, 6, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
+                    [&](int q, int64_t off) {
+                        return ((q & 1) ? yi : xi)[(q >> 1) * plane + off];
+                    });
+        float lsum = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < kReg * kTile; e += blockDim.x) {
+                const int row = e / kTile, j = e - row * kTile;
+                float sx = 0.f, sy = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
+#pragma unroll
+                for (int k = 0; k < kSsimW; ++k) {
+                    const float w = sm.w[k], xv = sm.r[2 * c][row][j + k],
+                                yv = sm.r[2 * c + 1][row][j + k];
+                    sx += w * xv;
+                    sy += w * yv;
+                    sxx += w * xv * xv;
+                    syy += w * yv * yv;
+                    sxy += w * xv * yv;
+                }
+                sm.h[0][row][j] = sx;
+                sm.h[1][row][j] = sy;
+                sm.h[2][row][j] = sxx;
+                sm.h[3][row][j] = syy;
+                sm.h[4][row][j] = sxy;
+            }
+            __syncthreads();
+            const float mx = blur_col(sm, 0, ly, lx), my = blur_col(sm, 1, ly, lx);
+            const float exx = blur_col(sm, 2, ly, lx), eyy = blur_col(sm, 3, ly, lx);
+            const float exy = blur_col(sm, 4, ly, lx);
+            const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+            const float D = B1 * B2;
+            const float S = A1 * A2 / D;
+            const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
+            const float dvx = -S / B2;
+            const float dcxy = 2.f * A1 / D;
+            if (inside) {
+                const int64_t base = 9 * view.pix_base + (int64_t)(3 * c) * plane +
+                                     (int64_t)py * W + px;
+                abc[base] = dmu - 2.f * mx * dvx - my * dcxy;
+                abc[base + plane] = dvx;
+                abc[base + 2 * plane] = dcxy;
+                lsum += 1.f - S;
+            }
+        }
+        const bool covered = tile_active[tile] == 1;
+        const float tot = block_sum(sm, covered ? lsum : 0.f);
+        if (threadIdx.x == 0 && loss_per_scene && covered)
+            atomicAdd(loss_per_scene + view.scene, lambda * view.loss_scale * tot);
+    }
+}
+
+// Pass 2, covered tiles only: dL/dC = (1 - lambda) dL1/dC - lambda * scale *
+// d(sum S)/dx, where dL1/dC = sign(C - C*) * scale was written by the forward
+// pass; (1 - lambda) |C - C*| * scale is added to the loss.
+__global__ void __launch_bounds__(kTilePixels)
+ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* __restrict__ tiles,
+                 const int32_t* __restrict__ n_tiles, const uint8_t* __restrict__ tile_active,
+                 const float* __restrict__ image, const float* __restrict__ target, float lambda,
+                 const float* __restrict__ abc, float* __restrict__ dL_dimage,
+                 float* __restrict__ loss_per_scene) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SsimSmem& sm = *reinterpret_cast<SsimSmem*>(smem_raw);
+    ssim_window(sm.w);
+    const int n = *n_tiles;
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const int tile = tiles[t];
+        if (tile_active[tile] != 1) continue;  // uniform over the block
+        const ClsView& view = views[view_of_tile(views, n_views, tile)];
+        const int local = tile - view.tile_base;
+        const int tx = local % view.tiles_x, ty = local / view.tiles_x;
+        const int W = view.cam.width, H = view.cam.height;
+        const int64_t plane = (int64_t)W * H;
+        const float* m = abc + 9 * view.pix_base;
+        const int px = tx * kTile + lx, py = ty * kTile + ly;
+        const bool inside = px < W && py < H;
+        __syncthreads();
+        load_region(sm, 9, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
+                    [&](int q, int64_t off) { return m[q * plane + off]; });
+        float lsum = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < 3 * kReg * kTile; e += blockDim.x) {
+                const int q = e / (kReg * kTile), rem = e - q * kReg * kTile;
+                const int row = rem / kTile, j = rem - row * kTile;
+                float acc = 0.f;
+#pragma unroll
+                for (int k = 0; k < kSsimW; ++k) acc += sm.w[k] * sm.r[3 * c + q][row][j + k];
+                sm.h[q][row][j] = acc;
+            }
+            __syncthreads();
+            if (inside) {
+                const float ga = blur_col(sm, 0, ly, lx), gb = blur_col(sm, 1, ly, lx),
+                            gc = blur_col(sm, 2, ly, lx);
+                const int64_t i = plane_index(view, c, px, py);
+                const float xv = image[i], yv = target[i];
+                const float gs = ga + 2.f * xv * gb + yv * gc;
+                dL_dimage[i] = (1.f - lambda) * dL_dimage[i] - lambda * view.loss_scale * gs;
+                lsum += fabsf(xv - yv);
+            }
+        }
+        const float tot = block_sum(sm, lsum);
+        if (threadIdx.x == 0 && loss_per_scene)
+            atomicAdd(loss_per_scene + view.scene, (1.f - lambda) * view.loss_scale * tot);
+    }
+}
+
+static int g_ssim_blocks = 0;
+
+}  // namespace cls
+
+using namespace cls;
+
+extern "C" size_t cls_ssim_buffer_size(const ClsBatchInfo* info) {
+    return info ? (size_t)info->total_pixels * 9 : 0;
+}
+
+extern "C" int cls_ssim_loss(const ClsView* views_dev, const ClsBatchInfo* info,
+                             const int32_t* tiles, const int32_t* n_tiles_dev,
+                             const uint8_t* tile_active, const float* image, const float* target,
+                             float lambda, float* abc, float* dL_dimage, float* loss_per_scene,
+                             cls_stream_t stream) {
+    if (!views_dev || !info || !tiles || !n_tiles_dev || !tile_active || !image || !target ||
+        !abc || !dL_dimage || info->n_views <= 0 || info->total_tiles <= 0 ||
+        !(lambda >= 0.0f && lambda <= 1.0f))
+        return CLS_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if (g_ssim_blocks == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(ssim_maps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SsimSmem));
+        cudaFuncSetAttribute(ssim_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SsimSmem));
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim_maps_kernel, kTilePixels,
+                                                      sizeof(SsimSmem));
+        g_ssim_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
+    const int blocks = (int)hmin64(info->total_tiles, g_ssim_blocks);
+    ssim_maps_kernel<<<blocks, kTilePixels, sizeof(SsimSmem), s>>>(
+        views_dev, info->n_views, tiles, n_tiles_dev, tile_active, image, target, lambda, abc,
+        loss_per_scene);
+    ssim_grad_kernel<<<blocks, kTilePixels, sizeof(SsimSmem), s>>>(
+        views_dev, info->n_views, tiles, n_tiles_dev, tile_active, image, target, lambda, abc,
+        dL_dimage, loss_per_scene);
+    CLS_CHECK_LAUNCH();
+    return CLS_OK;
+}

@@ -19,7 +19,8 @@ import torch
 
 from . import _abi as abi
 
-LOSS_MODES = {"none": 0, "l1": 1, "l2": 2}
+LOSS_MODES = {"none": 0, "l1": 1, "l2": 2, "l1+ssim": 1}
+SSIM_LAMBDA = 0.2  # weight of D-SSIM in the base 3DGS optimiser's loss
 
 
 def sh_coeffs(degree: int) -> int:
@@ -104,7 +105,8 @@ class Batch:
     """Scene/view tables of one launch batch and every buffer the hot path uses."""
 
     def __init__(self, scenes: Sequence[SceneState], cams_per_scene: Sequence[Sequence],
-                 device="cuda", layout: int = 1, lazy: bool = True, prefix_cache: bool = True):
+                 device="cuda", layout: int = 1, lazy: bool = True, prefix_cache: bool = True,
+                 ssim: bool = False):
         """layout 1: pairs bucketed by (tile, depth bin); with `lazy` the
         renderer sorts the depth bins it reaches (cls_sort_tiles only pre-sorts
         bins above CLS_LAZY_MAX_BIN keys), otherwise cls_sort_tiles sorts every
@@ -112,8 +114,11 @@ class Batch:
         radix sort (cls_sort_keys). `prefix_cache` keeps each tile's static
         prefix across iterations (valid while the static rows of the scenes do
         not change, which masked Adam guarantees); off, every iteration
-        rebuilds it."""
+        rebuilds it. `ssim` adds the D-SSIM term to an L1 loss (the base
+        optimiser's (1 - 0.2) L1 + 0.2 D-SSIM); the ring of tiles around the
+        covered ones is then rendered too (the window needs it)."""
         self.device = device
+        self.ssim = bool(ssim)
         self.layout = layout
         self.lazy = lazy and layout == 1
         self.prefix_mode = 1 if prefix_cache else 0
@@ -177,6 +182,8 @@ class Batch:
         self._epochs = [st.epoch for st in self.scenes]
         self.reset_prefix()
         self.reproject = False  # project every Gaussian on the next call (after pruning)
+        self.abc = (torch.empty(abi.cls_ssim_buffer_size(info), dtype=torch.float32, device=dev)
+                    if self.ssim else None)
         self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
                                    device=dev)
         self.adam_ws = torch.zeros(max(abi.cls_adam_workspace_size(S), 256), dtype=torch.uint8,
@@ -240,7 +247,8 @@ class Batch:
             _ptr(b.tile_active), _ptr(b.active_tiles), _ptr(b.n_active_tiles),
             _ptr(b.keys), _ptr(b.vals), b.capacity, _ptr(b.n_pairs), _ptr(b.ranges),
             _ptr(b.bin_offsets), _ptr(b.cut) if b.use_cut else None, _ptr(b.tile_cache),
-            b.prefix_mode, _ptr(b.status), _ptr(b.proj_ws), b.proj_ws.numel(), b.stream()),
+            b.prefix_mode, 1 if b.ssim else 0, _ptr(b.status), _ptr(b.proj_ws),
+            b.proj_ws.numel(), b.stream()),
             "cls_project_and_bin")
 
     def plan_capacity(self, slack: float = 1.5, extra: int = 1 << 16):
@@ -296,7 +304,13 @@ class Batch:
 
     def forward(self, loss_mode: int, bg=(0.0, 0.0, 0.0)):
         """Render the active tiles into `image` (the backward pass reads it),
-        with the fused loss when loss_mode is 1 (L1) or 2 (L2)."""
+        with the fused loss when loss_mode is 1 (L1) or 2 (L2), then the D-SSIM
+        term if the batch has it."""
+        self.render(loss_mode, bg)
+        if self.ssim and loss_mode:
+            self.apply_ssim(loss_mode)
+
+    def render(self, loss_mode: int, bg=(0.0, 0.0, 0.0)):
         b = self
         if loss_mode:
             b.loss.zero_()
@@ -316,6 +330,16 @@ class Batch:
             b._forward_call(loss_mode, bg, _ptr(b.trunc), _ptr(b.trunc_count),
                             _ptr(b.trunc) + 4 * cap, None, _ptr(b.cut), rerun=True)
 
+    def apply_ssim(self, loss_mode: int = 1):
+        """Combine the forward pass's L1 gradient with the D-SSIM term."""
+        b = self
+        if loss_mode != 1:
+            raise ValueError("the D-SSIM term combines with the L1 loss")
+        abi.check(abi.cls_ssim_loss(
+            _ptr(b.views_dev), b.info, _ptr(b.active_tiles), _ptr(b.n_active_tiles),
+            _ptr(b.tile_active), _ptr(b.image), _ptr(b.target), SSIM_LAMBDA, _ptr(b.abc),
+            _ptr(b.dL_dimage), _ptr(b.loss), b.stream()), "cls_ssim_loss")
+
     def _forward_call(self, loss_mode, bg, tiles, n_tiles, list_ranks, cut_in, cut_out,
                       rerun=False):
         b = self
@@ -329,7 +353,8 @@ class Batch:
             _ptr(b.prefix_state), _ptr(b.prefix_last), bg,
             _ptr(b.target) if loss_mode else None, loss_mode,
             _ptr(b.image), _ptr(b.T_final), _ptr(b.n_contrib),
-            _ptr(b.dL_dimage) if loss_mode else None, _ptr(b.loss) if loss_mode else None,
+            _ptr(b.dL_dimage) if loss_mode else None,
+            _ptr(b.loss) if loss_mode and not b.ssim else None,
             _ptr(b.counter), b.stream()), "cls_render_forward")
 
     def _sorted_vals(self):
@@ -506,7 +531,8 @@ class LocalUpdate:
             lift(self.state, self.cams, masks, vote_mode, device)
         else:
             raise ValueError("give either an active set or change masks")
-        self.batch = Batch([self.state], [self.cams], device, layout, lazy)
+        self.batch = Batch([self.state], [self.cams], device, layout, lazy,
+                           ssim=loss == "l1+ssim")
         if targets is not None:
             self.batch.set_targets(targets)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
@@ -535,7 +561,7 @@ class LocalUpdate:
         self.state = state
         dev = state.params.device
         lift(state, self.cams, masks, vote_mode, dev)
-        self.batch = Batch([state], [self.cams], dev, layout, lazy)
+        self.batch = Batch([state], [self.cams], dev, layout, lazy, ssim=loss == "l1+ssim")
         self.batch.target = targets.to(dev, non_blocking=True)
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
         self._init_region(0, None)
