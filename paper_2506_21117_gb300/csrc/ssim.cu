@@ -13,7 +13,8 @@
 // holds every pixel within 10 of a covered one); pass 2 blurs a, b, c at the
 // covered tiles' pixels and combines. A block handles one 16 x 16 tile: it
 // loads the 26 x 26 region (5-pixel halo) of every plane it needs at once,
-// then blurs one channel at a time with a separable 11-tap window.
+// then applies the separable 11-tap window, two adjacent outputs per thread
+// and direction so each loaded value serves both.
 #include "common.cuh"
 
 namespace cls {
@@ -44,17 +45,10 @@ __device__ __forceinline__ int64_t plane_index(const ClsView& v, int c, int x, i
 
 struct SsimSmem {
     float w[kSsimW];
-    float r[9][kReg][kReg];   // region planes: x, y of each channel (pass 1); a, b, c (pass 2)
-    float h[5][kReg][kTile];  // horizontal sums of one channel
+    float r[9][kReg][kReg];       // region planes: x, y of each channel (pass 1); a, b, c (pass 2)
+    float h[3][5][kReg][kTile];   // horizontal sums per channel (5 in pass 1, 3 in pass 2)
     float red[8];
 };
-
-__device__ __forceinline__ float blur_col(const SsimSmem& sm, int q, int i, int j) {
-    float s = 0.f;
-#pragma unroll
-    for (int k = 0; k < kSsimW; ++k) s += sm.w[k] * sm.h[q][i + k][j];
-    return s;
-}
 
 __device__ __forceinline__ float block_sum(SsimSmem& sm, float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -81,6 +75,70 @@ __device__ __forceinline__ void load_region(SsimSmem& sm, int np, int x0, int y0
     }
 }
 
+// Horizontal 11-tap sums, two adjacent outputs per work item (12 loads per
+// input plane instead of 22). Pass 1 (NQ = 5): from x, y of a channel,
+// sums of x, y, x^2, y^2, x y; pass 2 (NQ = 3): sums of a, b, c.
+template <int NQ>
+__device__ __forceinline__ void blur_rows_all(SsimSmem& sm) {
+    constexpr int kItems = 3 * kReg * (kTile / 2);
+    for (int e = threadIdx.x; e < kItems; e += blockDim.x) {
+        const int c = e / (kReg * (kTile / 2)), rem = e - c * kReg * (kTile / 2);
+        const int row = rem / (kTile / 2), j = 2 * (rem - row * (kTile / 2));
+        if (NQ == 5) {
+            const float* xr = &sm.r[2 * c][row][j];
+            const float* yr = &sm.r[2 * c + 1][row][j];
+            float s[2][5] = {};
+#pragma unroll
+            for (int k = 0; k <= kSsimW; ++k) {
+                const float xv = xr[k], yv = yr[k];
+                const float xx = xv * xv, yy = yv * yv, xy = xv * yv;
+                if (k < kSsimW) {
+                    const float w = sm.w[k];
+                    s[0][0] += w * xv; s[0][1] += w * yv; s[0][2] += w * xx;
+                    s[0][3] += w * yy; s[0][4] += w * xy;
+                }
+                if (k > 0) {
+                    const float w = sm.w[k - 1];
+                    s[1][0] += w * xv; s[1][1] += w * yv; s[1][2] += w * xx;
+                    s[1][3] += w * yy; s[1][4] += w * xy;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                sm.h[c][q][row][j] = s[0][q];
+                sm.h[c][q][row][j + 1] = s[1][q];
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float* vr = &sm.r[3 * c + q][row][j];
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int k = 0; k <= kSsimW; ++k) {
+                    const float v = vr[k];
+                    if (k < kSsimW) s0 += sm.w[k] * v;
+                    if (k > 0) s1 += sm.w[k - 1] * v;
+                }
+                sm.h[c][q][row][j] = s0;
+                sm.h[c][q][row][j + 1] = s1;
+            }
+        }
+    }
+}
+
+// Vertical 11-tap sums of quantity q of channel c at rows i, i + 1, column j.
+__device__ __forceinline__ void blur_col2(const SsimSmem& sm, int c, int q, int i, int j,
+                                          float& o0, float& o1) {
+    o0 = 0.f;
+    o1 = 0.f;
+#pragma unroll
+    for (int k = 0; k <= kSsimW; ++k) {
+        const float v = sm.h[c][q][i + k][j];
+        if (k < kSsimW) o0 += sm.w[k] * v;
+        if (k > 0) o1 += sm.w[k - 1] * v;
+    }
+}
+
 // Pass 1: S, a, b, c at every pixel of every rendered tile; lambda (1 - S)
 // summed into the loss over the covered tiles' pixels.
 __global__ void __launch_bounds__(kTilePixels)
@@ -92,7 +150,6 @@ ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
     SsimSmem& sm = *reinterpret_cast<SsimSmem*>(smem_raw);
     ssim_window(sm.w);
     const int n = *n_tiles;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int tile = tiles[t];
         const ClsView& view = views[view_of_tile(views, n_views, tile)];
@@ -102,48 +159,36 @@ ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
         const int64_t plane = (int64_t)W * H;
         const float* xi = image + 3 * view.pix_base;
         const float* yi = target + 3 * view.pix_base;
-        const int px = tx * kTile + lx, py = ty * kTile + ly;
-        const bool inside = px < W && py < H;
         __syncthreads();
         load_region(sm, 6, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
                     [&](int q, int64_t off) {
                         return ((q & 1) ? yi : xi)[(q >> 1) * plane + off];
                     });
+        __syncthreads();
+        blur_rows_all<5>(sm);
+        __syncthreads();
         float lsum = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            __syncthreads();
-            for (int e = threadIdx.x; e < kReg * kTile; e += blockDim.x) {
-                const int row = e / kTile, j = e - row * kTile;
-                float sx = 0.f, sy = 0.f, sxx = 0.f, syy = 0.f, sxy = 0.f;
+        // vertical sums and the maps: (channel, column, row pair) items
+        for (int e = threadIdx.x; e < 3 * kTile * (kTile / 2); e += blockDim.x) {
+            const int c = e / (kTile * (kTile / 2)), rem = e - c * kTile * (kTile / 2);
+            const int i = 2 * (rem / kTile), j = rem - (rem / kTile) * kTile;
+            float v[5][2];
 #pragma unroll
-                for (int k = 0; k < kSsimW; ++k) {
-                    const float w = sm.w[k], xv = sm.r[2 * c][row][j + k],
-                                yv = sm.r[2 * c + 1][row][j + k];
-                    sx += w * xv;
-                    sy += w * yv;
-                    sxx += w * xv * xv;
-                    syy += w * yv * yv;
-                    sxy += w * xv * yv;
-                }
-                sm.h[0][row][j] = sx;
-                sm.h[1][row][j] = sy;
-                sm.h[2][row][j] = sxx;
-                sm.h[3][row][j] = syy;
-                sm.h[4][row][j] = sxy;
-            }
-            __syncthreads();
-            const float mx = blur_col(sm, 0, ly, lx), my = blur_col(sm, 1, ly, lx);
-            const float exx = blur_col(sm, 2, ly, lx), eyy = blur_col(sm, 3, ly, lx);
-            const float exy = blur_col(sm, 4, ly, lx);
-            const float vx = exx - mx * mx, vy = eyy - my * my, cxy = exy - mx * my;
-            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-            const float D = B1 * B2;
-            const float S = A1 * A2 / D;
-            const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
-            const float dvx = -S / B2;
-            const float dcxy = 2.f * A1 / D;
-            if (inside) {
+            for (int q = 0; q < 5; ++q) blur_col2(sm, c, q, i, j, v[q][0], v[q][1]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int px = tx * kTile + j, py = ty * kTile + i + u;
+                if (!(px < W && py < H)) continue;
+                const float mx = v[0][u], my = v[1][u];
+                const float vx = v[2][u] - mx * mx, vy = v[3][u] - my * my,
+                            cxy = v[4][u] - mx * my;
+                const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+                const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+                const float D = B1 * B2;
+                const float S = A1 * A2 / D;
+                const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
+                const float dvx = -S / B2;
+                const float dcxy = 2.f * A1 / D;
                 const int64_t base = 9 * view.pix_base + (int64_t)(3 * c) * plane +
                                      (int64_t)py * W + px;
                 abc[base] = dmu - 2.f * mx * dvx - my * dcxy;
@@ -172,7 +217,6 @@ ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
     SsimSmem& sm = *reinterpret_cast<SsimSmem*>(smem_raw);
     ssim_window(sm.w);
     const int n = *n_tiles;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int tile = tiles[t];
         if (tile_active[tile] != 1) continue;  // uniform over the block
@@ -182,30 +226,27 @@ ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
         const int W = view.cam.width, H = view.cam.height;
         const int64_t plane = (int64_t)W * H;
         const float* m = abc + 9 * view.pix_base;
-        const int px = tx * kTile + lx, py = ty * kTile + ly;
-        const bool inside = px < W && py < H;
         __syncthreads();
         load_region(sm, 9, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
                     [&](int q, int64_t off) { return m[q * plane + off]; });
+        __syncthreads();
+        blur_rows_all<3>(sm);
+        __syncthreads();
         float lsum = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            __syncthreads();
-            for (int e = threadIdx.x; e < 3 * kReg * kTile; e += blockDim.x) {
-                const int q = e / (kReg * kTile), rem = e - q * kReg * kTile;
-                const int row = rem / kTile, j = rem - row * kTile;
-                float acc = 0.f;
+        for (int e = threadIdx.x; e < 3 * kTile * (kTile / 2); e += blockDim.x) {
+            const int c = e / (kTile * (kTile / 2)), rem = e - c * kTile * (kTile / 2);
+            const int i = 2 * (rem / kTile), j = rem - (rem / kTile) * kTile;
+            float g[3][2];
 #pragma unroll
-                for (int k = 0; k < kSsimW; ++k) acc += sm.w[k] * sm.r[3 * c + q][row][j + k];
-                sm.h[q][row][j] = acc;
-            }
-            __syncthreads();
-            if (inside) {
-                const float ga = blur_col(sm, 0, ly, lx), gb = blur_col(sm, 1, ly, lx),
-                            gc = blur_col(sm, 2, ly, lx);
-                const int64_t i = plane_index(view, c, px, py);
-                const float xv = image[i], yv = target[i];
-                const float gs = ga + 2.f * xv * gb + yv * gc;
-                dL_dimage[i] = (1.f - lambda) * dL_dimage[i] - lambda * view.loss_scale * gs;
+            for (int q = 0; q < 3; ++q) blur_col2(sm, c, q, i, j, g[q][0], g[q][1]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int px = tx * kTile + j, py = ty * kTile + i + u;
+                if (!(px < W && py < H)) continue;
+                const int64_t idx = plane_index(view, c, px, py);
+                const float xv = image[idx], yv = target[idx];
+                const float gs = g[0][u] + 2.f * xv * g[1][u] + yv * g[2][u];
+                dL_dimage[idx] = (1.f - lambda) * dL_dimage[idx] - lambda * view.loss_scale * gs;
                 lsum += fabsf(xv - yv);
             }
         }
