@@ -285,6 +285,35 @@ def workload_fd(seed: int = 0):
     return scene, cams, targets
 
 
+def workload_addition(n: int = 100_000, n_views: int = 8, size: int = 800,
+                      fraction: float = 0.05, sh_degree: int = 3, seed: int = 0):
+    """An object appears: the uniform scene with every Gaussian inside a random
+    box removed (so lifting finds almost nothing there), ring views whose change
+    masks are the box's projection. Returns (scene, cams, masks, box)."""
+    scene = uniform_scene(n, sh_degree, seed)
+    box = random_box_in_unit_cube(fraction, seed)
+    keep = ~inside_box(scene["means"], box)
+    scene = {k: v[keep] for k, v in scene.items()}
+    cams = ring_cameras(n_views, 4.0, size, size)
+    masks = [box_change_mask(c, box) for c in cams]
+    return scene, cams, masks, box
+
+
+def sampling_draws(seed: int = 0):
+    """The random numbers new-point sampling consumes, as a function
+    (round, kind, shape) -> float32 array: kind "box" and "comp" uniform in
+    [0, 1), "normal" standard normal; each (round, kind) has its own stream."""
+    codes = {"box": 1, "comp": 2, "normal": 3}
+    below_one = np.nextafter(np.float32(1.0), np.float32(0.0))
+
+    def draws(round_: int, kind: str, shape):
+        rng = np.random.default_rng([seed, round_, codes[kind]])
+        if kind == "normal":
+            return rng.standard_normal(shape).astype(np.float32)
+        return np.minimum(rng.random(shape).astype(np.float32), below_one)
+    return draws
+
+
 def serving_scenes(n_scenes: int = 64, n_lo: int = 50_000, n_hi: int = 500_000,
                    sh_degree: int = 3, seed: int = 0):
     """Resident scenes of the serving workload: Gaussian counts log-uniform in
