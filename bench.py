@@ -365,6 +365,7 @@ def run_ours(args, rank, world):
     e2e = run_e2e(args, lu, targets, masks, cams)
     active_np = lu.state.active.cpu().numpy().astype(bool)
     sphere = run_sphere_region(lu)
+    sampling = run_sampling()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -383,6 +384,7 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "gpu_launches": int(bt.launches_per_step() * args.steps),
         "sphere_region": sphere,
+        "new_point_sampling": sampling,
     }
     if ssim_roof is not None:
         ssim_roof["peak"] = hbm_peak
@@ -423,6 +425,36 @@ def run_sphere_region(lu):
     return {"active_gaussians": A, "spheres": region.k, "kmeans_iters": 16,
             "fit_ms": e[0].elapsed_time(e[1]), "prune_check_ms": e[2].elapsed_time(e[3]),
             "removed": removed, "note": "prune_check_ms includes reading the removed count back"}
+
+
+def run_sampling():
+    """New-point sampling for an appearing object at the local-update size
+    (100k Gaussians, 8 views of 800x800, the Gaussians of a 5% box removed),
+    from an empty O to 5000 points (box round, then K-Means mixture rounds, each
+    filtered by the vote), then the new Gaussians' initialisation; wall time
+    of the host-driven rounds (each reads the kept count back)."""
+    import torch
+    from paper_2506_21117_gb300 import synthetic as S
+    from paper_2506_21117_gb300.sampling import init_gaussians, sample_points
+    from paper_2506_21117_gb300.update import SceneState
+    scene, cams, masks, _ = S.workload_addition(n=100_000, n_views=8, size=800, seed=0)
+    st = SceneState(scene, 3)
+    st.set_active(np.zeros(st.n, bool))
+    masks_dev = torch.from_numpy(np.concatenate([m.reshape(-1) for m in masks])).cuda()
+    draws = S.sampling_draws(0)
+    sample_points(st, cams, masks_dev, 500, draws)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = sample_points(st, cams, masks_dev, 5000, draws)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    rows = init_gaussians(out["new"], 3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"workload": "100k Gaussians, 8 views 800x800, empty 5% box, target 5000 points",
+            "points": int(out["points"].shape[0]), "rounds": out["rounds"],
+            "sample_ms": (t1 - t0) * 1e3, "init_ms": (t2 - t1) * 1e3,
+            "new_gaussians": int(rows.shape[0])}
 
 
 def run_serving(args, seed=0):

@@ -475,6 +475,49 @@ int cls_prune_outside_spheres(float* params, int32_t row_stride, uint8_t* active
                               cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * New-point sampling for appearing objects (Sec. 3.2 "Gaussian Sampling for
+ * New Objects", New Point Sampling; Supp. Full-Scene and Region Point
+ * Sampling). The caller runs the rounds: an empty point set O is replaced by
+ * the vote-kept part of a uniform box sample (cls_points_bbox,
+ * cls_box_sample, cls_lift_change_masks on the samples, cls_gather_points);
+ * a non-empty one grows by the vote-kept part of n/5 mixture draws
+ * (cls_fit_spheres for the K-Means clusters of O, cls_region_mixture,
+ * cls_mixture_sample, vote, gather). Points are rows of 4 floats (x, y, z,
+ * unused). Random numbers are inputs: u in [0, 1), z standard normal.
+ *   cls_points_bbox: per-axis min and max of n parameter rows -> lohi[6]
+ *     (min xyz, max xyz; device); scratch: 6 uint32 (device)
+ *   cls_box_sample: points[i] = lo + u[i] (hi - lo) per axis (float32 ops)
+ *   cls_gather_points: points[i] = src row idx[i] (or row i if idx is NULL),
+ *     i < min(*n_dev, n_max) (or n_max if n_dev is NULL)
+ *   cls_region_mixture: per cluster (labels/clusters/counts from
+ *     cls_fit_spheres on the same points), |p_far - c| of the member of
+ *     largest float32 squared distance (ties to the lowest position) ->
+ *     absv [k][4]; scratch: CLS_MAX_SPHERES uint64 (device)
+ *   cls_mixture_sample: per draw i, component j = first with
+ *     floor(u[i] * n_points) < (members of clusters 0..j) (float64), point =
+ *     c_j + sqrt(|v_j|) z[i] per axis (float32 ops)
+ *   cls_init_point_gaussians: the base method's initialisation of a point
+ *     cloud without colours: parameter rows (stride >= 16) with the point as
+ *     mean, opacity 0.1, identity rotation, SH zero (grey), isotropic
+ *     log-scale 0.5 log(d), d = ((d1 + d2) + d3) / 3 over the squared
+ *     distances to the three nearest other points (fewer if fewer; float32),
+ *     at least 1e-7 (written to mean_sq[n]). Brute force, O(n^2). */
+int cls_points_bbox(const float* params, int32_t n, int32_t row_stride, float* lohi,
+                    uint32_t* scratch, cls_stream_t stream);
+int cls_box_sample(const float* lohi, const float* u, int32_t n, float* points,
+                   cls_stream_t stream);
+int cls_gather_points(const float* src, int32_t stride, const int32_t* idx,
+                      const int32_t* n_dev, int32_t n_max, float* points, cls_stream_t stream);
+int cls_region_mixture(const float* points, int32_t n, const int32_t* labels,
+                       const ClsSphere* clusters, const int32_t* counts, int32_t k,
+                       unsigned long long* scratch, float* absv, cls_stream_t stream);
+int cls_mixture_sample(const ClsSphere* clusters, const float* absv, const int32_t* counts,
+                       int32_t k, const float* u, const float* z, int32_t m, float* points,
+                       cls_stream_t stream);
+int cls_init_point_gaussians(const float* points, int32_t n, int32_t row_stride,
+                             float* mean_sq, float* rows, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Masked Adam on the active set (Supp. "3DGS Optimization in Changed
  * Regions"): increments each scene's adam_step t, then for every active row
  * and every float of it: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;

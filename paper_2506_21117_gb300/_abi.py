@@ -102,6 +102,12 @@ SIGNATURES = {
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
     "cls_ssim_buffer_size": (SZ, [P]),
     "cls_ssim_loss": (C.c_int, [P, P, P, P, P, P, P, F32, P, P, P, P]),
+    "cls_points_bbox": (C.c_int, [P, I32, I32, P, P, P]),
+    "cls_box_sample": (C.c_int, [P, P, I32, P, P]),
+    "cls_gather_points": (C.c_int, [P, I32, P, P, I32, P, P]),
+    "cls_region_mixture": (C.c_int, [P, I32, P, P, P, I32, P, P, P]),
+    "cls_mixture_sample": (C.c_int, [P, P, P, I32, P, P, I32, P, P]),
+    "cls_init_point_gaussians": (C.c_int, [P, I32, I32, P, P, P]),
     "cls_spheres_workspace_size": (SZ, [I32]),
     "cls_fit_spheres": (C.c_int, [P, I32, P, I32, I32, I32, P, P, P, P, SZ, P]),
     "cls_prune_workspace_size": (SZ, [I32]),
@@ -304,3 +310,27 @@ def cls_ssim_loss(views_dev, info, tiles, n_tiles_dev, tile_active, image, targe
                   dL_dimage, loss_per_scene, stream) -> int:
     return load().cls_ssim_loss(views_dev, C.byref(info), tiles, n_tiles_dev, tile_active, image,
                                 target, lam, abc, dL_dimage, loss_per_scene, stream)
+
+
+def cls_points_bbox(params, n, row_stride, lohi, scratch, stream) -> int:
+    return load().cls_points_bbox(params, n, row_stride, lohi, scratch, stream)
+
+
+def cls_box_sample(lohi, u, n, points, stream) -> int:
+    return load().cls_box_sample(lohi, u, n, points, stream)
+
+
+def cls_gather_points(src, stride, idx, n_dev, n_max, points, stream) -> int:
+    return load().cls_gather_points(src, stride, idx, n_dev, n_max, points, stream)
+
+
+def cls_region_mixture(points, n, labels, clusters, counts, k, scratch, absv, stream) -> int:
+    return load().cls_region_mixture(points, n, labels, clusters, counts, k, scratch, absv, stream)
+
+
+def cls_mixture_sample(clusters, absv, counts, k, u, z, m, points, stream) -> int:
+    return load().cls_mixture_sample(clusters, absv, counts, k, u, z, m, points, stream)
+
+
+def cls_init_point_gaussians(points, n, row_stride, mean_sq, rows, stream) -> int:
+    return load().cls_init_point_gaussians(points, n, row_stride, mean_sq, rows, stream)

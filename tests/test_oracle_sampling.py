@@ -67,12 +67,11 @@ def _addition():
 
 def test_sampling_from_nothing_fills_the_changed_region():
     scene, cams, masks, box = _addition()
-    c, o = fx.votes(scene["means"], cams, masks)
-    act = fx.vote_rule(c, o, len(cams))
-    out = osa.sample_points(scene["means"][act], scene["means"], cams, masks, 400,
+    out = osa.sample_points(np.zeros((0, 3), np.float32), scene["means"], cams, masks, 400,
                             S.sampling_draws(0))
     pts = out["points"]
-    assert pts.shape[0] >= 400 and out["rounds"] <= osa.MAX_ROUNDS
+    assert pts.shape[0] >= 400 and 2 <= out["rounds"] <= osa.MAX_ROUNDS
+    assert out["new"].shape[0] == pts.shape[0]
     # every kept point passes the vote
     c2, o2 = fx.votes(pts, cams, masks)
     assert fx.vote_rule(c2, o2, len(cams)).all()
