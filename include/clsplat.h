@@ -518,6 +518,25 @@ int cls_init_point_gaussians(const float* points, int32_t n, int32_t row_stride,
                              float* mean_sq, float* rows, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * History recovery and merging of updates (Supp. "History Recovery" and its
+ * algorithm; "Batched Updates"): stable partitions of rows by a mask.
+ *   cls_flag_map mode 0: map[dst] = the source row of dst when the rows with
+ *     flags = 0 come first in order, then those with flags = 1 (the reorder of
+ *     G^{t-1} before update t); mode 1: map[i] = i - ones_before(i) if
+ *     flags[i] = 0, else ~ones_before(i) (recovery of G^{t-1}: unchanged rows
+ *     from G^t's first #static rows, changed rows from the stored O^t).
+ *     n_flagged_dev: device int32 count of set flags. workspace:
+ *     cls_flag_map_workspace_size(n) bytes.
+ *   cls_gather_rows: dst row i = a[map[i]] if map[i] >= 0 else b[~map[i]];
+ *     rows of `stride` floats (a multiple of 4). */
+size_t cls_flag_map_workspace_size(int32_t n);
+int cls_flag_map(const uint8_t* flags, int32_t n, int32_t mode, int32_t* map,
+                 int32_t* n_flagged_dev, void* workspace, size_t workspace_bytes,
+                 cls_stream_t stream);
+int cls_gather_rows(const float* a, const float* b, const int32_t* map, int32_t n_out,
+                    int32_t stride, float* dst, cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Masked Adam on the active set (Supp. "3DGS Optimization in Changed
  * Regions"): increments each scene's adam_step t, then for every active row
  * and every float of it: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;

@@ -102,6 +102,9 @@ SIGNATURES = {
     "cls_adam_step_active": (C.c_int, [P, P, P, F32, F32, F32, F32, P, SZ, P]),
     "cls_ssim_buffer_size": (SZ, [P]),
     "cls_ssim_loss": (C.c_int, [P, P, P, P, P, P, P, F32, P, P, P, P]),
+    "cls_flag_map_workspace_size": (SZ, [I32]),
+    "cls_flag_map": (C.c_int, [P, I32, I32, P, P, P, SZ, P]),
+    "cls_gather_rows": (C.c_int, [P, P, P, I32, I32, P, P]),
     "cls_points_bbox": (C.c_int, [P, I32, I32, P, P, P]),
     "cls_box_sample": (C.c_int, [P, P, I32, P, P]),
     "cls_gather_points": (C.c_int, [P, I32, P, P, I32, P, P]),
@@ -334,3 +337,16 @@ def cls_mixture_sample(clusters, absv, counts, k, u, z, m, points, stream) -> in
 
 def cls_init_point_gaussians(points, n, row_stride, mean_sq, rows, stream) -> int:
     return load().cls_init_point_gaussians(points, n, row_stride, mean_sq, rows, stream)
+
+
+def cls_flag_map_workspace_size(n) -> int:
+    return load().cls_flag_map_workspace_size(n)
+
+
+def cls_flag_map(flags, n, mode, map_, n_flagged_dev, workspace, workspace_bytes, stream) -> int:
+    return load().cls_flag_map(flags, n, mode, map_, n_flagged_dev, workspace, workspace_bytes,
+                               stream)
+
+
+def cls_gather_rows(a, b, map_, n_out, stride, dst, stream) -> int:
+    return load().cls_gather_rows(a, b, map_, n_out, stride, dst, stream)
