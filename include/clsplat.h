@@ -538,7 +538,8 @@ int cls_gather_rows(const float* a, const float* b, const int32_t* map, int32_t 
 
 /* ------------------------------------------------------------------------
  * Masked Adam on the active set (Supp. "3DGS Optimization in Changed
- * Regions"): increments each scene's adam_step t, then for every active row
+ * Regions"): increments the adam_step t of each scene with active Gaussians
+ * (a scene with none is left untouched), then for every active row
  * and every float of it: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps). Rows of
  * Gaussians outside O^t (params, adam_m, adam_v) are never touched.

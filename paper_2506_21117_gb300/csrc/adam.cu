@@ -10,6 +10,7 @@ __global__ void adam_advance_kernel(const ClsScene* __restrict__ scenes, int n_s
                                     float b2, float2* __restrict__ bias) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n_scenes) return;
+    if (scenes[s].n_active <= 0) return;  // nothing to update: the step count stays
     int32_t* step = scenes[s].adam_step;
     const int t = *step + 1;
     *step = t;

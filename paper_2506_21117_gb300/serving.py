@@ -13,10 +13,17 @@ updates of different scenes share the GPU:
   while others run join the next iteration);
 * one engine step runs one iteration of every in-flight request in the same
   launches (one scene table and one view table spanning all requests, views of
-  different resolutions side by side), captured once per batch composition in
-  a CUDA graph and replayed while the composition is unchanged;
+  different resolutions side by side); a composition's first step runs
+  eagerly, its second is captured in a CUDA graph, and later steps replay it;
+* admission work (optimiser reset, copies, lifting) and a new composition's
+  tables and capacity plan run on a side stream, so the host waits only for
+  that small work, never for the queued steps; the main stream waits for it
+  with an event;
 * a request completes after its iterations; its latency is arrival to
-  completion, read back with its loss.
+  completion, read back with its loss. A completed request's scene is
+  deactivated in the batch (its active count set to 0 in the device table,
+  which a captured graph reads too); the batch is rebuilt only when a request
+  is admitted.
 
 The plain baseline runs the same requests one at a time on the same kernels.
 `Scheduler` holds the host-side policy and runs without a GPU.
@@ -25,6 +32,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 from typing import Callable, Dict, List, Optional, Sequence
 
@@ -154,8 +162,12 @@ class Server:
         self.sched = Scheduler(max_slots, budget)
         self.batch = None
         self.graph = None
+        self.fresh = False
         self.composition = None
         self.device_targets: Dict[int, object] = {}
+        self.side = torch.cuda.Stream()
+        self.capture_stream = torch.cuda.Stream()
+        self.scene_free: Dict[int, object] = {}  # event after a scene's last queued step
         self.stats = {"steps": 0, "graph_captures": 0, "graph_replays": 0, "rebuilds": 0}
 
     # -- request life cycle ----------------------------------------------------
@@ -165,29 +177,49 @@ class Server:
         self.sched.submit(req)
 
     def _start(self, req: Request) -> None:
-        """Admission on the device: reset the scene's optimiser, copy the
+        """Admission on the device (side stream, after the scene's previous
+        request's queued steps): reset the scene's optimiser, copy the
         request's masks and targets from pinned host memory, lift."""
         from .update import lift
         torch = self.torch
         st = self.states[req.scene]
-        st.adam_m.zero_()
-        st.adam_v.zero_()
-        st.adam_step.zero_()
-        masks = req.masks.to(st.params.device, non_blocking=True)
-        self.device_targets[req.rid] = req.targets.to(st.params.device, non_blocking=True)
-        lift(st, req.cams, masks, self.vote_mode, st.params.device)
+        main = torch.cuda.current_stream()
+        with torch.cuda.stream(self.side):
+            if req.scene in self.scene_free:
+                self.side.wait_event(self.scene_free.pop(req.scene))
+            st.adam_m.zero_()
+            st.adam_v.zero_()
+            st.adam_step.zero_()
+            masks = req.masks.to(st.params.device, non_blocking=True)
+            tgt = req.targets.to(st.params.device, non_blocking=True)
+            lift(st, req.cams, masks, self.vote_mode, st.params.device)
+        tgt.record_stream(main)
+        for t in (st.active, st.active_idx, st.adam_m, st.adam_v, st.adam_step):
+            t.record_stream(main)
+        self.device_targets[req.rid] = tgt
         req.n_active = st.n_active
 
     def _rebuild(self) -> None:
+        """Tables, buffers and capacity plan of the new composition on the side
+        stream; the main stream waits for them."""
         from .update import Batch
         torch = self.torch
         reqs = self.sched.inflight
-        self.batch = Batch([self.states[r.scene] for r in reqs], [r.cams for r in reqs],
-                           self.states[reqs[0].scene].params.device)
-        self.batch.target = torch.cat([self.device_targets[r.rid] for r in reqs])
-        self.batch.plan_capacity()
+        main = torch.cuda.current_stream()
+        with torch.cuda.stream(self.side):
+            b = Batch([self.states[r.scene] for r in reqs], [r.cams for r in reqs],
+                      self.states[reqs[0].scene].params.device)
+            b.target = torch.cat([self.device_targets[r.rid] for r in reqs])
+            b.plan_capacity()
+            ready = torch.cuda.Event()
+            ready.record(self.side)
+        b.record_stream(main)
+        main.wait_event(ready)
+        self.batch = b
+        self.batch_requests = list(reqs)
         self.composition = tuple(r.rid for r in reqs)
         self.graph = None
+        self.fresh = True
         self.stats["rebuilds"] += 1
 
     def _iteration(self) -> None:
@@ -200,27 +232,41 @@ class Server:
 
     def _step(self) -> None:
         torch = self.torch
-        if not self.graphs:
-            self._iteration()
+        if not self.graphs or (self.graph is None and self.fresh):
+            self._iteration()  # a composition's first step runs eagerly
+            self.fresh = False
         elif self.graph is None:
-            self._iteration()  # eager first iteration of a composition (warm-up)
-            torch.cuda.synchronize()
+            # second step of a composition: capture it (nothing runs while
+            # capturing), then replay it for this step
             g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g):
+            main = torch.cuda.current_stream()
+            self.capture_stream.wait_stream(main)
+            with torch.cuda.stream(self.capture_stream):
+                g.capture_begin()
                 self._iteration()
+                g.capture_end()
+            main.wait_stream(self.capture_stream)
+            g.replay()
             self.graph = g
             self.stats["graph_captures"] += 1
-            # the captured iteration did not run; the eager one stands for this step
+            self.stats["graph_replays"] += 1
         else:
             self.graph.replay()
             self.stats["graph_replays"] += 1
         self.stats["steps"] += 1
 
     def _finish(self, done: Sequence[Request]) -> None:
+        """Read the finished requests' losses, take their scenes out of the
+        batch's later iterations, and mark the scenes free after that."""
+        torch = self.torch
         order = {r.rid: i for i, r in enumerate(self.batch_requests)}
         self.pending_losses.append((self.batch.loss.clone(), [(r, order[r.rid]) for r in done]))
+        self.batch.deactivate([order[r.rid] for r in done])
+        free = torch.cuda.Event()
+        free.record()
         for r in done:
             self.device_targets.pop(r.rid, None)
+            self.scene_free[r.scene] = free
 
     # -- driving loops -----------------------------------------------------------
     def serve(self, schedule: Sequence[Request], realtime: bool = True,
@@ -233,6 +279,17 @@ class Server:
         `run_ahead` steps ahead of the device. With a `deadline` (seconds
         after the start) no request is admitted after it; requests not
         finished are counted as `unfinished`."""
+        torch = self.torch
+        gc_was = gc.isenabled()
+        gc.disable()  # no collector pauses inside the loop; collected once after it
+        try:
+            return self._serve(schedule, realtime, run_ahead, deadline)
+        finally:
+            if gc_was:
+                gc.enable()
+            gc.collect()
+
+    def _serve(self, schedule, realtime, run_ahead, deadline) -> Dict[str, float]:
         torch = self.torch
         pending = collections.deque(sorted(schedule, key=lambda r: r.arrival))
         self.pending_losses = []
@@ -262,9 +319,9 @@ class Server:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - self.clock(), 0.002)))
                 continue
-            if self.composition != tuple(r.rid for r in self.sched.inflight):
-                self._rebuild()
-            self.batch_requests = list(self.sched.inflight)
+            in_batch = set(self.composition or ())
+            if any(r.rid not in in_batch for r in self.sched.inflight):
+                self._rebuild()  # admissions; completions only deactivate
             self._step()
             ev = torch.cuda.Event(enable_timing=True)
             ev.record()

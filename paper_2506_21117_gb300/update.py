@@ -72,6 +72,14 @@ def _bytes(ctypes_array) -> torch.Tensor:
     return torch.frombuffer(bytearray(raw), dtype=torch.uint8)
 
 
+def _upload(ctypes_array, device) -> torch.Tensor:
+    """A host table on the device without waiting for the stream: through
+    pinned memory, asynchronously on the current stream."""
+    if torch.device(device).type != "cuda":
+        return _bytes(ctypes_array).to(device)
+    return _bytes(ctypes_array).pin_memory().to(device, non_blocking=True)
+
+
 class SceneState:
     """One scene resident on the device: parameter rows, Adam moments and step."""
 
@@ -146,8 +154,8 @@ class Batch:
         self.info = abi.ClsBatchInfo()
         abi.check(abi.cls_batch_prepare(self.scene_tab, self.view_tab, self.info),
                   "cls_batch_prepare")
-        self.scenes_dev = _bytes(self.scene_tab).to(device)
-        self.views_dev = _bytes(self.view_tab).to(device)
+        self.scenes_dev = _upload(self.scene_tab, device)
+        self.views_dev = _upload(self.view_tab, device)
         info = self.info
         dev = device
         self.records = torch.zeros(info.total_records * 12, dtype=torch.float32, device=dev)
@@ -226,9 +234,24 @@ class Batch:
             self.scene_tab[s].n_active = st.n_active
         abi.check(abi.cls_batch_prepare(self.scene_tab, self.view_tab, self.info),
                   "cls_batch_prepare")
-        self.scenes_dev.copy_(_bytes(self.scene_tab))
-        self.views_dev.copy_(_bytes(self.view_tab))
+        self.scenes_dev.copy_(_bytes(self.scene_tab).pin_memory(), non_blocking=True)
+        self.views_dev.copy_(_bytes(self.view_tab).pin_memory(), non_blocking=True)
         self.reproject = True
+
+    def deactivate(self, scene_indices) -> None:
+        """Drop scenes from the work of later iterations without rebuilding:
+        their active count becomes 0 in the device table (no active tiles, no
+        gradient, no optimiser step), which captured graphs also read."""
+        for s in scene_indices:
+            self.scene_tab[s].n_active = 0
+        self.scenes_dev.copy_(_bytes(self.scene_tab).pin_memory(), non_blocking=True)
+
+    def record_stream(self, stream) -> None:
+        """Mark every device buffer as used on `stream` (for a batch built on
+        another stream), so the allocator does not reuse its memory early."""
+        for t in vars(self).values():
+            if isinstance(t, torch.Tensor) and t.is_cuda:
+                t.record_stream(stream)
 
     def reset_prefix(self):
         """Forget every tile's static prefix (the next iteration rebuilds it)."""
