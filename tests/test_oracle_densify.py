@@ -1,0 +1,66 @@
+"""Pins of the densification oracle (base 3DGS adaptive density control
+restricted to O^t; Supp. "History Recovery", "Implementation Details")."""
+import numpy as np
+
+from oracle import densify as od
+
+
+def _scene(n=6):
+    means = np.zeros((n, 3), np.float32)
+    ls = np.full((n, 3), np.log(0.005), np.float32)
+    quats = np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1))
+    logits = np.zeros(n, np.float32)
+    return means, ls, quats, logits
+
+
+def test_clone_split_prune_rules():
+    means, ls, quats, logits = _scene()
+    extent = 1.0  # clone if largest scale <= 0.01
+    ls[1] = np.log(0.05)          # big enough to split
+    ls[2] = np.log(0.05)          # large but low gradient: untouched
+    logits[3] = -10.0             # low opacity: pruned
+    ls[4] = np.log(0.005)         # clone candidate with low opacity: pruned, no clone
+    logits[4] = -10.0
+    active = np.array([0, 1, 2, 3, 4])
+    accum = np.array([1e-3, 1e-3, 1e-5, 1e-3, 1e-3, 0], np.float32)
+    denom = np.array([2, 2, 2, 2, 2, 0], np.float32)
+    z = np.zeros((5, 2, 3), np.float32)
+    out = od.densify(means, ls, quats, logits, active, accum, denom, np.zeros(6), extent, z,
+                     big=False)
+    assert sorted(out["removed"].tolist()) == [1, 3, 4]
+    assert out["src"].tolist() == [0, 1, 1]           # clone of 0, two children of 1
+    np.testing.assert_allclose(out["log_scales"][1:], np.log(0.05 / 1.6), rtol=1e-6)
+    assert np.all(out["means"] == 0)                   # z = 0: children at the centre
+
+
+def test_split_children_are_samples_of_the_gaussian():
+    means, ls, quats, logits = _scene(1)
+    means[0] = [1, 2, 3]
+    ls[0] = np.log([0.2, 0.1, 0.05])
+    quats[0] = [np.cos(np.pi / 4), 0, 0, np.sin(np.pi / 4)]  # 90 degrees about z
+    z = np.array([[[1, 0, 0], [0, 1, 0]]], np.float32)
+    out = od.densify(means, ls, quats, logits, np.array([0]), np.array([1.0], np.float32),
+                     np.array([1.0], np.float32), np.zeros(1), 1.0, z, big=False)
+    # R maps x to y and y to -x
+    np.testing.assert_allclose(out["means"][0], [1, 2.2, 3], atol=1e-6)
+    np.testing.assert_allclose(out["means"][1], [0.9, 2, 3], atol=1e-6)
+
+
+def test_big_rule_only_after_reset():
+    means, ls, quats, logits = _scene(2)
+    maxr = np.array([30.0, 5.0])
+    acc = np.zeros(2, np.float32)
+    den = np.zeros(2, np.float32)
+    z = np.zeros((2, 2, 3), np.float32)
+    a = od.densify(means, ls, quats, logits, np.array([0, 1]), acc, den, maxr, 1.0, z, big=False)
+    b = od.densify(means, ls, quats, logits, np.array([0, 1]), acc, den, maxr, 1.0, z, big=True)
+    assert a["removed"].size == 0 and b["removed"].tolist() == [0]
+
+
+def test_accumulate_ndc_norm():
+    acc = np.zeros(3, np.float32)
+    den = np.zeros(3, np.float32)
+    mr = np.zeros(3)
+    od.accumulate(acc, den, mr, [0, 1, 2], [1e-3, 2e-3, 5.0], [0.0, 1e-3, 5.0], [3, 4, 0], 200, 100)
+    np.testing.assert_allclose(acc, [0.1, np.hypot(0.2, 0.05), 0.0], rtol=1e-6)
+    assert den.tolist() == [1, 1, 0] and mr.tolist() == [3, 4, 0]
