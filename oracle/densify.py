@@ -13,7 +13,10 @@ removed, and (after the first opacity reset) those larger than 20 pixels on
 screen or 0.1 x the extent in the world. Here all of it applies to O^t only.
 
 Readings (each also in the design notes): the accumulation takes each view of
-an iteration as one observation; the decisions compare float32 quantities
+an iteration as one observation, with the gradient of that view's own loss
+(the iteration's loss is the mean over its n views, so n x its gradient);
+the opacity reset (every 3000 iterations) caps the logit of O^t at
+logit(0.01) and restarts the Adam moments of that entry; the decisions compare float32 quantities
 with thresholds computed once in float64 and rounded to float32: mean norm
 (float32 accum / denom) >= 0.0002, largest log-scale <= log(0.01 extent),
 opacity logit < logit(0.005), largest log-scale > log(0.1 extent); the split
@@ -36,6 +39,7 @@ N_SPLIT = 2
 SPLIT_SHRINK = 0.8 * N_SPLIT
 MAX_SCREEN = 20.0
 BIG_WORLD = 0.1
+RESET_OPACITY = 0.01
 
 
 def thresholds(extent: float) -> Dict[str, np.float32]:
@@ -95,13 +99,28 @@ def densify(means, log_scales, quats, logits, active_idx, accum, denom, max_radi
             "means": np.array(new_means).reshape(-1, 3), "log_scales": np.array(new_ls, F).reshape(-1, 3)}
 
 
-def accumulate(accum, denom, max_radius, gids, du, dv, radius, W, H):
+def accumulate(accum, denom, max_radius, gids, du, dv, radius, W, H, n_views=1):
     """One view's statistics: for each visible Gaussian (radius > 0), the
-    norm of its NDC-space positional gradient (pixel gradient x W/2, H/2)."""
+    norm of its NDC-space positional gradient (pixel gradient x W/2, H/2)
+    for the view's own loss (x n_views when du, dv are gradients of the mean
+    over n_views views)."""
     for g, a, b, r in zip(gids, du, dv, radius):
         if r <= 0:
             continue
-        gx, gy = F(F(a) * F(0.5 * W)), F(F(b) * F(0.5 * H))
+        gx, gy = F(F(a) * F(0.5 * W * n_views)), F(F(b) * F(0.5 * H * n_views))
         accum[g] = F(accum[g] + F(np.sqrt(F(gx * gx + gy * gy))))
         denom[g] += 1
         max_radius[g] = max(max_radius[g], float(r))
+
+
+def reset_limit() -> np.float32:
+    return F(np.log(RESET_OPACITY / (1.0 - RESET_OPACITY)))
+
+
+def reset_opacity(logits, active_idx):
+    """Opacity reset of O^t: sigmoid(logit) becomes min(sigmoid(logit), 0.01)
+    (in the logit domain, min(logit, logit(0.01)))."""
+    out = np.array(logits, F)
+    idx = np.asarray(active_idx, np.int64)
+    out[idx] = np.minimum(out[idx], reset_limit())
+    return out

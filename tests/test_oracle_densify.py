@@ -64,3 +64,21 @@ def test_accumulate_ndc_norm():
     od.accumulate(acc, den, mr, [0, 1, 2], [1e-3, 2e-3, 5.0], [0.0, 1e-3, 5.0], [3, 4, 0], 200, 100)
     np.testing.assert_allclose(acc, [0.1, np.hypot(0.2, 0.05), 0.0], rtol=1e-6)
     assert den.tolist() == [1, 1, 0] and mr.tolist() == [3, 4, 0]
+
+
+def test_accumulate_per_view_loss_scaling():
+    """With the batch loss the mean over 4 views, one view's own gradient is
+    4 x the batch gradient."""
+    acc = np.zeros(1, np.float32)
+    den = np.zeros(1, np.float32)
+    mr = np.zeros(1)
+    od.accumulate(acc, den, mr, [0], [1e-3], [0.0], [1], 200, 100, n_views=4)
+    np.testing.assert_allclose(acc, [0.4], rtol=1e-6)
+
+
+def test_opacity_reset_caps_sigmoid():
+    logits = np.array([-8.0, -4.0, 0.0, 3.0, 5.0], np.float32)
+    out = od.reset_opacity(logits, [1, 2, 3])
+    sig = lambda x: 1 / (1 + np.exp(-np.asarray(x, np.float64)))
+    np.testing.assert_allclose(sig(out[1:4]), np.minimum(sig(logits[1:4]), 0.01), rtol=1e-6)
+    assert out[0] == logits[0] and out[4] == logits[4]
