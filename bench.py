@@ -365,6 +365,7 @@ def run_ours(args, rank, world):
     e2e = run_e2e(args, lu, targets, masks, cams)
     active_np = lu.state.active.cpu().numpy().astype(bool)
     sphere = run_sphere_region(lu)
+    densify = run_densify(lu)
     sampling = run_sampling()
 
     line = {
@@ -384,6 +385,7 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "gpu_launches": int(bt.launches_per_step() * args.steps),
         "sphere_region": sphere,
+        "densification": densify,
         "new_point_sampling": sampling,
     }
     if ssim_roof is not None:
@@ -425,6 +427,41 @@ def run_sphere_region(lu):
     return {"active_gaussians": A, "spheres": region.k, "kmeans_iters": 16,
             "fit_ms": e[0].elapsed_time(e[1]), "prune_check_ms": e[2].elapsed_time(e[3]),
             "removed": removed, "note": "prune_check_ms includes reading the removed count back"}
+
+
+def run_densify(lu):
+    """Densification of the benchmark's O^t (base 3DGS adaptive density
+    control restricted to O^t): the per-iteration statistics pass, one
+    densification step (clone/split/prune, reading its counts back) and the
+    rebuild of the batch for the grown scene; CUDA events on the launching
+    stream, the rebuild by wall clock."""
+    import torch
+    from paper_2506_21117_gb300 import synthetic as S
+    from paper_2506_21117_gb300.densify import Densifier
+    st = lu.state
+    A0 = st.n_active
+    d = Densifier(st, lu.cams, S.densify_draws(0))
+    lu.batch.refresh_active()  # the pruning check above may have shrunk O^t
+    lu.render_pass(True, False)
+    d.accumulate(lu.batch)  # warm-up
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    d.accumulate(lu.batch)
+    e[1].record()
+    torch.cuda.synchronize()
+    e[2].record()
+    added, removed = d.densify(3000)
+    e[3].record()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lu._rebuild_batch()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    return {"active_gaussians": A0, "accumulate_ms": e[0].elapsed_time(e[1]),
+            "densify_ms": e[2].elapsed_time(e[3]), "rebuild_ms": (t1 - t0) * 1e3,
+            "added": added, "removed": removed, "active_after": st.n_active,
+            "note": "statistics of two iterations; densify_ms includes reading the counts back"}
 
 
 def run_sampling():

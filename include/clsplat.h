@@ -537,6 +537,71 @@ int cls_gather_rows(const float* a, const float* b, const int32_t* map, int32_t 
                     int32_t stride, float* dst, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Densification restricted to O^t (Supp. "History Recovery": duplication and
+ * pruning only affect O^t; Supp. "Implementation Details": the base 3DGS
+ * optimiser's adaptive density control with its defaults).
+ *
+ * cls_densify_accumulate: statistics of one scene's iteration. For every
+ * active Gaussian g (rank a in active_idx) and every view j of
+ * [first_view, first_view + n_views) with records[view.rec_base + g].radius
+ * > 0: gx = grad2d[view.g2_base + a][0] * (W/2 * n_views), gy = [1] * (H/2 *
+ * n_views) (the gradient of that view's own loss in NDC units; the batch loss
+ * is the mean over the views), accum[g] += sqrt(gx^2 + gy^2), denom[g] += 1,
+ * max_radius[g] = max(max_radius[g], radius); all float32, round to nearest,
+ * views in order. accum, denom, max_radius: [n] device floats, caller-zeroed
+ * at the start of a densification interval.
+ *
+ * cls_densify: one densification step of one scene. Per active Gaussian
+ * (float32 comparisons with the rule's thresholds): avg = accum / denom (0 if
+ * denom = 0); selected if avg >= grad_threshold; a selected Gaussian whose
+ * largest log-scale is <= clone_log_scale is cloned, otherwise split into two
+ * children mu + R(q) (exp(log-scale) * z) with log-scales reduced by
+ * log_shrink; a Gaussian is pruned if its opacity logit < min_logit or, with
+ * `big`, its max_radius > 20 or its largest log-scale > big_log_scale (a
+ * clone inherits the test; a child takes it on its own log-scales with
+ * max_radius 0). Split and pruned originals are removed: opacity logit -inf,
+ * active flag 0. New rows take ids n, n+1, ... in rank order (per Gaussian:
+ * its clone, then its children), copy the source row except the changed
+ * entries, get zero Adam moments and active flag 1.
+ *   params, adam_m, adam_v: [capacity][row_stride]; capacity >= n + 2 n_active
+ *   active: [capacity] uint8 flags; active_idx: O^t ascending (n_active)
+ *   z: [n_active][2][3] standard normals (input; row a for rank a)
+ *   new_src: [2 n_active] source id per new row
+ *   active_idx_out: the next O^t (kept originals in order, then the new ids),
+ *     capacity entries; must not alias active_idx
+ *   counts_dev: device int32[3] = new rows, kept originals, next n_active
+ *   removed: optional [n_active] uint8, 1 where the original was removed
+ *   (active_idx, z and new_src may be NULL when n_active = 0)
+ *   workspace: cls_densify_workspace_size(n_active) bytes
+ * The accumulated statistics are read only (the caller resets them).
+ *
+ * cls_opacity_reset: the base optimiser's periodic opacity reset on O^t:
+ * logit = min(logit, limit); Adam moments of that entry set to 0. */
+typedef struct ClsDensifyRule {
+    float grad_threshold;   /* mean NDC-gradient norm that selects a Gaussian */
+    float clone_log_scale;  /* log(percent_dense * extent) */
+    float min_logit;        /* logit(min opacity) */
+    float big_log_scale;    /* log(0.1 * extent) */
+    float log_shrink;       /* log(0.8 * 2) */
+    int32_t big;            /* apply the size rules (after the first opacity reset) */
+} ClsDensifyRule;
+
+int cls_densify_accumulate(const ClsView* views_dev, int32_t first_view, int32_t n_views,
+                           const ClsProjected* records, const float* grad2d,
+                           const int32_t* active_idx, int32_t n_active, float* accum,
+                           float* denom, float* max_radius, cls_stream_t stream);
+size_t cls_densify_workspace_size(int32_t n_active);
+int cls_densify(float* params, float* adam_m, float* adam_v, int32_t row_stride, int32_t n,
+                int64_t capacity, uint8_t* active, const int32_t* active_idx, int32_t n_active,
+                const float* accum, const float* denom, const float* max_radius,
+                const ClsDensifyRule* rule, const float* z, int32_t* new_src,
+                int32_t* active_idx_out, int32_t* counts_dev, uint8_t* removed, void* workspace,
+                size_t workspace_bytes, cls_stream_t stream);
+int cls_opacity_reset(float* params, float* adam_m, float* adam_v, int32_t row_stride,
+                      const int32_t* active_idx, int32_t n_active, float limit,
+                      cls_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Masked Adam on the active set (Supp. "3DGS Optimization in Changed
  * Regions"): increments the adam_step t of each scene with active Gaussians
  * (a scene with none is left untouched), then for every active row

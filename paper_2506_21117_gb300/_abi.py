@@ -69,6 +69,13 @@ MAX_SPHERES = 10
 class ClsSphere(C.Structure):
     _fields_ = [("cx", C.c_float), ("cy", C.c_float), ("cz", C.c_float), ("radius", C.c_float)]
 
+
+class ClsDensifyRule(C.Structure):
+    _fields_ = [("grad_threshold", C.c_float), ("clone_log_scale", C.c_float),
+                ("min_logit", C.c_float), ("big_log_scale", C.c_float),
+                ("log_shrink", C.c_float), ("big", C.c_int32)]
+
+
 TILE_CACHE_BYTES = 16
 
 assert C.sizeof(ClsCamera) == 88 and C.sizeof(ClsScene) == 72
@@ -115,6 +122,11 @@ SIGNATURES = {
     "cls_fit_spheres": (C.c_int, [P, I32, P, I32, I32, I32, P, P, P, P, SZ, P]),
     "cls_prune_workspace_size": (SZ, [I32]),
     "cls_prune_outside_spheres": (C.c_int, [P, I32, P, P, I32, P, P, I32, P, P, P, SZ, P]),
+    "cls_densify_accumulate": (C.c_int, [P, I32, I32, P, P, P, I32, P, P, P, P]),
+    "cls_densify_workspace_size": (SZ, [I32]),
+    "cls_densify": (C.c_int, [P, P, P, I32, I32, I64, P, P, I32, P, P, P, P, P, P, P, P, P, P,
+                              SZ, P]),
+    "cls_opacity_reset": (C.c_int, [P, P, P, I32, P, I32, F32, P]),
 }
 
 _lib = None
@@ -350,3 +362,28 @@ def cls_flag_map(flags, n, mode, map_, n_flagged_dev, workspace, workspace_bytes
 
 def cls_gather_rows(a, b, map_, n_out, stride, dst, stream) -> int:
     return load().cls_gather_rows(a, b, map_, n_out, stride, dst, stream)
+
+
+def cls_densify_accumulate(views_dev, first_view, n_views, records, grad2d, active_idx,
+                           n_active, accum, denom, max_radius, stream) -> int:
+    return load().cls_densify_accumulate(views_dev, first_view, n_views, records, grad2d,
+                                         active_idx, n_active, accum, denom, max_radius, stream)
+
+
+def cls_densify_workspace_size(n_active) -> int:
+    return load().cls_densify_workspace_size(n_active)
+
+
+def cls_densify(params, adam_m, adam_v, row_stride, n, capacity, active, active_idx, n_active,
+                accum, denom, max_radius, rule, z, new_src, active_idx_out, counts_dev, removed,
+                workspace, workspace_bytes, stream) -> int:
+    return load().cls_densify(params, adam_m, adam_v, row_stride, n, capacity, active,
+                              active_idx, n_active, accum, denom, max_radius, _ref(rule), z,
+                              new_src, active_idx_out, counts_dev, removed, workspace,
+                              workspace_bytes, stream)
+
+
+def cls_opacity_reset(params, adam_m, adam_v, row_stride, active_idx, n_active, limit,
+                      stream) -> int:
+    return load().cls_opacity_reset(params, adam_m, adam_v, row_stride, active_idx, n_active,
+                                    limit, stream)

@@ -314,6 +314,16 @@ def sampling_draws(seed: int = 0):
     return draws
 
 
+def densify_draws(seed: int = 0):
+    """The standard normals the split of densification consumes, as a
+    function (step, n_active) -> float32 [n_active][2][3]; each densification
+    step has its own stream."""
+    def draws(step: int, n_active: int):
+        rng = np.random.default_rng([seed, step, 4])
+        return rng.standard_normal((n_active, 2, 3)).astype(np.float32)
+    return draws
+
+
 def serving_scenes(n_scenes: int = 64, n_lo: int = 50_000, n_hi: int = 500_000,
                    sh_degree: int = 3, seed: int = 0):
     """Resident scenes of the serving workload: Gaussian counts log-uniform in

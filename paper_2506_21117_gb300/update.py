@@ -539,10 +539,11 @@ class LocalUpdate:
                  vote_mode: int = 0, loss: str = "l1", lr: float = 1e-3,
                  bg=(0.0, 0.0, 0.0), device="cuda", capacity_slack: float = 1.5,
                  layout: int = 1, lazy: bool = True, prune_every: int = 0,
-                 sphere_k: Optional[int] = None):
+                 sphere_k: Optional[int] = None, densify: Optional[dict] = None):
         """prune_every > 0 fits the sphere region of the lifted O^t and removes
         the Gaussians that leave it every `prune_every` iterations (the paper
-        uses 15)."""
+        uses 15). `densify` (a dict of Densifier options with at least
+        `draws`) turns on adaptive density control of O^t."""
         self.cams = list(cams)
         self.loss_mode = LOSS_MODES[loss]
         self.lr = lr
@@ -558,15 +559,30 @@ class LocalUpdate:
                            ssim=loss == "l1+ssim")
         if targets is not None:
             self.batch.set_targets(targets)
+        self.capacity_slack = capacity_slack
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
-        self._init_region(prune_every, sphere_k)
+        self._init_region(prune_every, sphere_k, densify)
         torch.cuda.synchronize()
 
-    def _init_region(self, prune_every: int, sphere_k: Optional[int]):
+    def _init_region(self, prune_every: int, sphere_k: Optional[int],
+                     densify: Optional[dict] = None):
         self.prune_every = int(prune_every)
         self.iteration = 0
         self.removed = 0
         self.region = SphereRegion(self.state, sphere_k) if self.prune_every > 0 else None
+        self.densifier = None
+        if densify:
+            from .densify import Densifier
+            self.densifier = Densifier(self.state, self.cams, **densify)
+
+    def _rebuild_batch(self):
+        """New batch tables and buffers after the scene grew."""
+        old = self.batch
+        b = Batch([self.state], [self.cams], old.device, old.layout, old.lazy,
+                  prefix_cache=old.prefix_mode == 1, ssim=old.ssim)
+        b.target = old.target
+        self.batch = b
+        self.pairs_planned = b.plan_capacity(self.capacity_slack)
 
     @classmethod
     def from_resident(cls, state: SceneState, cams, targets, masks, vote_mode: int = 0,
@@ -586,6 +602,7 @@ class LocalUpdate:
         lift(state, self.cams, masks, vote_mode, dev)
         self.batch = Batch([state], [self.cams], dev, layout, lazy, ssim=loss == "l1+ssim")
         self.batch.target = targets.to(dev, non_blocking=True)
+        self.capacity_slack = capacity_slack
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
         self._init_region(0, None)
         return self
@@ -601,8 +618,28 @@ class LocalUpdate:
                 b.adam(self.lr)
 
     def step(self):
-        self.render_pass(True, True)
-        self.iteration += 1
+        d = self.densifier
+        if d is None:
+            self.render_pass(True, True)
+            self.iteration += 1
+        else:
+            # the base optimiser's order: statistics, densification (no
+            # optimiser step on that iteration), then the opacity reset
+            it = self.iteration + 1
+            self.render_pass(True, False)
+            grew = False
+            if it < d.until:
+                d.accumulate(self.batch)
+                if d.due(it):
+                    d.densify(it)
+                    grew = True
+            if not grew:
+                self.batch.adam(self.lr)
+            if d.reset_due(it):
+                d.reset_opacity()
+            if grew:
+                self._rebuild_batch()
+            self.iteration = it
         if self.region is not None and self.iteration % self.prune_every == 0:
             k = prune_outside(self.state, self.region)
             if k:
