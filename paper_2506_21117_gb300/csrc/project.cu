@@ -712,22 +712,29 @@ bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __res
     }
 }
 
-// Can depth bin `bin` be emitted into any tile of rectangle x0..x1, y0..y1?
-// False only if on every row the bin lies below the smallest first emitted
-// bin or above the largest cut (conservative: emission still tests each cell).
-__device__ __forceinline__ bool bin_window_possible(const uint8_t* t_front, const uint8_t* t_cut,
-                                                    int64_t total_tiles, const ClsView& view,
-                                                    int x0, int x1, int y0, int y1, int bin) {
+// First and last rows of rectangle x0..x1, y0..y1 on which depth bin `bin`
+// can be emitted (per row: the smallest first emitted bin and the largest cut
+// over the row's tiles); false if there is none. Conservative: emission still
+// tests each cell of the rows in between.
+__device__ __forceinline__ bool bin_window_rows(const uint8_t* t_front, const uint8_t* t_cut,
+                                                int64_t total_tiles, const ClsView& view, int x0,
+                                                int x1, int y0, int y1, int bin, int& first,
+                                                int& last) {
     const int w = x1 - x0 + 1;
     const int l = 31 - __clz(w);
-    const int64_t lv = (int64_t)l * total_tiles + view.tile_base;
-    for (int y = y0; y <= y1; ++y) {
-        const int64_t a = lv + (int64_t)y * view.tiles_x + x0, b = a + w - (1 << l);
-        const int f = min(t_front[a], t_front[b]);
-        const int c = max(t_cut[a], t_cut[b]);
-        if (f <= bin && bin <= c) return true;
-    }
-    return false;
+    const int64_t lv = (int64_t)l * total_tiles + view.tile_base + x0;
+    auto row_ok = [&](int y) {
+        const int64_t a = lv + (int64_t)y * view.tiles_x, b = a + w - (1 << l);
+        return min(t_front[a], t_front[b]) <= bin && bin <= max(t_cut[a], t_cut[b]);
+    };
+    int y = y0;
+    while (y <= y1 && !row_ok(y)) ++y;
+    if (y > y1) return false;
+    first = y;
+    y = y1;
+    while (y > first && !row_ok(y)) --y;
+    last = y;
+    return true;
 }
 
 // Bucketed emission, load-balanced: a warp takes 32 pair-producing Gaussians of
@@ -740,9 +747,10 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                      uint64_t* __restrict__ keys, int64_t capacity,
                      const uint32_t* __restrict__ work_list,
-                     const int32_t* __restrict__ work_count, const uint8_t* __restrict__ cut,
-                     const uint8_t* __restrict__ front, const uint8_t* __restrict__ t_front,
-                     const uint8_t* __restrict__ t_cut, int64_t total_tiles) {
+                     const int32_t* __restrict__ work_count, int32_t* __restrict__ next_group,
+                     const uint8_t* __restrict__ cut, const uint8_t* __restrict__ front,
+                     const uint8_t* __restrict__ t_front, const uint8_t* __restrict__ t_cut,
+                     int64_t total_tiles) {
     // rank of each tile of the view, then its last and first emitted depth bin
     extern __shared__ int32_t s_rank[];
     const ClsView& view = views[blockIdx.y];
@@ -760,8 +768,13 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
     const int lane = threadIdx.x & 31;
     const int n = work_count[blockIdx.y];
     const uint32_t lo = zmin[blockIdx.y], hi = zmax[blockIdx.y];
-    const int warps_total = gridDim.x * (kBinBlock / 32);
-    for (int w = blockIdx.x * (kBinBlock / 32) + (threadIdx.x >> 5); w * 32 < n; w += warps_total) {
+    // a few blocks per SM; each warp takes groups of 32 work items from the
+    // view's counter (the tables above are filled once per block)
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(next_group + blockIdx.y, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w * 32 >= n) break;
         const int item = w * 32 + lane;
         int x0 = 0, x1 = -1, y0 = 0, y1 = -1, area = 0, bin = 0;
         uint32_t zb = 0, rec = 0;
@@ -770,8 +783,13 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
             rec = (uint32_t)(view.rec_base + g);
             if (record_rect(view, records, rec, x0, x1, y0, y1, zb)) {
                 bin = depth_bin(zb, lo, hi);
-                if (bin_window_possible(t_front, t_cut, total_tiles, view, x0, x1, y0, y1, bin))
+                int r0, r1;
+                if (bin_window_rows(t_front, t_cut, total_tiles, view, x0, x1, y0, y1, bin, r0,
+                                    r1)) {
+                    y0 = r0;
+                    y1 = r1;
                     area = (x1 - x0 + 1) * (y1 - y0 + 1);
+                }
             }
         }
         int incl = area;
@@ -809,9 +827,14 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                 const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, own);
                 sub[u] = -1;
                 if (c < total) {
+                    // row q and column k - q w of cell k: a float estimate of
+                    // k / w (off by at most one), then corrected exactly
                     const int k = c - (o_incl - o_area);
-                    const int q = k / o_w;
-                    const int cell = (o_y0 + q) * Tx + o_x0 + (k - q * o_w);
+                    int q = (int)(((float)k + 0.5f) * __frcp_rn((float)o_w));
+                    int rem = k - q * o_w;
+                    if (rem < 0) { --q; rem += o_w; }
+                    else if (rem >= o_w) { ++q; rem -= o_w; }
+                    const int cell = (o_y0 + q) * Tx + o_x0 + rem;
                     const int r = s_rank[cell];
                     if (r >= 0 && o_bin <= (int)s_cut[cell] && o_bin >= (int)s_front[cell]) {
                         sub[u] = (int64_t)r * kDepthBins + o_bin;
@@ -959,7 +982,7 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.big_count = o; o = align256(o + 4);
     L.bins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
     L.work_list = o; o = align256(o + (size_t)info->total_records * 4);
-    L.work_count = o; o = align256(o + (size_t)V * 4);
+    L.work_count = o; o = align256(o + (size_t)V * 8);  // + per-view emission counters
     L.front = o; o = align256(o + (size_t)info->total_tiles);
     L.t_front = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
     L.t_cut = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
@@ -971,6 +994,7 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
 
 static int g_max_view_tiles_checked = 0;
 static int g_grid_cap_set = 0;
+static int g_sms = 0;  // SM count of the current device
 
 extern "C" size_t cls_project_workspace_size(const ClsBatchInfo* info) {
     return info ? proj_layout(info).total : 0;
@@ -1074,7 +1098,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     if (layout == 1) {
         cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
         cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
-        cudaMemsetAsync(work_count, 0, (size_t)V * 4, s);
+        cudaMemsetAsync(work_count, 0, (size_t)V * 8, s);
     }
     count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
                                                       (int)cpv, partials,
@@ -1111,11 +1135,21 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             sub_partials, capacity, bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
         bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
             views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
-        const unsigned emit_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
-                                                      2048);
+        if (g_sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+            if (g_sms < 1) g_sms = 1;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel, kBinBlock,
+                                                      (size_t)max_view_tiles * 6);
+        const int64_t resident = (int64_t)g_sms * (per_sm > 0 ? per_sm : 1);
+        const unsigned emit_blocks = (unsigned)hmin64(
+            hmin64((info->max_n + kBinBlock - 1) / kBinBlock, 2048), (resident + V - 1) / V);
         emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 6, s>>>(
             views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, bin_cut, front, t_front, t_cut, info->total_tiles);
+            work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;
