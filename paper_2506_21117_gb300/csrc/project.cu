@@ -269,6 +269,21 @@ tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
 // active Gaussian, its lanes over the rectangle's cells; each block reduces
 // into a private copy of its view's tile grid in shared memory and merges it
 // into the global grid once.
+// q = k / w and rem = k - q w for 0 <= k < 2^22 and w >= 1: a float estimate
+// of k / w, off by at most one, then corrected exactly (cheaper than an
+// integer division).
+__device__ __forceinline__ void divmod_small(int k, int w, int& q, int& rem) {
+    q = (int)__fdividef((float)k + 0.5f, (float)w);
+    rem = k - q * w;
+    if (rem < 0) {
+        --q;
+        rem += w;
+    } else if (rem >= w) {
+        ++q;
+        rem -= w;
+    }
+}
+
 constexpr int kZminThreads = 1024;
 
 __global__ void __launch_bounds__(kZminThreads)
@@ -311,8 +326,9 @@ active_zmin_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
         const int w = x1 - x0 + 1;
         const int area = w * (y1 - y0 + 1);
         for (int k = lane; k < area; k += 32) {
-            const int q = k / w;
-            const int cell = (y0 + q) * view.tiles_x + x0 + (k - q * w);
+            int q, rem;
+            divmod_small(k, w, q, rem);
+            const int cell = (y0 + q) * view.tiles_x + x0 + rem;
             if (zb < s_z[cell]) atomicMin(&s_z[cell], zb);
         }
     }
@@ -827,13 +843,9 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                 const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, own);
                 sub[u] = -1;
                 if (c < total) {
-                    // row q and column k - q w of cell k: a float estimate of
-                    // k / w (off by at most one), then corrected exactly
                     const int k = c - (o_incl - o_area);
-                    int q = (int)(((float)k + 0.5f) * __frcp_rn((float)o_w));
-                    int rem = k - q * o_w;
-                    if (rem < 0) { --q; rem += o_w; }
-                    else if (rem >= o_w) { ++q; rem -= o_w; }
+                    int q, rem;
+                    divmod_small(k, o_w, q, rem);
                     const int cell = (o_y0 + q) * Tx + o_x0 + rem;
                     const int r = s_rank[cell];
                     if (r >= 0 && o_bin <= (int)s_cut[cell] && o_bin >= (int)s_front[cell]) {

@@ -617,6 +617,22 @@ class LocalUpdate:
             if with_adam:
                 b.adam(self.lr)
 
+    def capture(self):
+        """One iteration (project/bin, sort, forward + loss, backward, masked
+        Adam) recorded as a CUDA graph, to replay with `.replay()`: valid while
+        the batch, its targets and the active set stay as they are (no
+        pruning or densification in between)."""
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            g.capture_begin()
+            self.render_pass(True, True)
+            g.capture_end()
+        torch.cuda.current_stream().wait_stream(side)
+        return g
+
     def step(self):
         d = self.densifier
         if d is None:
