@@ -495,16 +495,26 @@ stamp_bins_kernel(const ClsView* __restrict__ views, const ClsProjected* __restr
     }
 }
 
+// Per (depth bin, view): the 2D prefix sum of the bin's difference grid gives
+// each tile's count of pairs in that bin; the counts of the rendered tiles go
+// to counts[rank * kDepthBins + bin] (the layout the bucket scan reads).
 __global__ void __launch_bounds__(256)
 bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins,
-                   int64_t total_sat, int smem_cap) {
+                   int64_t total_sat, int smem_cap, const int32_t* __restrict__ tile_rank,
+                   int32_t* __restrict__ counts) {
     extern __shared__ int32_t s_grid[];
     const ClsView& view = views[blockIdx.y];
     const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
-    int32_t* G = bins + blockIdx.x * total_sat + view.sat_base;
+    const int b = blockIdx.x;
+    int32_t* G = bins + b * total_sat + view.sat_base;
+    const int32_t* rank = tile_rank + view.tile_base;
     const int p = smem_pitch(Tx);
     if ((int64_t)Ty * p * 4 > smem_cap) {
         prefix2d(G, Ty, Tx, Wd);
+        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
+            const int r = rank[t];
+            if (r >= 0) counts[(int64_t)r * kDepthBins + b] = G[(int64_t)(t / Tx) * Wd + t % Tx];
+        }
         return;
     }
     for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
@@ -514,34 +524,25 @@ bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins
     __syncthreads();
     prefix2d_smem(s_grid, Ty, Tx, p);
     for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-        const int y = t / Tx, x = t - y * Tx;
-        G[(int64_t)y * Wd + x] = s_grid[y * p + x];
+        const int r = rank[t];
+        if (r >= 0) {
+            const int y = t / Tx, x = t - y * Tx;
+            counts[(int64_t)r * kDepthBins + b] = s_grid[y * p + x];
+        }
     }
 }
 
-// Pairs per (active tile rank, depth bin), entry e = rank * kDepthBins + bin.
-__device__ __forceinline__ int64_t sub_count(const ClsView* views, int n_views,
-                                             const int32_t* active_tiles, const int32_t* bins,
-                                             int64_t total_sat, int64_t e) {
-    const int t = (int)(e / kDepthBins), b = (int)(e - (int64_t)t * kDepthBins);
-    const int tile = active_tiles[t];
-    const ClsView& view = views[view_of_tile(views, n_views, tile)];
-    const int local = tile - view.tile_base;
-    const int ty = local / view.tiles_x, tx = local - ty * view.tiles_x;
-    return bins[b * total_sat + view.sat_base + (int64_t)ty * (view.tiles_x + 1) + tx];
-}
-
+// Pairs per (active tile rank, depth bin), entry e = rank * kDepthBins + bin,
+// are in `counts` (written by bins_prefix_kernel).
 __global__ void __launch_bounds__(kBinBlock)
-sub_count_kernel(const ClsView* __restrict__ views, int n_views,
-                 const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
-                 const int32_t* __restrict__ bins, int64_t total_sat,
+sub_count_kernel(const int32_t* __restrict__ n_active, const int32_t* __restrict__ counts,
                  int64_t* __restrict__ partials) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     const int64_t ne = (int64_t)(*n_active) * kDepthBins;
     int64_t cnt = 0;
     for (int it = 0; it < kBinItems; ++it) {
         const int64_t e = (int64_t)blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
-        if (e < ne) cnt += sub_count(views, n_views, active_tiles, bins, total_sat, e);
+        if (e < ne) cnt += counts[e];
     }
     int64_t tot;
     block_exclusive_sum<kBinBlock>(cnt, smem, tot);
@@ -555,7 +556,6 @@ sub_count_kernel(const ClsView* __restrict__ views, int n_views,
 __global__ void __launch_bounds__(kBinBlock)
 sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
                    const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
-                   const int32_t* __restrict__ bins, int64_t total_sat,
                    const int64_t* __restrict__ partials, int64_t capacity,
                    uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
                    uint32_t* __restrict__ ranges, const ClsTileCache* __restrict__ tile_cache,
@@ -566,7 +566,7 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
     int64_t base = partials[blockIdx.x];
     for (int it = 0; it < kBinItems; ++it) {
         const int64_t e = (int64_t)blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
-        const int64_t c = e < ne ? sub_count(views, n_views, active_tiles, bins, total_sat, e) : 0;
+        const int64_t c = e < ne ? cursor[e] : 0;  // the count, replaced by the offset
         int64_t tot;
         const int64_t off = base + block_exclusive_sum<kBinBlock>(c, smem, tot);
         base += tot;
@@ -1135,16 +1135,17 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                       2048);
         stamp_bins_kernel<<<dim3(work_blocks, V), kBinBlock, 0, s>>>(
             views_dev, records, zmin, zmax, work_list, work_count, bins, info->total_sat);
-        bins_prefix_kernel<<<dim3(kDepthBins, V), 256, grid_cap, s>>>(views_dev, bins,
-                                                                      info->total_sat, grid_cap);
-        sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
-            views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
-            sub_partials);
+        // per (rank, bin) counts go to `cursor`, which sub_offsets then
+        // turns into the buckets' slot cursors
+        bins_prefix_kernel<<<dim3(kDepthBins, V), 256, grid_cap, s>>>(
+            views_dev, bins, info->total_sat, grid_cap, tile_rank, cursor);
+        sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(n_active_tiles_dev, cursor,
+                                                                   sub_partials);
         scan_partials_kernel<<<1, 1024, 0, s>>>(sub_partials, sub_chunks, n_pairs_dev, nullptr,
                                                 capacity, status_dev);
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
-            views_dev, (int)V, active_tiles, n_active_tiles_dev, bins, info->total_sat,
-            sub_partials, capacity, bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
+            views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
+            bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
         bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
             views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
         if (g_sms == 0) {
