@@ -16,10 +16,21 @@ constexpr uint32_t kPrefixMargin = 1u << 17; // float ulps between a prefix boun
 // ---------------------------------------------------------------------------
 // Projection. mode 0: every Gaussian of the view's scene (slot -1); mode 1:
 // the scene's active Gaussians (slot = view.g2_base + rank).
+// ---------------------------------------------------------------------------
+// Dynamic render mask: every active Gaussian adds +1 over its tile rectangle
+// in a per-view difference grid (four corner updates), whose 2D prefix sum is
+// the number of active rectangles covering each tile.
+__device__ __forceinline__ void stamp_rect(int32_t* grid, int Wd, int x0, int x1, int y0, int y1) {
+    atomicAdd(grid + (int64_t)y0 * Wd + x0, 1);
+    atomicAdd(grid + (int64_t)y0 * Wd + x1 + 1, -1);
+    atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x0, -1);
+    atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x1 + 1, 1);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kProjBlock)
 project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-               ClsProjected* __restrict__ records) {
+               ClsProjected* __restrict__ records, int32_t* __restrict__ diff) {
     const ClsView& view = views[blockIdx.y];
     const ClsScene& sc = scenes[view.scene];
     const int i = blockIdx.x * kProjBlock + threadIdx.x;
@@ -66,6 +77,8 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
         r2 = make_float4(fmaxf(col[2], 0.f), __int_as_float(slot), P.z, 0.f);
         radius = (int)P.radius;
         if (radius < 1) radius = 1;  // cannot happen for a finite positive lambda
+        // an active Gaussian stamps its tile rectangle into the render mask
+        if (MODE == 1) stamp_rect(diff + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
     } else {
         r2 = make_float4(0.f, __int_as_float(slot), 0.f, 0.f);
     }
@@ -74,17 +87,6 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
     out[0] = r0;
     out[1] = r1;
     out[2] = r2;
-}
-
-// ---------------------------------------------------------------------------
-// Dynamic render mask: every active Gaussian adds +1 over its tile rectangle
-// in a per-view difference grid (four corner updates), whose 2D prefix sum is
-// the number of active rectangles covering each tile.
-__device__ __forceinline__ void stamp_rect(int32_t* grid, int Wd, int x0, int x1, int y0, int y1) {
-    atomicAdd(grid + (int64_t)y0 * Wd + x0, 1);
-    atomicAdd(grid + (int64_t)y0 * Wd + x1 + 1, -1);
-    atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x0, -1);
-    atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x1 + 1, 1);
 }
 
 __device__ __forceinline__ bool record_rect(const ClsView& view, const ClsProjected* records,
@@ -96,19 +98,6 @@ __device__ __forceinline__ bool record_rect(const ClsView& view, const ClsProjec
     zbits = __float_as_uint(c2.z);
     if (radius <= 0) return false;
     return tile_rect(c0.x, c0.y, (float)radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1);
-}
-
-__global__ void __launch_bounds__(256)
-stamp_active_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-                    const ClsProjected* __restrict__ records, int32_t* __restrict__ diff) {
-    const ClsView& view = views[blockIdx.y];
-    const ClsScene& sc = scenes[view.scene];
-    const int i = blockIdx.x * 256 + threadIdx.x;
-    if (i >= sc.n_active) return;
-    int x0, x1, y0, y1;
-    uint32_t zb;
-    if (!record_rect(view, records, view.rec_base + sc.active_idx[i], x0, x1, y0, y1, zb)) return;
-    stamp_rect(diff + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
 }
 
 // In-place 2D inclusive prefix sum of a (rows x cols) grid with row pitch Wd.
@@ -1079,17 +1068,14 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         g_grid_cap_set = grid_cap;
     }
 
-    if (project_mode == 0 && info->max_n > 0)
-        project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
-                             s>>>(scenes_dev, views_dev, records);
-    if (info->max_active > 0)
-        project_kernel<1><<<dim3((info->max_active + kProjBlock - 1) / kProjBlock, V), kProjBlock,
-                             0, s>>>(scenes_dev, views_dev, records);
     cudaMemsetAsync(diff, 0, (size_t)info->total_sat * 4, s);
     cudaMemsetAsync(big_count, 0, 4, s);
-    if (info->max_active > 0)
-        stamp_active_kernel<<<dim3((info->max_active + 255) / 256, V), 256, 0, s>>>(
-            scenes_dev, views_dev, records, diff);
+    if (project_mode == 0 && info->max_n > 0)
+        project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
+                             s>>>(scenes_dev, views_dev, records, diff);
+    if (info->max_active > 0)  // active records, and their rectangles stamped into `diff`
+        project_kernel<1><<<dim3((info->max_active + kProjBlock - 1) / kProjBlock, V), kProjBlock,
+                             0, s>>>(scenes_dev, views_dev, records, diff);
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
                                               grid_cap, tile_ring);
     if (info->max_active > 0)

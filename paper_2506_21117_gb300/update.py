@@ -412,9 +412,9 @@ class Batch:
             _ptr(b.adam_ws), b.adam_ws.numel(), b.stream()), "cls_adam_step_active")
 
     def launches_per_step(self) -> int:
-        """Kernels of one iteration. project_and_bin (mode 1): project,
-        stamp and nearest-active depth (3 if any Gaussian is active), tile
-        mask, compaction, count,
+        """Kernels of one iteration. project_and_bin (mode 1): project (with
+        the render-mask stamps) and nearest-active depth (2 if any Gaussian
+        is active), tile mask, compaction, count,
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
         prefix, bucket counts, scan, offsets, emission window tables, emit (7). Sort: flat
         hist + scan + passes (+ copy if odd) + ranges; bucketed 1 or 2.
@@ -422,7 +422,7 @@ class Batch:
         collection and sort, rerun);
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
-        proj = (3 if active else 0) + 3 + (7 if self.layout == 1 else 3)
+        proj = (2 if active else 0) + 3 + (7 if self.layout == 1 else 3)
         if self.layout == 1:
             sort = 2 if self.lazy else 1
         else:
