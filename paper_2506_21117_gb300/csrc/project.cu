@@ -1068,6 +1068,12 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         g_grid_cap_set = grid_cap;
     }
 
+    if (g_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms < 1) g_sms = 1;
+    }
     cudaMemsetAsync(diff, 0, (size_t)info->total_sat * 4, s);
     cudaMemsetAsync(big_count, 0, 4, s);
     if (project_mode == 0 && info->max_n > 0)
@@ -1079,8 +1085,10 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
                                               grid_cap, tile_ring);
     if (info->max_active > 0)
-        active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads - 1) /
-                                                       kZminThreads, 38), V),
+        // one warp per active Gaussian; two 1024-thread blocks per SM
+        active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads / 32 - 1) /
+                                                       (kZminThreads / 32),
+                                                   (2 * g_sms + V - 1) / V), V),
                              kZminThreads, (size_t)max_view_tiles * 4, s>>>(
             scenes_dev, views_dev, records, tile_cache);
     compact_tiles_kernel<<<1, 1024, 0, s>>>(tile_active, info->total_tiles, active_tiles,
@@ -1134,12 +1142,6 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
         bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
             views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
-        if (g_sms == 0) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-            if (g_sms < 1) g_sms = 1;
-        }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel, kBinBlock,
                                                       (size_t)max_view_tiles * 6);
