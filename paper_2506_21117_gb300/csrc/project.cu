@@ -721,16 +721,15 @@ bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __res
 // can be emitted (per row: the smallest first emitted bin and the largest cut
 // over the row's tiles); false if there is none. Conservative: emission still
 // tests each cell of the rows in between.
-__device__ __forceinline__ bool bin_window_rows(const uint8_t* t_front, const uint8_t* t_cut,
-                                                int64_t total_tiles, const ClsView& view, int x0,
-                                                int x1, int y0, int y1, int bin, int& first,
-                                                int& last) {
+__device__ __forceinline__ bool bin_window_rows(const uint8_t* tf, const uint8_t* tc,
+                                                int64_t level_stride, int Tx, int x0, int x1,
+                                                int y0, int y1, int bin, int& first, int& last) {
     const int w = x1 - x0 + 1;
     const int l = 31 - __clz(w);
-    const int64_t lv = (int64_t)l * total_tiles + view.tile_base + x0;
+    const int64_t lv = (int64_t)l * level_stride + x0;
     auto row_ok = [&](int y) {
-        const int64_t a = lv + (int64_t)y * view.tiles_x, b = a + w - (1 << l);
-        return min(t_front[a], t_front[b]) <= bin && bin <= max(t_cut[a], t_cut[b]);
+        const int64_t a = lv + (int64_t)y * Tx, b = a + w - (1 << l);
+        return min(tf[a], tf[b]) <= bin && bin <= max(tc[a], tc[b]);
     };
     int y = y0;
     while (y <= y1 && !row_ok(y)) ++y;
@@ -746,7 +745,12 @@ __device__ __forceinline__ bool bin_window_rows(const uint8_t* t_front, const ui
 // one view, prefix-sums their rectangle areas, and spreads the rectangle cells
 // over its lanes (each lane finds the owner of its cell by a binary search over
 // the prefix); an active cell claims a slot in its (tile, depth bin) bucket.
-__global__ void __launch_bounds__(kBinBlock)
+// One 1024-thread block per SM holds its view's tile ranks, cuts, first bins
+// and (when they fit in `smem_bytes`) the row sparse tables in shared memory,
+// so the per-Gaussian row scans do not wait on L2.
+constexpr int kEmitThreads = 1024;
+
+__global__ void __launch_bounds__(kEmitThreads)
 emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
                      const int32_t* __restrict__ tile_rank, const uint32_t* __restrict__ zmin,
                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
@@ -755,7 +759,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                      const int32_t* __restrict__ work_count, int32_t* __restrict__ next_group,
                      const uint8_t* __restrict__ cut, const uint8_t* __restrict__ front,
                      const uint8_t* __restrict__ t_front, const uint8_t* __restrict__ t_cut,
-                     int64_t total_tiles) {
+                     int64_t total_tiles, int smem_bytes) {
     // rank of each tile of the view, then its last and first emitted depth bin
     extern __shared__ int32_t s_rank[];
     const ClsView& view = views[blockIdx.y];
@@ -763,11 +767,28 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
     const int nt = Tx * view.tiles_y;
     uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_rank + nt);
     uint8_t* s_front = s_cut + nt;
-    for (int i = threadIdx.x; i < nt; i += kBinBlock) {
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
         const int r = tile_rank[view.tile_base + i];
         s_rank[i] = r;
         s_cut[i] = cut ? cut[view.tile_base + i] : (uint8_t)(kDepthBins - 1);
         s_front[i] = r >= 0 ? front[view.tile_base + i] : (uint8_t)0;
+    }
+    // the row sparse tables of the view (levels 0 .. L-1, 2^(L-1) <= Tx)
+    const int levels = 32 - __clz(Tx);
+    const uint8_t* tf = t_front + view.tile_base;
+    const uint8_t* tc = t_cut + view.tile_base;
+    int64_t level_stride = total_tiles;
+    if ((int64_t)nt * (6 + 2 * levels) <= smem_bytes) {
+        uint8_t* s_tf = s_front + nt;
+        uint8_t* s_tc = s_tf + (int64_t)levels * nt;
+        for (int l = 0; l < levels; ++l)
+            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+                s_tf[l * nt + i] = t_front[(int64_t)l * total_tiles + view.tile_base + i];
+                s_tc[l * nt + i] = t_cut[(int64_t)l * total_tiles + view.tile_base + i];
+            }
+        tf = s_tf;
+        tc = s_tc;
+        level_stride = nt;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -789,8 +810,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
             if (record_rect(view, records, rec, x0, x1, y0, y1, zb)) {
                 bin = depth_bin(zb, lo, hi);
                 int r0, r1;
-                if (bin_window_rows(t_front, t_cut, total_tiles, view, x0, x1, y0, y1, bin, r0,
-                                    r1)) {
+                if (bin_window_rows(tf, tc, level_stride, Tx, x0, x1, y0, y1, bin, r0, r1)) {
                     y0 = r0;
                     y1 = r1;
                     area = (x1 - x0 + 1) * (y1 - y0 + 1);
@@ -1142,15 +1162,18 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
         bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
             views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
+        // shared memory for the tables of views up to 2^8 tiles wide
+        const int emit_smem = (int)hmin64(max_view_tiles * (6 + 2 * 8), 200 * 1024);
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel, kBinBlock,
-                                                      (size_t)max_view_tiles * 6);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
+                                                      kEmitThreads, (size_t)emit_smem);
         const int64_t resident = (int64_t)g_sms * (per_sm > 0 ? per_sm : 1);
         const unsigned emit_blocks = (unsigned)hmin64(
-            hmin64((info->max_n + kBinBlock - 1) / kBinBlock, 2048), (resident + V - 1) / V);
-        emit_bucketed_kernel<<<dim3(emit_blocks, V), kBinBlock, (size_t)max_view_tiles * 6, s>>>(
+            hmin64((info->max_n + kEmitThreads - 1) / kEmitThreads, 2048), (resident + V - 1) / V);
+        emit_bucketed_kernel<<<dim3(emit_blocks, V), kEmitThreads, (size_t)emit_smem, s>>>(
             views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles);
+            work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles,
+            emit_smem);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;
