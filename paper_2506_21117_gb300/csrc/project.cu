@@ -827,10 +827,12 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
         const int wdt = x1 - x0 + 1;
         // four cells per lane per round, so four slot claims are in flight
         // before the first key is stored
-        constexpr int kU = 4;
+        // kU cells per lane per round, so kU slot claims are in flight before
+        // the first key is stored
+        constexpr int kU = 8;
         for (int c0 = 0; c0 < total; c0 += 32 * kU) {
-            int64_t sub[kU];
-            uint64_t key[kU];
+            int32_t sub[kU];
+            uint32_t kz[kU], kr[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int c = c0 + u * 32 + lane;
@@ -848,8 +850,8 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                 const int o_y0 = __shfl_sync(0xffffffffu, y0, own);
                 const int o_w = __shfl_sync(0xffffffffu, wdt, own);
                 const int o_bin = __shfl_sync(0xffffffffu, bin, own);
-                const uint32_t o_zb = __shfl_sync(0xffffffffu, zb, own);
-                const uint32_t o_rec = __shfl_sync(0xffffffffu, rec, own);
+                kz[u] = __shfl_sync(0xffffffffu, zb, own);
+                kr[u] = __shfl_sync(0xffffffffu, rec, own);
                 sub[u] = -1;
                 if (c < total) {
                     const int k = c - (o_incl - o_area);
@@ -857,18 +859,16 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                     divmod_small(k, o_w, q, rem);
                     const int cell = (o_y0 + q) * Tx + o_x0 + rem;
                     const int r = s_rank[cell];
-                    if (r >= 0 && o_bin <= (int)s_cut[cell] && o_bin >= (int)s_front[cell]) {
-                        sub[u] = (int64_t)r * kDepthBins + o_bin;
-                        key[u] = ((uint64_t)o_zb << 32) | o_rec;
-                    }
+                    if (r >= 0 && o_bin <= (int)s_cut[cell] && o_bin >= (int)s_front[cell])
+                        sub[u] = r * kDepthBins + o_bin;
                 }
             }
-            int64_t p[kU];
+            int32_t p[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
 #pragma unroll
             for (int u = 0; u < kU; ++u)
-                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = key[u];
+                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = ((uint64_t)kz[u] << 32) | kr[u];
         }
     }
 }
@@ -1073,6 +1073,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         g_max_view_tiles_checked = 1;
     }
     if (layout == 1 && max_view_tiles * 6 > 200 * 1024) return CLS_ERR_INVALID_ARG;
+    if (layout == 1 && subs >= INT32_MAX) return CLS_ERR_INVALID_ARG;  // int32 bucket ids
     if (max_view_tiles * 4 > 200 * 1024) return CLS_ERR_INVALID_ARG;  // nearest-active grid
     // shared-memory grids of the prefix sums (larger views use global memory)
     const int grid_cap = (int)hmin64(max_view_tiles * 4 + 16 * 1024, 200 * 1024);
