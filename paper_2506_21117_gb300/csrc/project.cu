@@ -1,5 +1,7 @@
 // Projection, dynamic render mask and (Gaussian, tile) pair emission
 // (Supp. "Local Optimization Kernel", item 1; base 3DGS preprocessing).
+#include <algorithm>
+
 #include "scan.cuh"
 
 namespace cls {
@@ -749,6 +751,7 @@ __device__ __forceinline__ bool bin_window_rows(const uint8_t* tf, const uint8_t
 // and (when they fit in `smem_bytes`) the row sparse tables in shared memory,
 // so the per-Gaussian row scans do not wait on L2.
 constexpr int kEmitThreads = 1024;
+constexpr int kEmitGroups = 16;  // groups per warp and block lifetime
 
 __global__ void __launch_bounds__(kEmitThreads)
 emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
@@ -762,9 +765,11 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
                      int64_t total_tiles, int smem_bytes) {
     // rank of each tile of the view, then its last and first emitted depth bin
     extern __shared__ int32_t s_rank[];
-    const ClsView& view = views[blockIdx.y];
+    const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x;
     const int nt = Tx * view.tiles_y;
+    // blocks past the view's work leave before filling their tables
+    if (*(volatile int32_t*)(next_group + blockIdx.x) * 32 >= work_count[blockIdx.x]) return;
     uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_rank + nt);
     uint8_t* s_front = s_cut + nt;
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
@@ -792,13 +797,14 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int n = work_count[blockIdx.y];
-    const uint32_t lo = zmin[blockIdx.y], hi = zmax[blockIdx.y];
-    // a few blocks per SM; each warp takes groups of 32 work items from the
-    // view's counter (the tables above are filled once per block)
-    for (;;) {
+    const int n = work_count[blockIdx.x];
+    const uint32_t lo = zmin[blockIdx.x], hi = zmax[blockIdx.x];
+    // each warp takes up to kEmitGroups groups of 32 work items from the
+    // view's counter (the tables above are filled once per block), so blocks
+    // retire regularly and kernels of other streams get SMs in between
+    for (int taken = 0; taken < kEmitGroups; ++taken) {
         int w = 0;
-        if (lane == 0) w = atomicAdd(next_group + blockIdx.y, 1);
+        if (lane == 0) w = atomicAdd(next_group + blockIdx.x, 1);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w * 32 >= n) break;
         const int item = w * 32 + lane;
@@ -1168,10 +1174,15 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
                                                       kEmitThreads, (size_t)emit_smem);
+        // enough blocks for every view's largest possible work list (blocks
+        // without work leave at once), at least one resident wave
         const int64_t resident = (int64_t)g_sms * (per_sm > 0 ? per_sm : 1);
+        const int64_t per_block = (int64_t)(kEmitThreads / 32) * kEmitGroups * 32;
         const unsigned emit_blocks = (unsigned)hmin64(
-            hmin64((info->max_n + kEmitThreads - 1) / kEmitThreads, 2048), (resident + V - 1) / V);
-        emit_bucketed_kernel<<<dim3(emit_blocks, V), kEmitThreads, (size_t)emit_smem, s>>>(
+            std::max<int64_t>((info->max_n + per_block - 1) / per_block, (resident + V - 1) / V),
+            65535);
+        // the view index varies fastest, so the first wave spreads over all views
+        emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
             views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
             work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles,
             emit_smem);

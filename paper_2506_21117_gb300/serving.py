@@ -165,7 +165,9 @@ class Server:
         self.fresh = False
         self.composition = None
         self.device_targets: Dict[int, object] = {}
-        self.side = torch.cuda.Stream()
+        # admission and planning run beside the queued steps; high priority so
+        # their short kernels take SMs as soon as the steps' blocks retire
+        self.side = torch.cuda.Stream(priority=-1)
         self.capture_stream = torch.cuda.Stream()
         self.scene_free: Dict[int, object] = {}  # event after a scene's last queued step
         self.stats = {"steps": 0, "graph_captures": 0, "graph_replays": 0, "rebuilds": 0}
