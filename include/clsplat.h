@@ -240,6 +240,9 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  *                             exceeds `capacity`, CLS_ERR_CAPACITY is written
  *                             to status_dev and only `capacity` pairs are kept
  *                             (offsets and ranges are clamped to capacity).
+ *                             With capacity 0 (keys may then be NULL) the
+ *                             bucketed layout only counts: n_pairs, offsets
+ *                             and ranges, no emission.
  * Tile rectangle: radius r = ceil(3 sqrt(lambda_max(Sigma'))), tiles
  * floor((u - r)/16) .. floor((u + r)/16) clamped to the grid (same for v).
  * records [total_records] ClsProjected.

@@ -1167,6 +1167,10 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
             bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
+        if (keys == nullptr || capacity == 0) {  // counting only (capacity planning)
+            CLS_CHECK_LAUNCH();
+            return CLS_OK;
+        }
         bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
             views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
         // shared memory for the tables of views up to 2^8 tiles wide

@@ -72,6 +72,17 @@ def _bytes(ctypes_array) -> torch.Tensor:
     return torch.frombuffer(bytearray(raw), dtype=torch.uint8)
 
 
+_COPY_STREAMS: Dict[object, object] = {}
+
+
+def _copy_stream(device):
+    """One side stream per device for host-to-device uploads."""
+    key = torch.device(device)
+    if key not in _COPY_STREAMS:
+        _COPY_STREAMS[key] = torch.cuda.Stream(device=key)
+    return _COPY_STREAMS[key]
+
+
 def _upload(ctypes_array, device) -> torch.Tensor:
     """A host table on the device without waiting for the stream: through
     pinned memory, asynchronously on the current stream."""
@@ -199,6 +210,7 @@ class Batch:
         self.capacity = 0
         self.keys = self.vals = self.keys_alt = self.vals_alt = self.sort_ws = None
         self.target = None
+        self.target_ready = None  # event of an asynchronous target upload
 
     # -- geometry of per-pixel buffers ---------------------------------------
     def view_slices(self):
@@ -335,6 +347,9 @@ class Batch:
 
     def render(self, loss_mode: int, bg=(0.0, 0.0, 0.0)):
         b = self
+        if b.target_ready is not None:  # targets still on their way
+            torch.cuda.current_stream().wait_event(b.target_ready)
+            b.target_ready = None
         if loss_mode:
             b.loss.zero_()
         cut = b.use_cut
@@ -601,7 +616,16 @@ class LocalUpdate:
         dev = state.params.device
         lift(state, self.cams, masks, vote_mode, dev)
         self.batch = Batch([state], [self.cams], dev, layout, lazy, ssim=loss == "l1+ssim")
-        self.batch.target = targets.to(dev, non_blocking=True)
+        # the targets travel on a copy stream while lifting and planning run;
+        # the first forward pass waits for them
+        main = torch.cuda.current_stream()
+        copy = _copy_stream(dev)
+        copy.wait_stream(main)
+        with torch.cuda.stream(copy):
+            tgt = targets.to(dev, non_blocking=True)
+        tgt.record_stream(main)
+        self.batch.target = tgt
+        self.batch.target_ready = copy.record_event()
         self.capacity_slack = capacity_slack
         self.pairs_planned = self.batch.plan_capacity(capacity_slack)
         self._init_region(0, None)
