@@ -39,8 +39,8 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
-// Farthest-point initialisation, one round: nearest[i] = min(nearest[i],
-// d2(p_i, centre j-1)) (round 1 starts it), then the arg-max over i of
+// Farthest-point initialisation, one step: nearest[i] = min(nearest[i],
+// d2(p_i, centre j-1)) (the first step starts it), then the arg-max over i of
 // nearest[i] (ties to the lowest i) as the 64-bit key (bits(d2) << 32) |
 // ~i, reduced with atomicMax.
 __global__ void __launch_bounds__(kSphBlock)
