@@ -35,13 +35,17 @@ struct BwdPixel {
 };
 
 // One list entry at one pixel: the forward pass's alpha and T, the colour
-// behind, and (for an active Gaussian) the entry's 2D gradient added to gr[].
+// behind, and (for an active Gaussian) the entry's colour gradient added to
+// gr[6..8] and dL/dpower (0 unless the entry contributes with alpha below the
+// clamp) returned in `dpow` with the pixel's dy; the caller turns those into
+// the per-thread sums of the centre, conic and opacity gradients.
 // a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
 template <bool ACTIVE>
 __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float t,
-                                          const float4& a, const float4& bb, float cb, float* gr) {
+                                          const float4& a, const float4& bb, float cb, float* gr,
+                                          float& dpow, float& dy) {
     if (pos >= p.end) return false;
-    const float dy = p.fy - a.y;
+    dy = p.fy - a.y;
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
     if (power2 > 0.0f) return false;
     const float G = ex2_approx(power2);
@@ -53,18 +57,10 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float 
     p.R2 = __fmaf_rn(-cb, w, p.R2);
     if (ACTIVE) {
         const float inv_om = __fdividef(1.0f, 1.0f - alpha);
-        const float A = -2.0f * kLn2 * a.z, B = -kLn2 * a.w, C = -2.0f * kLn2 * bb.x;
         const float cg = bb.z * p.g0 + bb.w * p.g1 + cb * p.g2;
         const float gR = p.g0 * p.R0 + p.g1 * p.R1 + p.g2 * p.R2;
         const float dLda = p.T * cg - gR * inv_om;
-        const bool clamped = bb.y * G > kAlphaMax;
-        const float dpow = clamped ? 0.f : dLda * alpha;
-        gr[0] += dpow * (A * dx + B * dy);
-        gr[1] += dpow * (C * dy + B * dx);
-        gr[2] += -0.5f * dx * dx * dpow;
-        gr[3] += -dx * dy * dpow;
-        gr[4] += -0.5f * dy * dy * dpow;
-        gr[5] += clamped ? 0.f : dLda * G;
+        dpow = bb.y * G > kAlphaMax ? 0.f : dLda * alpha;
         gr[6] += w * p.g0;
         gr[7] += w * p.g1;
         gr[8] += w * p.g2;
@@ -237,17 +233,29 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const int pos = s_pos[k];
                     const float dx = p0.fx - a.x;
                     const float t = a.z * dx;
+                    float P0 = 0.f, P1 = 0.f, dy0 = 0.f, dy1 = 0.f;
                     if (!active) {
-                        bwd_entry<false>(p0, pos, dx, t, a, bb, cb, nullptr);
-                        bwd_entry<false>(p1, pos, dx, t, a, bb, cb, nullptr);
+                        bwd_entry<false>(p0, pos, dx, t, a, bb, cb, nullptr, P0, dy0);
+                        bwd_entry<false>(p1, pos, dx, t, a, bb, cb, nullptr, P1, dy1);
                         continue;
                     }
                     any_active = true;
+                    // per-thread sums over its two pixels (one column: dx shared)
+                    // of dpow x (dx, dy, dx^2, dx dy, dy^2, 1) and of w g; the
+                    // conic's coefficients and the opacity are applied per tile
                     float gr[kGradComps];
-#pragma unroll
-                    for (int q = 0; q < kGradComps; ++q) gr[q] = 0.f;
-                    const bool c0 = bwd_entry<true>(p0, pos, dx, t, a, bb, cb, gr);
-                    const bool c1 = bwd_entry<true>(p1, pos, dx, t, a, bb, cb, gr);
+                    gr[6] = gr[7] = gr[8] = 0.f;
+                    const bool c0 = bwd_entry<true>(p0, pos, dx, t, a, bb, cb, gr, P0, dy0);
+                    const bool c1 = bwd_entry<true>(p1, pos, dx, t, a, bb, cb, gr, P1, dy1);
+                    {
+                        const float D = P0 + P1, q0 = P0 * dy0, q1 = P1 * dy1;
+                        gr[0] = dx * D;
+                        gr[1] = q0 + q1;
+                        gr[2] = dx * gr[0];
+                        gr[3] = dx * gr[1];
+                        gr[4] = __fmaf_rn(q0, dy0, q1 * dy1);
+                        gr[5] = D;
+                    }
                     float* dst = &s_g[k - k0][warp][0];
                     if (__any_sync(0xffffffffu, c0 || c1)) {
                         const float y = reduce8_scatter(gr, lane);
@@ -268,10 +276,28 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                         const int ent = e / kGradComps, comp = e - ent * kGradComps;
                         const int slot = s_slot[k0 + ent];
                         if (slot < 0) continue;
-                        float sum = 0.f;
+                        float S = 0.f, S2 = 0.f;  // this component's sums; S2 the other of du/dv
 #pragma unroll
-                        for (int w = 0; w < kBwdWarps; ++w) sum += s_g[ent][w][comp];
-                        if (sum != 0.f) atomicAdd(grad2d + (int64_t)slot * kG2Stride + comp, sum);
+                        for (int w = 0; w < kBwdWarps; ++w) {
+                            S += s_g[ent][w][comp];
+                            if (comp < 2) S2 += s_g[ent][w][comp ^ 1];
+                        }
+                        // conic (A, B, C) and opacity of the entry, from its staged form
+                        const float4 a = s_a[k0 + ent];
+                        const float4 bb = s_b[k0 + ent];
+                        const float A = -2.0f * kLn2 * a.z, B = -kLn2 * a.w,
+                                    C = -2.0f * kLn2 * bb.x;
+                        float g;
+                        switch (comp) {
+                            case 0: g = A * S + B * S2; break;   // du
+                            case 1: g = C * S + B * S2; break;   // dv
+                            case 2: g = -0.5f * S; break;        // dA
+                            case 3: g = -S; break;               // dB
+                            case 4: g = -0.5f * S; break;        // dC
+                            case 5: g = S / bb.y; break;         // dopacity
+                            default: g = S;                      // colour
+                        }
+                        if (g != 0.f) atomicAdd(grad2d + (int64_t)slot * kG2Stride + comp, g);
                     }
                     __syncthreads();
                 }
