@@ -218,7 +218,11 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  * Kernel", item 1; base 3DGS preprocessing).
  * project_mode 0 projects every Gaussian of every view (the frozen occluders;
  * do this once per camera set), mode 1 re-projects only the active Gaussians
- * (every iteration, after the parameters change). Then:
+ * (every iteration, after the parameters change). Mode 2 (bucketed layout,
+ * keys and a capacity > 0 required) only writes the bucket offsets and emits
+ * the pairs that the immediately preceding call counted with capacity 0,
+ * with the same arguments otherwise and the same workspace: nothing it reads
+ * may change in between. Then:
  *   tile_active[total_tiles]  uint8: 1 iff a non-culled active Gaussian's
  *                             tile rectangle holds the tile
  *   active_tiles[total_tiles] int32: ascending global ids of active tiles,
@@ -241,8 +245,10 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  *                             to status_dev and only `capacity` pairs are kept
  *                             (offsets and ranges are clamped to capacity).
  *                             With capacity 0 (keys may then be NULL) the
- *                             bucketed layout only counts: n_pairs, offsets
- *                             and ranges, no emission.
+ *                             bucketed layout only counts: n_pairs, the
+ *                             tile mask and list (ranges stay zero); the
+ *                             per-bucket counts stay in the workspace for
+ *                             project_mode 2.
  * Tile rectangle: radius r = ceil(3 sqrt(lambda_max(Sigma'))), tiles
  * floor((u - r)/16) .. floor((u + r)/16) clamped to the grid (same for v).
  * records [total_records] ClsProjected.

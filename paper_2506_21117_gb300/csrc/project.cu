@@ -981,6 +981,11 @@ using namespace cls;
 
 namespace {
 
+__global__ void capacity_check_kernel(const int64_t* n_pairs, int64_t capacity,
+                                      int32_t* status) {
+    if (threadIdx.x == 0 && *n_pairs > capacity) set_status(status, CLS_ERR_CAPACITY);
+}
+
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
         bins, work_list, work_count, front, t_front, t_cut, total;
@@ -1043,7 +1048,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     if (!info || !scenes_dev || !views_dev || !records || !tile_active || !active_tiles ||
         !n_active_tiles_dev || !n_pairs_dev || !status_dev || !workspace || capacity < 0 ||
         !tile_cache || (prefix_mode != 0 && prefix_mode != 1) || (tile_ring != 0 && tile_ring != 1) ||
-        (project_mode != 0 && project_mode != 1) || (layout != 0 && layout != 1) ||
+        project_mode < 0 || project_mode > 2 || (layout != 0 && layout != 1) ||
+        (project_mode == 2 && (layout != 1 || keys == nullptr || capacity <= 0)) ||
         (capacity > 0 && !keys) || (layout == 0 && capacity > 0 && !vals) ||
         (layout == 1 && (!ranges || !bin_offsets)))
         return CLS_ERR_INVALID_ARG;
@@ -1101,6 +1107,42 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_sms < 1) g_sms = 1;
     }
+    // bucketed layout, after the count: bucket offsets (clamped to the
+    // capacity), the emission window tables and the emission
+    const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
+    auto emit_stage = [&]() {
+        sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
+            views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
+            bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
+        bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
+            views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
+        // shared memory for the tables of views up to 2^8 tiles wide
+        const int emit_smem = (int)hmin64(max_view_tiles * (6 + 2 * 8), 200 * 1024);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
+                                                      kEmitThreads, (size_t)emit_smem);
+        // enough blocks for every view's largest possible work list (blocks
+        // without work leave at once), at least one resident wave
+        const int64_t resident = (int64_t)g_sms * (per_sm > 0 ? per_sm : 1);
+        const int64_t per_block = (int64_t)(kEmitThreads / 32) * kEmitGroups * 32;
+        const unsigned emit_blocks = (unsigned)hmin64(
+            std::max<int64_t>((info->max_n + per_block - 1) / per_block, (resident + V - 1) / V),
+            65535);
+        // the view index varies fastest, so the first wave spreads over all views
+        emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
+            views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
+            work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles,
+            emit_smem);
+    };
+    if (project_mode == 2) {  // the previous call counted these pairs: emit them
+        if (cpv > 0) {
+            cudaMemsetAsync(work_count + V, 0, (size_t)V * 4, s);  // emission group counters
+            capacity_check_kernel<<<1, 32, 0, s>>>(n_pairs_dev, capacity, status_dev);
+            emit_stage();
+        }
+        CLS_CHECK_LAUNCH();
+        return CLS_OK;
+    }
     cudaMemsetAsync(diff, 0, (size_t)info->total_sat * 4, s);
     cudaMemsetAsync(big_count, 0, 4, s);
     if (project_mode == 0 && info->max_n > 0)
@@ -1149,7 +1191,6 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                 nullptr, nullptr, nullptr, nullptr, keys, vals,
                                                 capacity, big_list, big_count);
     } else {
-        const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
         cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
         cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
         const unsigned work_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
@@ -1164,32 +1205,13 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                                    sub_partials);
         scan_partials_kernel<<<1, 1024, 0, s>>>(sub_partials, sub_chunks, n_pairs_dev, nullptr,
                                                 capacity, status_dev);
-        sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
-            views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
-            bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
-        if (keys == nullptr || capacity == 0) {  // counting only (capacity planning)
+        // counting only (capacity planning): the per-bucket counts stay in
+        // `cursor` for a following call in project_mode 2
+        if (keys == nullptr || capacity == 0) {
             CLS_CHECK_LAUNCH();
             return CLS_OK;
         }
-        bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
-            views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
-        // shared memory for the tables of views up to 2^8 tiles wide
-        const int emit_smem = (int)hmin64(max_view_tiles * (6 + 2 * 8), 200 * 1024);
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
-                                                      kEmitThreads, (size_t)emit_smem);
-        // enough blocks for every view's largest possible work list (blocks
-        // without work leave at once), at least one resident wave
-        const int64_t resident = (int64_t)g_sms * (per_sm > 0 ? per_sm : 1);
-        const int64_t per_block = (int64_t)(kEmitThreads / 32) * kEmitGroups * 32;
-        const unsigned emit_blocks = (unsigned)hmin64(
-            std::max<int64_t>((info->max_n + per_block - 1) / per_block, (resident + V - 1) / V),
-            65535);
-        // the view index varies fastest, so the first wave spreads over all views
-        emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
-            views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles,
-            emit_smem);
+        emit_stage();
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;

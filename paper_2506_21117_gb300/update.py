@@ -211,6 +211,7 @@ class Batch:
         self.keys = self.vals = self.keys_alt = self.vals_alt = self.sort_ws = None
         self.target = None
         self.target_ready = None  # event of an asynchronous target upload
+        self.counted = False  # the last binning only counted (capacity planning)
 
     # -- geometry of per-pixel buffers ---------------------------------------
     def view_slices(self):
@@ -249,6 +250,7 @@ class Batch:
         self.scenes_dev.copy_(_bytes(self.scene_tab).pin_memory(), non_blocking=True)
         self.views_dev.copy_(_bytes(self.view_tab).pin_memory(), non_blocking=True)
         self.reproject = True
+        self.counted = False
 
     def deactivate(self, scene_indices) -> None:
         """Drop scenes from the work of later iterations without rebuilding:
@@ -257,6 +259,7 @@ class Batch:
         for s in scene_indices:
             self.scene_tab[s].n_active = 0
         self.scenes_dev.copy_(_bytes(self.scene_tab).pin_memory(), non_blocking=True)
+        self.counted = False
 
     def record_stream(self, stream) -> None:
         """Mark every device buffer as used on `stream` (for a batch built on
@@ -268,6 +271,7 @@ class Batch:
     def reset_prefix(self):
         """Forget every tile's static prefix (the next iteration rebuilds it)."""
         self.tile_cache.fill_(-1)
+        self.counted = False
 
     def project_and_bin(self, mode: int):
         b = self
@@ -277,6 +281,10 @@ class Batch:
         if epochs != b._epochs:  # an active set changed: the frozen rows did too
             b._epochs = epochs
             b.reset_prefix()
+            b.counted = False
+        if b.counted and mode == 1:  # the planning pass counted this binning already
+            mode = 2
+        b.counted = False
         abi.check(abi.cls_project_and_bin(
             _ptr(b.scenes_dev), _ptr(b.views_dev), b.info, mode, b.layout, _ptr(b.records),
             _ptr(b.tile_active), _ptr(b.active_tiles), _ptr(b.n_active_tiles),
@@ -296,6 +304,9 @@ class Batch:
         self.status.zero_()
         cap = max(int(need * slack) + extra, cap_before)
         self.allocate_keys(cap)
+        # the next binning (nothing changes before the first iteration) only
+        # emits what this one counted
+        self.counted = self.layout == 1
         return need
 
     def allocate_keys(self, capacity: int):
