@@ -1,8 +1,8 @@
 // Backward pass of the local optimisation (Supp. "Local Optimization Kernel",
 // items 2 and 3).
 //
-// Pixel part: one 128-thread block per active tile (persistent, queue of
-// tiles), two pixels per thread. Each pixel starts from the state the forward
+// Pixel part: one 64-thread block per active tile (persistent, queue of
+// tiles), four pixels of one column per thread. Each pixel starts from the state the forward
 // pass kept after the tile's static prefix (nothing in front of it depends on
 // an active Gaussian) and walks its list front to back, up to the earlier of
 // its last contributor and the tile's last active entry (nothing behind both
@@ -23,8 +23,11 @@ namespace cls {
 constexpr int kSub = 32;      // list entries reduced per shared-memory flush
 constexpr int kGradComps = 9; // du dv dA dB dC dopacity dr dg db
 constexpr int kG2Stride = 12;
-constexpr int kBwdThreads = kTilePixels / 2;  // two pixels per thread: rows ly and ly + 8
+constexpr int kPPT = 4;  // pixels per thread: one column, rows ly, ly + 4, ly + 8, ly + 12
+constexpr int kRowStep = kTile / kPPT;
+constexpr int kBwdThreads = kTilePixels / kPPT;
 constexpr int kBwdWarps = kBwdThreads / 32;
+constexpr int kStage = kTilePixels / kBwdThreads;  // list entries staged per thread
 
 // Walk state of one pixel: T in front of the next entry, R = colour not yet
 // composited (final colour minus everything in front, background included).
@@ -141,12 +144,12 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
     __shared__ int s_slot[kTilePixels];
     __shared__ int s_pos[kTilePixels];
     __shared__ float s_g[kSub][kBwdWarps][kGradComps + 1];
-    __shared__ int s_cnt[2][kBwdWarps];
+    __shared__ int s_cnt[kStage][kBwdWarps];
     __shared__ int s_tile;
     __shared__ int s_maxend;
     const int n_tiles = *n_active_tiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, 8)
+    const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, kRowStep)
     for (;;) {
         if (threadIdx.x == 0) {
             s_tile = atomicAdd(work_counter, 1);
@@ -169,12 +172,14 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const uint32_t start = ranges[2 * (int64_t)tile];
         const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
-        BwdPixel p0, p1;
-        bwd_load_pixel(p0, view, tx * kTile + lx, ty * kTile + ly, n_prefix, c.last_active + 1,
-                       prefix_state, image, n_contrib, dL_dimage);
-        bwd_load_pixel(p1, view, tx * kTile + lx, ty * kTile + ly + 8, n_prefix,
-                       c.last_active + 1, prefix_state, image, n_contrib, dL_dimage);
-        const int my_end = max(p0.end, p1.end);
+        BwdPixel p[kPPT];
+        int my_end = 0;
+#pragma unroll
+        for (int j = 0; j < kPPT; ++j) {
+            bwd_load_pixel(p[j], view, tx * kTile + lx, ty * kTile + ly + j * kRowStep, n_prefix,
+                           c.last_active + 1, prefix_state, image, n_contrib, dL_dimage);
+            my_end = max(my_end, p[j].end);
+        }
         if (my_end > n_prefix) atomicMax(&s_maxend, my_end);
         __syncthreads();
         const int max_end = s_maxend;
@@ -183,10 +188,10 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
             const int nb = min(kTilePixels, max_end - lo);
             // stage the batch, dropping entries the forward pass's tile cull
             // drops (no pixel of the tile reaches alpha >= 1/255), in order
-            uint32_t rec[2];
-            unsigned mk[2];
+            uint32_t rec[kStage];
+            unsigned mk[kStage];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < kStage; ++r) {
                 const int i = r * kBwdThreads + threadIdx.x;
                 bool keep = false;
                 rec[r] = 0;
@@ -199,9 +204,10 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                 if (lane == 0) s_cnt[r][warp] = __popc(mk[r]);
             }
             __syncthreads();
-            int nk = 0, base[2] = {0, 0};
+            int nk = 0, base[kStage];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < kStage; ++r) {
+                base[r] = 0;
 #pragma unroll
                 for (int w = 0; w < kBwdWarps; ++w) {
                     if (w == warp) base[r] = nk;
@@ -209,7 +215,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                 }
             }
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+            for (int r = 0; r < kStage; ++r) {
                 if (mk[r] & (1u << lane)) {
                     const int k = base[r] + __popc(mk[r] & ((1u << lane) - 1u));
                     const float4* q = reinterpret_cast<const float4*>(records + rec[r]);
@@ -231,33 +237,45 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const float cb = s_c[k];
                     const bool active = s_slot[k] >= 0;  // uniform over the block
                     const int pos = s_pos[k];
-                    const float dx = p0.fx - a.x;
+                    const float dx = p[0].fx - a.x;  // one column: shared by the pixels
                     const float t = a.z * dx;
-                    float P0 = 0.f, P1 = 0.f, dy0 = 0.f, dy1 = 0.f;
+                    float P[kPPT], dy[kPPT];
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j) P[j] = dy[j] = 0.f;
                     if (!active) {
-                        bwd_entry<false>(p0, pos, dx, t, a, bb, cb, nullptr, P0, dy0);
-                        bwd_entry<false>(p1, pos, dx, t, a, bb, cb, nullptr, P1, dy1);
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j)
+                            bwd_entry<false>(p[j], pos, dx, t, a, bb, cb, nullptr, P[j], dy[j]);
                         continue;
                     }
                     any_active = true;
-                    // per-thread sums over its two pixels (one column: dx shared)
-                    // of dpow x (dx, dy, dx^2, dx dy, dy^2, 1) and of w g; the
-                    // conic's coefficients and the opacity are applied per tile
+                    // per-thread sums over its pixels of dpow x (dx, dy, dx^2,
+                    // dx dy, dy^2, 1) and of w g; the conic's coefficients and
+                    // the opacity are applied per tile
                     float gr[kGradComps];
                     gr[6] = gr[7] = gr[8] = 0.f;
-                    const bool c0 = bwd_entry<true>(p0, pos, dx, t, a, bb, cb, gr, P0, dy0);
-                    const bool c1 = bwd_entry<true>(p1, pos, dx, t, a, bb, cb, gr, P1, dy1);
+                    bool contrib = false;
+#pragma unroll
+                    for (int j = 0; j < kPPT; ++j)
+                        contrib |= bwd_entry<true>(p[j], pos, dx, t, a, bb, cb, gr, P[j], dy[j]);
                     {
-                        const float D = P0 + P1, q0 = P0 * dy0, q1 = P1 * dy1;
+                        float D = 0.f, Sy = 0.f, Syy = 0.f;
+#pragma unroll
+                        for (int j = 0; j < kPPT; ++j) {
+                            const float q = P[j] * dy[j];
+                            D += P[j];
+                            Sy += q;
+                            Syy = __fmaf_rn(q, dy[j], Syy);
+                        }
                         gr[0] = dx * D;
-                        gr[1] = q0 + q1;
+                        gr[1] = Sy;
                         gr[2] = dx * gr[0];
-                        gr[3] = dx * gr[1];
-                        gr[4] = __fmaf_rn(q0, dy0, q1 * dy1);
+                        gr[3] = dx * Sy;
+                        gr[4] = Syy;
                         gr[5] = D;
                     }
                     float* dst = &s_g[k - k0][warp][0];
-                    if (__any_sync(0xffffffffu, c0 || c1)) {
+                    if (__any_sync(0xffffffffu, contrib)) {
                         const float y = reduce8_scatter(gr, lane);
                         float z = gr[8];
 #pragma unroll
