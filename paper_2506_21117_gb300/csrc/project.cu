@@ -334,49 +334,61 @@ active_zmin_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
 // and the static-prefix decision of every active tile: its cache holds while
 // no active Gaussian of the tile lies in front of the boundary; otherwise the
 // boundary moves a margin in front of the nearest active Gaussian and the
-// prefix is rebuilt by the next forward pass.
+// prefix is rebuilt by the next forward pass. Two passes over chunks of
+// kCompactChunk tiles around one scan of the chunk counts.
+constexpr int kCompactPer = 4;  // consecutive tiles per thread
+constexpr int kCompactChunk = 1024 * kCompactPer;
+
 __global__ void __launch_bounds__(1024)
-compact_tiles_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
-                     int32_t* __restrict__ active_tiles, int32_t* __restrict__ n_active_tiles,
-                     int32_t* __restrict__ tile_rank, ClsTileCache* __restrict__ tile_cache,
-                     int prefix_mode) {
-    constexpr int kPer = 4;  // consecutive tiles per thread
-    __shared__ int32_t smem[1024 / 32 + 1];
-    int32_t carry = 0;
-    for (int64_t base = 0; base < n_tiles; base += 1024 * kPer) {
-        const int64_t t0 = base + (int64_t)threadIdx.x * kPer;
-        unsigned f = 0;
+compact_count_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
+                     ClsTileCache* __restrict__ tile_cache, int prefix_mode,
+                     int64_t* __restrict__ partials) {
+    __shared__ int64_t smem[1024 / 32 + 1];
+    const int64_t t0 = (int64_t)blockIdx.x * kCompactChunk + (int64_t)threadIdx.x * kCompactPer;
+    int64_t cnt = 0;
 #pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int64_t t = t0 + j;
-            if (t < n_tiles && tile_active[t]) {
-                f |= 1u << j;
-                const ClsTileCache c = tile_cache[t];
-                const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
-                                  c.zmin_active >= c.zb;
-                if (!keep) {
-                    tile_cache[t].zb = c.zmin_active > kPrefixMargin
-                                           ? c.zmin_active - kPrefixMargin : 0u;
-                    tile_cache[t].n_prefix = CLS_PREFIX_UNKNOWN;
-                }
+    for (int j = 0; j < kCompactPer; ++j) {
+        const int64_t t = t0 + j;
+        if (t < n_tiles && tile_active[t]) {
+            ++cnt;
+            const ClsTileCache c = tile_cache[t];
+            const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
+                              c.zmin_active >= c.zb;
+            if (!keep) {
+                tile_cache[t].zb = c.zmin_active > kPrefixMargin ? c.zmin_active - kPrefixMargin
+                                                                 : 0u;
+                tile_cache[t].n_prefix = CLS_PREFIX_UNKNOWN;
             }
         }
-        int32_t tot;
-        int32_t r = carry + block_exclusive_sum<1024>((int32_t)__popc(f), smem, tot);
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int64_t t = t0 + j;
-            if (t >= n_tiles) break;
-            if (f & (1u << j)) {
-                active_tiles[r] = (int32_t)t;
-                tile_rank[t] = r++;
-            } else {
-                tile_rank[t] = -1;
-            }
-        }
-        carry += tot;
     }
-    if (threadIdx.x == 0) *n_active_tiles = carry;
+    int64_t tot;
+    block_exclusive_sum<1024>(cnt, smem, tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024)
+compact_write_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
+                     const int64_t* __restrict__ offsets, int32_t* __restrict__ active_tiles,
+                     int32_t* __restrict__ tile_rank) {
+    __shared__ int64_t smem[1024 / 32 + 1];
+    const int64_t t0 = (int64_t)blockIdx.x * kCompactChunk + (int64_t)threadIdx.x * kCompactPer;
+    unsigned f = 0;
+#pragma unroll
+    for (int j = 0; j < kCompactPer; ++j)
+        if (t0 + j < n_tiles && tile_active[t0 + j]) f |= 1u << j;
+    int64_t tot;
+    int64_t r = offsets[blockIdx.x] + block_exclusive_sum<1024>((int64_t)__popc(f), smem, tot);
+#pragma unroll
+    for (int j = 0; j < kCompactPer; ++j) {
+        const int64_t t = t0 + j;
+        if (t >= n_tiles) break;
+        if (f & (1u << j)) {
+            active_tiles[r] = (int32_t)t;
+            tile_rank[t] = (int32_t)r++;
+        } else {
+            tile_rank[t] = -1;
+        }
+    }
 }
 
 __device__ __forceinline__ int rect_count(const int32_t* S, int Wd, int x0, int x1, int y0,
@@ -988,7 +1000,7 @@ __global__ void capacity_check_kernel(const int64_t* n_pairs, int64_t capacity,
 
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, work_list, work_count, front, t_front, t_cut, total;
+        bins, work_list, work_count, front, t_front, t_cut, compact, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1018,6 +1030,8 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.front = o; o = align256(o + (size_t)info->total_tiles);
     L.t_front = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
     L.t_cut = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
+    L.compact = o;
+    o = align256(o + (size_t)((info->total_tiles + kCompactChunk - 1) / kCompactChunk + 1) * 8);
     L.total = o;
     return L;
 }
@@ -1160,9 +1174,16 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                    (2 * g_sms + V - 1) / V), V),
                              kZminThreads, (size_t)max_view_tiles * 4, s>>>(
             scenes_dev, views_dev, records, tile_cache);
-    compact_tiles_kernel<<<1, 1024, 0, s>>>(tile_active, info->total_tiles, active_tiles,
-                                            n_active_tiles_dev, tile_rank, tile_cache,
-                                            prefix_mode);
+    {
+        const int64_t chunks = (info->total_tiles + kCompactChunk - 1) / kCompactChunk;
+        int64_t* cparts = reinterpret_cast<int64_t*>(ws + L.compact);
+        compact_count_kernel<<<(unsigned)chunks, 1024, 0, s>>>(tile_active, info->total_tiles,
+                                                               tile_cache, prefix_mode, cparts);
+        scan_partials_kernel<<<1, 1024, 0, s>>>(cparts, chunks, nullptr, n_active_tiles_dev, -1,
+                                                nullptr);
+        compact_write_kernel<<<(unsigned)chunks, 1024, 0, s>>>(tile_active, info->total_tiles,
+                                                               cparts, active_tiles, tile_rank);
+    }
     if (cpv == 0) {
         cudaMemsetAsync(n_pairs_dev, 0, sizeof(int64_t), s);
         if (layout == 1) cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);

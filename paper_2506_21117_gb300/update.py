@@ -440,7 +440,7 @@ class Batch:
     def launches_per_step(self) -> int:
         """Kernels of one iteration. project_and_bin (mode 1): project (with
         the render-mask stamps) and nearest-active depth (2 if any Gaussian
-        is active), tile mask, compaction, count,
+        is active), tile mask, compaction (count, scan, write), pair count,
         then flat: scan, emit, emit-big (3) or bucketed: bin stamps, bin
         prefix, bucket counts, scan, offsets, emission window tables, emit (7). Sort: flat
         hist + scan + passes (+ copy if odd) + ranges; bucketed 1 or 2.
@@ -448,7 +448,7 @@ class Batch:
         collection and sort, rerun);
         backward 2, Adam 2."""
         active = 2 if self.info.max_active > 0 else 0
-        proj = (2 if active else 0) + 3 + (7 if self.layout == 1 else 3)
+        proj = (2 if active else 0) + 5 + (7 if self.layout == 1 else 3)
         if self.layout == 1:
             sort = 2 if self.lazy else 1
         else:
