@@ -595,47 +595,30 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
     }
 }
 
-// Flat layout: pairs in view, Gaussian, row-major tile order at scanned offsets.
-// Bucketed layout: pair (g, tile) goes to bucket (rank(tile), bin(g)) at an
-// atomically claimed slot; the order inside a bucket is fixed later by the
-// per-bucket sort. Rectangles larger than kBigArea tiles go to a list that one
-// warp per Gaussian emits.
-template <int LAYOUT>
+// Flat layout: pairs in view, Gaussian, row-major tile order at scanned
+// offsets. Rectangles larger than kBigArea tiles go to a list that one warp per
+// Gaussian emits (emit_big_kernel).
 __global__ void __launch_bounds__(kBinBlock)
 emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                   const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
-                  const uint8_t* __restrict__ tile_active, const int32_t* __restrict__ tile_rank,
-                  int chunks_per_view, const int64_t* __restrict__ offsets,
-                  const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
-                  const uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
-                  uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
-                  uint4* __restrict__ big_list, int32_t* __restrict__ big_count) {
+                  const uint8_t* __restrict__ tile_active, int chunks_per_view,
+                  const int64_t* __restrict__ offsets, uint64_t* __restrict__ keys,
+                  uint32_t* __restrict__ vals, int64_t capacity, uint4* __restrict__ big_list,
+                  int32_t* __restrict__ big_count) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
-    extern __shared__ int32_t s_rank[];  // bucketed: this view's tile ranks
     const ClsView& view = views[blockIdx.y];
     const int n = scenes[view.scene].n;
-    int64_t base = LAYOUT == 0 ? offsets[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] : 0;
-    if (LAYOUT == 1) {
-        for (int i = threadIdx.x; i < view.tiles_x * view.tiles_y; i += kBinBlock)
-            s_rank[i] = tile_rank[view.tile_base + i];
-        __syncthreads();
-    }
-    const uint32_t lo = LAYOUT == 1 ? zmin[blockIdx.y] : 0u;
-    const uint32_t hi = LAYOUT == 1 ? zmax[blockIdx.y] : 0u;
+    int64_t base = offsets[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x];
     for (int it = 0; it < kBinItems; ++it) {
         const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
         int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
         uint32_t zb = 0;
         const int64_t cnt = g < n ? pair_count(view, records, sat, g, x0, x1, y0, y1, zb) : 0;
-        int64_t pos = 0;
-        if (LAYOUT == 0) {
-            int64_t tot;
-            pos = base + block_exclusive_sum<kBinBlock>(cnt, smem, tot);
-            base += tot;
-        }
+        int64_t tot;
+        int64_t pos = base + block_exclusive_sum<kBinBlock>(cnt, smem, tot);
+        base += tot;
         if (cnt == 0) continue;
         const uint32_t rec = (uint32_t)(view.rec_base + g);
-        const int bin = LAYOUT == 1 ? depth_bin(zb, lo, hi) : 0;
         const int area = (x1 - x0 + 1) * (y1 - y0 + 1);
         if (area > kBigArea) {
             const int slot = atomicAdd(big_count, 1);
@@ -643,28 +626,15 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
                                         (uint32_t)(pos >> 32));
             continue;
         }
-        if (LAYOUT == 0) {
-            for (int ty = y0; ty <= y1; ++ty) {
-                const int64_t row = (int64_t)view.tile_base + (int64_t)ty * view.tiles_x;
-                for (int tx = x0; tx <= x1; ++tx) {
-                    if (!tile_active[row + tx]) continue;
-                    if (pos < capacity) {
-                        keys[pos] = ((uint64_t)(row + tx) << 32) | zb;
-                        vals[pos] = rec;
-                    }
-                    ++pos;
+        for (int ty = y0; ty <= y1; ++ty) {
+            const int64_t row = (int64_t)view.tile_base + (int64_t)ty * view.tiles_x;
+            for (int tx = x0; tx <= x1; ++tx) {
+                if (!tile_active[row + tx]) continue;
+                if (pos < capacity) {
+                    keys[pos] = ((uint64_t)(row + tx) << 32) | zb;
+                    vals[pos] = rec;
                 }
-            }
-        } else {
-            const uint64_t key = ((uint64_t)zb << 32) | rec;
-            for (int ty = y0; ty <= y1; ++ty) {
-                const int* rrow = s_rank + ty * view.tiles_x;
-                for (int tx = x0; tx <= x1; ++tx) {
-                    const int r = rrow[tx];
-                    if (r < 0) continue;
-                    const int64_t p = atomicAdd(cursor + (int64_t)r * kDepthBins + bin, 1);
-                    if (p < capacity) keys[p] = key;
-                }
+                ++pos;
             }
         }
     }
@@ -938,15 +908,12 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
     }
 }
 
-// One warp per large rectangle; lanes walk its tiles in row-major order. The
-// flat layout keeps that order with a ballot prefix.
-template <int LAYOUT>
+// One warp per large rectangle (flat layout); lanes walk its tiles in
+// row-major order, kept with a ballot prefix.
 __global__ void __launch_bounds__(256)
 emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
-                const uint8_t* __restrict__ tile_active, const int32_t* __restrict__ tile_rank,
-                const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
-                const uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
-                uint64_t* __restrict__ keys, uint32_t* __restrict__ vals, int64_t capacity,
+                const uint8_t* __restrict__ tile_active, uint64_t* __restrict__ keys,
+                uint32_t* __restrict__ vals, int64_t capacity,
                 const uint4* __restrict__ big_list, const int32_t* __restrict__ big_count) {
     const int lane = threadIdx.x & 31;
     const int nbig = *big_count;
@@ -960,7 +927,6 @@ emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restric
         const int wdt = x1 - x0 + 1;
         const int area = wdt * (y1 - y0 + 1);
         int64_t pos = ((int64_t)item.w << 32) | item.z;
-        const int bin = LAYOUT == 1 ? depth_bin(zb, zmin[item.y], zmax[item.y]) : 0;
         for (int k0 = 0; k0 < area; k0 += 32) {
             const int k = k0 + lane;
             int64_t tile = 0;
@@ -971,18 +937,12 @@ emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restric
                 on = tile_active[tile] != 0;
             }
             const uint32_t m = __ballot_sync(0xffffffffu, on);
-            if (LAYOUT == 0) {
-                const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
-                if (on && p < capacity) {
-                    keys[p] = ((uint64_t)tile << 32) | zb;
-                    vals[p] = item.x;
-                }
-                pos += __popc(m);
-            } else if (on) {
-                const int64_t sub = (int64_t)tile_rank[tile] * kDepthBins + bin;
-                const int64_t p = atomicAdd(cursor + sub, 1);
-                if (p < capacity) keys[p] = ((uint64_t)zb << 32) | item.x;
+            const int64_t p = pos + __popc(m & ((1u << lane) - 1u));
+            if (on && p < capacity) {
+                keys[p] = ((uint64_t)tile << 32) | zb;
+                vals[p] = item.x;
             }
+            pos += __popc(m);
         }
     }
 }
@@ -1205,12 +1165,11 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     if (layout == 0) {
         scan_partials_kernel<<<1, 1024, 0, s>>>(partials, cpv * V, n_pairs_dev, nullptr, capacity,
                                                 status_dev);
-        emit_pairs_kernel<0><<<rec_grid, kBinBlock, 0, s>>>(
-            scenes_dev, views_dev, records, sat, tile_active, tile_rank, (int)cpv, partials,
-            nullptr, nullptr, nullptr, nullptr, keys, vals, capacity, big_list, big_count);
-        emit_big_kernel<0><<<1024, 256, 0, s>>>(views_dev, records, tile_active, tile_rank,
-                                                nullptr, nullptr, nullptr, nullptr, keys, vals,
-                                                capacity, big_list, big_count);
+        emit_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
+                                                          tile_active, (int)cpv, partials, keys,
+                                                          vals, capacity, big_list, big_count);
+        emit_big_kernel<<<1024, 256, 0, s>>>(views_dev, records, tile_active, keys, vals,
+                                             capacity, big_list, big_count);
     } else {
         cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
         cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
