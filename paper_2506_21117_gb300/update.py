@@ -169,7 +169,8 @@ class Batch:
         self.views_dev = _upload(self.view_tab, device)
         info = self.info
         dev = device
-        self.records = torch.zeros(info.total_records * 12, dtype=torch.float32, device=dev)
+        # records: the first binning projects every Gaussian (reproject below)
+        self.records = torch.empty(info.total_records * 12, dtype=torch.float32, device=dev)
         self.tile_active = torch.zeros(info.total_tiles, dtype=torch.uint8, device=dev)
         self.active_tiles = torch.zeros(info.total_tiles, dtype=torch.int32, device=dev)
         self.n_active_tiles = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -181,9 +182,10 @@ class Batch:
         self.image = torch.zeros(info.total_pixels * 3, dtype=torch.float32, device=dev)
         self.dL_dimage = torch.zeros(info.total_pixels * 3, dtype=torch.float32, device=dev)
         self.loss = torch.zeros(S, dtype=torch.float32, device=dev)
-        self.grad2d = torch.zeros(max(info.total_g2, 1) * abi.G2_STRIDE, dtype=torch.float32,
+        # grad2d: zeroed by the backward pass; grads: written for every active row
+        self.grad2d = torch.empty(max(info.total_g2, 1) * abi.G2_STRIDE, dtype=torch.float32,
                                   device=dev)
-        self.grads = torch.zeros(max(info.total_grad_rows, 1) * info.max_row_stride,
+        self.grads = torch.empty(max(info.total_grad_rows, 1) * info.max_row_stride,
                                  dtype=torch.float32, device=dev)
         self.counter = torch.zeros(4, dtype=torch.int32, device=dev)
         self.bin_offsets = torch.zeros(abi.cls_bin_offsets_size(info), dtype=torch.int32,
@@ -196,11 +198,12 @@ class Batch:
         # static-prefix cache: per tile (ClsTileCache), per pixel state after the prefix
         self.tile_cache = torch.empty(info.total_tiles * abi.TILE_CACHE_BYTES // 4,
                                       dtype=torch.int32, device=dev)
-        self.prefix_state = torch.zeros(info.total_pixels * 4, dtype=torch.float32, device=dev)
-        self.prefix_last = torch.zeros(info.total_pixels, dtype=torch.int32, device=dev)
+        # read only for tiles whose prefix a forward pass has written
+        self.prefix_state = torch.empty(info.total_pixels * 4, dtype=torch.float32, device=dev)
+        self.prefix_last = torch.empty(info.total_pixels, dtype=torch.int32, device=dev)
         self._epochs = [st.epoch for st in self.scenes]
         self.reset_prefix()
-        self.reproject = False  # project every Gaussian on the next call (after pruning)
+        self.reproject = True  # project every Gaussian on the next call (first, after pruning)
         self.abc = (torch.empty(abi.cls_ssim_buffer_size(info), dtype=torch.float32, device=dev)
                     if self.ssim else None)
         self.proj_ws = torch.zeros(abi.cls_project_workspace_size(info), dtype=torch.uint8,
