@@ -225,8 +225,9 @@ extern "C" int cls_densify(float* params, float* adam_m, float* adam_v, int32_t 
                            void* workspace, size_t workspace_bytes, cls_stream_t stream) {
     if (!params || !adam_m || !adam_v || !active || !accum || !denom || !max_radius || !rule ||
         !active_idx_out || !counts_dev || !workspace ||
-        (n_active > 0 && (!active_idx || !z || !new_src)) || n < 0 || n_active < 0 || n_active > n || row_stride < 16 ||
-        row_stride % 4 != 0 || capacity < (int64_t)n + 2 * (int64_t)n_active ||
+        (n_active > 0 && (!active_idx || !z || !new_src)) || n < 0 || n_active < 0 ||
+        n_active > n || row_stride < 16 || row_stride % 4 != 0 ||
+        capacity < (int64_t)n + 2 * (int64_t)n_active ||
         capacity > INT32_MAX || active_idx_out == active_idx ||
         workspace_bytes < cls_densify_workspace_size(n_active))
         return CLS_ERR_INVALID_ARG;
