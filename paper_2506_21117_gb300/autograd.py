@@ -2,10 +2,11 @@
 
 Forward: cls_project_and_bin (active Gaussians re-projected), the per-tile
 sort, cls_render_forward on the active tiles (no fused loss). Backward: the
-hand-written adjoint cls_render_backward, which walks each pixel's list from
-its last contributor to the front and recovers the transmittance in front of
-every Gaussian by division, so the forward pass stores only two values per
-pixel (final T and the last contributor). The gradient reaches only the rows
+hand-written adjoint cls_render_backward, which walks each pixel's list front
+to back again up to its last contributor, recomputing the transmittance in
+front of every Gaussian with the forward pass's own operations and taking the
+colour behind it as the final colour minus what has been composited, so
+nothing per (pixel, Gaussian) is stored. The gradient reaches only the rows
 of the active set O^t (Supp. "Local Optimization Kernel", item 3); the rows of
 frozen Gaussians get zero. Pixels of inactive tiles are returned as zero: no
 Gaussian of O^t reaches them, so their gradient is not needed (Sec. 3.3).
