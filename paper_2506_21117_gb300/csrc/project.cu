@@ -813,8 +813,6 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         const int wdt = x1 - x0 + 1;
-        // four cells per lane per round, so four slot claims are in flight
-        // before the first key is stored
         // kU cells per lane per round, so kU slot claims are in flight before
         // the first key is stored
         constexpr int kU = 8;
