@@ -501,7 +501,7 @@ stamp_bins_kernel(const ClsView* __restrict__ views, const ClsProjected* __restr
 // Per (depth bin, view): the 2D prefix sum of the bin's difference grid gives
 // each tile's count of pairs in that bin; the counts of the rendered tiles go
 // to counts[rank * kDepthBins + bin] (the layout the bucket scan reads).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins,
                    int64_t total_sat, int smem_cap, const int32_t* __restrict__ tile_rank,
                    int32_t* __restrict__ counts) {
@@ -1177,7 +1177,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             views_dev, records, zmin, zmax, work_list, work_count, bins, info->total_sat);
         // per (rank, bin) counts go to `cursor`, which sub_offsets then
         // turns into the buckets' slot cursors
-        bins_prefix_kernel<<<dim3(kDepthBins, V), 256, grid_cap, s>>>(
+        bins_prefix_kernel<<<dim3(kDepthBins, V), 512, grid_cap, s>>>(
             views_dev, bins, info->total_sat, grid_cap, tile_rank, cursor);
         sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(n_active_tiles_dev, cursor,
                                                                    sub_partials);
