@@ -218,7 +218,9 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  * Kernel", item 1; base 3DGS preprocessing).
  * project_mode 0 projects every Gaussian of every view (the frozen occluders;
  * do this once per camera set), mode 1 re-projects only the active Gaussians
- * (every iteration, after the parameters change). Mode 2 (bucketed layout,
+ * (every iteration, after the parameters change); the records and the
+ * workspace (which keeps every record's tile rectangle) of earlier calls
+ * supply the rest, so both must be kept between calls. Mode 2 (bucketed layout,
  * keys and a capacity > 0 required) only writes the bucket offsets and emits
  * the pairs that the immediately preceding call counted with capacity 0,
  * with the same arguments otherwise and the same workspace: nothing it reads

@@ -29,10 +29,33 @@ __device__ __forceinline__ void stamp_rect(int32_t* grid, int Wd, int x0, int x1
     atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x1 + 1, 1);
 }
 
+// Tile rectangle and depth bits of every record, written by the projection
+// (16 B: x0 | x1 << 16, y0 | y1 << 16, depth bits, 1 if the record has
+// pairs-to-be else 0), so binning reads 16 B per record instead of its 48.
+__device__ __forceinline__ uint4 pack_rect(bool valid, int x0, int x1, int y0, int y1,
+                                           uint32_t zbits) {
+    return valid ? make_uint4((uint32_t)x0 | ((uint32_t)x1 << 16),
+                              (uint32_t)y0 | ((uint32_t)y1 << 16), zbits, 1u)
+                 : make_uint4(0u, 0u, 0u, 0u);
+}
+
+__device__ __forceinline__ bool record_rect(const uint4* rects, int64_t rec, int& x0, int& x1,
+                                            int& y0, int& y1, uint32_t& zbits) {
+    const uint4 r = rects[rec];
+    zbits = r.z;
+    if (r.w == 0u) return false;
+    x0 = (int)(r.x & 0xffffu);
+    x1 = (int)(r.x >> 16);
+    y0 = (int)(r.y & 0xffffu);
+    y1 = (int)(r.y >> 16);
+    return true;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kProjBlock)
 project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-               ClsProjected* __restrict__ records, int32_t* __restrict__ diff) {
+               ClsProjected* __restrict__ records, uint4* __restrict__ rects,
+               int32_t* __restrict__ diff) {
     const ClsView& view = views[blockIdx.y];
     const ClsScene& sc = scenes[view.scene];
     const int i = blockIdx.x * kProjBlock + threadIdx.x;
@@ -53,7 +76,7 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
     const float4 q = *reinterpret_cast<const float4*>(row + 8);
     Proj P;
     project_gaussian(cam, m, ls, q, P);
-    int x0, x1, y0, y1;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     bool valid = P.valid && tile_rect(P.u, P.v, P.radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1);
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     int radius = 0;
@@ -85,22 +108,14 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
         r2 = make_float4(0.f, __int_as_float(slot), 0.f, 0.f);
     }
     r2.w = __int_as_float(radius);
+    rects[view.rec_base + g] = pack_rect(valid, x0, x1, y0, y1, __float_as_uint(r2.z));
     float4* out = reinterpret_cast<float4*>(records + view.rec_base + g);
     out[0] = r0;
     out[1] = r1;
     out[2] = r2;
 }
 
-__device__ __forceinline__ bool record_rect(const ClsView& view, const ClsProjected* records,
-                                            int64_t rec, int& x0, int& x1, int& y0, int& y1,
-                                            uint32_t& zbits) {
-    const float4 c0 = reinterpret_cast<const float4*>(records + rec)[0];
-    const float4 c2 = reinterpret_cast<const float4*>(records + rec)[2];
-    const int radius = __float_as_int(c2.w);
-    zbits = __float_as_uint(c2.z);
-    if (radius <= 0) return false;
-    return tile_rect(c0.x, c0.y, (float)radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1);
-}
+
 
 // In-place 2D inclusive prefix sum of a (rows x cols) grid with row pitch Wd.
 __device__ __forceinline__ void prefix2d(int32_t* G, int rows, int cols, int Wd) {
@@ -398,10 +413,10 @@ __device__ __forceinline__ int rect_count(const int32_t* S, int Wd, int x0, int 
 }
 
 // Pairs of one record (active tiles inside its rectangle), O(1) from the SAT.
-__device__ __forceinline__ int pair_count(const ClsView& view, const ClsProjected* records,
+__device__ __forceinline__ int pair_count(const ClsView& view, const uint4* rects,
                                           const int32_t* sat, int g, int& x0, int& x1, int& y0,
                                           int& y1, uint32_t& zbits) {
-    if (!record_rect(view, records, view.rec_base + g, x0, x1, y0, y1, zbits)) return 0;
+    if (!record_rect(rects, view.rec_base + g, x0, x1, y0, y1, zbits)) return 0;
     return rect_count(sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
 }
 
@@ -409,7 +424,7 @@ __device__ __forceinline__ int pair_count(const ClsView& view, const ClsProjecte
 // Gaussians that produce pairs (bucketed layout).
 __global__ void __launch_bounds__(kBinBlock)
 count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-                   const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
+                   const uint4* __restrict__ rects, const int32_t* __restrict__ sat,
                    int chunks_per_view, int64_t* __restrict__ partials,
                    uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
                    uint32_t* __restrict__ work_list, int32_t* __restrict__ work_count) {
@@ -429,7 +444,7 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
         if (g < n) {
             int x0, x1, y0, y1;
             uint32_t zb;
-            const int c = pair_count(view, records, sat, g, x0, x1, y0, y1, zb);
+            const int c = pair_count(view, rects, sat, g, x0, x1, y0, y1, zb);
             if (c > 0) {
                 cnt += c;
                 lo = min(lo, zb);
@@ -480,7 +495,7 @@ __device__ __forceinline__ int depth_bin(uint32_t zb, uint32_t lo, uint32_t hi) 
 // difference grid; the prefix sums then give pairs per (tile, depth bin).
 // (the pair-producing records of each view are those of its work list)
 __global__ void __launch_bounds__(kBinBlock)
-stamp_bins_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
+stamp_bins_kernel(const ClsView* __restrict__ views, const uint4* __restrict__ rects,
                   const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
                   const uint32_t* __restrict__ work_list, const int32_t* __restrict__ work_count,
                   int32_t* __restrict__ bins, int64_t total_sat) {
@@ -490,7 +505,7 @@ stamp_bins_kernel(const ClsView* __restrict__ views, const ClsProjected* __restr
     for (int i = blockIdx.x * kBinBlock + threadIdx.x; i < n; i += gridDim.x * kBinBlock) {
         int x0, x1, y0, y1;
         uint32_t zb;
-        if (!record_rect(view, records, view.rec_base + work_list[view.rec_base + i], x0, x1, y0,
+        if (!record_rect(rects, view.rec_base + work_list[view.rec_base + i], x0, x1, y0,
                          y1, zb))
             continue;
         const int b = depth_bin(zb, lo, hi);
@@ -600,7 +615,7 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
 // Gaussian emits (emit_big_kernel).
 __global__ void __launch_bounds__(kBinBlock)
 emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
-                  const ClsProjected* __restrict__ records, const int32_t* __restrict__ sat,
+                  const uint4* __restrict__ rects, const int32_t* __restrict__ sat,
                   const uint8_t* __restrict__ tile_active, int chunks_per_view,
                   const int64_t* __restrict__ offsets, uint64_t* __restrict__ keys,
                   uint32_t* __restrict__ vals, int64_t capacity, uint4* __restrict__ big_list,
@@ -613,7 +628,7 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
         const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
         int x0 = 0, x1 = -1, y0 = 0, y1 = -1;
         uint32_t zb = 0;
-        const int64_t cnt = g < n ? pair_count(view, records, sat, g, x0, x1, y0, y1, zb) : 0;
+        const int64_t cnt = g < n ? pair_count(view, rects, sat, g, x0, x1, y0, y1, zb) : 0;
         int64_t tot;
         int64_t pos = base + block_exclusive_sum<kBinBlock>(cnt, smem, tot);
         base += tot;
@@ -736,7 +751,7 @@ constexpr int kEmitThreads = 1024;
 constexpr int kEmitGroups = 16;  // groups per warp and block lifetime
 
 __global__ void __launch_bounds__(kEmitThreads)
-emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
+emit_bucketed_kernel(const ClsView* __restrict__ views, const uint4* __restrict__ rects,
                      const int32_t* __restrict__ tile_rank, const uint32_t* __restrict__ zmin,
                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                      uint64_t* __restrict__ keys, int64_t capacity,
@@ -795,7 +810,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const ClsProjected* __re
         if (item < n) {
             const uint32_t g = work_list[view.rec_base + item];
             rec = (uint32_t)(view.rec_base + g);
-            if (record_rect(view, records, rec, x0, x1, y0, y1, zb)) {
+            if (record_rect(rects, rec, x0, x1, y0, y1, zb)) {
                 bin = depth_bin(zb, lo, hi);
                 int r0, r1;
                 if (bin_window_rows(tf, tc, level_stride, Tx, x0, x1, y0, y1, bin, r0, r1)) {
@@ -867,7 +882,7 @@ constexpr int kCompleteChunks = 64;
 
 __global__ void __launch_bounds__(256)
 complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
-                      const ClsProjected* __restrict__ records, const uint32_t* __restrict__ zmin,
+                      const uint4* __restrict__ rects, const uint32_t* __restrict__ zmin,
                       const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                       uint64_t* __restrict__ keys, int64_t capacity,
                       const uint32_t* __restrict__ work_list,
@@ -896,7 +911,7 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
             const uint32_t rec = (uint32_t)(view.rec_base + work_list[view.rec_base + i]);
             int x0, x1, y0, y1;
             uint32_t zb;
-            if (!record_rect(view, records, rec, x0, x1, y0, y1, zb)) continue;
+            if (!record_rect(rects, rec, x0, x1, y0, y1, zb)) continue;
             if (tx < x0 || tx > x1 || ty < y0 || ty > y1) continue;
             const int bin = depth_bin(zb, zmin[v], zmax[v]);
             if (bin <= old_cut || bin < first_bin) continue;
@@ -909,7 +924,7 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
 // One warp per large rectangle (flat layout); lanes walk its tiles in
 // row-major order, kept with a ballot prefix.
 __global__ void __launch_bounds__(256)
-emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restrict__ records,
+emit_big_kernel(const ClsView* __restrict__ views, const uint4* __restrict__ rects,
                 const uint8_t* __restrict__ tile_active, uint64_t* __restrict__ keys,
                 uint32_t* __restrict__ vals, int64_t capacity,
                 const uint4* __restrict__ big_list, const int32_t* __restrict__ big_count) {
@@ -921,7 +936,7 @@ emit_big_kernel(const ClsView* __restrict__ views, const ClsProjected* __restric
         const ClsView& view = views[item.y];
         int x0, x1, y0, y1;
         uint32_t zb;
-        record_rect(view, records, item.x, x0, x1, y0, y1, zb);
+        record_rect(rects, item.x, x0, x1, y0, y1, zb);
         const int wdt = x1 - x0 + 1;
         const int area = wdt * (y1 - y0 + 1);
         int64_t pos = ((int64_t)item.w << 32) | item.z;
@@ -958,7 +973,7 @@ __global__ void capacity_check_kernel(const int64_t* n_pairs, int64_t capacity,
 
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, work_list, work_count, front, t_front, t_cut, compact, total;
+        bins, work_list, work_count, front, t_front, t_cut, compact, rects, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -990,6 +1005,7 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.t_cut = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
     L.compact = o;
     o = align256(o + (size_t)((info->total_tiles + kCompactChunk - 1) / kCompactChunk + 1) * 8);
+    L.rects = o; o = align256(o + (size_t)info->total_records * 16);
     L.total = o;
     return L;
 }
@@ -1049,6 +1065,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     uint8_t* front = reinterpret_cast<uint8_t*>(ws + L.front);
     uint8_t* t_front = reinterpret_cast<uint8_t*>(ws + L.t_front);
     uint8_t* t_cut = reinterpret_cast<uint8_t*>(ws + L.t_cut);
+    uint4* rects = reinterpret_cast<uint4*>(ws + L.rects);  // kept from call to call
     const int64_t subs = info->total_tiles * kDepthBins;
     const int64_t max_view_tiles = info->max_view_tiles;
     if (layout == 1 && g_max_view_tiles_checked == 0) {
@@ -1102,7 +1119,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             65535);
         // the view index varies fastest, so the first wave spreads over all views
         emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
-            views_dev, records, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
+            views_dev, rects, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
             work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles,
             emit_smem);
     };
@@ -1119,10 +1136,10 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     cudaMemsetAsync(big_count, 0, 4, s);
     if (project_mode == 0 && info->max_n > 0)
         project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
-                             s>>>(scenes_dev, views_dev, records, diff);
+                             s>>>(scenes_dev, views_dev, records, rects, diff);
     if (info->max_active > 0)  // active records, and their rectangles stamped into `diff`
         project_kernel<1><<<dim3((info->max_active + kProjBlock - 1) / kProjBlock, V), kProjBlock,
-                             0, s>>>(scenes_dev, views_dev, records, diff);
+                             0, s>>>(scenes_dev, views_dev, records, rects, diff);
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
                                               grid_cap, tile_ring);
     if (info->max_active > 0)
@@ -1154,7 +1171,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
         cudaMemsetAsync(work_count, 0, (size_t)V * 8, s);
     }
-    count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
+    count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, rects, sat,
                                                       (int)cpv, partials,
                                                       layout == 1 ? zmin : nullptr,
                                                       layout == 1 ? zmax : nullptr,
@@ -1163,10 +1180,10 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     if (layout == 0) {
         scan_partials_kernel<<<1, 1024, 0, s>>>(partials, cpv * V, n_pairs_dev, nullptr, capacity,
                                                 status_dev);
-        emit_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, records, sat,
+        emit_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, rects, sat,
                                                           tile_active, (int)cpv, partials, keys,
                                                           vals, capacity, big_list, big_count);
-        emit_big_kernel<<<1024, 256, 0, s>>>(views_dev, records, tile_active, keys, vals,
+        emit_big_kernel<<<1024, 256, 0, s>>>(views_dev, rects, tile_active, keys, vals,
                                              capacity, big_list, big_count);
     } else {
         cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
@@ -1174,7 +1191,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         const unsigned work_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
                                                       2048);
         stamp_bins_kernel<<<dim3(work_blocks, V), kBinBlock, 0, s>>>(
-            views_dev, records, zmin, zmax, work_list, work_count, bins, info->total_sat);
+            views_dev, rects, zmin, zmax, work_list, work_count, bins, info->total_sat);
         // per (rank, bin) counts go to `cursor`, which sub_offsets then
         // turns into the buckets' slot cursors
         bins_prefix_kernel<<<dim3(kDepthBins, V), 512, grid_cap, s>>>(
@@ -1209,7 +1226,8 @@ extern "C" int cls_complete_truncated(const ClsView* views_dev, const ClsBatchIn
     char* ws = static_cast<char*>(workspace);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     complete_tiles_kernel<<<1024, 256, 0, s>>>(
-        views_dev, info->n_views, records, reinterpret_cast<uint32_t*>(ws + L.zmin),
+        views_dev, info->n_views, reinterpret_cast<const uint4*>(ws + L.rects),
+        reinterpret_cast<uint32_t*>(ws + L.zmin),
         reinterpret_cast<uint32_t*>(ws + L.zmax), reinterpret_cast<int32_t*>(ws + L.cursor), keys,
         capacity, reinterpret_cast<uint32_t*>(ws + L.work_list),
         reinterpret_cast<int32_t*>(ws + L.work_count), trunc, trunc_count, trunc_cap,
