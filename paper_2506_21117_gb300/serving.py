@@ -59,15 +59,17 @@ class Request:
 
 def estimate_footprint(n_gauss: int, cams: Sequence, pairs_per_tile: int = 1024) -> int:
     """Device bytes one in-flight request needs beyond its resident scene:
-    projected records (48 B per Gaussian and view), per-pixel buffers (image,
-    target, dL/dimage, final T, last contributor, state after the static
-    prefix: 64 B), per-tile tables and a
-    key allowance of `pairs_per_tile` pairs of 16 B (key + scratch) per tile."""
+    per Gaussian and view the projected record (48 B) and its binning
+    workspace (packed rectangle, work-list entry, large-rectangle slot: 36 B),
+    per-pixel buffers (image, target, dL/dimage, final T, last contributor,
+    state after the static prefix: 64 B), per-tile tables and a key allowance
+    of `pairs_per_tile` pairs of 16 B (key + scratch) per tile."""
     total = 0
     for c in cams:
         W, H = int(c["width"]), int(c["height"])
         tiles = ((W + 15) // 16) * ((H + 15) // 16)
-        total += n_gauss * 48 + W * H * 64 + tiles * (256 * 8 + 80) + tiles * pairs_per_tile * 16
+        total += n_gauss * (48 + 36) + W * H * 64 + tiles * (256 * 8 + 80) + \
+            tiles * pairs_per_tile * 16
     return total
 
 
