@@ -82,3 +82,36 @@ def test_opacity_reset_caps_sigmoid():
     sig = lambda x: 1 / (1 + np.exp(-np.asarray(x, np.float64)))
     np.testing.assert_allclose(sig(out[1:4]), np.minimum(sig(logits[1:4]), 0.01), rtol=1e-6)
     assert out[0] == logits[0] and out[4] == logits[4]
+
+
+def test_history_recovers_after_densification():
+    """Densification only appends rows after the static ones and tombstones rows
+    of O^t, so History Recovery still rebuilds G^{t-1} exactly (Supp. "History
+    Recovery": duplication and pruning only affect O^t)."""
+    from oracle import history as oh
+    rng = np.random.default_rng(7)
+    n = 300
+    means = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    ls = rng.uniform(-6, -1, (n, 3)).astype(np.float32)
+    quats = rng.standard_normal((n, 4)).astype(np.float32)
+    logits = rng.uniform(-7, 3, n).astype(np.float32)
+    rows = np.concatenate([means, logits[:, None], ls, np.zeros((n, 1), np.float32), quats],
+                          axis=1)
+    I = rng.uniform(size=n) < 0.3
+    g_t, entry = oh.begin_update(rows, I)
+    k = int((~I).sum())
+    A = np.arange(k, n)                                   # O^t is the tail
+    accum = (rng.uniform(0, 1e-3, n) * 4).astype(np.float32)
+    denom = np.full(n, 4, np.float32)
+    z = rng.standard_normal((A.size, 2, 3)).astype(np.float32)
+    out = od.densify(g_t[:, 0:3], g_t[:, 4:7], g_t[:, 8:12], g_t[:, 3], A, accum, denom,
+                     np.zeros(n), 2.0, z, big=False)
+    assert out["src"].size > 0 and out["removed"].size > 0
+    new = g_t[out["src"]].copy()
+    new[:, 0:3] = out["means"]
+    new[:, 4:7] = out["log_scales"]
+    g_after = np.concatenate([g_t, new])
+    g_after[out["removed"], 3] = -np.inf                  # tombstones inside O^t
+    assert np.all(out["removed"] >= k)                    # static rows untouched
+    back = oh.recover(g_after, entry)
+    assert np.array_equal(back.view(np.uint32), rows.view(np.uint32))
