@@ -337,13 +337,26 @@ int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t* bin_offse
  *   key_bits          significant key bits (<= 64); passes = ceil(bits / 8)
  *   ranges            optional uint32 [n_tiles][2] (start, end); tiles with
  *                     no pair get (0, 0); may be NULL
- * A look-back wait that exceeds its iteration bound writes CLS_ERR_TIMEOUT
- * to status_dev and the pass completes with unspecified order. */
+ * A look-back wait (a partition polling the state of the one before it)
+ * that exceeds CLS_SORT_SPIN_LIMIT polls writes CLS_ERR_TIMEOUT to status_dev;
+ * the pass then goes on with the prefix summed so far, so every write stays
+ * inside the buffers but the order is unspecified. The call never hangs. */
+#define CLS_SORT_SPIN_LIMIT (1 << 22)
 size_t cls_sort_workspace_size(int64_t capacity, int32_t key_bits);
 int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                   const int64_t* n_pairs_dev, int64_t capacity, int32_t key_bits,
                   uint32_t* ranges, int64_t n_tiles, int32_t* status_dev, void* workspace,
                   size_t workspace_bytes, cls_stream_t stream);
+/* cls_sort_keys with the look-back bound given: at most `spin_limit` polls
+ * (>= 0; CLS_ERR_INVALID_ARG otherwise) per wait before CLS_ERR_TIMEOUT. A
+ * small bound makes the timeout path reachable on purpose (0: give up at the
+ * first partition that has not published yet); cls_sort_keys passes
+ * CLS_SORT_SPIN_LIMIT. */
+int cls_sort_keys_bounded(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                          uint32_t* vals_alt, const int64_t* n_pairs_dev, int64_t capacity,
+                          int32_t key_bits, uint32_t* ranges, int64_t n_tiles,
+                          int32_t* status_dev, void* workspace, size_t workspace_bytes,
+                          int64_t spin_limit, cls_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Forward render of the active tiles only (Supp. "Local Optimization

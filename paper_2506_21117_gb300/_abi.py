@@ -102,6 +102,7 @@ SIGNATURES = {
     "cls_sort_tiles": (C.c_int, [P, P, P, P, P, I64, I64, I32, P, P, P, I64, P, P, P, SZ, P]),
     "cls_sort_workspace_size": (SZ, [I64, I32]),
     "cls_sort_keys": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, P]),
+    "cls_sort_keys_bounded": (C.c_int, [P, P, P, P, P, I64, I32, P, I64, P, P, SZ, I64, P]),
     "cls_render_forward": (C.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, I64, P, P,
                                      P, P, P, I32, P, P, P, P, P, P, P]),
     "cls_render_backward": (C.c_int, [P, P, P, P, P, I32, P, P, P, P, P, P, P, P, P, P, P, P]),
@@ -255,6 +256,14 @@ def cls_sort_keys(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bit
                   n_tiles, status_dev, workspace, workspace_bytes, stream) -> int:
     return load().cls_sort_keys(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bits,
                                 ranges, n_tiles, status_dev, workspace, workspace_bytes, stream)
+
+
+def cls_sort_keys_bounded(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity, key_bits,
+                          ranges, n_tiles, status_dev, workspace, workspace_bytes, spin_limit,
+                          stream) -> int:
+    return load().cls_sort_keys_bounded(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity,
+                                        key_bits, ranges, n_tiles, status_dev, workspace,
+                                        workspace_bytes, spin_limit, stream)
 
 
 def cls_render_forward(views_dev, info, records, vals, vals_stride, ranges, active_tiles,

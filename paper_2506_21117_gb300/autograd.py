@@ -21,7 +21,12 @@ from .update import Batch, SceneState
 
 
 class ActiveRasterizer:
-    """Holds the device buffers of one scene and its views for the Function."""
+    """Holds the device buffers of one scene and its views for the Function.
+
+    The buffers are shared by every call: a forward must be followed by its
+    own backward before the next forward (each call bumps `generation`, and a
+    backward of an older call raises). The parameters must not change in place
+    between a forward and its backward (torch's version check raises)."""
 
     def __init__(self, state: SceneState, cams, bg=(0.0, 0.0, 0.0), layout: int = 1):
         self.state = state
@@ -32,6 +37,7 @@ class ActiveRasterizer:
         self.batch = Batch([state], [self.cams], state.params.device, layout,
                            prefix_cache=False)
         self.batch.plan_capacity()
+        self.generation = 0
 
     def __call__(self, params: torch.Tensor) -> List[torch.Tensor]:
         """Images [3, H, W] per view; differentiable w.r.t. `params`, which must
@@ -49,15 +55,30 @@ class _RasterizeActive(torch.autograd.Function):
         b = rast.batch
         b.status.zero_()
         b.project_and_bin(1)
+        need = int(b.n_pairs.item())
+        if need > b.capacity:
+            # the caller's optimiser moved or grew Gaussians past the planned
+            # pair capacity: size the key buffers again and bin once more
+            b.allocate_keys(int(need * 1.5) + (1 << 16))
+            b.status.zero_()
+            b.project_and_bin(1)
         b.sort()
         b.image.zero_()
         b.forward(0, rast.bg)
+        b.check_status()
+        rast.generation += 1
         ctx.rast = rast
+        ctx.generation = rast.generation
+        ctx.save_for_backward(params)
         return b.image.clone()
 
     @staticmethod
     def backward(ctx, grad_image: torch.Tensor):
         rast = ctx.rast
+        ctx.saved_tensors  # raises if the parameters changed in place since the forward
+        if ctx.generation != rast.generation:
+            raise RuntimeError("ActiveRasterizer: the buffers hold a later forward call; run "
+                               "each forward's backward before the next forward")
         b = rast.batch
         st = rast.state
         b.dL_dimage.copy_(grad_image.contiguous().view(-1))

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/clsplat.h"
 
 namespace cls {
@@ -22,6 +24,44 @@ inline int64_t hmin64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 // Stream handle of the C ABI is the CUDA runtime's stream handle.
 inline cudaStream_t as_stream(cls_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Launch facts that depend on the device (its SM count, the resident blocks of
+// a persistent kernel, raised shared-memory limits, which are per device too):
+// computed once per device under a lock, so concurrent first calls do not
+// race and a device with another SM count or occupancy gets its own value.
+// Devices past kMaxDevices compute the value on every call.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+    std::mutex m;
+    int value[kMaxDevices] = {};
+};
+
+template <typename F>
+inline int per_device(PerDevice& c, F compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        dev = 0;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return compute(dev);
+    std::lock_guard<std::mutex> lock(c.m);
+    if (c.value[dev] == 0) c.value[dev] = compute(dev);
+    return c.value[dev];
+}
+
+inline int device_sms(int dev) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Blocks of `kernel` resident on the whole device (persistent grids).
+template <typename K>
+inline int resident_blocks(int dev, K kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    return device_sms(dev) * (per_sm > 0 ? per_sm : 1);
+}
 
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }

@@ -1012,9 +1012,9 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
 
 }  // namespace
 
-static int g_max_view_tiles_checked = 0;
-static int g_grid_cap_set = 0;
-static int g_sms = 0;  // SM count of the current device
+// SM count of the device; the kernels' raised shared-memory limits are set
+// with it, once per device
+static PerDevice g_proj_sms;
 
 extern "C" size_t cls_project_workspace_size(const ClsBatchInfo* info) {
     return info ? proj_layout(info).total : 0;
@@ -1068,34 +1068,18 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     uint4* rects = reinterpret_cast<uint4*>(ws + L.rects);  // kept from call to call
     const int64_t subs = info->total_tiles * kDepthBins;
     const int64_t max_view_tiles = info->max_view_tiles;
-    if (layout == 1 && g_max_view_tiles_checked == 0) {
-        cudaFuncSetAttribute(emit_bucketed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        g_max_view_tiles_checked = 1;
-    }
     if (layout == 1 && max_view_tiles * 6 > 200 * 1024) return CLS_ERR_INVALID_ARG;
     if (layout == 1 && subs >= INT32_MAX) return CLS_ERR_INVALID_ARG;  // int32 bucket ids
     if (max_view_tiles * 4 > 200 * 1024) return CLS_ERR_INVALID_ARG;  // nearest-active grid
     // shared-memory grids of the prefix sums (larger views use global memory)
     const int grid_cap = (int)hmin64(max_view_tiles * 4 + 16 * 1024, 200 * 1024);
-    if (g_grid_cap_set < grid_cap) {
-        cudaFuncSetAttribute(tile_mask_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(bins_prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(active_zmin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             200 * 1024);
-        cudaFuncSetAttribute(bin_window_tables_kernel,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        g_grid_cap_set = grid_cap;
-    }
-
-    if (g_sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_sms < 1) g_sms = 1;
-    }
+    const int sms = per_device(g_proj_sms, [](int dev) {
+        for (const void* k : {(const void*)emit_bucketed_kernel, (const void*)tile_mask_kernel,
+                              (const void*)bins_prefix_kernel, (const void*)active_zmin_kernel,
+                              (const void*)bin_window_tables_kernel})
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        return device_sms(dev);
+    });
     // bucketed layout, after the count: bucket offsets (clamped to the
     // capacity), the emission window tables and the emission
     const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
@@ -1112,7 +1096,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                                       kEmitThreads, (size_t)emit_smem);
         // enough blocks for every view's largest possible work list (blocks
         // without work leave at once), at least one resident wave
-        const int64_t resident = (int64_t)g_sms * (per_sm > 0 ? per_sm : 1);
+        const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
         const int64_t per_block = (int64_t)(kEmitThreads / 32) * kEmitGroups * 32;
         const unsigned emit_blocks = (unsigned)hmin64(
             std::max<int64_t>((info->max_n + per_block - 1) / per_block, (resident + V - 1) / V),
@@ -1146,7 +1130,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         // one warp per active Gaussian; two 1024-thread blocks per SM
         active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads / 32 - 1) /
                                                        (kZminThreads / 32),
-                                                   (2 * g_sms + V - 1) / V), V),
+                                                   (2 * sms + V - 1) / V), V),
                              kZminThreads, (size_t)max_view_tiles * 4, s>>>(
             scenes_dev, views_dev, records, tile_cache);
     {

@@ -532,7 +532,7 @@ backward_gaussian_kernel(const ClsScene* __restrict__ scenes, const ClsView* __r
     }
 }
 
-static int g_bwd_blocks = 0;
+static PerDevice g_bwd_blocks;
 
 }  // namespace cls
 
@@ -557,14 +557,10 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
     cudaStream_t s = as_stream(stream);
     if (info->total_g2 > 0)
         cudaMemsetAsync(grad2d, 0, (size_t)info->total_g2 * kG2Stride * sizeof(float), s);
-    if (g_bwd_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_bwd_kernel, kBwdThreads, 0);
-        g_bwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
-    const int blocks = (int)hmin64(info->total_tiles, g_bwd_blocks);
+    const int bwd_blocks = per_device(g_bwd_blocks, [](int dev) {
+        return resident_blocks(dev, render_bwd_kernel, kBwdThreads, 0);
+    });
+    const int blocks = (int)hmin64(info->total_tiles, bwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(
         views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,

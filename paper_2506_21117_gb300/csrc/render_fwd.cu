@@ -443,7 +443,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
     }
 }
 
-static int g_fwd_blocks = 0;
+static PerDevice g_fwd_blocks;
 
 }  // namespace cls
 
@@ -472,17 +472,12 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
         info->total_tiles <= 0)
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (g_fwd_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int fwd_blocks = per_device(g_fwd_blocks, [](int dev) {
         cudaFuncSetAttribute(render_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(FwdSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, render_fwd_kernel, kFwdThreads,
-                                                      sizeof(FwdSmem));
-        g_fwd_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
-    const int blocks = (int)hmin64(info->total_tiles, g_fwd_blocks);
+        return resident_blocks(dev, render_fwd_kernel, kFwdThreads, sizeof(FwdSmem));
+    });
+    const int blocks = (int)hmin64(info->total_tiles, fwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_fwd_kernel<<<blocks, kFwdThreads, sizeof(FwdSmem), s>>>(
         views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,

@@ -19,7 +19,6 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr int kMaxPasses = 8;
-constexpr int64_t kSpinLimit = 1 << 22;  // bounded look-back wait
 
 struct SortSmem {
     uint64_t keys[kPartKeys];
@@ -93,7 +92,8 @@ sort_pass_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
                  uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                  const int64_t* __restrict__ n_dev, int64_t capacity, int shift,
                  const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ state,
-                 int* __restrict__ part_counter, int32_t* __restrict__ status) {
+                 int* __restrict__ part_counter, int32_t* __restrict__ status,
+                 int64_t spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem& sm = *reinterpret_cast<SortSmem*>(smem_raw);
     const int64_t n = sort_count(n_dev, capacity);
@@ -174,7 +174,7 @@ sort_pass_kernel(const uint64_t* __restrict__ keys_in, const uint32_t* __restric
                 const uint32_t st = load_state(state + j * kRadix + d);
                 const uint32_t flag = st & ~kValueMask;
                 if (flag == 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         set_status(status, CLS_ERR_TIMEOUT);
                         break;
                     }
@@ -243,8 +243,8 @@ __global__ void tile_ranges_kernel(const uint64_t* __restrict__ keys,
     }
 }
 
-static int g_sm_count = 0;
-static int g_pass_blocks_per_sm = 0;
+static PerDevice g_sort_sms;
+static PerDevice g_pass_blocks;
 
 }  // namespace cls
 
@@ -272,13 +272,14 @@ extern "C" size_t cls_sort_workspace_size(int64_t capacity, int32_t key_bits) {
     return t;
 }
 
-extern "C" int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
-                             uint32_t* vals_alt, const int64_t* n_pairs_dev, int64_t capacity,
-                             int32_t key_bits, uint32_t* ranges, int64_t n_tiles,
-                             int32_t* status_dev, void* workspace, size_t workspace_bytes,
-                             cls_stream_t stream) {
+extern "C" int cls_sort_keys_bounded(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                                     uint32_t* vals_alt, const int64_t* n_pairs_dev,
+                                     int64_t capacity, int32_t key_bits, uint32_t* ranges,
+                                     int64_t n_tiles, int32_t* status_dev, void* workspace,
+                                     size_t workspace_bytes, int64_t spin_limit,
+                                     cls_stream_t stream) {
     if (capacity < 0 || capacity >= (int64_t)kValueMask || key_bits <= 0 || key_bits > 64 ||
-        !n_pairs_dev || !status_dev || !workspace ||
+        !n_pairs_dev || !status_dev || !workspace || spin_limit < 0 ||
         workspace_bytes < cls_sort_workspace_size(capacity, key_bits) ||
         (capacity > 0 && (!keys || !vals || !keys_alt || !vals_alt)) || (ranges && n_tiles <= 0))
         return CLS_ERR_INVALID_ARG;
@@ -288,17 +289,12 @@ extern "C" int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
         CLS_CHECK_LAUNCH();
         return CLS_OK;
     }
-    if (g_sm_count == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    const int sm_count = per_device(g_sort_sms, [](int dev) { return device_sms(dev); });
+    const int pass_blocks_max = per_device(g_pass_blocks, [](int dev) {
         cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SortSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_pass_blocks_per_sm, sort_pass_kernel,
-                                                      kSortBlock, sizeof(SortSmem));
-        if (g_pass_blocks_per_sm < 1) g_pass_blocks_per_sm = 1;
-        if (g_sm_count < 1) g_sm_count = 1;
-    }
+        return resident_blocks(dev, sort_pass_kernel, kSortBlock, sizeof(SortSmem));
+    });
     const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
     size_t off_hist, off_cnt, off_state, total;
     sort_layout(capacity, passes, &off_hist, &off_cnt, &off_state, &total);
@@ -309,10 +305,10 @@ extern "C" int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
     cudaMemsetAsync(ws, 0, total, s);
 
     const int64_t parts = sort_parts(capacity);
-    const int hist_blocks = (int)hmin64((capacity + 255) / 256, (int64_t)g_sm_count * 8);
+    const int hist_blocks = (int)hmin64((capacity + 255) / 256, (int64_t)sm_count * 8);
     sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys, n_pairs_dev, capacity, passes, hist);
     sort_hist_scan_kernel<<<passes, kRadix, 0, s>>>(hist);
-    const int pass_blocks = (int)hmin64(parts, (int64_t)g_sm_count * g_pass_blocks_per_sm);
+    const int pass_blocks = (int)hmin64(parts, (int64_t)pass_blocks_max);
     uint64_t* kin = keys;
     uint32_t* vin = vals;
     uint64_t* kout = keys_alt;
@@ -320,18 +316,28 @@ extern "C" int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
     for (int p = 0; p < passes; ++p) {
         sort_pass_kernel<<<pass_blocks, kSortBlock, sizeof(SortSmem), s>>>(
             kin, vin, kout, vout, n_pairs_dev, capacity, p * kRadixBits, hist + p * kRadix,
-            state + (int64_t)p * parts * kRadix, counters + p, status_dev);
+            state + (int64_t)p * parts * kRadix, counters + p, status_dev, spin_limit);
         uint64_t* tk = kin; kin = kout; kout = tk;
         uint32_t* tv = vin; vin = vout; vout = tv;
     }
     if (kin != keys) {
-        sort_copy_kernel<<<g_sm_count * 4, 256, 0, s>>>(kin, vin, keys, vals, n_pairs_dev,
+        sort_copy_kernel<<<sm_count * 4, 256, 0, s>>>(kin, vin, keys, vals, n_pairs_dev,
                                                         capacity);
     }
     if (ranges) {
-        tile_ranges_kernel<<<g_sm_count * 4, 256, 0, s>>>(keys, n_pairs_dev, capacity, n_tiles,
+        tile_ranges_kernel<<<sm_count * 4, 256, 0, s>>>(keys, n_pairs_dev, capacity, n_tiles,
                                                           ranges);
     }
     CLS_CHECK_LAUNCH();
     return CLS_OK;
+}
+
+extern "C" int cls_sort_keys(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                             uint32_t* vals_alt, const int64_t* n_pairs_dev, int64_t capacity,
+                             int32_t key_bits, uint32_t* ranges, int64_t n_tiles,
+                             int32_t* status_dev, void* workspace, size_t workspace_bytes,
+                             cls_stream_t stream) {
+    return cls_sort_keys_bounded(keys, vals, keys_alt, vals_alt, n_pairs_dev, capacity,
+                                 key_bits, ranges, n_tiles, status_dev, workspace,
+                                 workspace_bytes, CLS_SORT_SPIN_LIMIT, stream);
 }

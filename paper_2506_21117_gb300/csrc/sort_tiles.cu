@@ -300,7 +300,7 @@ sort_bins_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
     }
 }
 
-static int g_tiles_blocks = 0;
+static PerDevice g_tiles_blocks;
 
 }  // namespace cls
 
@@ -329,21 +329,16 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
         ((cut || trunc) && min_bin <= 1))
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (g_tiles_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tiles_blocks = per_device(g_tiles_blocks, [](int dev) {
         cudaFuncSetAttribute(sort_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSortSmem));
         cudaFuncSetAttribute(sort_bins_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(TileSortSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_tiles_kernel, kTB,
-                                                      sizeof(TileSortSmem));
-        g_tiles_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
+        return resident_blocks(dev, sort_tiles_kernel, kTB, sizeof(TileSortSmem));
+    });
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     if (min_bin <= 1) {
-        sort_tiles_kernel<<<(int)hmin64(total_tiles, g_tiles_blocks), kTB, sizeof(TileSortSmem),
+        sort_tiles_kernel<<<(int)hmin64(total_tiles, tiles_blocks), kTB, sizeof(TileSortSmem),
                             s>>>(keys, keys_alt, bin_offsets, n_active_tiles_dev, active_tiles,
                                  tile_cache, work_counter);
     } else {
@@ -354,7 +349,7 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
         collect_bins_kernel<<<1024, 256, 0, s>>>(bin_offsets, n_active_tiles_dev, active_tiles,
                                                  cut, trunc, trunc_count, trunc_cap, tile_cache,
                                                  min_bin, list, count, cap);
-        sort_bins_kernel<<<g_tiles_blocks, kTB, sizeof(TileSortSmem), s>>>(keys, keys_alt, list,
+        sort_bins_kernel<<<tiles_blocks, kTB, sizeof(TileSortSmem), s>>>(keys, keys_alt, list,
                                                                           count, cap, work_counter);
     }
     CLS_CHECK_LAUNCH();

@@ -256,7 +256,7 @@ ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
     }
 }
 
-static int g_ssim_blocks = 0;
+static PerDevice g_ssim_blocks;
 
 }  // namespace cls
 
@@ -276,20 +276,14 @@ extern "C" int cls_ssim_loss(const ClsView* views_dev, const ClsBatchInfo* info,
         !(lambda >= 0.0f && lambda <= 1.0f))
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (g_ssim_blocks == 0) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ssim_blocks = per_device(g_ssim_blocks, [](int dev) {
         cudaFuncSetAttribute(ssim_maps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SsimSmem));
         cudaFuncSetAttribute(ssim_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SsimSmem));
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssim_maps_kernel, kTilePixels,
-                                                      sizeof(SsimSmem));
-        g_ssim_blocks = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }
-    const int blocks = (int)hmin64(info->total_tiles, g_ssim_blocks);
+        return resident_blocks(dev, ssim_maps_kernel, kTilePixels, sizeof(SsimSmem));
+    });
+    const int blocks = (int)hmin64(info->total_tiles, ssim_blocks);
     ssim_maps_kernel<<<blocks, kTilePixels, sizeof(SsimSmem), s>>>(
         views_dev, info->n_views, tiles, n_tiles_dev, tile_active, image, target, lambda, abc,
         loss_per_scene);

@@ -55,6 +55,46 @@ class Request:
     it: int = 0
     loss: float = float("nan")
     n_active: int = 0
+    status: str = "queued"  # then "ok", "rejected: ...", "empty: ..." or "error: ..."
+
+
+def _numel(x) -> int:
+    return int(x.numel()) if hasattr(x, "numel") and callable(x.numel) else int(np.size(x))
+
+
+def validate_request(req: Request) -> Optional[str]:
+    """Host-side checks of a request before it is queued; the reason it is
+    rejected, or None. A view needs a positive size, a finite pose and finite,
+    positive focal lengths; the masks and targets must match the views' pixel
+    counts (uint8 masks, float32 [3][H][W] targets, views concatenated); a
+    change mask with no set pixel lifts no Gaussian, so there is nothing to
+    optimise. Non-finite target values are not scanned here (that would read
+    every pixel on the host); they show up as a non-finite loss, which marks
+    the finished request as an error."""
+    if not req.cams:
+        return "no views"
+    if req.iters <= 0:
+        return "the number of iterations must be positive"
+    pix = 0
+    for c in req.cams:
+        W, H = int(c["width"]), int(c["height"])
+        if W <= 0 or H <= 0:
+            return "view size must be positive"
+        pose = np.concatenate([np.ravel(np.asarray(c[k], np.float64)) for k in ("R", "t", "pos")]
+                              + [np.array([c["fx"], c["fy"], c["cx"], c["cy"], c["znear"]],
+                                          np.float64)])
+        if not np.all(np.isfinite(pose)):
+            return "camera pose or intrinsics not finite"
+        if not (c["fx"] > 0 and c["fy"] > 0):
+            return "focal lengths must be positive"
+        pix += W * H
+    if req.masks is None or _numel(req.masks) != pix:
+        return "change masks do not match the views"
+    if not bool(req.masks.any()):
+        return "empty change mask: no Gaussian can be lifted"
+    if req.targets is None or _numel(req.targets) != 3 * pix:
+        return "target images do not match the views"
+    return None
 
 
 def estimate_footprint(n_gauss: int, cams: Sequence, pairs_per_tile: int = 1024) -> int:
@@ -85,13 +125,27 @@ class Scheduler:
         self.inflight: List[Request] = []
         self.rejected: List[Request] = []
         self.finished: List[Request] = []
+        self.empty: List[Request] = []
         self.used = 0
 
     def submit(self, req: Request) -> None:
-        if req.footprint > self.budget:
+        reason = validate_request(req)
+        if reason is None and req.footprint > self.budget:
+            reason = "footprint exceeds the device budget"
+        if reason is not None:
+            req.status = "rejected: " + reason
             self.rejected.append(req)
             return
         self.queue.append(req)
+
+    def retire_empty(self, req: Request, now: float, reason: str) -> None:
+        """An admitted request whose lifting found no active Gaussian: it
+        leaves the in-flight set without running an iteration."""
+        self.inflight = [r for r in self.inflight if r is not req]
+        self.used -= req.footprint
+        req.done = now
+        req.status = "empty: " + reason
+        self.empty.append(req)
 
     def admit(self, now: float) -> List[Request]:
         """Move every queued request that fits into the in-flight set, in
@@ -124,6 +178,8 @@ class Scheduler:
                 r.done = now
                 done.append(r)
         if done:
+            for r in done:
+                r.status = "ok"
             self.inflight = [r for r in self.inflight if r.done < 0]
             for r in done:
                 self.used -= r.footprint
@@ -176,7 +232,11 @@ class Server:
 
     # -- request life cycle ----------------------------------------------------
     def submit(self, req: Request) -> None:
-        if req.footprint == 0:
+        if not 0 <= req.scene < len(self.states):
+            req.status = "rejected: unknown scene"
+            self.sched.rejected.append(req)
+            return
+        if req.footprint == 0 and req.cams:
             req.footprint = estimate_footprint(self.states[req.scene].n, req.cams)
         self.sched.submit(req)
 
@@ -319,6 +379,9 @@ class Server:
             started = self.sched.admit(now)
             for r in started:
                 self._start(r)
+                if r.n_active == 0:  # lifting found nothing to optimise
+                    self.sched.retire_empty(r, self.clock(), "no Gaussian lifted")
+                    self.device_targets.pop(r.rid, None)
             if not self.sched.inflight:
                 if pending:
                     time.sleep(max(0.0, min(pending[0].arrival - self.clock(), 0.002)))
@@ -345,12 +408,16 @@ class Server:
             vals = loss.cpu().numpy()
             for r, i in items:
                 r.loss = float(vals[i])
+                if not np.isfinite(r.loss):
+                    r.status = "error: non-finite loss"
         if self.batch is not None:
             self.batch.check_status()
         wall = max(r.done for r in self.sched.finished) - t0 if self.sched.finished else 0.0
         out = latency_stats(self.sched.finished, max(wall, 1e-9))
         out.update(self.stats)
         out["rejected"] = len(self.sched.rejected)
+        out["empty"] = len(self.sched.empty)
+        out["errors"] = sum(1 for r in self.sched.finished if r.status.startswith("error"))
         out["unfinished"] = unfinished
         return out
 

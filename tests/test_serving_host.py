@@ -1,11 +1,28 @@
 """Host-side policy of the serving loop (no GPU): FIFO admission, slots,
-HBM-footprint budget, one in-flight update per scene, completion."""
-from paper_2506_21117_gb300.serving import Request, Scheduler, estimate_footprint, latency_stats
+HBM-footprint budget, one in-flight update per scene, completion, and the
+rejection of malformed requests (non-finite poses, empty or mismatched change
+masks) before they reach the device."""
+import numpy as np
+
+from paper_2506_21117_gb300 import synthetic as S
+from paper_2506_21117_gb300.serving import (Request, Scheduler, estimate_footprint,
+                                            latency_stats, validate_request)
+
+CAMS = S.ring_cameras(2, 4.0, 24, 16)
 
 
-def _req(rid, scene, fp, iters=3, arrival=0.0):
-    return Request(rid=rid, scene=scene, cams=[], masks=None, targets=None, iters=iters,
-                   arrival=arrival, footprint=fp)
+def _inputs(cams=CAMS):
+    pix = sum(int(c["width"]) * int(c["height"]) for c in cams)
+    masks = np.zeros(pix, np.uint8)
+    masks[pix // 3: pix // 2] = 1
+    return masks, np.full(3 * pix, 0.5, np.float32)
+
+
+def _req(rid, scene, fp, iters=3, arrival=0.0, cams=CAMS, masks=None, targets=None):
+    m, t = _inputs(cams)
+    return Request(rid=rid, scene=scene, cams=cams, masks=m if masks is None else masks,
+                   targets=t if targets is None else targets, iters=iters, arrival=arrival,
+                   footprint=fp)
 
 
 def test_fifo_slots_and_budget():
@@ -52,3 +69,50 @@ def test_footprint_grows_with_views_and_resolution():
     assert estimate_footprint(1000, c2) > estimate_footprint(1000, c1)
     assert estimate_footprint(1000, c3) > estimate_footprint(1000, c1)
     assert estimate_footprint(2000, c1) > estimate_footprint(1000, c1)
+
+
+def test_malformed_requests_are_rejected_with_a_reason():
+    s = Scheduler(max_slots=4, budget=10**9)
+    nan_pose = [dict(c) for c in CAMS]
+    nan_pose[1]["t"] = np.array([0.0, float("nan"), 4.0])
+    bad_focal = [dict(c) for c in CAMS]
+    bad_focal[0]["fx"] = 0.0
+    m, t = _inputs()
+    cases = {
+        "pose": _req(0, 0, 10, cams=nan_pose),
+        "focal": _req(1, 1, 10, cams=bad_focal),
+        "empty": _req(2, 2, 10, masks=np.zeros_like(m)),
+        "masks": _req(3, 3, 10, masks=m[:-1]),
+        "targets": _req(4, 4, 10, targets=t[:-3]),
+        "views": Request(rid=5, scene=5, cams=[], masks=m, targets=t, footprint=10),
+        "iters": _req(6, 6, 10, iters=0),
+    }
+    for r in cases.values():
+        s.submit(r)
+    good = _req(7, 7, 10)
+    s.submit(good)
+    assert [r.rid for r in s.queue] == [7] and good.status == "queued"
+    assert len(s.rejected) == len(cases)
+    assert all(r.status.startswith("rejected: ") for r in s.rejected)
+    assert "not finite" in cases["pose"].status
+    assert "focal" in cases["focal"].status
+    assert "empty change mask" in cases["empty"].status
+    assert "masks do not match" in cases["masks"].status
+    assert "target images do not match" in cases["targets"].status
+    assert "no views" in cases["views"].status and "iterations" in cases["iters"].status
+    assert validate_request(good) is None
+    assert [r.rid for r in s.admit(0.0)] == [7]
+
+
+def test_request_with_nothing_lifted_leaves_without_iterations():
+    s = Scheduler(max_slots=2, budget=100)
+    a, b = _req(0, 0, 40), _req(1, 0, 40)
+    s.submit(a)
+    s.submit(b)
+    assert [r.rid for r in s.admit(0.0)] == [0]    # scene 0 busy
+    s.retire_empty(a, 0.5, "no Gaussian lifted")
+    assert a.status.startswith("empty: ") and a.done == 0.5 and s.used == 0
+    assert [r.rid for r in s.admit(0.5)] == [1]    # the scene is free again
+    assert s.advance(1.0) == [] and s.advance(2.0) == []
+    assert [r.rid for r in s.advance(3.0)] == [1] and b.status == "ok"
+    assert s.empty == [a] and a not in s.finished
