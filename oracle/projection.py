@@ -33,10 +33,10 @@ from . import sh as shb
 T64 = torch.float64
 
 
-def cam64(cam) -> Dict[str, object]:
+def cam64(cam, dtype=T64) -> Dict[str, object]:
     """The camera as the library sees it: every field rounded to float32 once,
-    then widened to float64."""
-    f = lambda a: torch.tensor(np.asarray(a, dtype=np.float32).astype(np.float64), dtype=T64)
+    then widened to float64 (or kept in float32 with dtype=torch.float32)."""
+    f = lambda a: torch.tensor(np.asarray(a, dtype=np.float32).astype(np.float64), dtype=dtype)
     return {
         "R": f(np.asarray(cam["R"]).reshape(3, 3)), "t": f(cam["t"]), "pos": f(cam["pos"]),
         "fx": float(np.float32(cam["fx"])), "fy": float(np.float32(cam["fy"])),
@@ -45,10 +45,14 @@ def cam64(cam) -> Dict[str, object]:
     }
 
 
-def scene64(scene: Dict[str, np.ndarray], requires_grad: bool = False) -> Dict[str, torch.Tensor]:
+def scene64(scene: Dict[str, np.ndarray], requires_grad: bool = False,
+            dtype=T64) -> Dict[str, torch.Tensor]:
+    """Parameter tensors in float64 (the oracle), or in float32 with
+    dtype=torch.float32: the same arithmetic rounded to single precision, which
+    measures how far float32 rounding alone moves each value."""
     out = {}
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
-        out[k] = torch.tensor(np.asarray(scene[k], dtype=np.float64), dtype=T64,
+        out[k] = torch.tensor(np.asarray(scene[k], dtype=np.float64), dtype=dtype,
                               requires_grad=requires_grad)
     return out
 
@@ -85,8 +89,9 @@ def ewa_jacobian(p: torch.Tensor, c) -> torch.Tensor:
 
 
 def project(g: Dict[str, torch.Tensor], cam, sh_degree: int) -> Dict[str, torch.Tensor]:
-    """2D quantities of every Gaussian for one camera (no culling here)."""
-    c = cam64(cam)
+    """2D quantities of every Gaussian for one camera (no culling here), in
+    the precision of the parameter tensors."""
+    c = cam64(cam, g["means"].dtype)
     p = g["means"] @ c["R"].T + c["t"]
     px, py, pz = p.unbind(-1)
     u = c["fx"] * px / pz + c["cx"]

@@ -41,6 +41,23 @@ def tile_list(pidx: Dict[str, np.ndarray], tx: int, ty: int) -> np.ndarray:
     return ids[order]
 
 
+def saturated_length(u, v, conic, opacity, rgb, px, py, bg, start: int = 256) -> int:
+    """Length of the list prefix that holds every composited entry of every
+    pixel: the first of 256, 512, 1024, ... (or the whole list) at which the
+    stop rule has ended all pixels. Entries behind it are composited at no
+    pixel, so compositing the prefix gives the same result as the whole
+    list (used to bound the oracle's work on long lists)."""
+    L = int(u.shape[0])
+    n = start
+    with torch.no_grad():
+        while n < L:
+            if bool(composite(u[:n], v[:n], conic[:n], opacity[:n], rgb[:n], px, py,
+                              bg)["stopped"].all()):
+                return n
+            n *= 2
+    return L
+
+
 def tile_pixels(cam, tx: int, ty: int):
     W, H = int(cam["width"]), int(cam["height"])
     xs = np.arange(tx * fx.TILE, min((tx + 1) * fx.TILE, W))
@@ -55,6 +72,9 @@ def loss_terms(colour, target, kind: str):
 
 
 SSIM_LOSSES = ("ssim", "l1+ssim")
+# |C - C*| below which the sign of an L1 term is ambiguous between float32 and
+# float64 (the GPU's pixels agree with the oracle's to about 1e-6)
+KINK_TOL = 1e-5
 
 
 def view_loss_ssim(image, target, kind: str):
@@ -72,7 +92,8 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
            bg=(0.0, 0.0, 0.0), targets: Optional[Sequence[np.ndarray]] = None,
            loss: str = "l1", need_grad: bool = False,
            tiles: Optional[Sequence[Sequence[tuple]]] = None,
-           margin: float = 1e-4):
+           margin: float = 1e-4, dtype=T64, truncate: bool = False,
+           hold_ambiguous: bool = False, held: Optional[Sequence[np.ndarray]] = None):
     """Render every view (or only `tiles[j]` of view j).
 
     Returns a dict with per-view `image` [3, H, W] (NaN where not rendered),
@@ -82,14 +103,32 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
     float64 gradient of every parameter array (`grads`, numpy, same shapes as
     the scene). The loss is the mean over views of the per-view loss; for the
     D-SSIM kinds (`SSIM_LOSSES`, whole images only) `dL_dimage` holds the
-    float64 gradient of the loss with respect to each view's image."""
+    float64 gradient of the loss with respect to each view's image.
+
+    hold_ambiguous=True holds the colour of every pixel with an ambiguous
+    threshold decision (composite's `ambiguous`, and for the L1 kinds a
+    channel within KINK_TOL of its target) constant in the loss: the
+    loss value is unchanged, but no gradient flows through that pixel's
+    compositing, so the gradient no longer depends on a branch that float32
+    and float64 may take differently. `held` (per view, [H, W] bools) gives
+    those pixels explicitly instead. The pixels held are returned in
+    `held` (per view).
+
+    truncate=True composites each tile over the list prefix that holds every
+    composited entry (`saturated_length`): the same result with less work on
+    long lists.
+
+    dtype=torch.float32 runs the same arithmetic in single precision (every
+    value, every sum); set against the float64 result it measures the rounding
+    error that float32 arithmetic alone leaves in each pixel and gradient. The
+    discrete decisions stay those of `fp32_index` either way."""
     if loss in SSIM_LOSSES and tiles is not None:
         raise ValueError("the D-SSIM losses are defined on whole images")
     V = len(cams)
-    bg_t = torch.tensor(bg, dtype=T64)
-    g = scene64(scene, requires_grad=need_grad)
+    bg_t = torch.tensor(bg, dtype=dtype)
+    g = scene64(scene, requires_grad=need_grad, dtype=dtype)
     out = {"image": [], "T_final": [], "n_contrib": [], "n_incl": [], "near": [], "pidx": [],
-           "near_ids": set(), "loss": 0.0, "dL_dimage": []}
+           "near_ids": set(), "loss": 0.0, "dL_dimage": [], "held": []}
     proj_outs, proj_grads = [], []
     for j, cam in enumerate(cams):
         W, H = int(cam["width"]), int(cam["height"])
@@ -99,24 +138,47 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
         P = project(g, cam, sh_degree)
         leaves = {k: P[k].detach().clone().requires_grad_(need_grad)
                   for k in ("u", "v", "conic", "opacity", "rgb")}
+        # how far the float32 centres (which the library computes exactly as
+        # fp32_index does) lie from these values: the scale of the float32
+        # error in every exponent, for the ambiguity test
+        err_u = torch.from_numpy(np.abs(pidx["u"].astype(np.float64) -
+                                        P["u"].detach().double().numpy()))
+        err_v = torch.from_numpy(np.abs(pidx["v"].astype(np.float64) -
+                                        P["v"].detach().double().numpy()))
         img = np.full((3, H, W), np.nan)
         Tf = np.full((H, W), np.nan)
         nc = np.full((H, W), -1, np.int64)
         ni = np.full((H, W), -1, np.int64)
         near = np.zeros((H, W), bool)
+        hold = np.zeros((H, W), bool)
         tgt = None if targets is None else torch.tensor(
-            np.asarray(targets[j], np.float64), dtype=T64)
+            np.asarray(targets[j], np.float64), dtype=dtype)
         norm = 1.0 / (3.0 * H * W * V)
         todo = tiles[j] if tiles is not None else [(x, y) for y in range(Ty) for x in range(Tx)]
-        whole = torch.zeros(3, H * W, dtype=T64) if loss in SSIM_LOSSES else None
+        whole = torch.zeros(3, H * W, dtype=dtype) if loss in SSIM_LOSSES else None
         for (tx, ty) in todo:
             ids_np = tile_list(pidx, tx, ty)
             ids = torch.tensor(ids_np, dtype=torch.int64)
             px, py = tile_pixels(cam, tx, ty)
+            if truncate:
+                n_keep = saturated_length(leaves["u"][ids], leaves["v"][ids],
+                                          leaves["conic"][ids], leaves["opacity"][ids],
+                                          leaves["rgb"][ids], px, py, bg_t)
+                ids_np, ids = ids_np[:n_keep], ids[:n_keep]
             cr = composite(leaves["u"][ids], leaves["v"][ids], leaves["conic"][ids],
-                           leaves["opacity"][ids], leaves["rgb"][ids], px, py, bg_t, margin)
+                           leaves["opacity"][ids], leaves["rgb"][ids], px, py, bg_t, margin,
+                           du=err_u[ids].to(dtype), dv=err_v[ids].to(dtype))
             col = cr["colour"]
             pxn, pyn = px.numpy(), py.numpy()
+            if held is not None or hold_ambiguous:
+                if held is not None:
+                    h = torch.from_numpy(np.asarray(held[j], bool)[pyn, pxn])
+                else:
+                    h = cr["ambiguous"]
+                    if tgt is not None and loss in ("l1", "l1+ssim"):
+                        h = h | ((col.detach() - tgt[:, py, px].T).abs() < KINK_TOL).any(dim=1)
+                hold[pyn, pxn] = h.numpy()
+                col = torch.where(h[:, None], col.detach(), col)
             img[:, pyn, pxn] = col.detach().numpy().T
             Tf[pyn, pxn] = cr["T_final"].detach().numpy()
             nc[pyn, pxn] = cr["n_contrib"].numpy()
@@ -145,6 +207,7 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
         out["n_contrib"].append(nc)
         out["n_incl"].append(ni)
         out["near"].append(near)
+        out["held"].append(hold)
         if need_grad:
             for k, leaf in leaves.items():
                 if leaf.grad is not None:
@@ -153,7 +216,7 @@ def render(scene: Dict[str, np.ndarray], cams: Sequence, sh_degree: int,
     if need_grad:
         if proj_outs:
             torch.autograd.backward(proj_outs, proj_grads)
-        out["grads"] = {k: (g[k].grad.numpy().copy() if g[k].grad is not None
+        out["grads"] = {k: (g[k].grad.numpy().astype(np.float64) if g[k].grad is not None
                             else np.zeros(g[k].shape)) for k in PARAM_KEYS}
     return out
 
@@ -174,10 +237,12 @@ def active_tiles(scene, cams, active: np.ndarray) -> List[List[tuple]]:
 
 
 def local_step_reference(scene, cams, sh_degree, targets, active, loss="l1",
-                         bg=(0.0, 0.0, 0.0)):
+                         bg=(0.0, 0.0, 0.0), dtype=T64, hold_ambiguous: bool = False,
+                         held=None):
     """Full-image gradient restricted to O^t (rows of static Gaussians are
-    zero), plus the full-image render."""
-    r = render(scene, cams, sh_degree, bg, targets, loss, need_grad=True)
+    zero), plus the full-image render (`render` gives the options)."""
+    r = render(scene, cams, sh_degree, bg, targets, loss, need_grad=True, dtype=dtype,
+               hold_ambiguous=hold_ambiguous, held=held)
     for k in PARAM_KEYS:
         r["grads"][k][~active] = 0.0
     return r

@@ -18,6 +18,7 @@ STATUS_NAMES = {0: "CLS_OK", 1: "CLS_ERR_INVALID_ARG", 2: "CLS_ERR_CAPACITY",
                 3: "CLS_ERR_CUDA", 4: "CLS_ERR_TIMEOUT"}
 TILE = 16
 G2_STRIDE = 12
+CLS_SORT_SPIN_LIMIT = 1 << 22
 
 
 class ClsCamera(C.Structure):

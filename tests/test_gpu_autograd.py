@@ -48,7 +48,7 @@ def test_capacity_overflow_replans_and_matches():
     assert rast.batch.capacity >= int(rast.batch.n_pairs.item())
     assert torch.equal(rast.batch.image, want_img)
     torch.testing.assert_close(params.grad, want_grad, rtol=1e-4, atol=1e-9)
-    assert float(loss2) == pytest.approx(float(loss), rel=1e-6)
+    assert float(loss2.detach()) == pytest.approx(float(loss.detach()), rel=1e-6)
     print(f"capacity {planned} -> shrunk -> re-planned {rast.batch.capacity}")
 
 

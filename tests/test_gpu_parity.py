@@ -3,13 +3,21 @@
 Bit-exact: projected centres/radii/depth bits, change votes, the tile mask,
 sorted keys and values, tile ranges. Float: pixels within 1e-4 absolute per
 channel; gradients within 1e-3 relative, |g - g_ref| <= 1e-3 max(|g_ref|,
-floor), floor = 5e-2 x the RMS of the parameter group. Below 5% of the RMS an
-entry is a cancellation of per-pixel terms of up to ~10x RMS size; summing
-~10^3 of them in float32 (unit roundoff 6e-8, error growing like sqrt(n))
-leaves ~2e-5 x RMS of rounding, so those entries are held to 5e-5 x RMS
-absolute. Pixels and Gaussians whose float64 branch sits within a
-relative 1e-4 of a threshold (alpha = 1/255, the T < 1e-4 stop, the 0.99
-clamp) are reported and excluded; their share is asserted to be small.
+floor), floor = GRAD_FLOOR x the RMS of the parameter group.
+
+The floor is measured, not estimated: the oracle's own arithmetic run in
+float32 (`dtype=torch.float32`, the same mathematics rounded to single
+precision) against float64 leaves gaps that need floors of up to 1.5e-2 x RMS
+on these workloads (cancellations of per-pixel terms that float32 cannot
+resolve below ~1e-5 x RMS); each gradient test prints that float32 figure
+beside the GPU's own (the smallest floor under which every GPU entry passes).
+
+Threshold decisions: a pixel where a reached alpha, stop or clamp decision
+sits within 3e-4 relative of its threshold may take the other branch in
+float32. Pixels are compared away from those (at most 1% of them); for the
+gradients every active Gaussian is compared, with the colour of such pixels
+held constant on both sides (the oracle detaches it, the GPU test zeroes dL/dC
+there before the backward pass), so no Gaussian is left out.
 """
 import math
 
@@ -26,7 +34,8 @@ pytestmark = pytest.mark.gpu
 
 PIX_TOL = 1e-4
 GRAD_RTOL = 1e-3
-GRAD_FLOOR = 5e-2
+GRAD_FLOOR = 2e-2
+HELD_MAX = 0.02  # share of rendered pixels held constant for the gradient checks
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,11 +45,12 @@ def _built():
 
 
 def _update(scene, cams, deg, targets=None, active=None, loss="l1", masks=None, layout=1,
-            lazy=True):
+            lazy=True, backward=None):
     from paper_2506_21117_gb300.update import LocalUpdate
     lu = LocalUpdate(scene, cams, deg, targets=targets, active=active, loss=loss, masks=masks,
                      layout=layout, lazy=lazy)
-    lu.render_pass(with_backward=targets is not None, with_adam=False)
+    lu.render_pass(with_backward=targets is not None if backward is None else backward,
+                   with_adam=False)
     torch.cuda.synchronize()
     lu.batch.check_status()
     return lu
@@ -85,28 +95,77 @@ def _small_local(seed=0, n=6000, deg=3, size=(100, 75), views=3, frac=0.05):
     return scene, cams, masks, targets
 
 
-def _compare_grads(lu, ref, active, deg, exclude=(), rows=None):
+def hold_and_backward(batch, held):
+    """Zero dL/dC at the held pixels (per view, [H, W] bools from the
+    oracle) and run the backward pass again from the forward pass's state.
+    Returns the share of rendered pixels held."""
+    dev = batch.dL_dimage.device
+    n_held = 0
+    for (base, H, W), h in zip(batch.view_slices(), held):
+        flat = torch.from_numpy(np.flatnonzero(np.asarray(h, bool).reshape(-1))).to(dev)
+        n_held += int(flat.numel())
+        for c in range(3):
+            batch.dL_dimage[3 * base + c * H * W + flat] = 0.0
+    batch.backward()
+    torch.cuda.synchronize()
+    batch.check_status()
+    rendered = int((batch.tile_active > 0).sum().item()) * 256
+    return n_held / max(rendered, 1)
+
+
+def needed_floor(g, r, rms):
+    """Smallest floor (in units of the group RMS) under which every entry of
+    g passes against r."""
+    over = np.abs(g - r) > GRAD_RTOL * np.abs(r)
+    return float(np.abs(g - r)[over].max() / (GRAD_RTOL * rms)) if over.any() else 0.0
+
+
+def _compare_grads(lu, ref, active, deg, rows=None, ref32=None, label=""):
     """GPU gradient rows of the active set (from the update's buffer, or the
-    given [A][stride] array) against the oracle's."""
+    given [A][stride] array) against the oracle's, every active Gaussian.
+    Prints, per parameter group, the floor the GPU needs and (with `ref32`,
+    the float32 evaluation of the oracle on the same held pixels) the floor
+    float32 arithmetic itself needs. Returns the largest GPU floor."""
     from paper_2506_21117_gb300.update import unpack_rows
     A = int(active.sum())
     if rows is None:
         rows = lu.batch.grads[: A * lu.state.stride].view(A, lu.state.stride).cpu().numpy()
     got = unpack_rows(rows.astype(np.float64), deg)
     idx = np.flatnonzero(active)
-    keep = ~np.isin(idx, np.array(sorted(exclude), dtype=np.int64))
     worst = 0.0
+    report = []
     for k in ostep.PARAM_KEYS:
-        r = ref["grads"][k][idx].reshape(A, -1)[keep]
-        g = got[k].reshape(A, -1)[keep]
+        r = ref["grads"][k][idx].reshape(A, -1)
+        g = got[k].reshape(A, -1)
         rms = math.sqrt(float(np.mean(r * r))) if r.size else 0.0
-        floor = GRAD_FLOOR * rms
-        bound = GRAD_RTOL * np.maximum(np.abs(r), floor)
-        excess = np.abs(g - r) / np.maximum(bound, 1e-30)
-        worst = max(worst, float(excess.max()) if excess.size else 0.0)
+        bound = GRAD_RTOL * np.maximum(np.abs(r), GRAD_FLOOR * rms)
+        f_gpu = needed_floor(g, r, rms)
+        f32 = (needed_floor(ref32["grads"][k][idx].reshape(A, -1), r, rms)
+               if ref32 is not None else float("nan"))
+        report.append(f"{k} {f_gpu:.1e}/{f32:.1e}")
+        worst = max(worst, f_gpu)
         bad = np.argwhere(np.abs(g - r) > bound)
-        assert bad.size == 0, (k, bad[:5].tolist(), g[tuple(bad[0])], r[tuple(bad[0])], floor)
-    return worst, int((~keep).sum())
+        assert bad.size == 0, (k, bad[:5].tolist(), g[tuple(bad[0])], r[tuple(bad[0])],
+                               GRAD_FLOOR * rms)
+    print(f"{label}: {A} active Gaussians, none excluded; floor needed GPU/float32: "
+          + ", ".join(report))
+    return worst
+
+
+def _grad_case(scene, cams, deg, targets, active, loss, label, **kw):
+    """Forward on the GPU, the oracle with ambiguous pixels held (float64 and
+    float32), the GPU backward with the same pixels held, comparison."""
+    lu = _update(scene, cams, deg, targets=targets, active=active, loss=loss, backward=False,
+                 **kw)
+    ref = ostep.local_step_reference(scene, cams, deg, targets, active, loss,
+                                     hold_ambiguous=True)
+    ref32 = ostep.local_step_reference(scene, cams, deg, targets, active, loss,
+                                       dtype=torch.float32, held=ref["held"])
+    share = hold_and_backward(lu.batch, ref["held"])
+    assert share <= HELD_MAX, share
+    _compare_grads(lu, ref, active, deg, ref32=ref32,
+                   label=f"{label} ({100 * share:.2f}% of rendered pixels held)")
+    return lu, ref
 
 
 # ---------------------------------------------------------------- indexing --
@@ -281,59 +340,49 @@ def test_forward_pixels_local_tiles_only():
 
 def test_gradients_plain_l1():
     scene, cams, targets = S.workload_plain()
-    active = np.ones(2000, bool)
-    lu = _update(scene, cams, 0, targets=targets, active=active, loss="l1")
-    ref = ostep.local_step_reference(scene, cams, 0, targets, active, "l1")
-    worst, excl = _compare_grads(lu, ref, active, 0, exclude=ref["near_ids"])
-    print(f"plain L1 gradients: worst error/bound {worst:.3f}, {excl} Gaussians excluded")
-    assert excl <= 0.05 * active.sum()
+    _grad_case(scene, cams, 0, targets, np.ones(2000, bool), "l1", "plain L1")
 
 
 def test_gradients_two_view_l2_sh1():
     scene, cams, targets = S.workload_fd()
-    active = np.ones(500, bool)
-    lu = _update(scene, cams, 1, targets=targets, active=active, loss="l2")
-    ref = ostep.local_step_reference(scene, cams, 1, targets, active, "l2")
-    worst, excl = _compare_grads(lu, ref, active, 1, exclude=ref["near_ids"])
-    print(f"two-view L2 gradients: worst error/bound {worst:.3f}, {excl} excluded")
-    assert excl <= 0.05 * active.sum()
+    _grad_case(scene, cams, 1, targets, np.ones(500, bool), "l2", "two-view L2 SH1")
 
 
-def test_gradients_local_active_set_equal_full_image_gradients():
+@pytest.mark.parametrize("seed", [5, 3, 7])
+def test_gradients_local_active_set_equal_full_image_gradients(seed):
     """Exactness of the local kernel: O^t's gradients from the active tiles
     equal the oracle's full-image, full-scene gradients."""
-    scene, cams, masks, targets = _small_local(seed=5)
+    scene, cams, masks, targets = _small_local(seed=seed)
     active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
-    lu = _update(scene, cams, 3, targets=targets, active=active, loss="l1")
-    ref = ostep.local_step_reference(scene, cams, 3, targets, active, "l1")
-    worst, excl = _compare_grads(lu, ref, active, 3, exclude=ref["near_ids"])
-    print(f"local SH3 gradients: {int(active.sum())} active, worst {worst:.3f}, {excl} excluded")
-    assert excl <= 0.1 * active.sum()
+    _grad_case(scene, cams, 3, targets, active, "l1", f"local SH3 seed {seed}")
 
 
 def test_autograd_function_matches_oracle_gradient():
     """The hand-written adjoint behind torch.autograd.Function: an L2 loss
     written in torch over the rendered images back-propagates through
     cls_render_backward to the oracle's float64 gradient (which is itself
-    pinned by central finite differences)."""
+    pinned by central finite differences). The colours of the pixels with an
+    ambiguous threshold decision are held constant on both sides."""
     from paper_2506_21117_gb300.autograd import ActiveRasterizer
     from paper_2506_21117_gb300.update import SceneState
     scene, cams, targets = S.workload_fd()
     active = np.ones(500, bool)
+    ref = ostep.local_step_reference(scene, cams, 1, targets, active, "l2",
+                                     hold_ambiguous=True)
     st = SceneState(scene, 1)
     st.set_active(active)
     rast = ActiveRasterizer(st, cams)
     params = st.params.requires_grad_(True)
     imgs = rast(params)
     tg = [torch.from_numpy(t).cuda() for t in targets]
+    held = [torch.from_numpy(h).cuda() for h in ref["held"]]
+    imgs = [torch.where(h[None], im.detach(), im) for im, h in zip(imgs, held)]
     loss = sum(((im - t) ** 2).sum() / (3 * im.shape[1] * im.shape[2])
                for im, t in zip(imgs, tg)) / len(imgs)
     loss.backward()
-    ref = ostep.local_step_reference(scene, cams, 1, targets, active, "l2")
-    assert abs(float(loss) - ref["loss"]) <= 1e-5 * ref["loss"]
+    assert abs(float(loss.detach()) - ref["loss"]) <= 1e-5 * ref["loss"]
     rows = params.grad.detach().cpu().numpy()
-    worst, excl = _compare_grads(None, ref, active, 1, exclude=ref["near_ids"], rows=rows)
-    print(f"autograd.Function L2 gradients: worst error/bound {worst:.3f}, {excl} excluded")
+    _compare_grads(None, ref, active, 1, rows=rows, label="autograd.Function L2")
 
 
 def _slab_scene():
@@ -489,10 +538,11 @@ def test_static_prefix_cache_after_active_gaussians_move():
     tl = ostep.active_tiles(moved, cams, active)
     ref = ostep.render(moved, cams, 3, targets=targets, tiles=tl)
     _compare_pixels(lu, ref, cams)
-    gref = ostep.local_step_reference(moved, cams, 3, targets, active, "l1")
-    worst, excl = _compare_grads(lu, gref, active, 3, exclude=gref["near_ids"])
-    print(f"moved: gradients worst error/bound {worst:.3f}, {excl} excluded")
-    assert excl <= 0.05 * active.sum()
+    gref = ostep.local_step_reference(moved, cams, 3, targets, active, "l1",
+                                      hold_ambiguous=True)
+    share = hold_and_backward(b, gref["held"])
+    assert share <= HELD_MAX, share
+    _compare_grads(lu, gref, active, 3, label="moved active Gaussians")
 
 
 # -------------------------------------------------------------------- Adam --

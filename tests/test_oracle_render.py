@@ -315,3 +315,87 @@ def test_local_gradient_equals_full_image_gradient():
         np.testing.assert_allclose(loc["grads"][k][active], full["grads"][k][active],
                                    rtol=1e-12, atol=1e-18)
     assert sum(len(t) for t in tiles) < sum(fx.tiles_of(c)[0] * fx.tiles_of(c)[1] for c in cams)
+
+
+def _fd_case():
+    scene, cams, targets = S.workload_fd()
+    return scene, cams, targets, np.ones(scene["means"].shape[0], bool)
+
+
+def test_held_pixels_split_the_gradient():
+    """Holding pixel colours constant removes exactly their share of the
+    gradient: the L2 loss is a sum over pixels, so the gradient with a set H
+    held plus the gradient with its complement held is the plain gradient;
+    holding nothing changes nothing; holding every pixel gives zero."""
+    scene, cams, targets, active = _fd_case()
+    plain = step.local_step_reference(scene, cams, 1, targets, active, "l2")
+    rng = np.random.default_rng(3)
+    H = [rng.uniform(size=(int(c["height"]), int(c["width"]))) < 0.3 for c in cams]
+    a = step.local_step_reference(scene, cams, 1, targets, active, "l2", held=H)
+    b = step.local_step_reference(scene, cams, 1, targets, active, "l2",
+                                  held=[~h for h in H])
+    none = step.local_step_reference(scene, cams, 1, targets, active, "l2",
+                                     held=[np.zeros_like(h) for h in H])
+    every = step.local_step_reference(scene, cams, 1, targets, active, "l2",
+                                      held=[np.ones_like(h) for h in H])
+    for k in step.PARAM_KEYS:
+        g = plain["grads"][k]
+        scale = np.abs(g).max()
+        np.testing.assert_allclose(a["grads"][k] + b["grads"][k], g, rtol=0, atol=1e-12 * scale)
+        assert np.array_equal(none["grads"][k], g)
+        assert np.abs(every["grads"][k]).max() == 0.0
+        assert np.abs(a["grads"][k] - g).max() > 1e-6 * scale  # the held share is not nothing
+    assert a["loss"] == pytest.approx(plain["loss"], rel=1e-15)
+    assert all(np.array_equal(x, y) for x, y in zip(a["held"], H))
+
+
+def test_ambiguous_pixels_are_those_near_a_threshold():
+    """A pixel is ambiguous exactly when a reached decision sits within the
+    relative margin of its threshold: one Gaussian whose alpha at the pixel is
+    (1/255)(1 + d) is ambiguous for |d| below the margin and not above it."""
+    for d, want in ((1e-5, True), (-2e-4, True), (1e-3, False), (-5e-3, False)):
+        op = 0.5
+        power = math.log((1.0 + d) / 255.0 / op)
+        dx = math.sqrt(-2.0 * power)  # conic A = 1 along x
+        r = composite(_t([5.5 - dx]), _t([5.5]), _t([[1.0, 0.0, 1.0]]), _t([op]),
+                      _t([[0.5, 0.5, 0.5]]), torch.tensor([5]), torch.tensor([5]),
+                      _t([0.0, 0.0, 0.0]), grad_margin=3e-4)
+        assert bool(r["ambiguous"][0]) is want, d
+
+
+def test_truncated_lists_give_the_same_result():
+    """Compositing each tile over the prefix that holds every composited entry
+    gives the same gradients and images as the whole list."""
+    scene, cams, masks, targets = (lambda s: (s[0], s[2], s[3], None))(
+        S.workload_local(n=20000, n_views=2, size=96))
+    targets = [S.random_image(c, 9 + j) for j, c in enumerate(cams)]
+    active = np.zeros(20000, bool)
+    active[::50] = True
+    full = step.local_step_reference(scene, cams, 3, targets, active, "l1")
+    cut = step.render(scene, cams, 3, targets=targets, loss="l1", need_grad=True,
+                      truncate=True)
+    for k in step.PARAM_KEYS:
+        g = full["grads"][k][active]
+        np.testing.assert_allclose(cut["grads"][k][active], g, rtol=0,
+                                   atol=1e-13 * np.abs(g).max())
+    for x, y in zip(full["image"], cut["image"]):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-13)
+    assert all(np.array_equal(x, y) for x, y in zip(full["n_contrib"], cut["n_contrib"]))
+
+
+def test_float32_evaluation_stays_within_float32_rounding():
+    """The oracle's arithmetic in float32 gives pixels within 1e-5 of float64
+    and gradients whose largest gap is a small multiple of float32 rounding of
+    the group's size (and far from float64 agreement), which is what the
+    parity floor is measured with."""
+    scene, cams, targets, active = _fd_case()
+    r64 = step.local_step_reference(scene, cams, 1, targets, active, "l2")
+    r32 = step.local_step_reference(scene, cams, 1, targets, active, "l2",
+                                    dtype=torch.float32)
+    for a, b, n in zip(r64["image"], r32["image"], r64["near"]):
+        assert np.abs(a - b)[:, ~n].max() <= 1e-5
+    for k in step.PARAM_KEYS:
+        g64, g32 = r64["grads"][k], r32["grads"][k]
+        rms = math.sqrt(float(np.mean(g64 * g64)))
+        gap = np.abs(g32 - g64).max() / rms
+        assert 1e-8 < gap < 1e-3, (k, gap)
