@@ -12,7 +12,7 @@ extent, else split into 2 Gaussians sampled from it with scales divided by
 removed, and (after the first opacity reset) those larger than 20 pixels on
 screen or 0.1 x the extent in the world. Here all of it applies to O^t only.
 
-Readings (each also in the design notes): the accumulation takes each view of
+Readings of points the paper leaves open: the accumulation takes each view of
 an iteration as one observation, with the gradient of that view's own loss
 (the iteration's loss is the mean over its n views, so n x its gradient);
 the opacity reset (every 3000 iterations) caps the logit of O^t at

@@ -14,7 +14,7 @@ separately, so nothing is fused), floor/ceil/rint are exact, and exp is the
 Cody-Waite reduction plus a degree-7 Taylor polynomial written out below, so
 that no vendor math routine decides an integer.
 
-Readings of silent points (each also listed in the design notes):
+Readings of points the paper leaves silent:
   * pinhole camera, pixel (i, j) covers [i, i+1) x [j, j+1);
   * near plane z > znear (0.2), otherwise culled / counted outside the image;
   * 2D covariance gets +0.3 on the diagonal; the perspective Jacobian uses the

@@ -12,7 +12,7 @@ point); every drawn point is kept only if it passes the majority vote of
 Sec. 3.2. The new points are then initialised as the base 3DGS method
 initialises a point cloud.
 
-Readings (each also in the design notes):
+Readings of points the paper leaves open:
   * the draws are inputs: per round, uniform numbers in [0, 1) (n x 3 for the
     box, n/5 for the component choice) and standard normals (n/5 x 3), made
     by the seeded input generator, so both implementations consume the same

@@ -9,7 +9,7 @@ with radius 1.1 x the 98th quantile of the members' distances to m_i; Supp.
 ("3DGS Optimization in Changed Regions") removes, every 15 iterations, each
 Gaussian of O^t whose centre lies in no sphere.
 
-Readings (each also in the design notes):
+Readings of points the paper leaves open:
   * clusters: the paper's HDBSCAN (minimum cluster size 1000) is a third-party
     serial algorithm and out of scope; K-Means (Lloyd) stands in, with
     K = min(10, max(1, A // 1000)) for A changed Gaussians (at most one cluster

@@ -43,18 +43,19 @@ struct BwdPixel {
 // clamp) returned in `dpow` with the pixel's dy; the caller turns those into
 // the per-thread sums of the centre, conic and opacity gradients.
 // a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
+// Written without branches: the walk-end and skip decisions select what is
+// kept (a skipped entry has weight exactly zero and leaves T as it was), so
+// the pixels of a thread form independent straight-line chains.
 template <bool ACTIVE>
 __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float t,
                                           const float4& a, const float4& bb, float cb, float* gr,
                                           float& dpow, float& dy) {
-    if (pos >= p.end) return false;
     dy = p.fy - a.y;
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
-    if (power2 > 0.0f) return false;
     const float G = ex2_approx(power2);
     const float alpha = fminf(kAlphaMax, bb.y * G);
-    if (alpha < kAlphaMin) return false;
-    const float w = alpha * p.T;
+    const bool live = pos < p.end && power2 <= 0.0f && alpha >= kAlphaMin;
+    const float w = live ? alpha * p.T : 0.0f;
     p.R0 = __fmaf_rn(-bb.z, w, p.R0);
     p.R1 = __fmaf_rn(-bb.w, w, p.R1);
     p.R2 = __fmaf_rn(-cb, w, p.R2);
@@ -63,13 +64,13 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float 
         const float cg = bb.z * p.g0 + bb.w * p.g1 + cb * p.g2;
         const float gR = p.g0 * p.R0 + p.g1 * p.R1 + p.g2 * p.R2;
         const float dLda = p.T * cg - gR * inv_om;
-        dpow = bb.y * G > kAlphaMax ? 0.f : dLda * alpha;
+        dpow = (live && !(bb.y * G > kAlphaMax)) ? dLda * alpha : 0.f;
         gr[6] += w * p.g0;
         gr[7] += w * p.g1;
         gr[8] += w * p.g2;
     }
-    p.T = p.T * (1.0f - alpha);
-    return true;
+    p.T = live ? p.T * (1.0f - alpha) : p.T;
+    return live;
 }
 
 // Warp reduce-scatter of eight values: after it, lane L holds the warp sum of

@@ -130,25 +130,28 @@ __device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0
     return st;
 }
 
+// One list entry at one pixel, without branches: every quantity is computed
+// and the skip (power > 0, alpha < 1/255), stop (T (1 - alpha) < 1e-4) and done
+// decisions select what is kept, so the two pixels of a thread form
+// independent straight-line chains the compiler can interleave. A skipped or
+// stopped entry adds exactly zero to the colour and leaves T and the last
+// contributor as they were, so the result is the same as with branches.
 __device__ __forceinline__ void composite_one(float dx, float t, float dy, const float4& a,
                                               const float4& bb, float cb, uint32_t pos,
                                               PixelState& ps) {
-    if (ps.done) return;
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
-    if (power2 > 0.0f) return;
     const float alpha = fminf(kAlphaMax, bb.y * ex2_approx(power2));
-    if (alpha < kAlphaMin) return;
     const float test_T = ps.T * (1.0f - alpha);
-    if (test_T < kTMin) {
-        ps.done = true;
-        return;
-    }
-    const float w = alpha * ps.T;
-    ps.c0 += bb.z * w;
-    ps.c1 += bb.w * w;
-    ps.c2 += cb * w;
-    ps.T = test_T;
-    ps.last = pos + 1;
+    const bool live = !ps.done && power2 <= 0.0f && alpha >= kAlphaMin;
+    const bool stop = live && test_T < kTMin;
+    const bool take = live && !stop;
+    const float w = take ? alpha * ps.T : 0.0f;
+    ps.c0 = __fmaf_rn(bb.z, w, ps.c0);
+    ps.c1 = __fmaf_rn(bb.w, w, ps.c1);
+    ps.c2 = __fmaf_rn(cb, w, ps.c2);
+    ps.T = take ? test_T : ps.T;
+    ps.last = take ? pos + 1 : ps.last;
+    ps.done = ps.done || stop;
 }
 
 // Composite staged records k0 .. k1 - 1 into two pixels of one column.

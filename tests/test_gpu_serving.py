@@ -63,15 +63,12 @@ def test_result_alone_equals_result_in_mix():
     assert st["graph_replays"] > 0
     assert r_alone[0].n_active == r_mix[0].n_active > 0
     d = np.abs(p_alone - p_mix)
-    frac_over = float(np.mean(d > 1e-4))
-    print(f"alone vs mix: max |dtheta| {d.max():.2e}, share above 1e-4: {frac_over:.2e}, "
+    print(f"alone vs mix: max |dtheta| {d.max():.2e} over {d.size} parameters, "
           f"loss {r_alone[0].loss:.6f} vs {r_mix[0].loss:.6f}")
-    # the loss of the last iteration agrees within 1e-3 relative; parameters
-    # within 1e-4 except for entries whose gradient sits at rounding level,
-    # where Adam's normalised step may take either sign (bounded by ITERS * 10 lr)
+    # every parameter within 1e-4 (the runs differ only in the order in which
+    # float atomics add the per-tile gradient sums), the loss within 1e-3
+    assert d.max() <= 1e-4
     assert abs(r_alone[0].loss - r_mix[0].loss) <= 1e-3 * abs(r_alone[0].loss)
-    assert frac_over <= 1e-3
-    assert d.max() <= 10 * LR * ITERS
     # the frozen rows did not move in either run
     from paper_2506_21117_gb300.update import pack_params
     rows = pack_params(scenes[0], 3)
