@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--e2e-updates", type=int, default=3)
     p.add_argument("--iters-per-update", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-tiles", type=int, default=4)
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other workloads (plain, local update, FD) and the 1/10%% sweep")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serving-scenes", type=int, default=64)
     p.add_argument("--serving-seconds", type=float, default=30.0,
@@ -235,52 +236,16 @@ def pair_producing_records(bt):
     return total
 
 
-def design_bytes(lu):
-    """Algorithmic DRAM bytes one iteration of this design moves, per stage,
-    from one more pass's own counters (run after the timed region):
-
-      A active Gaussians, V views, N records per view (every Gaussian), R
-      parameter-row bytes (3 + 3 + 4 + 1 + 3 (l+1)^2 floats), Np pair-producing
-      records, E pairs emitted (counted from the key buffer, pre-filled with a
-      value no key takes), S keys in the depth bins the forward pass sorts (the
-      bins from the one holding a tile's walk start to the one holding its last
-      composited entry), F / B list entries the forward / backward pass needs
-      per tile (walk start to the deepest pixel's last contributor; for the
-      backward, to the tile's last active entry), Pf / Pb pixels they walk, Tr
-      rendered tiles, G the summed-area grid entries (per view (Tx+1)(Ty+1)).
-
-      project_and_bin  A V (R + 48 + 16)       rows read, records and packed
-                                               rectangles written
-                       + N V 16 + Np 4         rectangles read by the count,
-                                               work list written
-                       + 3 x 256 G 4           depth-bin grid: clear, stamps,
-                                               prefix pass
-                       + 5 x 256 Tr 4          per (tile, bin) counts, offsets,
-                                               cursors
-                       + Np 20 + 8 E           emission: rectangle + list entry
-                                               read, keys written
-      sort (large bins)  16 per key in a bin above the forward's sort limit
-      render_forward   16 S + 48 F             keys sorted in shared memory and
-                                               written back, records staged
-                       + 64 Pf                 target, image, T, last
-                                               contributor, dL/dC, prefix state
-      render_backward  56 B + 44 Pb            keys and records, pixel state
-                       + A V 48 3 + 2 A R      2D gradients (clear, sum, read),
-                                               parameter rows and gradients
-      adam             A 7 R                   theta, m, v read and written, g read
-    """
+def walk_counts(bt):
+    """Per pass, from its buffers: the list entries the forward pass needs
+    per rendered tile (from the walk start, 0 or the cached prefix end, to the
+    deepest pixel's last contributor; pixels that stopped inside the prefix do
+    not walk), those the backward needs (to min(last contributor, the tile's
+    last active entry + 1)), the pixels each walks, and (bucketed layout) the
+    keys in the depth bins the forward sorts: from the bin holding the walk
+    start to the bin holding its last entry, with those in bins above the
+    renderer's own sort limit counted apart."""
     import torch
-    bt = lu.batch
-    st = lu.state
-    V = bt.n_views
-    A = st.n_active
-    row = 4 * (11 + 3 * (st.sh_degree + 1) ** 2)
-    bt.keys.fill_(-1)
-    lu.render_pass(with_backward=True, with_adam=True)
-    torch.cuda.synchronize()
-    bt.check_status()
-    n = min(int(bt.n_pairs.item()), bt.capacity)
-    E = int((bt.keys[:n] != -1).sum().item())
     nt = int(bt.n_active_tiles.item())
     tiles = bt.active_tiles[:nt].long()
     T = bt.info.total_tiles
@@ -299,21 +264,20 @@ def design_bytes(lu):
     bmax = zero.clone().scatter_reduce(0, tile_of[live], end_b[live], "amax")
     F = int(torch.clamp(fmax[tiles] - start_t[tiles], min=0).sum().item())
     Bn = int(torch.clamp(bmax[tiles] - start_t[tiles], min=0).sum().item())
-    Pf = int(live.sum().item())
+    Pf = int((live & (nc > start_t[tile_of])).sum().item())
     Pb = int((live & (end_b > start_t[tile_of])).sum().item())
-    # keys in the depth bins the forward pass sorts, and the large bins
     S = big = 0
     if bt.layout == 1 and nt:
-        off = bt.bin_offsets[: nt * 256 + 1].long()
+        off = bt.bin_offsets[: nt * 256].long().view(nt, 256)
         rng = bt.ranges.view(T, 2).long()
-        bins = torch.cat([off[:-1].view(nt, 256), rng[tiles, 1:2]], 1)  # [nt, 257]
+        bins = torch.cat([off, rng[tiles, 1:2]], 1)  # [nt, 257] bin starts, then the end
+        walked = fmax[tiles] > start_t[tiles]
         first = rng[tiles, 0] + start_t[tiles]
         last = rng[tiles, 0] + torch.clamp(fmax[tiles], min=1) - 1
-        walked = fmax[tiles] > start_t[tiles]
-        b_lo = torch.searchsorted(bins, first.view(-1, 1), right=True).view(-1) - 1
-        b_hi = torch.searchsorted(bins, last.view(-1, 1), right=True).view(-1) - 1
-        b_lo = b_lo.clamp(0, 255)
-        b_hi = torch.maximum(b_hi.clamp(0, 255), b_lo)
+        b_lo = (torch.searchsorted(bins, first.view(-1, 1), right=True).view(-1) - 1).clamp(0, 255)
+        b_hi = torch.maximum(
+            (torch.searchsorted(bins, last.view(-1, 1), right=True).view(-1) - 1).clamp(0, 255),
+            b_lo)
         lo = bins.gather(1, b_lo.view(-1, 1)).view(-1)
         hi = bins.gather(1, (b_hi + 1).view(-1, 1)).view(-1)
         S = int(torch.where(walked, hi - lo, torch.zeros_like(hi)).sum().item())
@@ -322,6 +286,66 @@ def design_bytes(lu):
         inwin = (k >= b_lo.view(-1, 1)) & (k <= b_hi.view(-1, 1)) & walked.view(-1, 1)
         big = int(torch.where(inwin & (size > abi_lazy_max()), size,
                               torch.zeros_like(size)).sum().item())
+    return {"rendered_tiles": nt, "rendered_pixels": int(on.sum().item()),
+            "forward_entries": F, "backward_entries": Bn,
+            "forward_pixels": Pf, "backward_pixels": Pb, "keys_sorted_by_forward": S,
+            "keys_in_large_bins": big}
+
+
+def design_bytes(lu):
+    """Algorithmic DRAM bytes one iteration of this design moves, per stage,
+    from one more pass's own counters (run after the timed region):
+
+      A active Gaussians, V views, N records per view (every Gaussian), R
+      parameter-row bytes (3 + 3 + 4 + 1 + 3 (l+1)^2 floats), Np pair-producing
+      records, E pairs emitted (counted from the key buffer, pre-filled with a
+      value no key takes), S keys in the depth bins the forward pass sorts (the
+      bins from the one holding a tile's walk start to the one holding its last
+      composited entry), F / B list entries the forward / backward pass needs
+      per tile (walk start to the deepest pixel's last contributor; for the
+      backward, to the tile's last active entry), Pr rendered pixels, Pb those
+      the backward walks, Tr rendered tiles, G the summed-area grid entries
+      (per view (Tx+1)(Ty+1)).
+
+      project_and_bin  A V (R + 48 + 16)       rows read, records and packed
+                                               rectangles written
+                       + N V 16 + Np 4         rectangles read by the count,
+                                               work list written
+                       + 3 x 256 G 4           depth-bin grid: clear, stamps,
+                                               prefix pass
+                       + 5 x 256 Tr 4          per (tile, bin) counts, offsets,
+                                               cursors
+                       + Np 20 + 8 E           emission: rectangle + list entry
+                                               read, keys written
+      sort (large bins)  16 per key in a bin above the forward's sort limit
+      render_forward   16 S + 48 F             keys sorted in shared memory and
+                                               written back, records staged
+                       + 64 Pr                 target, image, T, last
+                                               contributor, dL/dC, prefix state
+      render_backward  56 B + 44 Pb            keys and records, pixel state
+                       + 16 (Pr - Pb)          prefix state of pixels not walked
+                       + A V 48 3 + 2 A R      2D gradients (clear, sum, read),
+                                               parameter rows and gradients
+      adam             A 7 R                   theta, m, v read and written, g read
+    """
+    import torch
+    bt = lu.batch
+    st = lu.state
+    V = bt.n_views
+    A = st.n_active
+    row = 4 * (11 + 3 * (st.sh_degree + 1) ** 2)
+    bt.keys.fill_(-1)
+    lu.render_pass(with_backward=True, with_adam=True)
+    torch.cuda.synchronize()
+    bt.check_status()
+    n = min(int(bt.n_pairs.item()), bt.capacity)
+    E = int((bt.keys[:n] != -1).sum().item())
+    w = walk_counts(bt)
+    nt, F, Bn, Pf, Pb, S, big = (w[k] for k in ("rendered_tiles", "forward_entries",
+                                                "backward_entries", "forward_pixels",
+                                                "backward_pixels", "keys_sorted_by_forward",
+                                                "keys_in_large_bins"))
+    Pr = w["rendered_pixels"]
     Np = pair_producing_records(bt)
     N = sum(bt.scenes[bt.view_tab[j].scene].n for j in range(V))
     G = int(bt.info.total_sat)
@@ -329,15 +353,16 @@ def design_bytes(lu):
         "project_and_bin": A * V * (row + 64) + N * 16 + Np * 4 + 3 * 256 * G * 4 +
         5 * 256 * nt * 4 + Np * 20 + 8 * E,
         "sort_keys": 16 * big,
-        "render_forward": 16 * S + 48 * F + 64 * Pf,
-        "render_backward": 56 * Bn + 44 * Pb + A * V * 48 * 3 + 2 * A * row,
+        "render_forward": 16 * S + 48 * F + 64 * Pr,
+        "render_backward": 56 * Bn + 44 * Pb + 16 * (Pr - Pb) + A * V * 48 * 3 + 2 * A * row,
         "adam_step_active": 7 * A * row,
     }
     counters = {"active": A, "views": V, "records": N, "pair_producing_records": Np,
                 "pairs_emitted": E, "pairs_counted": int(bt.n_pairs.item()),
                 "keys_sorted_by_forward": S, "keys_in_large_bins": big,
                 "forward_entries": F, "backward_entries": Bn, "forward_pixels": Pf,
-                "backward_pixels": Pb, "rendered_tiles": nt, "sat_entries": G,
+                "backward_pixels": Pb, "rendered_pixels": Pr, "rendered_tiles": nt,
+                "sat_entries": G,
                 "row_bytes": row}
     return stages, counters
 
@@ -401,52 +426,87 @@ def setup_workload(args, seed):
 
 # -------------------------------------------------------------- CPU oracle ---
 
-def oracle_sample(scene, cams, targets, active, n_tiles_total, n_tiles, proj_frac=1.0,
-                  seed=0, cache=None):
-    """Time the oracle on a bounded sample of one iteration: the float32 index
-    projection plus the float64 projection with its backward for a fraction of
-    the Gaussians in view 0, and forward+backward of `n_tiles` active tiles of
-    view 0 (over the Gaussians whose rectangles reach them). Extrapolated to
-    every view and every active tile. Returns (seconds per iteration,
-    description)."""
+ORACLE_TILES = 64        # active tiles per oracle sample, drawn over every view
+ORACLE_PROJ_FRAC = 0.05  # share of the Gaussians projected (with backward) per sample
+
+
+def oracle_sample(scene, cams, targets, active, seed=0, cache=None):
+    """Time the float64 oracle, single-threaded, on a bounded sample of one
+    iteration of the workload: the float32 index projection plus the float64
+    projection with its backward for ORACLE_PROJ_FRAC of the Gaussians in
+    every view, and forward + backward (lists cut where every pixel stopped)
+    of ORACLE_TILES active tiles drawn at random over all views, each over
+    the Gaussians whose rectangles reach it. Extrapolated to every Gaussian
+    and every active tile. Returns (seconds per iteration, description). The
+    benchmark's cpu_baseline and the reference arm use this same sample."""
+    import torch
     from oracle import fp32_index as fx
     from oracle import projection as pj
     from oracle import step as ostep
     cache = {} if cache is None else cache
     n = scene["means"].shape[0]
     rng = np.random.default_rng(seed)
-    m = max(1, int(n * proj_frac))
-    sub = {k: v[:m] for k, v in scene.items()}
-    t0 = time.perf_counter()
-    fx.project_index(sub, cams[0])
-    g = pj.scene64(sub, requires_grad=True)
-    P = pj.project(g, cams[0], 3)
-    (P["u"].sum() + P["conic"].sum() + P["rgb"].sum()).backward()
-    t_proj = (time.perf_counter() - t0) * (n / m)
-    if "pidx0" not in cache:  # set-up, not timed
-        cache["pidx0"] = fx.project_index(scene, cams[0])
-        mk = fx.tile_mask(cache["pidx0"], active, cams[0])
-        ys, xs = np.nonzero(mk)
-        cache["tiles0"] = list(zip(xs.tolist(), ys.tolist()))
-    p0, tiles = cache["pidx0"], cache["tiles0"]
-    pick = [tiles[i] for i in rng.choice(len(tiles), size=min(n_tiles, len(tiles)),
-                                          replace=False)]
-    sel = np.zeros(n, bool)
-    for (tx, ty) in pick:
-        sel |= p0["valid"] & (p0["tx0"] <= tx) & (p0["tx1"] >= tx) & (p0["ty0"] <= ty) & \
-            (p0["ty1"] >= ty)
-    subs = {k: v[sel] for k, v in scene.items()}
-    t1 = time.perf_counter()
-    ostep.render(subs, cams[:1], 3, targets=targets[:1], loss="l1", need_grad=True,
-                 tiles=[pick])
-    per_tile = (time.perf_counter() - t1) / max(len(pick), 1)
-    it = len(cams) * t_proj + n_tiles_total * per_tile
-    desc = (f"float64 oracle, one iteration extrapolated from: index+float64 projection with "
-            f"backward of {m} of {n} Gaussians in view 0 (x{n / m:.0f}, x{len(cams)} views) "
-            f"and forward+backward of {len(pick)} active tiles of view 0 over the "
-            f"{int(sel.sum())} Gaussians reaching them (x{n_tiles_total / max(len(pick), 1):.0f} "
-            f"to all {n_tiles_total} active tiles of {len(cams)} views)")
+    if "tiles" not in cache:  # set-up, not timed
+        cache["pidx"] = [fx.project_index(scene, c) for c in cams]
+        cache["tiles"] = []
+        for j, (p, c) in enumerate(zip(cache["pidx"], cams)):
+            ys, xs = np.nonzero(fx.tile_mask(p, active, c))
+            cache["tiles"] += [(j, int(x), int(y)) for x, y in zip(xs, ys)]
+    all_tiles = cache["tiles"]
+    pick = [all_tiles[i] for i in rng.choice(len(all_tiles), size=min(ORACLE_TILES,
+                                                                         len(all_tiles)),
+                                                replace=False)]
+    m = max(1, int(n * ORACLE_PROJ_FRAC))
+    start = int(rng.integers(0, n - m + 1))
+    sub = {k: v[start:start + m] for k, v in scene.items()}
+    threads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        for c in cams:
+            fx.project_index(sub, c)
+            g = pj.scene64(sub, requires_grad=True)
+            P = pj.project(g, c, 3)
+            (P["u"].sum() + P["conic"].sum() + P["rgb"].sum()).backward()
+        t_proj = (time.perf_counter() - t0) * (n / m)
+        t_tiles = 0.0
+        for j in range(len(cams)):
+            mine = [(x, y) for (v, x, y) in pick if v == j]
+            if not mine:
+                continue
+            p = cache["pidx"][j]
+            sel = np.zeros(n, bool)
+            for (tx, ty) in mine:
+                sel |= p["valid"] & (p["tx0"] <= tx) & (p["tx1"] >= tx) & (p["ty0"] <= ty) & \
+                    (p["ty1"] >= ty)
+            subs = {k: v[sel] for k, v in scene.items()}
+            t1 = time.perf_counter()
+            ostep.render(subs, cams[j:j + 1], 3, targets=targets[j:j + 1], loss="l1",
+                         need_grad=True, tiles=[mine], truncate=True)
+            t_tiles += time.perf_counter() - t1
+    finally:
+        torch.set_num_threads(threads)
+    per_tile = t_tiles / max(len(pick), 1)
+    it = t_proj + len(all_tiles) * per_tile
+    desc = (f"float64 oracle on 1 thread, one iteration extrapolated from: index + float64 "
+            f"projection with backward of {m} of {n} Gaussians in each of {len(cams)} views "
+            f"(x{n / m:.0f}) and forward + backward of {len(pick)} active tiles drawn over all "
+            f"views, over the Gaussians reaching them (x{len(all_tiles) / max(len(pick), 1):.0f} "
+            f"to all {len(all_tiles)} active tiles)")
     return it, desc
+
+
+def cpu_fp32_iterations(scene, cams, targets, active, iters=2, loss="l1", sh_degree=3):
+    """The float32 OpenMP CPU baseline (the plain algorithm: every list built
+    and sorted each iteration, active tiles only) on all host cores: `iters`
+    full iterations (forward, backward, masked Adam), timed whole."""
+    from oracle import cpu_baseline as cb
+    b = cb.Baseline(scene, cams, sh_degree, targets, active, loss)
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        b.iteration()
+    dt = time.perf_counter() - t0
+    return iters / dt, os.cpu_count()
 
 
 # ---------------------------------------------------------------- our arm ---
@@ -664,13 +724,134 @@ def run_ours(args, rank, world):
         del lu, bt
         torch.cuda.empty_cache()
         line["serving"] = run_serving(args, seed=rank)
+    if not args.no_configs:
+        line["other_configs"] = run_configs(args)
+        line["active_fraction_sweep"] = run_sweep(args, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import torch as _t
-        sec, desc = oracle_sample(scene, cams, targets, active_np, tiles_on, args.cpu_tiles,
-                                  proj_frac=0.05)
-        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": _t.get_num_threads(),
-                                "kind": "oracle", "sample": desc}
+        sec, desc = oracle_sample(scene, cams, targets, active_np, seed=0)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": desc}
+        rate, cores = cpu_fp32_iterations(scene, cams, targets, active_np, iters=2)
+        line["cpu_fp32_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores,
+            "kind": "float32 OpenMP plain algorithm (oracle/cpu_fp32.cpp)",
+            "sample": "2 full iterations of the benchmark workload (forward, backward, masked "
+                      "Adam; every active tile's list built and sorted each iteration)"}
     return line
+
+
+def _replay_rate(lu, steps: int, warmup: int = 5):
+    """Iterations per second of a captured iteration replayed `steps` times
+    (after `warmup` eager iterations), CUDA events around the replays."""
+    import torch
+    for _ in range(warmup):
+        lu.step()
+    g = lu.capture()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        g.replay()
+    b.record()
+    torch.cuda.synchronize()
+    lu.batch.check_status()
+    ms = a.elapsed_time(b) / steps
+    return {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "replays": steps}
+
+
+def _target_images(scene, cams, sh_degree):
+    """Full renders of a scene with this library (the update's targets)."""
+    import torch
+    from paper_2506_21117_gb300.update import LocalUpdate
+    n = scene["means"].shape[0]
+    t = LocalUpdate(scene, cams, sh_degree, active=np.ones(n, bool), capacity_slack=1.05)
+    t.render_pass(with_backward=False)
+    torch.cuda.synchronize()
+    t.batch.check_status()
+    out = [x.cpu().numpy().copy() for x in t.batch.per_view(t.batch.image, 3)]
+    del t
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_configs(args):
+    """GPU timings of the other workloads, each in the launch configuration
+    of the benchmark (bucketed binning, lazy sort, cached prefix, CUDA-graph
+    replay): the plain render + backward + Adam (2,000 Gaussians, one 64x64
+    view, L1, all active), the local update (100,000 Gaussians, SH 3, eight
+    800x800 views, 5% box: lifting, planning and 30 iterations, wall clock,
+    plus the replay rate), the finite-difference workload (500 Gaussians,
+    SH 1, two 32x32 views, L2, all active)."""
+    import torch
+    from paper_2506_21117_gb300 import synthetic as S
+    from paper_2506_21117_gb300.update import LocalUpdate
+    out = {}
+    scene, cams, targets = S.workload_plain()
+    lu = LocalUpdate(scene, cams, 0, targets=targets, active=np.ones(2000, bool), loss="l1")
+    out["plain_2k_64x64_l1"] = _replay_rate(lu, 500)
+    scene, cams, targets = S.workload_fd()
+    lu = LocalUpdate(scene, cams, 1, targets=targets, active=np.ones(500, bool), loss="l2")
+    out["fd_500_2x32x32_l2"] = _replay_rate(lu, 500)
+    scene, target_scene, cams, masks, _ = S.workload_local(n=100_000, n_views=8, size=800)
+    targets = _target_images(target_scene, cams, 3)
+    LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1").run(3)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
+    lu.run(30)
+    loss = float(lu.batch.loss[0].item())
+    wall = time.perf_counter() - t0
+    rate = _replay_rate(lu, 200, warmup=0)
+    out["local_100k_8x800_30it"] = {
+        "update_wall_ms": wall * 1e3, "iters_per_s_incl_lift_and_plan": 30 / wall,
+        "replay": rate, "active_gaussians": lu.state.n_active,
+        "active_tiles": int(lu.batch.n_active_tiles.item()), "loss_after_30": loss}
+    del lu
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_sweep(args, rank):
+    """The benchmark workload with change boxes holding 1% and 10% of the
+    Gaussians (5% is the headline): replay rate and eager stage times."""
+    import torch
+    from paper_2506_21117_gb300.update import LocalUpdate
+    out = {}
+    for frac in (0.01, 0.10):
+        a = argparse.Namespace(**vars(args))
+        a.fraction = frac
+        scene, target_scene, cams, masks, _ = setup_workload(a, seed=rank)
+        targets = _target_images(target_scene, cams, 3)
+        lu = LocalUpdate(scene, cams, 3, targets=targets, masks=masks, loss="l1")
+        rate = _replay_rate(lu, 100, warmup=10)
+        bt = lu.batch
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        tot = [0.0] * 5
+        for _ in range(20):
+            ev[0].record()
+            bt.project_and_bin(1)
+            ev[1].record()
+            bt.sort()
+            ev[2].record()
+            bt.render(lu.loss_mode, lu.bg)
+            ev[3].record()
+            bt.backward()
+            ev[4].record()
+            bt.adam(lu.lr)
+            ev[5].record()
+            torch.cuda.synchronize()
+            for i in range(5):
+                tot[i] += ev[i].elapsed_time(ev[i + 1]) / 20
+        out[f"{int(round(frac * 100))}%"] = {
+            **rate, "active_gaussians": lu.state.n_active,
+            "active_tiles": int(bt.n_active_tiles.item()),
+            "stages_ms_eager": dict(zip(["project_and_bin", "sort_keys", "render_forward",
+                                          "render_backward", "adam_step_active"], tot))}
+        del lu, bt
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_sphere_region(lu):
@@ -857,15 +1038,12 @@ def run_reference(args, rank, world):
     scene, target_scene, cams, masks, box = setup_workload(args, seed=0)
     c, o = fx.votes(scene["means"], cams, masks)
     active = fx.vote_rule(c, o, len(cams))
-    tiles_total = sum(int(fx.tile_mask(fx.project_index(scene, cam), active, cam).sum())
-                      for cam in cams)
     from paper_2506_21117_gb300 import synthetic as S
     targets = [S.random_image(cam, 0) for cam in cams]
     times = []
     cache = {}
     for k in range(args.warmup + args.steps):
-        sec, desc = oracle_sample(scene, cams, targets, active, tiles_total, 1, proj_frac=0.01,
-                                  seed=k, cache=cache)
+        sec, desc = oracle_sample(scene, cams, targets, active, seed=k, cache=cache)
         if k >= args.warmup:
             times.append(sec)
     sec = sum(times) / len(times)
@@ -874,7 +1052,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": torch.get_num_threads(),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

@@ -199,9 +199,12 @@ int cls_lift_change_masks(const float* params, int32_t n, int32_t row_stride,
  * device that loads the library until the process exits).
  *  - n above CLS_LIFT_STATIC_MAX_N returns CLS_ERR_INVALID_ARG, nothing runs.
  *  - The first call on a device looks the array's device address up
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture. It allocates nothing (no cudaMalloc/cudaFree,
- *    no allocating library routine).
+ *    (cudaGetSymbolAddress) with that device current and keeps it for later
+ *    calls; make that first call before any stream capture. It allocates
+ *    nothing (no cudaMalloc/cudaFree, no allocating library routine).
+ *  - The kept address belongs to the device's current context: after
+ *    cudaDeviceReset on that device it is stale, so do not call this entry
+ *    again in a process that has reset the device.
  *  - All calls share the one array. Each call writes every slot it reads
  *    before reading it, so no clearing is needed, but two calls that overlap
  *    on the GPU (different streams, no ordering between them) race on it and

@@ -137,8 +137,8 @@ __device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0
 // stopped entry adds exactly zero to the colour and leaves T and the last
 // contributor as they were, so the result is the same as with branches.
 __device__ __forceinline__ void composite_one(float dx, float t, float dy, const float4& a,
-                                              const float4& bb, float cb, uint32_t pos,
-                                              PixelState& ps) {
+                                              const float4& bb, float cb, int k,
+                                              PixelState& ps, int& lastk) {
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
     const float alpha = fminf(kAlphaMax, bb.y * ex2_approx(power2));
     const float test_T = ps.T * (1.0f - alpha);
@@ -150,24 +150,29 @@ __device__ __forceinline__ void composite_one(float dx, float t, float dy, const
     ps.c1 = __fmaf_rn(bb.w, w, ps.c1);
     ps.c2 = __fmaf_rn(cb, w, ps.c2);
     ps.T = take ? test_T : ps.T;
-    ps.last = take ? pos + 1 : ps.last;
+    lastk = take ? k : lastk;
     ps.done = ps.done || stop;
 }
 
-// Composite staged records k0 .. k1 - 1 into two pixels of one column.
+// Composite staged records k0 .. k1 - 1 into two pixels of one column. The
+// last contributor is tracked as a staged index and turned into its list
+// position once at the end (one shared load per pixel instead of one per
+// entry).
 __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k1, float fx,
                                                 float fy0, float fy1, PixelState& p0,
                                                 PixelState& p1) {
+    int l0 = -1, l1 = -1;
     for (int k = k0; k < k1 && !(p0.done && p1.done); ++k) {
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
-        const uint32_t pos = sm.pos[k];
         const float dx = fx - a.x;
         const float t = a.z * dx;
-        composite_one(dx, t, fy0 - a.y, a, bb, cb, pos, p0);
-        composite_one(dx, t, fy1 - a.y, a, bb, cb, pos, p1);
+        composite_one(dx, t, fy0 - a.y, a, bb, cb, k, p0, l0);
+        composite_one(dx, t, fy1 - a.y, a, bb, cb, k, p1, l1);
     }
+    if (l0 >= 0) p0.last = sm.pos[l0] + 1;
+    if (l1 >= 0) p1.last = sm.pos[l1] + 1;
 }
 
 __device__ __forceinline__ void save_prefix(const PixelState& ps, const ClsView& view, int px,

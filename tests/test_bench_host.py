@@ -58,3 +58,70 @@ def test_walked_evaluations_brute_force():
                 bwd += max(0, min(nc[p], tc[t, 3] + 1) - start)
     got = bench.walked_evaluations(bt)
     assert got == {"forward": fwd, "backward": bwd, "full_list": full}
+
+
+def _bucketed_fake(seed=1):
+    """A fake bucketed pass: per rendered tile a contiguous key range split in
+    256 depth bins of random sizes, cached prefixes, last contributors."""
+    bt, tc, active, state = _fake_batch(seed)
+    rng = np.random.default_rng(seed + 10)
+    T = bt.info.total_tiles
+    act = bt.active_tiles[: int(bt.n_active_tiles.item())].numpy()
+    sizes = rng.integers(0, 3, (act.size, 256)) * rng.integers(0, 2, (act.size, 256))
+    sizes[rng.uniform(size=sizes.shape) < 0.01] = 1500   # a few bins above the sort limit
+    off = np.concatenate([[0], np.cumsum(sizes.ravel())]).astype(np.int64)
+    ranges = np.zeros((T, 2), np.int64)
+    for r, t in enumerate(act):
+        ranges[t] = off[r * 256], off[(r + 1) * 256]
+    bt.layout = 1
+    bt.bin_offsets = torch.from_numpy(off[:-1].astype(np.int32))
+    bt.ranges = torch.from_numpy(ranges.reshape(-1).astype(np.int32))
+    return bt, tc, active, state, sizes, off
+
+
+def test_walk_counts_brute_force():
+    bt, tc, active, state, sizes, off = _bucketed_fake()
+    nc = bt.n_contrib.numpy().astype(np.int64)
+    act = bt.active_tiles[: int(bt.n_active_tiles.item())].numpy()
+    rank = {int(t): r for r, t in enumerate(act)}
+    fmax, bmax = {}, {}
+    F = Bn = Pr = Pf = Pb = 0
+    for j in range(bt.n_views):
+        v = bt.view_tab[j]
+        for y in range(v.cam.height):
+            for x in range(v.cam.width):
+                p = v.pix_base + y * v.cam.width + x
+                t = v.tile_base + (y // 16) * v.tiles_x + x // 16
+                if t not in active:
+                    continue
+                Pr += 1
+                if state[p, 0] < 0:
+                    continue
+                start = 0 if tc[t, 1] == -1 else tc[t, 1]
+                e_b = min(nc[p], tc[t, 3] + 1)
+                fmax[t] = max(fmax.get(t, 0), nc[p])
+                bmax[t] = max(bmax.get(t, 0), e_b)
+                Pf += nc[p] > start
+                Pb += e_b > start
+    S = big = 0
+    for t in act:
+        t = int(t)
+        start = 0 if tc[t, 1] == -1 else tc[t, 1]
+        F += max(0, fmax.get(t, 0) - start)
+        Bn += max(0, bmax.get(t, 0) - start)
+        if fmax.get(t, 0) <= start:
+            continue
+        r = rank[t]
+        starts = off[r * 256: r * 256 + 256]
+        pos_first = off[r * 256] + start
+        pos_last = off[r * 256] + fmax[t] - 1
+        # the bin holding a position: the last bin that starts at or before it
+        b_lo = max(b for b in range(256) if starts[b] <= pos_first)
+        b_hi = max(b_lo, max(b for b in range(256) if starts[b] <= pos_last))
+        S += int(off[r * 256 + b_hi + 1] - off[r * 256 + b_lo])
+        big += int(sum(sizes[r, b] for b in range(b_lo, b_hi + 1) if sizes[r, b] > 1024))
+    got = bench.walk_counts(bt)
+    assert got == {"rendered_tiles": len(act), "rendered_pixels": Pr, "forward_entries": F,
+                   "backward_entries": Bn, "forward_pixels": Pf, "backward_pixels": Pb,
+                   "keys_sorted_by_forward": S, "keys_in_large_bins": big}
+    assert S > 0 and F > 0
