@@ -344,21 +344,28 @@ SERVING_RESOLUTIONS = [(640, 480), (800, 800), (1280, 720)]
 
 
 def serving_templates(scenes, centres, n_templates: int = 32, seed: int = 0):
-    """Update requests of the serving workload: a scene drawn uniformly, 2-8
-    views on a ring of radius 4 (random phase), one of three resolutions, and a
-    change box around the scene's best-seen cluster holding 1-10% of its
-    Gaussians. Returns dicts with scene, cams, masks (list of H x W uint8)."""
+    """Update requests of the serving workload: a scene drawn uniformly, one of
+    its clusters as the changed region, 2-8 views of it on a ring of radius 3
+    around the cluster centre (random phase, every view looking at the
+    centre, as new photos of a changed spot would), one of three resolutions,
+    and a change box around the centre holding 1-10% of the scene's
+    Gaussians, seen by every view so that lifting finds it. Returns dicts with
+    scene, cams, masks (list of H x W uint8)."""
     rng = np.random.default_rng(seed + 20)
     out = []
     for _ in range(n_templates):
         s = int(rng.integers(0, len(scenes)))
         V = int(rng.integers(2, 9))
         W, H = SERVING_RESOLUTIONS[int(rng.integers(0, len(SERVING_RESOLUTIONS)))]
+        centre = np.asarray(centres[s][int(rng.integers(0, len(centres[s])))], np.float64)
         phase = float(rng.uniform(0, 2 * math.pi))
-        angles = [phase + 2 * math.pi * k / V for k in range(V)]
-        cams = ring_cameras(V, 4.0, W, H, angles=angles)
+        cams = []
+        for k in range(V):
+            a = phase + 2 * math.pi * k / V
+            pos = centre + 3.0 * np.array([math.sin(a), 0.0, -math.cos(a)])
+            cams.append(look_at_camera(pos, centre, W, H))
         frac = float(rng.uniform(0.01, 0.10))
-        box = box_holding_fraction(scenes[s]["means"], change_cluster(centres[s], cams), frac)
+        box = box_holding_fraction(scenes[s]["means"], centre, frac)
         masks = [box_change_mask(c, box) for c in cams]
         out.append({"scene": s, "cams": cams, "masks": masks, "fraction": frac})
     return out

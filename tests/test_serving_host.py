@@ -116,3 +116,17 @@ def test_request_with_nothing_lifted_leaves_without_iterations():
     assert s.advance(1.0) == [] and s.advance(2.0) == []
     assert [r.rid for r in s.advance(3.0)] == [1] and b.status == "ok"
     assert s.empty == [a] and a not in s.finished
+
+
+def test_serving_templates_lift_a_change():
+    """Every update request of the serving workload lifts a non-empty active
+    set: its views surround the changed cluster, so the change box is inside
+    every change mask and the majority vote keeps its Gaussians."""
+    from oracle import fp32_index as fx
+    scenes, centres = S.serving_scenes(6, n_lo=20_000, n_hi=60_000, seed=3)
+    for tp in S.serving_templates(scenes, centres, 8, seed=3):
+        sc = scenes[tp["scene"]]
+        c, o = fx.votes(sc["means"], tp["cams"], tp["masks"])
+        active = fx.vote_rule(c, o, len(tp["cams"]))
+        assert active.sum() >= 0.005 * sc["means"].shape[0]
+        assert all(m.any() for m in tp["masks"])
