@@ -13,8 +13,9 @@
 // holds every pixel within 10 of a covered one); pass 2 blurs a, b, c at the
 // covered tiles' pixels and combines. A block handles one 16 x 16 tile: it
 // loads the 26 x 26 region (5-pixel halo) of every plane it needs at once,
-// then applies the separable 11-tap window, two adjacent outputs per thread
-// and direction so each loaded value serves both.
+// then applies the separable 11-tap window with the taps in registers, one
+// whole row (16 outputs from 26 inputs) or column (16 from 26) per work item,
+// so each value is read from shared memory once per pass.
 #include "common.cuh"
 
 namespace cls {
@@ -25,30 +26,96 @@ constexpr int kReg = kTile + 2 * kSsimR;        // 26 x 26 region
 constexpr float kSsimSigma = 1.5f;
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
-__device__ __forceinline__ void ssim_window(float* w) {
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int k = 0; k < kSsimW; ++k) {
-            const float d = (float)(k - kSsimR);
-            w[k] = expf(-(d * d) / (2.0f * kSsimSigma * kSsimSigma));
-            s += w[k];
-        }
-        for (int k = 0; k < kSsimW; ++k) w[k] /= s;
-    }
-}
-
 // Planar per-view images: channel c of pixel (x, y) of view v.
 __device__ __forceinline__ int64_t plane_index(const ClsView& v, int c, int x, int y) {
     const int64_t plane = (int64_t)v.cam.width * v.cam.height;
     return 3 * v.pix_base + c * plane + (int64_t)y * v.cam.width + x;
 }
 
+// The normalised 11-tap Gaussian window, in registers.
+__device__ __forceinline__ void ssim_taps(float* w) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSsimW; ++k) {
+        const float d = (float)(k - kSsimR);
+        w[k] = expf(-(d * d) / (2.0f * kSsimSigma * kSsimSigma));
+        s += w[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kSsimW; ++k) w[k] /= s;
+}
+
 struct SsimSmem {
-    float w[kSsimW];
-    float r[9][kReg][kReg];       // region planes: x, y of each channel (pass 1); a, b, c (pass 2)
-    float h[3][5][kReg][kTile];   // horizontal sums per channel (5 in pass 1, 3 in pass 2)
+    // region planes: x, y of each channel (pass 1); a, b, c of each channel
+    // (pass 2); after the horizontal sums, the vertical sums of the 16 x 16
+    // tile (15 planes in pass 1, 9 in pass 2) are written over them
+    float r[9][kReg][kReg];
+    float h[15][kReg][kTile];     // horizontal sums: 5 per channel (pass 1), 3 (pass 2)
     float red[8];
 };
+
+// Vertical sums of the tile written over the region planes: plane q, row i, col j.
+__device__ __forceinline__ float& vsum(SsimSmem& sm, int q, int i, int j) {
+    return (&sm.r[0][0][0])[(q * kTile + i) * kTile + j];
+}
+
+// One row of 26 inputs to 16 window sums, in registers.
+__device__ __forceinline__ void blur16(const float* in, const float* w, float* out) {
+#pragma unroll
+    for (int o = 0; o < kTile; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < kSsimW; ++k) acc = __fmaf_rn(w[k], in[o + k], acc);
+        out[o] = acc;
+    }
+}
+
+// Horizontal pass: item (plane p of the kNP planes of h, region row), the
+// 26 inputs of the row read once. Pass 1 (kNP = 15): p = 5 c + q with q in
+// x, y, x^2, y^2, x y of channel c; pass 2 (kNP = 9): p = 3 c + q, the a, b,
+// c planes as loaded.
+template <int kNP>
+__device__ __forceinline__ void blur_rows(SsimSmem& sm, const float* w) {
+    for (int e = threadIdx.x; e < kNP * kReg; e += blockDim.x) {
+        const int p = e / kReg, row = e - p * kReg;
+        float in[kReg];
+        if (kNP == 15) {
+            const int c = p / 5, q = p - 5 * c;
+            const float* xr = &sm.r[2 * c][row][0];
+            const float* yr = &sm.r[2 * c + 1][row][0];
+#pragma unroll
+            for (int k = 0; k < kReg; ++k) {
+                const float xv = xr[k];
+                const float yv = (q == 1 || q >= 3) ? yr[k] : 0.f;
+                in[k] = q == 0 ? xv : q == 1 ? yv : q == 2 ? xv * xv : q == 3 ? yv * yv : xv * yv;
+            }
+        } else {
+            const float* vr = &sm.r[p][row][0];
+#pragma unroll
+            for (int k = 0; k < kReg; ++k) in[k] = vr[k];
+        }
+        float out[kTile];
+        blur16(in, w, out);
+#pragma unroll
+        for (int o = 0; o < kTile; ++o) sm.h[p][row][o] = out[o];
+    }
+}
+
+// Vertical pass: item (plane, column), the 26 horizontal sums of the column
+// read once, the 16 results written to vsum (over the region planes).
+template <int kNP>
+__device__ __forceinline__ void blur_cols(SsimSmem& sm, const float* w) {
+    for (int e = threadIdx.x; e < kNP * kTile; e += blockDim.x) {
+        const int p = e / kTile, j = e - p * kTile;
+        float in[kReg];
+#pragma unroll
+        for (int k = 0; k < kReg; ++k) in[k] = sm.h[p][k][j];
+        float out[kTile];
+        blur16(in, w, out);
+#pragma unroll
+        for (int i = 0; i < kTile; ++i) vsum(sm, p, i, j) = out[i];
+    }
+}
 
 __device__ __forceinline__ float block_sum(SsimSmem& sm, float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -75,70 +142,6 @@ __device__ __forceinline__ void load_region(SsimSmem& sm, int np, int x0, int y0
     }
 }
 
-// Horizontal 11-tap sums, two adjacent outputs per work item (12 loads per
-// input plane instead of 22). Pass 1 (NQ = 5): from x, y of a channel,
-// sums of x, y, x^2, y^2, x y; pass 2 (NQ = 3): sums of a, b, c.
-template <int NQ>
-__device__ __forceinline__ void blur_rows_all(SsimSmem& sm) {
-    constexpr int kItems = 3 * kReg * (kTile / 2);
-    for (int e = threadIdx.x; e < kItems; e += blockDim.x) {
-        const int c = e / (kReg * (kTile / 2)), rem = e - c * kReg * (kTile / 2);
-        const int row = rem / (kTile / 2), j = 2 * (rem - row * (kTile / 2));
-        if (NQ == 5) {
-            const float* xr = &sm.r[2 * c][row][j];
-            const float* yr = &sm.r[2 * c + 1][row][j];
-            float s[2][5] = {};
-#pragma unroll
-            for (int k = 0; k <= kSsimW; ++k) {
-                const float xv = xr[k], yv = yr[k];
-                const float xx = xv * xv, yy = yv * yv, xy = xv * yv;
-                if (k < kSsimW) {
-                    const float w = sm.w[k];
-                    s[0][0] += w * xv; s[0][1] += w * yv; s[0][2] += w * xx;
-                    s[0][3] += w * yy; s[0][4] += w * xy;
-                }
-                if (k > 0) {
-                    const float w = sm.w[k - 1];
-                    s[1][0] += w * xv; s[1][1] += w * yv; s[1][2] += w * xx;
-                    s[1][3] += w * yy; s[1][4] += w * xy;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                sm.h[c][q][row][j] = s[0][q];
-                sm.h[c][q][row][j + 1] = s[1][q];
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float* vr = &sm.r[3 * c + q][row][j];
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int k = 0; k <= kSsimW; ++k) {
-                    const float v = vr[k];
-                    if (k < kSsimW) s0 += sm.w[k] * v;
-                    if (k > 0) s1 += sm.w[k - 1] * v;
-                }
-                sm.h[c][q][row][j] = s0;
-                sm.h[c][q][row][j + 1] = s1;
-            }
-        }
-    }
-}
-
-// Vertical 11-tap sums of quantity q of channel c at rows i, i + 1, column j.
-__device__ __forceinline__ void blur_col2(const SsimSmem& sm, int c, int q, int i, int j,
-                                          float& o0, float& o1) {
-    o0 = 0.f;
-    o1 = 0.f;
-#pragma unroll
-    for (int k = 0; k <= kSsimW; ++k) {
-        const float v = sm.h[c][q][i + k][j];
-        if (k < kSsimW) o0 += sm.w[k] * v;
-        if (k > 0) o1 += sm.w[k - 1] * v;
-    }
-}
-
 // Pass 1: S, a, b, c at every pixel of every rendered tile; lambda (1 - S)
 // summed into the loss over the covered tiles' pixels.
 __global__ void __launch_bounds__(kTilePixels)
@@ -148,7 +151,8 @@ ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
                  float* __restrict__ abc, float* __restrict__ loss_per_scene) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SsimSmem& sm = *reinterpret_cast<SsimSmem*>(smem_raw);
-    ssim_window(sm.w);
+    float w[kSsimW];
+    ssim_taps(w);
     const int n = *n_tiles;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int tile = tiles[t];
@@ -165,37 +169,34 @@ ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
                         return ((q & 1) ? yi : xi)[(q >> 1) * plane + off];
                     });
         __syncthreads();
-        blur_rows_all<5>(sm);
+        blur_rows<15>(sm, w);
+        __syncthreads();
+        blur_cols<15>(sm, w);
         __syncthreads();
         float lsum = 0.f;
-        // vertical sums and the maps: (channel, column, row pair) items
-        for (int e = threadIdx.x; e < 3 * kTile * (kTile / 2); e += blockDim.x) {
-            const int c = e / (kTile * (kTile / 2)), rem = e - c * kTile * (kTile / 2);
-            const int i = 2 * (rem / kTile), j = rem - (rem / kTile) * kTile;
-            float v[5][2];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) blur_col2(sm, c, q, i, j, v[q][0], v[q][1]);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int px = tx * kTile + j, py = ty * kTile + i + u;
-                if (!(px < W && py < H)) continue;
-                const float mx = v[0][u], my = v[1][u];
-                const float vx = v[2][u] - mx * mx, vy = v[3][u] - my * my,
-                            cxy = v[4][u] - mx * my;
-                const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-                const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-                const float D = B1 * B2;
-                const float S = A1 * A2 / D;
-                const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
-                const float dvx = -S / B2;
-                const float dcxy = 2.f * A1 / D;
-                const int64_t base = 9 * view.pix_base + (int64_t)(3 * c) * plane +
-                                     (int64_t)py * W + px;
-                abc[base] = dmu - 2.f * mx * dvx - my * dcxy;
-                abc[base + plane] = dvx;
-                abc[base + 2 * plane] = dcxy;
-                lsum += 1.f - S;
-            }
+        // the maps: (channel, row, column) items
+        for (int e = threadIdx.x; e < 3 * kTilePixels; e += blockDim.x) {
+            const int c = e / kTilePixels, rem = e - c * kTilePixels;
+            const int i = rem / kTile, j = rem - i * kTile;
+            const int px = tx * kTile + j, py = ty * kTile + i;
+            if (!(px < W && py < H)) continue;
+            const float mx = vsum(sm, 5 * c, i, j), my = vsum(sm, 5 * c + 1, i, j);
+            const float vx = vsum(sm, 5 * c + 2, i, j) - mx * mx;
+            const float vy = vsum(sm, 5 * c + 3, i, j) - my * my;
+            const float cxy = vsum(sm, 5 * c + 4, i, j) - mx * my;
+            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+            const float D = B1 * B2;
+            const float S = A1 * A2 / D;
+            const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
+            const float dvx = -S / B2;
+            const float dcxy = 2.f * A1 / D;
+            const int64_t base = 9 * view.pix_base + (int64_t)(3 * c) * plane +
+                                 (int64_t)py * W + px;
+            abc[base] = dmu - 2.f * mx * dvx - my * dcxy;
+            abc[base + plane] = dvx;
+            abc[base + 2 * plane] = dcxy;
+            lsum += 1.f - S;
         }
         const bool covered = tile_active[tile] == 1;
         const float tot = block_sum(sm, covered ? lsum : 0.f);
@@ -215,7 +216,8 @@ ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
                  float* __restrict__ loss_per_scene) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SsimSmem& sm = *reinterpret_cast<SsimSmem*>(smem_raw);
-    ssim_window(sm.w);
+    float w[kSsimW];
+    ssim_taps(w);
     const int n = *n_tiles;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const int tile = tiles[t];
@@ -230,25 +232,22 @@ ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
         load_region(sm, 9, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
                     [&](int q, int64_t off) { return m[q * plane + off]; });
         __syncthreads();
-        blur_rows_all<3>(sm);
+        blur_rows<9>(sm, w);
+        __syncthreads();
+        blur_cols<9>(sm, w);
         __syncthreads();
         float lsum = 0.f;
-        for (int e = threadIdx.x; e < 3 * kTile * (kTile / 2); e += blockDim.x) {
-            const int c = e / (kTile * (kTile / 2)), rem = e - c * kTile * (kTile / 2);
-            const int i = 2 * (rem / kTile), j = rem - (rem / kTile) * kTile;
-            float g[3][2];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) blur_col2(sm, c, q, i, j, g[q][0], g[q][1]);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int px = tx * kTile + j, py = ty * kTile + i + u;
-                if (!(px < W && py < H)) continue;
-                const int64_t idx = plane_index(view, c, px, py);
-                const float xv = image[idx], yv = target[idx];
-                const float gs = g[0][u] + 2.f * xv * g[1][u] + yv * g[2][u];
-                dL_dimage[idx] = (1.f - lambda) * dL_dimage[idx] - lambda * view.loss_scale * gs;
-                lsum += fabsf(xv - yv);
-            }
+        for (int e = threadIdx.x; e < 3 * kTilePixels; e += blockDim.x) {
+            const int c = e / kTilePixels, rem = e - c * kTilePixels;
+            const int i = rem / kTile, j = rem - i * kTile;
+            const int px = tx * kTile + j, py = ty * kTile + i;
+            if (!(px < W && py < H)) continue;
+            const int64_t idx = plane_index(view, c, px, py);
+            const float xv = image[idx], yv = target[idx];
+            const float gs = vsum(sm, 3 * c, i, j) + 2.f * xv * vsum(sm, 3 * c + 1, i, j) +
+                             yv * vsum(sm, 3 * c + 2, i, j);
+            dL_dimage[idx] = (1.f - lambda) * dL_dimage[idx] - lambda * view.loss_scale * gs;
+            lsum += fabsf(xv - yv);
         }
         const float tot = block_sum(sm, lsum);
         if (threadIdx.x == 0 && loss_per_scene)
