@@ -207,6 +207,7 @@ tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
     int32_t* S = sat + view.sat_base;
     const int p = smem_pitch(Tx);
     if ((int64_t)Ty * p * 4 <= smem_cap) {
+#pragma unroll 8
         for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
             const int y = t / Tx, x = t - y * Tx;
             s_grid[y * p + x] = D[(int64_t)y * Wd + x];
@@ -535,12 +536,14 @@ bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins
         }
         return;
     }
+#pragma unroll 8
     for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
         const int y = t / Tx, x = t - y * Tx;
         s_grid[y * p + x] = G[(int64_t)y * Wd + x];
     }
     __syncthreads();
     prefix2d_smem(s_grid, Ty, Tx, p);
+#pragma unroll 8
     for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
         const int r = rank[t];
         if (r >= 0) {
@@ -661,15 +664,26 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
 // cut 0). One block per view.
 constexpr int kRowLevels = 16;  // tiles per row < 2^16
 
+// Whether the emission kernel builds a view's row tables in its own shared
+// memory (`smem_bytes` of it: rank, cut and first bin per tile, then the
+// levels); views whose tables do not fit use the global ones that
+// bin_window_tables_kernel writes.
+__host__ __device__ __forceinline__ bool emit_tables_fit(int64_t nt, int Tx, int64_t smem_bytes) {
+    int levels = 0;
+    while ((1 << levels) <= Tx) ++levels;  // 2^(levels - 1) <= Tx < 2^levels
+    return nt * (6 + 2 * (int64_t)levels) <= smem_bytes;
+}
+
 __global__ void __launch_bounds__(1024)
 bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ tile_rank,
                          const uint8_t* __restrict__ front, const uint8_t* __restrict__ cut,
                          uint8_t* __restrict__ t_front, uint8_t* __restrict__ t_cut,
-                         int64_t total_tiles, int smem_cap) {
+                         int64_t total_tiles, int smem_cap, int emit_smem) {
     extern __shared__ uint8_t s_tab[];
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x, nt = Tx * view.tiles_y;
     const int64_t tb = view.tile_base;
+    if (emit_tables_fit(nt, Tx, emit_smem)) return;  // the emission builds them itself
     const int levels = 32 - __clz(Tx);  // 2^(levels - 1) <= Tx
     if ((int64_t)levels * nt * 2 <= smem_cap) {
         uint8_t* sf = s_tab;
@@ -780,14 +794,29 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const uint4* __restrict_
     const uint8_t* tf = t_front + view.tile_base;
     const uint8_t* tc = t_cut + view.tile_base;
     int64_t level_stride = total_tiles;
-    if ((int64_t)nt * (6 + 2 * levels) <= smem_bytes) {
+    if (emit_tables_fit(nt, Tx, smem_bytes)) {
+        // the row sparse tables of the view, built here in shared memory
+        // (level 0: first emitted bin / cut of rendered tiles, neutral 255 / 0
+        // elsewhere; level l: min / max over runs of 2^l tiles)
         uint8_t* s_tf = s_front + nt;
         uint8_t* s_tc = s_tf + (int64_t)levels * nt;
-        for (int l = 0; l < levels; ++l)
+        __syncthreads();
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const bool on = s_rank[i] >= 0;
+            s_tf[i] = on ? s_front[i] : (uint8_t)255;
+            s_tc[i] = on ? s_cut[i] : (uint8_t)0;
+        }
+        for (int l = 1; l < levels; ++l) {
+            __syncthreads();
+            const int h = 1 << (l - 1);
+            const int prev = (l - 1) * nt, cur = l * nt;
             for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-                s_tf[l * nt + i] = t_front[(int64_t)l * total_tiles + view.tile_base + i];
-                s_tc[l * nt + i] = t_cut[(int64_t)l * total_tiles + view.tile_base + i];
+                const int x = i % Tx;
+                if (x + 2 * h > Tx) continue;
+                s_tf[cur + i] = min(s_tf[prev + i], s_tf[prev + i + h]);
+                s_tc[cur + i] = max(s_tc[prev + i], s_tc[prev + i + h]);
             }
+        }
         tf = s_tf;
         tc = s_tc;
         level_stride = nt;
@@ -1087,10 +1116,11 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
             bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
-        bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
-            views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024);
         // shared memory for the tables of views up to 2^8 tiles wide
         const int emit_smem = (int)hmin64(max_view_tiles * (6 + 2 * 8), 200 * 1024);
+        bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
+            views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024,
+            emit_smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
                                                       kEmitThreads, (size_t)emit_smem);

@@ -69,7 +69,7 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float 
         gr[7] += w * p.g1;
         gr[8] += w * p.g2;
     }
-    p.T = live ? p.T * (1.0f - alpha) : p.T;
+    p.T -= w;  // T (1 - alpha) as the forward pass forms it: T - alpha T
     return live;
 }
 

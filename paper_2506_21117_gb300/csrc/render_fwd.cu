@@ -141,15 +141,16 @@ __device__ __forceinline__ void composite_one(float dx, float t, float dy, const
                                               PixelState& ps, int& lastk) {
     const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
     const float alpha = fminf(kAlphaMax, bb.y * ex2_approx(power2));
-    const float test_T = ps.T * (1.0f - alpha);
+    const float wa = alpha * ps.T;       // the entry's weight if composited
+    const float test_T = ps.T - wa;      // T (1 - alpha)
     const bool live = !ps.done && power2 <= 0.0f && alpha >= kAlphaMin;
     const bool stop = live && test_T < kTMin;
     const bool take = live && !stop;
-    const float w = take ? alpha * ps.T : 0.0f;
+    const float w = take ? wa : 0.0f;
     ps.c0 = __fmaf_rn(bb.z, w, ps.c0);
     ps.c1 = __fmaf_rn(bb.w, w, ps.c1);
     ps.c2 = __fmaf_rn(cb, w, ps.c2);
-    ps.T = take ? test_T : ps.T;
+    ps.T -= w;
     lastk = take ? k : lastk;
     ps.done = ps.done || stop;
 }

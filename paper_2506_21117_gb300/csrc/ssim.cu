@@ -83,11 +83,27 @@ __device__ __forceinline__ void blur_rows(SsimSmem& sm, const float* w) {
             const int c = p / 5, q = p - 5 * c;
             const float* xr = &sm.r[2 * c][row][0];
             const float* yr = &sm.r[2 * c + 1][row][0];
+            // one specialised loop per quantity (q is uniform over the item)
+            switch (q) {
+                case 0:
 #pragma unroll
-            for (int k = 0; k < kReg; ++k) {
-                const float xv = xr[k];
-                const float yv = (q == 1 || q >= 3) ? yr[k] : 0.f;
-                in[k] = q == 0 ? xv : q == 1 ? yv : q == 2 ? xv * xv : q == 3 ? yv * yv : xv * yv;
+                    for (int k = 0; k < kReg; ++k) in[k] = xr[k];
+                    break;
+                case 1:
+#pragma unroll
+                    for (int k = 0; k < kReg; ++k) in[k] = yr[k];
+                    break;
+                case 2:
+#pragma unroll
+                    for (int k = 0; k < kReg; ++k) in[k] = xr[k] * xr[k];
+                    break;
+                case 3:
+#pragma unroll
+                    for (int k = 0; k < kReg; ++k) in[k] = yr[k] * yr[k];
+                    break;
+                default:
+#pragma unroll
+                    for (int k = 0; k < kReg; ++k) in[k] = xr[k] * yr[k];
             }
         } else {
             const float* vr = &sm.r[p][row][0];
