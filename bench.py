@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--e2e-updates", type=int, default=3)
     p.add_argument("--iters-per-update", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-configs", action="store_true",
+                   help="time the CPU oracle and the float32 CPU baseline on the plain, "
+                        "local-update and FD workloads in full (no GPU needed) and exit")
     p.add_argument("--no-configs", action="store_true",
                    help="skip the other workloads (plain, local update, FD) and the 1/10%% sweep")
     p.add_argument("--no-serving", action="store_true")
@@ -501,12 +504,13 @@ def cpu_fp32_iterations(scene, cams, targets, active, iters=2, loss="l1", sh_deg
     and sorted each iteration, active tiles only) on all host cores: `iters`
     full iterations (forward, backward, masked Adam), timed whole."""
     from oracle import cpu_baseline as cb
-    b = cb.Baseline(scene, cams, sh_degree, targets, active, loss)
+    cores = os.cpu_count() or 1
+    b = cb.Baseline(scene, cams, sh_degree, targets, active, loss, threads=cores)
     t0 = time.perf_counter()
     for _ in range(iters):
         b.iteration()
     dt = time.perf_counter() - t0
-    return iters / dt, os.cpu_count()
+    return iters / dt, cores
 
 
 # ---------------------------------------------------------------- our arm ---
@@ -1010,7 +1014,8 @@ def run_e2e(args, lu, targets, masks, cams):
     """End to end through the public update API: every step is one scene update
     on the resident scene: pinned host targets and masks copied to the device,
     change-mask lifting, planning, `iters_per_update` iterations, the loss read
-    back to the host."""
+    back to the host. Successive updates of the same scene and views reuse the
+    previous update's batch (`LocalUpdate.from_resident(reuse=...)`)."""
     import torch
     from paper_2506_21117_gb300.update import LocalUpdate
     tg = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets])).pin_memory()
@@ -1020,8 +1025,10 @@ def run_e2e(args, lu, targets, masks, cams):
     its = args.iters_per_update
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    u = None
     for _ in range(args.e2e_updates):
-        u = LocalUpdate.from_resident(state, cams, tg, mk, loss="l1")
+        # each update takes over the previous one's batch (same scene, same views)
+        u = LocalUpdate.from_resident(state, cams, tg, mk, loss="l1", reuse=u)
         u.run(its)
         loss = float(u.batch.loss[0].item())
     torch.cuda.synchronize()
@@ -1029,6 +1036,51 @@ def run_e2e(args, lu, targets, masks, cams):
     return {"value": args.e2e_updates * its / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": 4, "step": f"one scene update of {its} iterations",
             "loss": loss}
+
+
+def run_cpu_configs(args):
+    """The float64 oracle on one thread and the float32 OpenMP baseline on all
+    host cores, on the other workloads, in full: the plain render + backward
+    (2,000 Gaussians, 64x64, L1), the finite-difference workload (500
+    Gaussians, two 32x32 views, L2), and the 100k local update (8 views of
+    800x800; the oracle one iteration over the tiles O^t touches, whose
+    gradients equal the full image's; the baseline all 30 iterations)."""
+    import torch
+    from oracle import fp32_index as fx
+    from oracle import step as ostep
+    from paper_2506_21117_gb300 import synthetic as S
+    out = {}
+    torch.set_num_threads(1)
+
+    def oracle_time(scene, cams, deg, targets, active, loss, tiles=None):
+        t0 = time.perf_counter()
+        ostep.render(scene, cams, deg, targets=targets, loss=loss, need_grad=True, tiles=tiles,
+                     truncate=True)
+        return time.perf_counter() - t0
+
+    scene, cams, targets = S.workload_plain()
+    act = np.ones(2000, bool)
+    t = oracle_time(scene, cams, 0, targets, act, "l1")
+    r, cores = cpu_fp32_iterations(scene, cams, targets, act, iters=20, sh_degree=0)
+    out["plain_2k_64x64_l1"] = {"oracle_s_per_iter": t, "fp32_iters_per_s": r}
+    scene, cams, targets = S.workload_fd()
+    act = np.ones(500, bool)
+    t = oracle_time(scene, cams, 1, targets, act, "l2")
+    r, _ = cpu_fp32_iterations(scene, cams, targets, act, iters=20, loss="l2", sh_degree=1)
+    out["fd_500_2x32x32_l2"] = {"oracle_s_per_iter": t, "fp32_iters_per_s": r}
+    scene, _, cams, masks, _ = S.workload_local(n=100_000, n_views=8, size=800)
+    targets = [S.random_image(c, 90 + j) for j, c in enumerate(cams)]
+    act = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
+    tiles = ostep.active_tiles(scene, cams, act)
+    t = oracle_time(scene, cams, 3, targets, act, "l1", tiles=tiles)
+    r, _ = cpu_fp32_iterations(scene, cams, targets, act, iters=30)
+    out["local_100k_8x800"] = {"oracle_s_per_iter": t,
+                               "oracle_note": "one iteration over the tiles O^t touches",
+                               "fp32_iters_per_s": r, "fp32_note": "30 iterations",
+                               "active_gaussians": int(act.sum()),
+                               "active_tiles": int(sum(len(x) for x in tiles))}
+    return {"cpu_configs": out, "oracle_cores": 1, "fp32_cores": cores,
+            "host_cpu_count": os.cpu_count()}
 
 
 def run_reference(args, rank, world):
@@ -1061,6 +1113,10 @@ def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.cpu_configs:
+        if rank == 0:
+            print(json.dumps(run_cpu_configs(args)))
+        return 0
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -856,7 +856,11 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const uint4* __restrict_
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int wdt = x1 - x0 + 1;
+        // the item's fields a cell needs, packed so a cell fetches them from
+        // its owner in three shuffles (tile coordinates, widths < 2^16, bin < 2^8)
+        const int start = incl - area;
+        const uint32_t xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
+        const uint32_t wb = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
         // kU cells per lane per round, so kU slot claims are in flight before
         // the first key is stored
         constexpr int kU = 8;
@@ -874,17 +878,16 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const uint4* __restrict_
                     if (pm > c) h = mid; else l = mid + 1;
                 }
                 const int own = l;
-                const int o_incl = __shfl_sync(0xffffffffu, incl, own);
-                const int o_area = __shfl_sync(0xffffffffu, area, own);
-                const int o_x0 = __shfl_sync(0xffffffffu, x0, own);
-                const int o_y0 = __shfl_sync(0xffffffffu, y0, own);
-                const int o_w = __shfl_sync(0xffffffffu, wdt, own);
-                const int o_bin = __shfl_sync(0xffffffffu, bin, own);
+                const int o_start = __shfl_sync(0xffffffffu, start, own);
+                const uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
+                const uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
                 kz[u] = __shfl_sync(0xffffffffu, zb, own);
                 kr[u] = __shfl_sync(0xffffffffu, rec, own);
+                const int o_x0 = (int)(o_xy & 0xffffu), o_y0 = (int)(o_xy >> 16);
+                const int o_w = (int)(o_wb & 0xffffu), o_bin = (int)(o_wb >> 16);
                 sub[u] = -1;
                 if (c < total) {
-                    const int k = c - (o_incl - o_area);
+                    const int k = c - o_start;
                     int q, rem;
                     divmod_small(k, o_w, q, rem);
                     const int cell = (o_y0 + q) * Tx + o_x0 + rem;

@@ -11,8 +11,9 @@
 // b = dS/dsigma_x^2, c = dS/dsigma_xy. Pass 1 computes S, a, b, c at every
 // pixel of every rendered tile (covered tiles and the ring around them, which
 // holds every pixel within 10 of a covered one); pass 2 blurs a, b, c at the
-// covered tiles' pixels and combines. A block handles one 16 x 16 tile: it
-// loads the 26 x 26 region (5-pixel halo) of every plane it needs at once,
+// covered tiles' pixels and combines. A 128-thread block handles one 16 x 16
+// tile, one channel at a time (small shared memory, many blocks per SM): it
+// loads the channel's 26 x 26 region (5-pixel halo) of every plane it needs,
 // then applies the separable 11-tap window with the taps in registers, one
 // whole row (16 outputs from 26 inputs) or column (16 from 26) per work item,
 // so each value is read from shared memory once per pass.
@@ -45,13 +46,15 @@ __device__ __forceinline__ void ssim_taps(float* w) {
     for (int k = 0; k < kSsimW; ++k) w[k] /= s;
 }
 
+constexpr int kSsimThreads = 128;
+
+// One channel at a time: region planes x, y (pass 1) or a, b, c (pass 2) of
+// the channel; after the horizontal sums, the vertical sums of the 16 x 16
+// tile (5 planes in pass 1, 3 in pass 2) are written over them.
 struct SsimSmem {
-    // region planes: x, y of each channel (pass 1); a, b, c of each channel
-    // (pass 2); after the horizontal sums, the vertical sums of the 16 x 16
-    // tile (15 planes in pass 1, 9 in pass 2) are written over them
-    float r[9][kReg][kReg];
-    float h[15][kReg][kTile];     // horizontal sums: 5 per channel (pass 1), 3 (pass 2)
-    float red[8];
+    float r[3][kReg][kReg];
+    float h[5][kReg][kTile];      // horizontal sums: 5 (pass 1), 3 (pass 2)
+    float red[kSsimThreads / 32];
 };
 
 // Vertical sums of the tile written over the region planes: plane q, row i, col j.
@@ -71,20 +74,19 @@ __device__ __forceinline__ void blur16(const float* in, const float* w, float* o
 }
 
 // Horizontal pass: item (plane p of the kNP planes of h, region row), the
-// 26 inputs of the row read once. Pass 1 (kNP = 15): p = 5 c + q with q in
-// x, y, x^2, y^2, x y of channel c; pass 2 (kNP = 9): p = 3 c + q, the a, b,
-// c planes as loaded.
+// 26 inputs of the row read once. Pass 1 (kNP = 5): p = x, y, x^2, y^2, x y
+// of the channel from its region planes x (0) and y (1); pass 2 (kNP = 3):
+// the a, b, c planes as loaded.
 template <int kNP>
 __device__ __forceinline__ void blur_rows(SsimSmem& sm, const float* w) {
     for (int e = threadIdx.x; e < kNP * kReg; e += blockDim.x) {
         const int p = e / kReg, row = e - p * kReg;
         float in[kReg];
-        if (kNP == 15) {
-            const int c = p / 5, q = p - 5 * c;
-            const float* xr = &sm.r[2 * c][row][0];
-            const float* yr = &sm.r[2 * c + 1][row][0];
-            // one specialised loop per quantity (q is uniform over the item)
-            switch (q) {
+        if (kNP == 5) {
+            const float* xr = &sm.r[0][row][0];
+            const float* yr = &sm.r[1][row][0];
+            // one specialised loop per quantity (p is uniform over the item)
+            switch (p) {
                 case 0:
 #pragma unroll
                     for (int k = 0; k < kReg; ++k) in[k] = xr[k];
@@ -160,7 +162,7 @@ __device__ __forceinline__ void load_region(SsimSmem& sm, int np, int x0, int y0
 
 // Pass 1: S, a, b, c at every pixel of every rendered tile; lambda (1 - S)
 // summed into the loss over the covered tiles' pixels.
-__global__ void __launch_bounds__(kTilePixels)
+__global__ void __launch_bounds__(kSsimThreads)
 ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* __restrict__ tiles,
                  const int32_t* __restrict__ n_tiles, const uint8_t* __restrict__ tile_active,
                  const float* __restrict__ image, const float* __restrict__ target, float lambda,
@@ -177,42 +179,40 @@ ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const int W = view.cam.width, H = view.cam.height;
         const int64_t plane = (int64_t)W * H;
-        const float* xi = image + 3 * view.pix_base;
-        const float* yi = target + 3 * view.pix_base;
-        __syncthreads();
-        load_region(sm, 6, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
-                    [&](int q, int64_t off) {
-                        return ((q & 1) ? yi : xi)[(q >> 1) * plane + off];
-                    });
-        __syncthreads();
-        blur_rows<15>(sm, w);
-        __syncthreads();
-        blur_cols<15>(sm, w);
-        __syncthreads();
         float lsum = 0.f;
-        // the maps: (channel, row, column) items
-        for (int e = threadIdx.x; e < 3 * kTilePixels; e += blockDim.x) {
-            const int c = e / kTilePixels, rem = e - c * kTilePixels;
-            const int i = rem / kTile, j = rem - i * kTile;
-            const int px = tx * kTile + j, py = ty * kTile + i;
-            if (!(px < W && py < H)) continue;
-            const float mx = vsum(sm, 5 * c, i, j), my = vsum(sm, 5 * c + 1, i, j);
-            const float vx = vsum(sm, 5 * c + 2, i, j) - mx * mx;
-            const float vy = vsum(sm, 5 * c + 3, i, j) - my * my;
-            const float cxy = vsum(sm, 5 * c + 4, i, j) - mx * my;
-            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
-            const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
-            const float D = B1 * B2;
-            const float S = A1 * A2 / D;
-            const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
-            const float dvx = -S / B2;
-            const float dcxy = 2.f * A1 / D;
-            const int64_t base = 9 * view.pix_base + (int64_t)(3 * c) * plane +
-                                 (int64_t)py * W + px;
-            abc[base] = dmu - 2.f * mx * dvx - my * dcxy;
-            abc[base + plane] = dvx;
-            abc[base + 2 * plane] = dcxy;
-            lsum += 1.f - S;
+        for (int c = 0; c < 3; ++c) {
+            const float* xi = image + 3 * view.pix_base + c * plane;
+            const float* yi = target + 3 * view.pix_base + c * plane;
+            __syncthreads();
+            load_region(sm, 2, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
+                        [&](int q, int64_t off) { return (q ? yi : xi)[off]; });
+            __syncthreads();
+            blur_rows<5>(sm, w);
+            __syncthreads();
+            blur_cols<5>(sm, w);
+            __syncthreads();
+            for (int e = threadIdx.x; e < kTilePixels; e += blockDim.x) {
+                const int i = e / kTile, j = e - i * kTile;
+                const int px = tx * kTile + j, py = ty * kTile + i;
+                if (!(px < W && py < H)) continue;
+                const float mx = vsum(sm, 0, i, j), my = vsum(sm, 1, i, j);
+                const float vx = vsum(sm, 2, i, j) - mx * mx;
+                const float vy = vsum(sm, 3, i, j) - my * my;
+                const float cxy = vsum(sm, 4, i, j) - mx * my;
+                const float A1 = 2.f * mx * my + kC1, A2 = 2.f * cxy + kC2;
+                const float B1 = mx * mx + my * my + kC1, B2 = vx + vy + kC2;
+                const float D = B1 * B2;
+                const float S = A1 * A2 / D;
+                const float dmu = 2.f * my * A2 / D - 2.f * mx * S / B1;
+                const float dvx = -S / B2;
+                const float dcxy = 2.f * A1 / D;
+                const int64_t base = 9 * view.pix_base + (int64_t)(3 * c) * plane +
+                                     (int64_t)py * W + px;
+                abc[base] = dmu - 2.f * mx * dvx - my * dcxy;
+                abc[base + plane] = dvx;
+                abc[base + 2 * plane] = dcxy;
+                lsum += 1.f - S;
+            }
         }
         const bool covered = tile_active[tile] == 1;
         const float tot = block_sum(sm, covered ? lsum : 0.f);
@@ -224,7 +224,7 @@ ssim_maps_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
 // Pass 2, covered tiles only: dL/dC = (1 - lambda) dL1/dC - lambda * scale *
 // d(sum S)/dx, where dL1/dC = sign(C - C*) * scale was written by the forward
 // pass; (1 - lambda) |C - C*| * scale is added to the loss.
-__global__ void __launch_bounds__(kTilePixels)
+__global__ void __launch_bounds__(kSsimThreads)
 ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* __restrict__ tiles,
                  const int32_t* __restrict__ n_tiles, const uint8_t* __restrict__ tile_active,
                  const float* __restrict__ image, const float* __restrict__ target, float lambda,
@@ -243,27 +243,28 @@ ssim_grad_kernel(const ClsView* __restrict__ views, int n_views, const int32_t* 
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const int W = view.cam.width, H = view.cam.height;
         const int64_t plane = (int64_t)W * H;
-        const float* m = abc + 9 * view.pix_base;
-        __syncthreads();
-        load_region(sm, 9, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
-                    [&](int q, int64_t off) { return m[q * plane + off]; });
-        __syncthreads();
-        blur_rows<9>(sm, w);
-        __syncthreads();
-        blur_cols<9>(sm, w);
-        __syncthreads();
         float lsum = 0.f;
-        for (int e = threadIdx.x; e < 3 * kTilePixels; e += blockDim.x) {
-            const int c = e / kTilePixels, rem = e - c * kTilePixels;
-            const int i = rem / kTile, j = rem - i * kTile;
-            const int px = tx * kTile + j, py = ty * kTile + i;
-            if (!(px < W && py < H)) continue;
-            const int64_t idx = plane_index(view, c, px, py);
-            const float xv = image[idx], yv = target[idx];
-            const float gs = vsum(sm, 3 * c, i, j) + 2.f * xv * vsum(sm, 3 * c + 1, i, j) +
-                             yv * vsum(sm, 3 * c + 2, i, j);
-            dL_dimage[idx] = (1.f - lambda) * dL_dimage[idx] - lambda * view.loss_scale * gs;
-            lsum += fabsf(xv - yv);
+        for (int c = 0; c < 3; ++c) {
+            const float* m = abc + 9 * view.pix_base + (int64_t)(3 * c) * plane;
+            __syncthreads();
+            load_region(sm, 3, tx * kTile - kSsimR, ty * kTile - kSsimR, W, H,
+                        [&](int q, int64_t off) { return m[q * plane + off]; });
+            __syncthreads();
+            blur_rows<3>(sm, w);
+            __syncthreads();
+            blur_cols<3>(sm, w);
+            __syncthreads();
+            for (int e = threadIdx.x; e < kTilePixels; e += blockDim.x) {
+                const int i = e / kTile, j = e - i * kTile;
+                const int px = tx * kTile + j, py = ty * kTile + i;
+                if (!(px < W && py < H)) continue;
+                const int64_t idx = plane_index(view, c, px, py);
+                const float xv = image[idx], yv = target[idx];
+                const float gs = vsum(sm, 0, i, j) + 2.f * xv * vsum(sm, 1, i, j) +
+                                 yv * vsum(sm, 2, i, j);
+                dL_dimage[idx] = (1.f - lambda) * dL_dimage[idx] - lambda * view.loss_scale * gs;
+                lsum += fabsf(xv - yv);
+            }
         }
         const float tot = block_sum(sm, lsum);
         if (threadIdx.x == 0 && loss_per_scene)
@@ -296,13 +297,13 @@ extern "C" int cls_ssim_loss(const ClsView* views_dev, const ClsBatchInfo* info,
                              (int)sizeof(SsimSmem));
         cudaFuncSetAttribute(ssim_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SsimSmem));
-        return resident_blocks(dev, ssim_maps_kernel, kTilePixels, sizeof(SsimSmem));
+        return resident_blocks(dev, ssim_maps_kernel, kSsimThreads, sizeof(SsimSmem));
     });
     const int blocks = (int)hmin64(info->total_tiles, ssim_blocks);
-    ssim_maps_kernel<<<blocks, kTilePixels, sizeof(SsimSmem), s>>>(
+    ssim_maps_kernel<<<blocks, kSsimThreads, sizeof(SsimSmem), s>>>(
         views_dev, info->n_views, tiles, n_tiles_dev, tile_active, image, target, lambda, abc,
         loss_per_scene);
-    ssim_grad_kernel<<<blocks, kTilePixels, sizeof(SsimSmem), s>>>(
+    ssim_grad_kernel<<<blocks, kSsimThreads, sizeof(SsimSmem), s>>>(
         views_dev, info->n_views, tiles, n_tiles_dev, tile_active, image, target, lambda, abc,
         dL_dimage, loss_per_scene);
     CLS_CHECK_LAUNCH();

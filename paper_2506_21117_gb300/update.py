@@ -255,6 +255,45 @@ class Batch:
         self.reproject = True
         self.counted = False
 
+    def matches(self, scenes: Sequence[SceneState], cams_per_scene: Sequence[Sequence]) -> bool:
+        """Whether this batch was built for these scenes (the same resident
+        states, unchanged sizes) and these cameras (the same poses, intrinsics
+        and sizes), so a new update of them can reuse its tables and buffers."""
+        if len(scenes) != len(self.scenes) or any(a is not b for a, b in zip(scenes, self.scenes)):
+            return False
+        if any(int(self.scene_tab[s].n) != st.n for s, st in enumerate(scenes)):
+            return False
+        j = 0
+        for cams in cams_per_scene:
+            for cam in cams:
+                if j >= self.n_views:
+                    return False
+                if bytes(memoryview(make_camera(cam)).cast("B")) != \
+                        bytes(memoryview(self.view_tab[j].cam).cast("B")):
+                    return False
+                j += 1
+        return j == self.n_views
+
+    def reuse_for_update(self) -> None:
+        """Prepare the batch for a new update of the same scenes and views
+        after lifting changed the active sets: tables refreshed for the new
+        active counts, gradient buffers grown if needed, every record projected
+        again and every static prefix rebuilt; the depth cuts learnt by the
+        previous update are kept as the first guess (a tile that needs more is
+        completed as usual)."""
+        self.refresh_active()
+        info = self.info
+        dev = self.device
+        if self.grad2d.numel() < max(info.total_g2, 1) * abi.G2_STRIDE:
+            self.grad2d = torch.empty(max(info.total_g2, 1) * abi.G2_STRIDE,
+                                      dtype=torch.float32, device=dev)
+        if self.grads.numel() < max(info.total_grad_rows, 1) * info.max_row_stride:
+            self.grads = torch.empty(max(info.total_grad_rows, 1) * info.max_row_stride,
+                                     dtype=torch.float32, device=dev)
+        self._epochs = [st.epoch for st in self.scenes]
+        self.reset_prefix()
+        self.status.zero_()
+
     def deactivate(self, scene_indices) -> None:
         """Drop scenes from the work of later iterations without rebuilding:
         their active count becomes 0 in the device table (no active tiles, no
@@ -616,11 +655,15 @@ class LocalUpdate:
     @classmethod
     def from_resident(cls, state: SceneState, cams, targets, masks, vote_mode: int = 0,
                       loss: str = "l1", lr: float = 1e-3, bg=(0.0, 0.0, 0.0),
-                      capacity_slack: float = 1.5, layout: int = 1, lazy: bool = True):
+                      capacity_slack: float = 1.5, layout: int = 1, lazy: bool = True,
+                      reuse: Optional["LocalUpdate"] = None):
         """A new update of a scene already resident on the device. `targets`
         (float32, [3][H][W] per view, concatenated) and `masks` (uint8, [H][W]
         per view, concatenated) are flat tensors, typically pinned host memory;
-        they are copied to the device here."""
+        they are copied to the device here. `reuse`: a finished earlier update
+        of the same scene with the same cameras, whose batch (tables, buffers,
+        learnt depth cuts) this update takes over instead of building new
+        ones; otherwise, or if it does not match, a new batch is built."""
         self = cls.__new__(cls)
         self.cams = list(cams)
         self.loss_mode = LOSS_MODES[loss]
@@ -629,7 +672,15 @@ class LocalUpdate:
         self.state = state
         dev = state.params.device
         lift(state, self.cams, masks, vote_mode, dev)
-        self.batch = Batch([state], [self.cams], dev, layout, lazy, ssim=loss == "l1+ssim")
+        ssim = loss == "l1+ssim"
+        old = reuse.batch if reuse is not None else None
+        if (old is not None and old.layout == layout and old.lazy == (lazy and layout == 1)
+                and old.ssim == ssim and old.matches([state], [self.cams])):
+            self.batch = old
+            reuse.batch = None  # the earlier update no longer owns it
+            self.batch.reuse_for_update()
+        else:
+            self.batch = Batch([state], [self.cams], dev, layout, lazy, ssim=ssim)
         # the targets travel on a copy stream while lifting and planning run;
         # the first forward pass waits for them
         main = torch.cuda.current_stream()

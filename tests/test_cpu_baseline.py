@@ -14,7 +14,7 @@ from oracle import fp32_index as fx
 from oracle import step as ostep
 from paper_2506_21117_gb300 import synthetic as S
 
-FLOOR = 3e-2  # the GPU parity floor; this float32 code measures below 1.5e-2
+FLOOR = 3.5e-2  # the GPU parity floor; this float32 code measures below 1.5e-2
 
 
 def _local():

@@ -11,14 +11,15 @@ oracle's own arithmetic run in float32 needs (`dtype=torch.float32`, the same
 mathematics rounded to single precision, against float64). Over these
 workloads the float32 evaluation needs up to 1.5e-2 (plain L1: cancelling
 per-pixel terms that float32 cannot resolve below ~1e-5 x RMS) and the GPU up
-to 2.0e-2 (local SH3 cases). The GPU's backward takes the colour behind an
-entry as the final colour minus what has been composited in front of it (no
-division, nothing stored per entry); its float32 error is relative to the
-pixel colour rather than to the (smaller) colour behind, which an emulation
-of both formulations in float32 measures at 7x the RMS error of summing the
-colour behind from the back. GRAD_FLOOR = 3e-2 covers the largest measured
-need with a 1.5x margin; the D-SSIM loss adds one float32 stage (the window
-sums of its image gradient) and measured 2.9e-2, so its tests use 4e-2.
+to 2.6e-2 (local SH3 cases with moved Gaussians; 2.8e-2 with the D-SSIM loss,
+which adds the float32 window sums of its image gradient). The GPU's backward
+takes the colour behind an entry as the final colour minus what has been
+composited in front of it (no division, nothing stored per entry); its float32
+error is relative to the pixel colour rather than to the (smaller) colour
+behind, which an emulation of both formulations in float32 measures at 7x the
+RMS error of summing the colour behind from the back. GRAD_FLOOR = 3.5e-2
+covers the largest measured need with a 1.25x margin for the run-to-run
+variation of the float atomics' summation order.
 
 Threshold decisions: a pixel where a reached alpha, stop or clamp decision
 sits closer to its threshold than the float32 error model of the oracle's
@@ -43,8 +44,8 @@ pytestmark = pytest.mark.gpu
 
 PIX_TOL = 1e-4
 GRAD_RTOL = 1e-3
-GRAD_FLOOR = 3e-2
-SSIM_GRAD_FLOOR = 4e-2
+GRAD_FLOOR = 3.5e-2
+SSIM_GRAD_FLOOR = GRAD_FLOOR
 HELD_MAX = 0.02  # share of rendered pixels held constant for the gradient checks
 
 
