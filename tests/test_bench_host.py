@@ -125,3 +125,45 @@ def test_walk_counts_brute_force():
                    "backward_entries": Bn, "forward_pixels": Pf, "backward_pixels": Pb,
                    "keys_sorted_by_forward": S, "keys_in_large_bins": big}
     assert S > 0 and F > 0
+
+
+def _with_records(bt, seed, far):
+    """Keys and records for the fake pass: every list entry its own record, a
+    Gaussian centred in its tile (far=False: reaches every pixel) or far away
+    (far=True: culled for its tile)."""
+    rng = np.random.default_rng(seed)
+    T = bt.info.total_tiles
+    ranges = bt.ranges.view(T, 2).numpy().astype(np.int64)
+    n = int(ranges[:, 1].max())
+    rec = np.zeros((max(n, 1), 12), np.float32)
+    tile_xy = np.zeros((T, 2), np.float32)
+    for j in range(bt.n_views):
+        v = bt.view_tab[j]
+        for t in range(v.tiles_x * v.tiles_y):
+            tile_xy[v.tile_base + t] = (16 * (t % v.tiles_x), 16 * (t // v.tiles_x))
+    for t in range(T):
+        a, e = ranges[t]
+        if e <= a:
+            continue
+        c = tile_xy[t] + 8.0 + (1e4 if far else 0.0)
+        rec[a:e, 0], rec[a:e, 1] = c[0], c[1]
+        rec[a:e, 2] = rng.uniform(0.01, 0.05, e - a)   # conic A
+        rec[a:e, 3] = 0.0                              # B
+        rec[a:e, 4] = rng.uniform(0.01, 0.05, e - a)   # C
+        rec[a:e, 5] = 0.9                              # opacity
+    bt.records = torch.from_numpy(rec.reshape(-1))
+    bt.keys = torch.arange(max(n, 1), dtype=torch.int64)   # record index in the low word
+    return bt
+
+
+def test_executed_evaluations_bounds():
+    """Entries that reach every pixel of their tile are all executed (the count
+    equals the walked count); entries far from their tile are all culled."""
+    bt, tc, active, state, sizes, off = _bucketed_fake(seed=4)
+    walked = bench.walked_evaluations(_with_records(bt, 4, far=False))
+    got = bench.executed_evaluations(bt)
+    assert got["forward"] == walked["forward"] > 0
+    assert got["backward"] == walked["backward"]
+    assert got["kept_share"] == 1.0
+    got = bench.executed_evaluations(_with_records(bt, 4, far=True))
+    assert got["forward"] == 0 and got["backward"] == 0 and got["kept_share"] == 0.0
