@@ -399,3 +399,81 @@ def test_float32_evaluation_stays_within_float32_rounding():
         rms = math.sqrt(float(np.mean(g64 * g64)))
         gap = np.abs(g32 - g64).max() / rms
         assert 1e-8 < gap < 1e-3, (k, gap)
+
+
+def _branch_scene():
+    """60 background Gaussians and three that sit on a branch of the image
+    formation: A far off-axis (its tangent x/z beyond 1.3 tan(fov/2), so the
+    EWA Jacobian uses the clamped tangent) but wide enough to reach the image;
+    B with a negative raw red channel (clamped to 0); C nearly opaque in front
+    (alpha clamped at 0.99 on its central pixels)."""
+    scene = S.uniform_scene(63, 1, seed=91)
+    for k in scene:
+        scene[k] = np.asarray(scene[k], np.float64).copy()
+    A, B, C = 60, 61, 62
+    scene["means"][A] = [3.4, 0.1, 0.0]
+    scene["log_scales"][A] = [0.05, -0.4, -0.2]
+    scene["opacity_logits"][A] = 1.0
+    scene["means"][B] = [0.1, -0.05, 0.3]
+    scene["log_scales"][B] = [-1.6, -1.7, -1.5]
+    scene["sh"][B, 0] = [-2.0, 0.8, 0.4]
+    scene["opacity_logits"][B] = 2.0
+    scene["means"][C] = [-0.2, 0.15, -1.5]
+    scene["log_scales"][C] = [-1.8, -1.7, -1.9]
+    scene["opacity_logits"][C] = 8.0
+    cams = [S.look_at_camera((0.0, 0.0, -4.0), (0.0, 0.0, 0.0), 48, 40)]
+    targets = [S.random_image(cams[0], 92)]
+    return scene, cams, targets, (A, B, C)
+
+
+def test_branch_gradients_match_central_differences():
+    """Central differences of the L2 loss for every parameter of three
+    Gaussians that each sit on one branch (clamped tangent, clamped colour,
+    clamped alpha), with the branch checked to be taken; probes whose discrete
+    structure changes are excluded and counted."""
+    from oracle.projection import project, scene64
+    scene, cams, targets, (A, B, C) = _branch_scene()
+    P = project(scene64(scene), cams[0], 1)
+    pz = (scene["means"] @ np.asarray(cams[0]["R"]).T + cams[0]["t"])[:, 2]
+    px = (scene["means"] @ np.asarray(cams[0]["R"]).T + cams[0]["t"])[:, 0]
+    lim = 1.3 * 0.5 * cams[0]["width"] / cams[0]["fx"]
+    assert abs(px[A] / pz[A]) > lim                              # tangent clamped
+    assert float(P["rgb_raw"][B, 0]) < 0 < float(P["rgb_raw"][B, 1])  # red clamped
+    u, v = float(P["u"][C]), float(P["v"][C])
+    Ac, Bc, Cc = (float(x) for x in P["conic"][C])
+    peak = max(float(P["opacity"][C]) * math.exp(
+        -0.5 * (Ac * (x + 0.5 - u) ** 2 + Cc * (y + 0.5 - v) ** 2) - Bc * (x + 0.5 - u) * (y + 0.5 - v))
+        for x in range(int(u) - 2, int(u) + 3) for y in range(int(v) - 2, int(v) + 3))
+    assert peak > 0.99                                           # alpha clamped on a pixel
+    ref = step.render(scene, cams, 1, targets=targets, loss="l2", need_grad=True)
+    assert ref["n_incl"][0].max() > 0
+    p = ref["pidx"][0]
+    assert p["valid"][A] and p["tx1"][A] >= 0 and p["tx0"][A] <= 2   # A reaches the image
+    G = ref["grads"]
+    h = 1e-5
+    checked = excluded = 0
+    per = {A: 0, B: 0, C: 0}
+    for g in (A, B, C):
+        for key in step.PARAM_KEYS:
+            arr = scene[key]
+            for flat in range(int(np.prod(arr.shape[1:])) if arr.ndim > 1 else 1):
+                sp = {k: v.copy() for k, v in scene.items()}
+                sm = {k: v.copy() for k, v in scene.items()}
+                idx = (g,) + np.unravel_index(flat, arr.shape[1:]) if arr.ndim > 1 else (g,)
+                sp[key][idx] += h
+                sm[key][idx] -= h
+                if _signature(sp, cams, 1, g) != _signature(sm, cams, 1, g):
+                    excluded += 1
+                    continue
+                fd = (step.loss_value(sp, cams, 1, targets, "l2") -
+                      step.loss_value(sm, cams, 1, targets, "l2")) / (2 * h)
+                ad = G[key][idx]
+                assert abs(fd - ad) <= 1e-5 * abs(ad) + 1e-10, (g, key, idx, fd, ad)
+                checked += 1
+                per[g] += 1
+    assert np.abs(G["means"][A]).max() > 1e-4                   # A reaches pixels
+    # the clamped red channel takes no gradient through any SH coefficient of B
+    assert np.all(G["sh"][B, :, 0] == 0.0)
+    assert np.any(G["sh"][B, :, 1] != 0.0)
+    print(f"branch finite differences: {checked} checked, {excluded} excluded, per Gaussian {per}")
+    assert min(per.values()) >= 15 and excluded <= 0.15 * (checked + excluded)
