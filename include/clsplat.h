@@ -241,10 +241,11 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  *     record index; `vals` is unused. Pairs are grouped by tile (tiles in
  *     active-tile order) and, inside a tile, by CLS_DEPTH_BINS depth bins
  *     that split the view's depth range of pair-producing Gaussians evenly in
- *     float-bit space (monotone in depth); the order inside a bin is
- *     unspecified until cls_sort_tiles. ranges[tile] = (start, end) of each
- *     tile ((0, 0) if inactive) and bin_offsets[r * CLS_DEPTH_BINS + b] the
- *     start of bin b of the r-th active tile (cls_bin_offsets_size entries).
+ *     float-bit space (up to float rounding; monotone in depth); the order
+ *     inside a bin is unspecified until cls_sort_tiles. ranges[tile] =
+ *     (start, end) of each tile ((0, 0) if inactive) and
+ *     bin_offsets[r * CLS_DEPTH_BINS + b] the start of bin b of the r-th
+ *     active tile (cls_bin_offsets_size entries).
  *   n_pairs_dev               device int64: number of pairs needed; if it
  *                             exceeds `capacity`, CLS_ERR_CAPACITY is written
  *                             to status_dev and only `capacity` pairs are kept

@@ -39,15 +39,19 @@ __device__ __forceinline__ uint4 pack_rect(bool valid, int x0, int x1, int y0, i
                  : make_uint4(0u, 0u, 0u, 0u);
 }
 
+__device__ __forceinline__ void unpack_rect(const uint4& r, int& x0, int& x1, int& y0, int& y1) {
+    x0 = (int)(r.x & 0xffffu);
+    x1 = (int)(r.x >> 16);
+    y0 = (int)(r.y & 0xffffu);
+    y1 = (int)(r.y >> 16);
+}
+
 __device__ __forceinline__ bool record_rect(const uint4* rects, int64_t rec, int& x0, int& x1,
                                             int& y0, int& y1, uint32_t& zbits) {
     const uint4 r = rects[rec];
     zbits = r.z;
     if (r.w == 0u) return false;
-    x0 = (int)(r.x & 0xffffu);
-    x1 = (int)(r.x >> 16);
-    y0 = (int)(r.y & 0xffffu);
-    y1 = (int)(r.y >> 16);
+    unpack_rect(r, x0, x1, y0, y1);
     return true;
 }
 
@@ -428,7 +432,7 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
                    const uint4* __restrict__ rects, const int32_t* __restrict__ sat,
                    int chunks_per_view, int64_t* __restrict__ partials,
                    uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
-                   uint32_t* __restrict__ work_list, int32_t* __restrict__ work_count) {
+                   uint4* __restrict__ work_list, int32_t* __restrict__ work_count) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     __shared__ int32_t smem32[kBinBlock / 32 + 1];
     __shared__ uint32_t s_lo, s_hi;
@@ -463,10 +467,16 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
         if (threadIdx.x == 0) s_base = nw > 0 ? atomicAdd(work_count + blockIdx.y, nw) : 0;
         __syncthreads();
         k += s_base;
+        // a work item is the record's packed rectangle with its record index
+        // in place of the visible flag
         for (int it = 0; it < kBinItems; ++it)
-            if (produces & (1u << it))
-                work_list[view.rec_base + k++] =
-                    (uint32_t)(blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x);
+            if (produces & (1u << it)) {
+                const int64_t rec = view.rec_base + blockIdx.x * kBinChunk + it * kBinBlock +
+                                    threadIdx.x;
+                uint4 r = rects[rec];
+                r.w = (uint32_t)rec;
+                work_list[view.rec_base + k++] = r;
+            }
     }
     if (zmin) {
         for (int o = 16; o > 0; o >>= 1) {
@@ -485,31 +495,41 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
     }
 }
 
-// Depth bin of a key inside its view's depth range (monotone in depth).
-__device__ __forceinline__ int depth_bin(uint32_t zb, uint32_t lo, uint32_t hi) {
-    if (zb <= lo) return 0;
-    if (zb >= hi) return kDepthBins - 1;
-    return (int)(((uint64_t)(zb - lo) * kDepthBins) / ((uint64_t)(hi - lo) + 1));
+// Depth bins of a view: its depth range [lo, hi] (float bits of the
+// pair-producing Gaussians' depths) cut into kDepthBins equal parts. The bin
+// of depth bits zb is floor((zb - lo) * scale), clamped; float rounding is
+// monotone, so bins stay monotone in depth, and every kernel derives the same
+// scale from the same lo and hi.
+struct DepthBins {
+    uint32_t lo;
+    float scale;
+};
+
+__device__ __forceinline__ DepthBins depth_bins(uint32_t lo, uint32_t hi) {
+    return DepthBins{lo, (float)kDepthBins / ((float)(hi - lo) + 1.0f)};
+}
+
+__device__ __forceinline__ int depth_bin(uint32_t zb, const DepthBins& d) {
+    if (zb <= d.lo) return 0;
+    return min((int)((float)(zb - d.lo) * d.scale), kDepthBins - 1);
 }
 
 // Bucketed layout: stamp every pair-producing rectangle into its depth bin's
 // difference grid; the prefix sums then give pairs per (tile, depth bin).
 // (the pair-producing records of each view are those of its work list)
 __global__ void __launch_bounds__(kBinBlock)
-stamp_bins_kernel(const ClsView* __restrict__ views, const uint4* __restrict__ rects,
+stamp_bins_kernel(const ClsView* __restrict__ views,
                   const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
-                  const uint32_t* __restrict__ work_list, const int32_t* __restrict__ work_count,
+                  const uint4* __restrict__ work_list, const int32_t* __restrict__ work_count,
                   int32_t* __restrict__ bins, int64_t total_sat) {
     const ClsView& view = views[blockIdx.y];
     const int n = work_count[blockIdx.y];
-    const uint32_t lo = zmin[blockIdx.y], hi = zmax[blockIdx.y];
+    const DepthBins db = depth_bins(zmin[blockIdx.y], zmax[blockIdx.y]);
     for (int i = blockIdx.x * kBinBlock + threadIdx.x; i < n; i += gridDim.x * kBinBlock) {
+        const uint4 r = work_list[view.rec_base + i];
         int x0, x1, y0, y1;
-        uint32_t zb;
-        if (!record_rect(rects, view.rec_base + work_list[view.rec_base + i], x0, x1, y0,
-                         y1, zb))
-            continue;
-        const int b = depth_bin(zb, lo, hi);
+        unpack_rect(r, x0, x1, y0, y1);
+        const int b = depth_bin(r.z, db);
         stamp_rect(bins + b * total_sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
     }
 }
@@ -573,7 +593,8 @@ sub_count_kernel(const int32_t* __restrict__ n_active, const int32_t* __restrict
 // Offsets of every (tile, bin) bucket and the per-tile ranges, clamped to the
 // key capacity so every later access stays inside the key buffer; the first
 // depth bin each tile emits (bins entirely in front of a cached prefix
-// boundary hold only prefix pairs and are not written).
+// boundary hold only prefix pairs and are not written); per view the rank of
+// its first rendered tile.
 __global__ void __launch_bounds__(kBinBlock)
 sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
                    const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
@@ -581,7 +602,7 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
                    uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
                    uint32_t* __restrict__ ranges, const ClsTileCache* __restrict__ tile_cache,
                    const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
-                   uint8_t* __restrict__ front) {
+                   uint8_t* __restrict__ front, int32_t* __restrict__ rank0) {
     __shared__ int64_t smem[kBinBlock / 32 + 1];
     const int64_t ne = (int64_t)(*n_active) * kDepthBins;
     int64_t base = partials[blockIdx.x];
@@ -602,8 +623,11 @@ sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
                 ranges[2 * tile] = o;
                 const ClsTileCache c = tile_cache[tile];
                 const int v = view_of_tile(views, n_views, (int)tile);
+                // the first rendered tile of its view
+                if (t == 0 || active_tiles[t - 1] < views[v].tile_base) rank0[v] = t;
                 front[tile] = c.n_prefix != CLS_PREFIX_UNKNOWN
-                                  ? (uint8_t)depth_bin(c.zb, zmin[v], zmax[v]) : (uint8_t)0;
+                                  ? (uint8_t)depth_bin(c.zb, depth_bins(zmin[v], zmax[v]))
+                                  : (uint8_t)0;
             }
             if (b == kDepthBins - 1) {
                 ranges[2 * tile + 1] = o_end;
@@ -658,195 +682,186 @@ emit_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict
     }
 }
 
-// Per tile row of every view: sparse tables of the first emitted depth bin
-// (minimum) and the depth cut (maximum) over runs of 2^l tiles, level l at
-// l * total_tiles + global tile id; inactive tiles are neutral (front 255,
-// cut 0). One block per view.
+// Emission windows. Every rendered tile emits the depth bins from its first
+// emitted bin (bins wholly in front of a cached prefix boundary are skipped)
+// to its depth cut. Per tile the two are packed into 16 bits, first bin in the
+// low byte and cut in the high byte; a tile that is not rendered holds the
+// neutral 0x00ff, which admits no bin.
+__device__ __forceinline__ uint32_t fc_pack(bool on, uint32_t first, uint32_t cut) {
+    return on ? (first | (cut << 8)) : 0x00ffu;
+}
+
+// Window of the union of two runs of tiles: the smaller first bin, the larger cut.
+__device__ __forceinline__ uint32_t fc_merge(uint32_t a, uint32_t b) {
+    return min(a & 0xffu, b & 0xffu) | (max(a >> 8, b >> 8) << 8);
+}
+
+__device__ __forceinline__ bool fc_admits(uint32_t w, int bin) {
+    return (int)(w & 0xffu) <= bin && bin <= (int)(w >> 8);
+}
+
+// Per tile row of every view: sparse tables of the packed windows over runs
+// of 2^l tiles for l >= 1, level l at (l - 1) * total_tiles + tile (level 0 is
+// the tiles' own windows).
 constexpr int kRowLevels = 16;  // tiles per row < 2^16
 
-// Whether the emission kernel builds a view's row tables in its own shared
-// memory (`smem_bytes` of it: rank, cut and first bin per tile, then the
-// levels); views whose tables do not fit use the global ones that
-// bin_window_tables_kernel writes.
-__host__ __device__ __forceinline__ bool emit_tables_fit(int64_t nt, int Tx, int64_t smem_bytes) {
+__host__ __device__ __forceinline__ int row_levels(int Tx) {
     int levels = 0;
     while ((1 << levels) <= Tx) ++levels;  // 2^(levels - 1) <= Tx < 2^levels
-    return nt * (6 + 2 * (int64_t)levels) <= smem_bytes;
+    return levels;
+}
+
+// Shared memory of the emission: per warp its group's 32 items (key, end of
+// its cells, corner, width and bin: 20 B each), per tile a packed word
+// (rank in the view's rendered tiles + 1 in the low half, 0 if not rendered;
+// the window in the high half) and, when they fit, the row tables' levels
+// 1 .. L-1. Views whose tables do not fit in `smem_bytes` use the global ones
+// that bin_window_tables_kernel writes.
+constexpr int kEmitThreads = 1024;
+constexpr int kEmitWarps = kEmitThreads / 32;
+constexpr int kEmitItemBytes = kEmitWarps * 32 * 20;
+
+__host__ __device__ __forceinline__ bool emit_tables_fit(int64_t nt, int Tx, int64_t smem_bytes) {
+    return nt * (4 + 2 * (int64_t)(row_levels(Tx) - 1)) + kEmitItemBytes <= smem_bytes;
 }
 
 __global__ void __launch_bounds__(1024)
 bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ tile_rank,
                          const uint8_t* __restrict__ front, const uint8_t* __restrict__ cut,
-                         uint8_t* __restrict__ t_front, uint8_t* __restrict__ t_cut,
-                         int64_t total_tiles, int smem_cap, int emit_smem) {
-    extern __shared__ uint8_t s_tab[];
+                         uint16_t* __restrict__ t_win, int64_t total_tiles, int emit_smem) {
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x, nt = Tx * view.tiles_y;
     const int64_t tb = view.tile_base;
     if (emit_tables_fit(nt, Tx, emit_smem)) return;  // the emission builds them itself
-    const int levels = 32 - __clz(Tx);  // 2^(levels - 1) <= Tx
-    if ((int64_t)levels * nt * 2 <= smem_cap) {
-        uint8_t* sf = s_tab;
-        uint8_t* sc = s_tab + (int64_t)levels * nt;
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-            const bool on = tile_rank[tb + i] >= 0;
-            sf[i] = on ? front[tb + i] : (uint8_t)255;
-            sc[i] = on ? (cut ? cut[tb + i] : (uint8_t)255) : (uint8_t)0;
-        }
-        for (int l = 1; l < levels; ++l) {
-            __syncthreads();
-            const int h = 1 << (l - 1);
-            const int prev = (l - 1) * nt, cur = l * nt;
-            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-                const int x = i % Tx;
-                if (x + 2 * h > Tx) continue;
-                sf[cur + i] = min(sf[prev + i], sf[prev + i + h]);
-                sc[cur + i] = max(sc[prev + i], sc[prev + i + h]);
-            }
-        }
-        __syncthreads();
-        for (int l = 0; l < levels; ++l)
-            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-                t_front[(int64_t)l * total_tiles + tb + i] = sf[l * nt + i];
-                t_cut[(int64_t)l * total_tiles + tb + i] = sc[l * nt + i];
-            }
-        return;
-    }
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+    auto win0 = [&](int i) {
         const bool on = tile_rank[tb + i] >= 0;
-        t_front[tb + i] = on ? front[tb + i] : (uint8_t)255;
-        t_cut[tb + i] = on ? (cut ? cut[tb + i] : (uint8_t)255) : (uint8_t)0;
-    }
-    for (int l = 1; l < kRowLevels && (1 << l) <= Tx; ++l) {
+        return fc_pack(on, on ? front[tb + i] : 0u, cut ? cut[tb + i] : 255u);
+    };
+    for (int i = threadIdx.x; i < nt; i += blockDim.x)
+        if (i % Tx + 2 <= Tx) t_win[tb + i] = (uint16_t)fc_merge(win0(i), win0(i + 1));
+    for (int l = 2; l < kRowLevels && (1 << l) <= Tx; ++l) {
         __syncthreads();
         const int h = 1 << (l - 1);
-        const int64_t prev = (int64_t)(l - 1) * total_tiles + tb, cur = prev + total_tiles;
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-            const int x = i % Tx;
-            if (x + 2 * h > Tx) continue;
-            t_front[cur + i] = min(t_front[prev + i], t_front[prev + i + h]);
-            t_cut[cur + i] = max(t_cut[prev + i], t_cut[prev + i + h]);
-        }
+        const int64_t prev = (int64_t)(l - 2) * total_tiles + tb, cur = prev + total_tiles;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x)
+            if (i % Tx + 2 * h <= Tx)
+                t_win[cur + i] = (uint16_t)fc_merge(t_win[prev + i], t_win[prev + i + h]);
     }
 }
 
 // First and last rows of rectangle x0..x1, y0..y1 on which depth bin `bin`
-// can be emitted (per row: the smallest first emitted bin and the largest cut
-// over the row's tiles); false if there is none. Conservative: emission still
-// tests each cell of the rows in between.
-__device__ __forceinline__ bool bin_window_rows(const uint8_t* tf, const uint8_t* tc,
-                                                int64_t level_stride, int Tx, int x0, int x1,
-                                                int y0, int y1, int bin, int& first, int& last) {
-    const int w = x1 - x0 + 1;
-    const int l = 31 - __clz(w);
-    const int64_t lv = (int64_t)l * level_stride + x0;
-    auto row_ok = [&](int y) {
-        const int64_t a = lv + (int64_t)y * Tx, b = a + w - (1 << l);
-        return min(tf[a], tf[b]) <= bin && bin <= max(tc[a], tc[b]);
-    };
+// can be emitted (a row qualifies when some tile of it admits the bin: two
+// overlapping runs of 2^l tiles cover the row's columns); false if there is
+// none. Conservative: the emission still tests every cell of the rows kept.
+// T: the level's packed windows, element stride st (2 for level 0, read from
+// the high halves of the tile words).
+__device__ __forceinline__ bool bin_window_rows(const uint16_t* T, int st, int Tx, int x0, int x1,
+                                                int y0, int y1, int l, int bin, int& first,
+                                                int& last) {
+    const int d = (x1 - x0 + 1 - (1 << l)) * st, step = Tx * st;
+    const uint16_t* p = T + (int64_t)(y0 * Tx + x0) * st;
     int y = y0;
-    while (y <= y1 && !row_ok(y)) ++y;
+    for (; y <= y1; ++y, p += step)
+        if (fc_admits(fc_merge(p[0], p[d]), bin)) break;
     if (y > y1) return false;
     first = y;
-    y = y1;
-    while (y > first && !row_ok(y)) --y;
+    p = T + (int64_t)(y1 * Tx + x0) * st;
+    for (y = y1; y > first; --y, p -= step)
+        if (fc_admits(fc_merge(p[0], p[d]), bin)) break;
     last = y;
     return true;
 }
 
-// Bucketed emission, load-balanced: a warp takes 32 pair-producing Gaussians of
-// one view, prefix-sums their rectangle areas, and spreads the rectangle cells
-// over its lanes (each lane finds the owner of its cell by a binary search over
-// the prefix); an active cell claims a slot in its (tile, depth bin) bucket.
-// One 1024-thread block per SM holds its view's tile ranks, cuts, first bins
-// and (when they fit in `smem_bytes`) the row sparse tables in shared memory,
-// so the per-Gaussian row scans do not wait on L2.
-constexpr int kEmitThreads = 1024;
+// Bucketed emission, load-balanced. A warp takes a group of 32 pair-producing
+// records of one view, cuts each rectangle to the rows where its depth bin can
+// be emitted and lays the cells of the cut rectangles end to end; per round
+// each lane walks kCells consecutive cells (one owner search per round, the
+// owner and the cell advanced in place), and a cell whose tile admits the
+// bin claims a slot in its (tile, depth bin) bucket. One 1024-thread block per
+// SM; warps take groups from a per-view counter, the next group claimed and
+// fetched while the current one is processed.
 constexpr int kEmitGroups = 16;  // groups per warp and block lifetime
+constexpr int kCells = 8;        // consecutive cells per lane and round
 
 __global__ void __launch_bounds__(kEmitThreads)
-emit_bucketed_kernel(const ClsView* __restrict__ views, const uint4* __restrict__ rects,
-                     const int32_t* __restrict__ tile_rank, const uint32_t* __restrict__ zmin,
+emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ tile_rank,
+                     const int32_t* __restrict__ rank0, const uint32_t* __restrict__ zmin,
                      const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                      uint64_t* __restrict__ keys, int64_t capacity,
-                     const uint32_t* __restrict__ work_list,
-                     const int32_t* __restrict__ work_count, int32_t* __restrict__ next_group,
-                     const uint8_t* __restrict__ cut, const uint8_t* __restrict__ front,
-                     const uint8_t* __restrict__ t_front, const uint8_t* __restrict__ t_cut,
+                     const uint4* __restrict__ work_list, const int32_t* __restrict__ work_count,
+                     int32_t* __restrict__ next_group, const uint8_t* __restrict__ cut,
+                     const uint8_t* __restrict__ front, const uint16_t* __restrict__ t_win,
                      int64_t total_tiles, int smem_bytes) {
-    // rank of each tile of the view, then its last and first emitted depth bin
-    extern __shared__ int32_t s_rank[];
+    extern __shared__ uint64_t s_key[];
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x;
     const int nt = Tx * view.tiles_y;
+    const int n = work_count[blockIdx.x];
     // blocks past the view's work leave before filling their tables
-    if (*(volatile int32_t*)(next_group + blockIdx.x) * 32 >= work_count[blockIdx.x]) return;
-    uint8_t* s_cut = reinterpret_cast<uint8_t*>(s_rank + nt);
-    uint8_t* s_front = s_cut + nt;
+    if (*(volatile int32_t*)(next_group + blockIdx.x) * 32 >= n) return;
+    int32_t* s_end = reinterpret_cast<int32_t*>(s_key + kEmitWarps * 32);
+    uint32_t* s_xy = reinterpret_cast<uint32_t*>(s_end + kEmitWarps * 32);
+    uint32_t* s_wb = s_xy + kEmitWarps * 32;
+    uint32_t* s_tile = s_wb + kEmitWarps * 32;
+    uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_tile + nt);
+    const int r0 = rank0[blockIdx.x];  // rank of the view's first rendered tile
+    const int64_t tb = view.tile_base;
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-        const int r = tile_rank[view.tile_base + i];
-        s_rank[i] = r;
-        s_cut[i] = cut ? cut[view.tile_base + i] : (uint8_t)(kDepthBins - 1);
-        s_front[i] = r >= 0 ? front[view.tile_base + i] : (uint8_t)0;
+        const int r = tile_rank[tb + i];
+        const bool on = r >= 0;
+        const uint32_t win = fc_pack(on, on ? front[tb + i] : 0u, cut ? cut[tb + i] : 255u);
+        s_tile[i] = (on ? (uint32_t)(r - r0 + 1) : 0u) | (win << 16);
     }
-    // the row sparse tables of the view (levels 0 .. L-1, 2^(L-1) <= Tx)
-    const int levels = 32 - __clz(Tx);
-    const uint8_t* tf = t_front + view.tile_base;
-    const uint8_t* tc = t_cut + view.tile_base;
-    int64_t level_stride = total_tiles;
-    if (emit_tables_fit(nt, Tx, smem_bytes)) {
-        // the row sparse tables of the view, built here in shared memory
-        // (level 0: first emitted bin / cut of rendered tiles, neutral 255 / 0
-        // elsewhere; level l: min / max over runs of 2^l tiles)
-        uint8_t* s_tf = s_front + nt;
-        uint8_t* s_tc = s_tf + (int64_t)levels * nt;
+    const int levels = row_levels(Tx);
+    const bool fits = emit_tables_fit(nt, Tx, smem_bytes);
+    if (fits) {  // the row tables of the view, built here in shared memory
         __syncthreads();
-        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-            const bool on = s_rank[i] >= 0;
-            s_tf[i] = on ? s_front[i] : (uint8_t)255;
-            s_tc[i] = on ? s_cut[i] : (uint8_t)0;
-        }
-        for (int l = 1; l < levels; ++l) {
+        for (int i = threadIdx.x; i < nt; i += blockDim.x)
+            if (i % Tx + 2 <= Tx) s_lv[i] = (uint16_t)fc_merge(s_tile[i] >> 16, s_tile[i + 1] >> 16);
+        for (int l = 2; l < levels; ++l) {
             __syncthreads();
             const int h = 1 << (l - 1);
-            const int prev = (l - 1) * nt, cur = l * nt;
-            for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-                const int x = i % Tx;
-                if (x + 2 * h > Tx) continue;
-                s_tf[cur + i] = min(s_tf[prev + i], s_tf[prev + i + h]);
-                s_tc[cur + i] = max(s_tc[prev + i], s_tc[prev + i + h]);
-            }
+            const int prev = (l - 2) * nt, cur = prev + nt;
+            for (int i = threadIdx.x; i < nt; i += blockDim.x)
+                if (i % Tx + 2 * h <= Tx) s_lv[cur + i] = (uint16_t)fc_merge(s_lv[prev + i], s_lv[prev + i + h]);
         }
-        tf = s_tf;
-        tc = s_tc;
-        level_stride = nt;
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int n = work_count[blockIdx.x];
-    const uint32_t lo = zmin[blockIdx.x], hi = zmax[blockIdx.x];
-    // each warp takes up to kEmitGroups groups of 32 work items from the
-    // view's counter (the tables above are filled once per block), so blocks
-    // retire regularly and kernels of other streams get SMs in between
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t* w_key = s_key + warp * 32;
+    int32_t* w_end = s_end + warp * 32;
+    uint32_t* w_xy = s_xy + warp * 32;
+    uint32_t* w_wb = s_wb + warp * 32;
+    const DepthBins db = depth_bins(zmin[blockIdx.x], zmax[blockIdx.x]);
+    const uint4* wl = work_list + view.rec_base;
+    int g_next = 0;
+    if (lane == 0) g_next = atomicAdd(next_group + blockIdx.x, 1);
+    g_next = __shfl_sync(0xffffffffu, g_next, 0);
+    uint4 it_next = make_uint4(0u, 0u, 0u, 0u);
+    if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
     for (int taken = 0; taken < kEmitGroups; ++taken) {
-        int w = 0;
-        if (lane == 0) w = atomicAdd(next_group + blockIdx.x, 1);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if (w * 32 >= n) break;
-        const int item = w * 32 + lane;
-        int x0 = 0, x1 = -1, y0 = 0, y1 = -1, area = 0, bin = 0;
-        uint32_t zb = 0, rec = 0;
-        if (item < n) {
-            const uint32_t g = work_list[view.rec_base + item];
-            rec = (uint32_t)(view.rec_base + g);
-            if (record_rect(rects, rec, x0, x1, y0, y1, zb)) {
-                bin = depth_bin(zb, lo, hi);
-                int r0, r1;
-                if (bin_window_rows(tf, tc, level_stride, Tx, x0, x1, y0, y1, bin, r0, r1)) {
-                    y0 = r0;
-                    y1 = r1;
-                    area = (x1 - x0 + 1) * (y1 - y0 + 1);
-                }
+        const int g = g_next;
+        const uint4 item = it_next;
+        if (g * 32 >= n) break;
+        if (taken + 1 < kEmitGroups) {  // claim and fetch the next group now
+            int gn = 0;
+            if (lane == 0) gn = atomicAdd(next_group + blockIdx.x, 1);
+            g_next = __shfl_sync(0xffffffffu, gn, 0);
+            if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
+        }
+        int x0 = 0, x1 = -1, y0 = 0, y1 = -1, bin = 0, area = 0;
+        if (g * 32 + lane < n) {
+            unpack_rect(item, x0, x1, y0, y1);
+            bin = depth_bin(item.z, db);
+            const int l = 31 - __clz(x1 - x0 + 1);
+            const uint16_t* T = l == 0 ? reinterpret_cast<const uint16_t*>(s_tile) + 1
+                                : fits ? s_lv + (l - 1) * nt
+                                       : t_win + (int64_t)(l - 1) * total_tiles + tb;
+            int ra, rb;
+            if (bin_window_rows(T, l == 0 ? 2 : 1, Tx, x0, x1, y0, y1, l, bin, ra, rb)) {
+                y0 = ra;
+                y1 = rb;
+                area = (x1 - x0 + 1) * (y1 - y0 + 1);
             }
         }
         int incl = area;
@@ -856,52 +871,69 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const uint4* __restrict_
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        // the item's fields a cell needs, packed so a cell fetches them from
-        // its owner in three shuffles (tile coordinates, widths < 2^16, bin < 2^8)
-        const int start = incl - area;
-        const uint32_t xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
-        const uint32_t wb = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
-        // kU cells per lane per round, so kU slot claims are in flight before
-        // the first key is stored
-        constexpr int kU = 8;
-        for (int c0 = 0; c0 < total; c0 += 32 * kU) {
-            int32_t sub[kU];
-            uint32_t kz[kU], kr[kU];
+        if (total == 0) continue;
+        __syncwarp();  // the previous group's item fields are no longer read
+        w_key[lane] = ((uint64_t)item.z << 32) | item.w;
+        w_end[lane] = incl;
+        w_xy[lane] = (uint32_t)x0 | ((uint32_t)y0 << 16);
+        w_wb[lane] = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
+        __syncwarp();
+        for (int c0 = 0; c0 < total; c0 += 32 * kCells) {
+            const int cf = c0 + lane * kCells;
+            // owner of cell cf: the first item whose cells end after it
+            int lo = 0, hi = 31;
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int c = c0 + u * 32 + lane;
-                int l = 0, h = 31;
+            for (int step = 0; step < 5; ++step) {
+                const int mid = (lo + hi) >> 1;
+                const int pm = __shfl_sync(0xffffffffu, incl, mid);
+                if (pm > cf) hi = mid; else lo = mid + 1;
+            }
+            int own = lo;
+            int end = w_end[own];
+            uint32_t xy = w_xy[own], wb = w_wb[own];
+            uint64_t key = w_key[own];
+            int w = (int)(wb & 0xffffu), ob = (int)(wb >> 16);
+            int q, rem;
+            divmod_small(max(cf - (own > 0 ? w_end[own - 1] : 0), 0), w, q, rem);
+            int cell = ((int)(xy >> 16) + q) * Tx + (int)(xy & 0xffffu) + rem;
+            int32_t sub[kCells];
+            uint64_t kk[kCells];
 #pragma unroll
-                for (int step = 0; step < 5; ++step) {
-                    const int mid = (l + h) >> 1;
-                    const int pm = __shfl_sync(0xffffffffu, incl, mid);
-                    if (pm > c) h = mid; else l = mid + 1;
-                }
-                const int own = l;
-                const int o_start = __shfl_sync(0xffffffffu, start, own);
-                const uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
-                const uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
-                kz[u] = __shfl_sync(0xffffffffu, zb, own);
-                kr[u] = __shfl_sync(0xffffffffu, rec, own);
-                const int o_x0 = (int)(o_xy & 0xffffu), o_y0 = (int)(o_xy >> 16);
-                const int o_w = (int)(o_wb & 0xffffu), o_bin = (int)(o_wb >> 16);
+            for (int u = 0; u < kCells; ++u) {
+                const int c = cf + u;
                 sub[u] = -1;
                 if (c < total) {
-                    const int k = c - o_start;
-                    int q, rem;
-                    divmod_small(k, o_w, q, rem);
-                    const int cell = (o_y0 + q) * Tx + o_x0 + rem;
-                    const int r = s_rank[cell];
-                    if (r >= 0 && o_bin <= (int)s_cut[cell] && o_bin >= (int)s_front[cell])
-                        sub[u] = r * kDepthBins + o_bin;
+                    if (c >= end) {  // the next item with cells starts at c
+                        do {
+                            ++own;
+                        } while (w_end[own] <= c);
+                        end = w_end[own];
+                        xy = w_xy[own];
+                        wb = w_wb[own];
+                        key = w_key[own];
+                        w = (int)(wb & 0xffffu);
+                        ob = (int)(wb >> 16);
+                        rem = 0;
+                        cell = (int)(xy >> 16) * Tx + (int)(xy & 0xffffu);
+                    }
+                    const uint32_t word = s_tile[cell];
+                    if (fc_admits(word >> 16, ob))
+                        sub[u] = (r0 + (int)(word & 0xffffu) - 1) * kDepthBins + ob;
+                    if (++rem == w) {
+                        rem = 0;
+                        cell += Tx - w + 1;
+                    } else {
+                        ++cell;
+                    }
                 }
+                kk[u] = key;
             }
-            int32_t p[kU];
+            int32_t p[kCells];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
+            for (int u = 0; u < kCells; ++u) p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
 #pragma unroll
-            for (int u = 0; u < kU; ++u)
-                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = ((uint64_t)kz[u] << 32) | kr[u];
+            for (int u = 0; u < kCells; ++u)
+                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = kk[u];
         }
     }
 }
@@ -914,10 +946,10 @@ constexpr int kCompleteChunks = 64;
 
 __global__ void __launch_bounds__(256)
 complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
-                      const uint4* __restrict__ rects, const uint32_t* __restrict__ zmin,
+                      const uint32_t* __restrict__ zmin,
                       const uint32_t* __restrict__ zmax, int32_t* __restrict__ cursor,
                       uint64_t* __restrict__ keys, int64_t capacity,
-                      const uint32_t* __restrict__ work_list,
+                      const uint4* __restrict__ work_list,
                       const int32_t* __restrict__ work_count, const int32_t* __restrict__ trunc,
                       const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
                       const uint8_t* __restrict__ front, int* __restrict__ item_counter) {
@@ -937,18 +969,18 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
         const int ty = local / view.tiles_x, tx = local - ty * view.tiles_x;
         const int n = work_count[v];
         const int first_bin = front[tile];
+        const DepthBins db = depth_bins(zmin[v], zmax[v]);
         const int per = (n + kCompleteChunks - 1) / kCompleteChunks;
         const int a = chunk * per, b = min(n, a + per);
         for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
-            const uint32_t rec = (uint32_t)(view.rec_base + work_list[view.rec_base + i]);
+            const uint4 r = work_list[view.rec_base + i];
             int x0, x1, y0, y1;
-            uint32_t zb;
-            if (!record_rect(rects, rec, x0, x1, y0, y1, zb)) continue;
+            unpack_rect(r, x0, x1, y0, y1);
             if (tx < x0 || tx > x1 || ty < y0 || ty > y1) continue;
-            const int bin = depth_bin(zb, zmin[v], zmax[v]);
+            const int bin = depth_bin(r.z, db);
             if (bin <= old_cut || bin < first_bin) continue;
             const int64_t p = atomicAdd(cursor + (int64_t)rank * kDepthBins + bin, 1);
-            if (p < capacity) keys[p] = ((uint64_t)zb << 32) | rec;
+            if (p < capacity) keys[p] = ((uint64_t)r.z << 32) | r.w;
         }
     }
 }
@@ -1005,7 +1037,7 @@ __global__ void capacity_check_kernel(const int64_t* n_pairs, int64_t capacity,
 
 struct ProjLayout {
     size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, work_list, work_count, front, t_front, t_cut, compact, rects, total;
+        bins, work_list, work_count, front, t_win, rank0, compact, rects, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1030,11 +1062,11 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.big_list = o; o = align256(o + (size_t)info->total_records * 16);
     L.big_count = o; o = align256(o + 4);
     L.bins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
-    L.work_list = o; o = align256(o + (size_t)info->total_records * 4);
+    L.work_list = o; o = align256(o + (size_t)info->total_records * 16);
     L.work_count = o; o = align256(o + (size_t)V * 8);  // + per-view emission counters
     L.front = o; o = align256(o + (size_t)info->total_tiles);
-    L.t_front = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
-    L.t_cut = o; o = align256(o + (size_t)info->total_tiles * kRowLevels);
+    L.t_win = o; o = align256(o + (size_t)info->total_tiles * (kRowLevels - 1) * 2);
+    L.rank0 = o; o = align256(o + (size_t)V * 4);
     L.compact = o;
     o = align256(o + (size_t)((info->total_tiles + kCompactChunk - 1) / kCompactChunk + 1) * 8);
     L.rects = o; o = align256(o + (size_t)info->total_records * 16);
@@ -1092,11 +1124,11 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     uint4* big_list = reinterpret_cast<uint4*>(ws + L.big_list);
     int32_t* big_count = reinterpret_cast<int32_t*>(ws + L.big_count);
     int32_t* bins = reinterpret_cast<int32_t*>(ws + L.bins);
-    uint32_t* work_list = reinterpret_cast<uint32_t*>(ws + L.work_list);
+    uint4* work_list = reinterpret_cast<uint4*>(ws + L.work_list);
     int32_t* work_count = reinterpret_cast<int32_t*>(ws + L.work_count);
     uint8_t* front = reinterpret_cast<uint8_t*>(ws + L.front);
-    uint8_t* t_front = reinterpret_cast<uint8_t*>(ws + L.t_front);
-    uint8_t* t_cut = reinterpret_cast<uint8_t*>(ws + L.t_cut);
+    uint16_t* t_win = reinterpret_cast<uint16_t*>(ws + L.t_win);
+    int32_t* rank0 = reinterpret_cast<int32_t*>(ws + L.rank0);
     uint4* rects = reinterpret_cast<uint4*>(ws + L.rects);  // kept from call to call
     const int64_t subs = info->total_tiles * kDepthBins;
     const int64_t max_view_tiles = info->max_view_tiles;
@@ -1107,8 +1139,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     const int grid_cap = (int)hmin64(max_view_tiles * 4 + 16 * 1024, 200 * 1024);
     const int sms = per_device(g_proj_sms, [](int dev) {
         for (const void* k : {(const void*)emit_bucketed_kernel, (const void*)tile_mask_kernel,
-                              (const void*)bins_prefix_kernel, (const void*)active_zmin_kernel,
-                              (const void*)bin_window_tables_kernel})
+                              (const void*)bins_prefix_kernel, (const void*)active_zmin_kernel})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         return device_sms(dev);
     });
@@ -1118,12 +1149,12 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     auto emit_stage = [&]() {
         sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
             views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
-            bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front);
+            bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front, rank0);
         // shared memory for the tables of views up to 2^8 tiles wide
-        const int emit_smem = (int)hmin64(max_view_tiles * (6 + 2 * 8), 200 * 1024);
-        bin_window_tables_kernel<<<V, 1024, 200 * 1024, s>>>(
-            views_dev, tile_rank, front, bin_cut, t_front, t_cut, info->total_tiles, 200 * 1024,
-            emit_smem);
+        const int emit_smem =
+            (int)hmin64(max_view_tiles * (4 + 2 * 7) + kEmitItemBytes, 200 * 1024);
+        bin_window_tables_kernel<<<V, 1024, 0, s>>>(views_dev, tile_rank, front, bin_cut, t_win,
+                                                     info->total_tiles, emit_smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
                                                       kEmitThreads, (size_t)emit_smem);
@@ -1136,9 +1167,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             65535);
         // the view index varies fastest, so the first wave spreads over all views
         emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
-            views_dev, rects, tile_rank, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, work_count + V, bin_cut, front, t_front, t_cut, info->total_tiles,
-            emit_smem);
+            views_dev, tile_rank, rank0, zmin, zmax, cursor, keys, capacity, work_list,
+            work_count, work_count + V, bin_cut, front, t_win, info->total_tiles, emit_smem);
     };
     if (project_mode == 2) {  // the previous call counted these pairs: emit them
         if (cpv > 0) {
@@ -1208,7 +1238,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         const unsigned work_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
                                                       2048);
         stamp_bins_kernel<<<dim3(work_blocks, V), kBinBlock, 0, s>>>(
-            views_dev, rects, zmin, zmax, work_list, work_count, bins, info->total_sat);
+            views_dev, zmin, zmax, work_list, work_count, bins, info->total_sat);
         // per (rank, bin) counts go to `cursor`, which sub_offsets then
         // turns into the buckets' slot cursors
         bins_prefix_kernel<<<dim3(kDepthBins, V), 512, grid_cap, s>>>(
@@ -1243,10 +1273,9 @@ extern "C" int cls_complete_truncated(const ClsView* views_dev, const ClsBatchIn
     char* ws = static_cast<char*>(workspace);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     complete_tiles_kernel<<<1024, 256, 0, s>>>(
-        views_dev, info->n_views, reinterpret_cast<const uint4*>(ws + L.rects),
-        reinterpret_cast<uint32_t*>(ws + L.zmin),
+        views_dev, info->n_views, reinterpret_cast<uint32_t*>(ws + L.zmin),
         reinterpret_cast<uint32_t*>(ws + L.zmax), reinterpret_cast<int32_t*>(ws + L.cursor), keys,
-        capacity, reinterpret_cast<uint32_t*>(ws + L.work_list),
+        capacity, reinterpret_cast<const uint4*>(ws + L.work_list),
         reinterpret_cast<int32_t*>(ws + L.work_count), trunc, trunc_count, trunc_cap,
         reinterpret_cast<uint8_t*>(ws + L.front), work_counter);
     CLS_CHECK_LAUNCH();
