@@ -141,14 +141,18 @@ typedef struct ClsProjected {
  * bits(z) < zb; the pixel state after the prefix is kept in prefix_state /
  * prefix_last (see cls_render_forward). cls_project_and_bin decides per active
  * tile whether the cache still holds (every active Gaussian of the tile has
- * bits(z) >= zb) or must be rebuilt (zb is then set a margin of 2^17 float
- * ulps, about 1.6%, in front of the tile's nearest active Gaussian, and
- * n_prefix to CLS_PREFIX_UNKNOWN); the forward pass writes the state and
- * n_prefix of rebuilt tiles and last_active of every tile it renders. */
+ * bits(z) >= zb) or must be rebuilt (n_prefix is then set to
+ * CLS_PREFIX_UNKNOWN and zb moved in front of the tile's nearest active
+ * Gaussian: in the flat layout a margin of 2^17 float ulps, about 1.6%, in
+ * front of its depth; in the bucketed layout to the lowest depth of the depth
+ * bin in front of the one that holds it); the forward pass writes the state and n_prefix of
+ * rebuilt tiles and last_active of every tile it renders. */
 typedef struct ClsTileCache {
     uint32_t zb;          /* prefix boundary, bits of a positive float depth */
     uint32_t n_prefix;    /* list entries in the prefix, or CLS_PREFIX_UNKNOWN */
-    uint32_t zmin_active; /* smallest bits(z) of the tile's active Gaussians */
+    uint32_t zmin_active; /* flat layout: smallest bits(z) of the tile's active
+                             Gaussians; bucketed: the lowest bits(z) of the depth
+                             bin of the nearest one (a lower bound of it) */
     int32_t last_active;  /* last list position of an active entry, -1 if none */
 } ClsTileCache;
 #define CLS_PREFIX_UNKNOWN 0xffffffffu
@@ -223,11 +227,16 @@ int cls_lift_change_masks_static(const float* params, int32_t n, int32_t row_str
  * do this once per camera set), mode 1 re-projects only the active Gaussians
  * (every iteration, after the parameters change); the records and the
  * workspace (which keeps every record's tile rectangle) of earlier calls
- * supply the rest, so both must be kept between calls. Mode 2 (bucketed layout,
- * keys and a capacity > 0 required) only writes the bucket offsets and emits
- * the pairs that the immediately preceding call counted with capacity 0,
- * with the same arguments otherwise and the same workspace: nothing it reads
- * may change in between. Then:
+ * supply the rest, so both must be kept between calls. In the bucketed layout
+ * the mode 0 call also fixes each view's depth bins (from the depths of its
+ * pair-producing Gaussians) and counts the static Gaussians' pairs per (tile,
+ * depth bin) once; mode 1 calls keep both, so between a mode 0 call and the
+ * mode 1 calls that follow it the active set and the static Gaussians must
+ * not change (the workspace must be zero-filled before its first use).
+ * Mode 2 (bucketed layout, keys and a capacity > 0 required) only writes the
+ * bucket offsets and emits the pairs that the immediately preceding call
+ * counted with capacity 0, with the same arguments otherwise and the same
+ * workspace: nothing it reads may change in between. Then:
  *   tile_active[total_tiles]  uint8: 1 iff a non-culled active Gaussian's
  *                             tile rectangle holds the tile
  *   active_tiles[total_tiles] int32: ascending global ids of active tiles,

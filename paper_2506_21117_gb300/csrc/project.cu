@@ -30,12 +30,13 @@ __device__ __forceinline__ void stamp_rect(int32_t* grid, int Wd, int x0, int x1
 }
 
 // Tile rectangle and depth bits of every record, written by the projection
-// (16 B: x0 | x1 << 16, y0 | y1 << 16, depth bits, 1 if the record has
-// pairs-to-be else 0), so binning reads 16 B per record instead of its 48.
+// (16 B: x0 | x1 << 16, y0 | y1 << 16, depth bits, and 1 for a visible static
+// record, 2 for a visible active one, 0 if the record has no tiles), so
+// binning reads 16 B per record instead of its 48.
 __device__ __forceinline__ uint4 pack_rect(bool valid, int x0, int x1, int y0, int y1,
-                                           uint32_t zbits) {
+                                           uint32_t zbits, uint32_t flag) {
     return valid ? make_uint4((uint32_t)x0 | ((uint32_t)x1 << 16),
-                              (uint32_t)y0 | ((uint32_t)y1 << 16), zbits, 1u)
+                              (uint32_t)y0 | ((uint32_t)y1 << 16), zbits, flag)
                  : make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -112,7 +113,8 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
         r2 = make_float4(0.f, __int_as_float(slot), 0.f, 0.f);
     }
     r2.w = __int_as_float(radius);
-    rects[view.rec_base + g] = pack_rect(valid, x0, x1, y0, y1, __float_as_uint(r2.z));
+    rects[view.rec_base + g] =
+        pack_rect(valid, x0, x1, y0, y1, __float_as_uint(r2.z), MODE == 1 ? 2u : 1u);
     float4* out = reinterpret_cast<float4*>(records + view.rec_base + g);
     out[0] = r0;
     out[1] = r1;
@@ -354,14 +356,15 @@ active_zmin_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
 // and the static-prefix decision of every active tile: its cache holds while
 // no active Gaussian of the tile lies in front of the boundary; otherwise the
 // boundary moves a margin in front of the nearest active Gaussian and the
-// prefix is rebuilt by the next forward pass. Two passes over chunks of
-// kCompactChunk tiles around one scan of the chunk counts.
+// prefix is rebuilt by the next forward pass (flat layout only, `decide` 1;
+// the bucketed layout decides in col_counts_kernel). Two passes over chunks
+// of kCompactChunk tiles around one scan of the chunk counts.
 constexpr int kCompactPer = 4;  // consecutive tiles per thread
 constexpr int kCompactChunk = 1024 * kCompactPer;
 
 __global__ void __launch_bounds__(1024)
 compact_count_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
-                     ClsTileCache* __restrict__ tile_cache, int prefix_mode,
+                     ClsTileCache* __restrict__ tile_cache, int prefix_mode, int decide,
                      int64_t* __restrict__ partials) {
     __shared__ int64_t smem[1024 / 32 + 1];
     const int64_t t0 = (int64_t)blockIdx.x * kCompactChunk + (int64_t)threadIdx.x * kCompactPer;
@@ -371,6 +374,7 @@ compact_count_kernel(const uint8_t* __restrict__ tile_active, int64_t n_tiles,
         const int64_t t = t0 + j;
         if (t < n_tiles && tile_active[t]) {
             ++cnt;
+            if (!decide) continue;
             const ClsTileCache c = tile_cache[t];
             const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
                               c.zmin_active >= c.zb;
@@ -514,125 +518,333 @@ __device__ __forceinline__ int depth_bin(uint32_t zb, const DepthBins& d) {
     return min((int)((float)(zb - d.lo) * d.scale), kDepthBins - 1);
 }
 
-// Bucketed layout: stamp every pair-producing rectangle into its depth bin's
-// difference grid; the prefix sums then give pairs per (tile, depth bin).
-// (the pair-producing records of each view are those of its work list)
+// Smallest depth bits whose depth bin is at least b (0 for b <= 0, all ones
+// for b >= kDepthBins): a binary search, exact because depth_bin is monotone.
+__device__ __forceinline__ uint32_t bin_edge(int b, const DepthBins& d) {
+    if (b <= 0) return 0u;
+    if (b >= kDepthBins) return 0xffffffffu;
+    uint64_t l = (uint64_t)d.lo + 1, h = 0xffffffffull;  // depth_bin(h) = kDepthBins - 1
+    while (l < h) {
+        const uint64_t m = (l + h) >> 1;
+        if (depth_bin((uint32_t)m, d) >= b) h = m; else l = m + 1;
+    }
+    return (uint32_t)l;
+}
+
+// ---------------------------------------------------------------------------
+// Bucketed layout: pairs per (tile, depth bin).
+//
+// A view's depth range (the depth bits of its pair-producing Gaussians) is
+// fixed by the call that projects every Gaussian (project_mode 0) and kept by
+// later calls, so a static Gaussian's depth bin does not change during an
+// update and its pairs per (tile, bin) form a fixed 2D prefix sum S of
+// difference-grid stamps, computed by that call. Every call stamps only the
+// active Gaussians' rectangles into a second difference grid A, prefix-sums
+// the bins they occupy, and adds the two at the rendered tiles. Both grids are
+// bin-fastest: entry (cell y * (Tx + 1) + x of the view, bin b) at
+// (sat_base + cell) * kDepthBins + b, so a block of kDepthBins threads walks a
+// row or a column with coalesced loads. The passes over A clear every entry
+// they read, so A is zero between calls.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void stamp_rect_bin(int32_t* G, int Wd, int b, int x0, int x1, int y0,
+                                               int y1) {
+    atomicAdd(G + ((int64_t)y0 * Wd + x0) * kDepthBins + b, 1);
+    atomicAdd(G + ((int64_t)y0 * Wd + x1 + 1) * kDepthBins + b, -1);
+    atomicAdd(G + ((int64_t)(y1 + 1) * Wd + x0) * kDepthBins + b, -1);
+    atomicAdd(G + ((int64_t)(y1 + 1) * Wd + x1 + 1) * kDepthBins + b, 1);
+}
+
+// S stamps: every visible static record of the view (rectangle flag 1).
 __global__ void __launch_bounds__(kBinBlock)
-stamp_bins_kernel(const ClsView* __restrict__ views,
-                  const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
-                  const uint4* __restrict__ work_list, const int32_t* __restrict__ work_count,
-                  int32_t* __restrict__ bins, int64_t total_sat) {
+stamp_static_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
+                    const uint4* __restrict__ rects, const uint32_t* __restrict__ zmin,
+                    const uint32_t* __restrict__ zmax, int32_t* __restrict__ S) {
     const ClsView& view = views[blockIdx.y];
-    const int n = work_count[blockIdx.y];
+    const int n = scenes[view.scene].n;
     const DepthBins db = depth_bins(zmin[blockIdx.y], zmax[blockIdx.y]);
-    for (int i = blockIdx.x * kBinBlock + threadIdx.x; i < n; i += gridDim.x * kBinBlock) {
-        const uint4 r = work_list[view.rec_base + i];
+    int32_t* G = S + view.sat_base * kDepthBins;
+    for (int g = blockIdx.x * kBinBlock + threadIdx.x; g < n; g += gridDim.x * kBinBlock) {
+        const uint4 r = rects[view.rec_base + g];
+        if (r.w != 1u) continue;
+        int x0, x1, y0, y1;
+        unpack_rect(r, x0, x1, y0, y1);
+        stamp_rect_bin(G, view.tiles_x + 1, depth_bin(r.z, db), x0, x1, y0, y1);
+    }
+}
+
+// A stamps: every visible active record of the view (rectangle flag 2), and
+// the range of bins they occupy (arange[v] lowest, arange[V + v] highest).
+__global__ void __launch_bounds__(kBinBlock)
+stamp_active_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
+                    const uint4* __restrict__ rects, const uint32_t* __restrict__ zmin,
+                    const uint32_t* __restrict__ zmax, int32_t* __restrict__ A,
+                    uint32_t* __restrict__ arange) {
+    const ClsView& view = views[blockIdx.y];
+    const ClsScene& sc = scenes[view.scene];
+    const DepthBins db = depth_bins(zmin[blockIdx.y], zmax[blockIdx.y]);
+    int32_t* G = A + view.sat_base * kDepthBins;
+    uint32_t lo = 0xffffffffu, hi = 0u;
+    for (int i = blockIdx.x * kBinBlock + threadIdx.x; i < sc.n_active;
+         i += gridDim.x * kBinBlock) {
+        const uint4 r = rects[view.rec_base + sc.active_idx[i]];
+        if (r.w == 0u) continue;
         int x0, x1, y0, y1;
         unpack_rect(r, x0, x1, y0, y1);
         const int b = depth_bin(r.z, db);
-        stamp_rect(bins + b * total_sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
+        lo = min(lo, (uint32_t)b);
+        hi = max(hi, (uint32_t)b);
+        stamp_rect_bin(G, view.tiles_x + 1, b, x0, x1, y0, y1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0 && hi >= lo) {
+        atomicMin(arange + blockIdx.y, lo);
+        atomicMax(arange + gridDim.y + blockIdx.y, hi);
     }
 }
 
-// Per (depth bin, view): the 2D prefix sum of the bin's difference grid gives
-// each tile's count of pairs in that bin; the counts of the rendered tiles go
-// to counts[rank * kDepthBins + bin] (the layout the bucket scan reads).
-__global__ void __launch_bounds__(512)
-bins_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ bins,
-                   int64_t total_sat, int smem_cap, const int32_t* __restrict__ tile_rank,
-                   int32_t* __restrict__ counts) {
-    extern __shared__ int32_t s_grid[];
+// Prefix sums along x of every row of a grid (blocks of kDepthBins threads
+// striding over the rows of view blockIdx.y, a thread per bin; with `arange`
+// only the view's occupied bins). With `clear`, the column x = Tx and the row
+// y = Ty, which no later pass reads, are cleared.
+__device__ __forceinline__ void row_prefix(int32_t* p, int Tx, int clear) {
+    int32_t run = 0;
+    int x = 0;
+    for (; x + 8 <= Tx; x += 8) {  // eight loads in flight
+        int32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = p[(int64_t)(x + k) * kDepthBins];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            run += v[k];
+            p[(int64_t)(x + k) * kDepthBins] = run;
+        }
+    }
+    for (; x < Tx; ++x) {
+        run += p[(int64_t)x * kDepthBins];
+        p[(int64_t)x * kDepthBins] = run;
+    }
+    if (clear) p[(int64_t)Tx * kDepthBins] = 0;
+}
+
+__global__ void __launch_bounds__(kDepthBins)
+row_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ G,
+                  const uint32_t* __restrict__ arange, int clear) {
     const ClsView& view = views[blockIdx.y];
     const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
-    const int b = blockIdx.x;
-    int32_t* G = bins + b * total_sat + view.sat_base;
-    const int32_t* rank = tile_rank + view.tile_base;
-    const int p = smem_pitch(Tx);
-    if ((int64_t)Ty * p * 4 > smem_cap) {
-        prefix2d(G, Ty, Tx, Wd);
-        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-            const int r = rank[t];
-            if (r >= 0) counts[(int64_t)r * kDepthBins + b] = G[(int64_t)(t / Tx) * Wd + t % Tx];
-        }
-        return;
-    }
-#pragma unroll 8
-    for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-        const int y = t / Tx, x = t - y * Tx;
-        s_grid[y * p + x] = G[(int64_t)y * Wd + x];
-    }
-    __syncthreads();
-    prefix2d_smem(s_grid, Ty, Tx, p);
-#pragma unroll 8
-    for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-        const int r = rank[t];
-        if (r >= 0) {
-            const int y = t / Tx, x = t - y * Tx;
-            counts[(int64_t)r * kDepthBins + b] = s_grid[y * p + x];
+    const uint32_t b = threadIdx.x;
+    if (arange && (b < arange[blockIdx.y] || b > arange[gridDim.y + blockIdx.y])) return;
+    for (int y = blockIdx.x; y <= Ty; y += gridDim.x) {
+        int32_t* p = G + (view.sat_base + (int64_t)y * Wd) * kDepthBins + b;
+        if (y < Ty) {
+            row_prefix(p, Tx, clear);
+        } else if (clear) {
+            for (int x = 0; x <= Tx; ++x) p[(int64_t)x * kDepthBins] = 0;
         }
     }
 }
 
-// Pairs per (active tile rank, depth bin), entry e = rank * kDepthBins + bin,
-// are in `counts` (written by bins_prefix_kernel).
-__global__ void __launch_bounds__(kBinBlock)
-sub_count_kernel(const int32_t* __restrict__ n_active, const int32_t* __restrict__ counts,
-                 int64_t* __restrict__ partials) {
-    __shared__ int64_t smem[kBinBlock / 32 + 1];
-    const int64_t ne = (int64_t)(*n_active) * kDepthBins;
-    int64_t cnt = 0;
-    for (int it = 0; it < kBinItems; ++it) {
-        const int64_t e = (int64_t)blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
-        if (e < ne) cnt += counts[e];
+// Prefix sums along y of S (after row_prefix_kernel): S then holds, at every
+// tile (y < Ty, x < Tx), its static pairs per bin. Blocks stride over the
+// columns of view blockIdx.y.
+__device__ __forceinline__ void col_prefix(int32_t* p, int Ty, int64_t step) {
+    int32_t run = 0;
+    int y = 0;
+    for (; y + 8 <= Ty; y += 8) {
+        int32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = p[(y + k) * step];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            run += v[k];
+            p[(y + k) * step] = run;
+        }
     }
+    for (; y < Ty; ++y) {
+        run += p[y * step];
+        p[y * step] = run;
+    }
+}
+
+__global__ void __launch_bounds__(kDepthBins)
+col_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ S) {
+    const ClsView& view = views[blockIdx.y];
+    const int Tx = view.tiles_x, Ty = view.tiles_y;
+    const int64_t step = (int64_t)(Tx + 1) * kDepthBins;
+    for (int x = blockIdx.x; x < Tx; x += gridDim.x)
+        col_prefix(S + (view.sat_base + x) * kDepthBins + threadIdx.x, Ty, step);
+}
+
+// Per (column, view) block, a thread per bin: walks the column's tiles,
+// completing A's prefix sums along y (and clearing A); at each rendered tile
+// writes its pairs per bin, S + A, to counts[rank * kDepthBins + bin]. Per
+// rendered tile also: its pair total (ttot[rank], and into its chunk's partial
+// sum), the nearest active Gaussian's depth bin ba (the first bin where A is
+// non-zero) and the static-prefix decision. A cached prefix holds while its
+// boundary zb lies at or in front of edge(ba), the lowest depth of bin ba
+// (then every active Gaussian of the tile has bits(z) >= zb); otherwise, or
+// with prefix_mode 0, the boundary moves to edge(ba - 1), one bin in front,
+// so that a nearest active Gaussian moving forward by less than a bin keeps
+// the prefix, and the prefix is rebuilt by the next forward pass.
+// front[tile] = first bin to emit. Rows are processed eight at a time, their
+// loads issued together.
+constexpr int kTileChunk = 64;  // tiles per partial sum of the pair totals
+
+__global__ void __launch_bounds__(kDepthBins)
+col_counts_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ S,
+                  int32_t* __restrict__ A, const uint32_t* __restrict__ arange,
+                  const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
+                  const int32_t* __restrict__ tile_rank, ClsTileCache* __restrict__ tile_cache,
+                  int prefix_mode, int32_t* __restrict__ counts, uint8_t* __restrict__ front,
+                  int32_t* __restrict__ ttot, int64_t* __restrict__ tile_partials) {
+    __shared__ int32_t s_tot[kDepthBins];
+    __shared__ int32_t s_ba[kDepthBins];
+    __shared__ int32_t s_rank[kDepthBins];
+    const ClsView& view = views[blockIdx.y];
+    const int Tx = view.tiles_x, Ty = view.tiles_y;
+    const int b = threadIdx.x, lane = b & 31, warp = b >> 5;
+    const bool occupied = (uint32_t)b >= arange[blockIdx.y] &&
+                          (uint32_t)b <= arange[gridDim.y + blockIdx.y];
+    const int64_t step = (int64_t)(Tx + 1) * kDepthBins;
+    const int64_t tb = view.tile_base;
+    const DepthBins db = depth_bins(zmin[blockIdx.y], zmax[blockIdx.y]);
+    for (int x = blockIdx.x; x < Tx; x += gridDim.x) {
+        const int32_t* sp = S + (view.sat_base + x) * kDepthBins + b;
+        int32_t* ap = A + (view.sat_base + x) * kDepthBins + b;
+        int32_t run = 0;
+        for (int y0 = 0; y0 < Ty; y0 += kDepthBins) {
+            const int ny = min(kDepthBins, Ty - y0);
+            if (b < ny) {
+                s_tot[b] = 0;
+                s_ba[b] = kDepthBins;
+                s_rank[b] = tile_rank[tb + (int64_t)(y0 + b) * Tx + x];
+            }
+            __syncthreads();
+            for (int j0 = 0; j0 < ny; j0 += 8) {
+                int32_t av[8], sv[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int j = j0 + k;
+                    const int64_t at = (int64_t)(y0 + j) * step;
+                    av[k] = occupied && j < ny ? ap[at] : 0;
+                    sv[k] = j < ny && s_rank[j] >= 0 ? sp[at] : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int j = j0 + k;
+                    if (j >= ny) break;  // uniform over the block
+                    if (occupied) {
+                        run += av[k];
+                        ap[(int64_t)(y0 + j) * step] = 0;
+                    }
+                    const int r = s_rank[j];
+                    if (r < 0) continue;
+                    const int32_t c = sv[k] + run;
+                    counts[(int64_t)r * kDepthBins + b] = c;
+                    int32_t s = c;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    const unsigned m = __ballot_sync(0xffffffffu, run > 0);
+                    if (lane == 0) {
+                        atomicAdd(&s_tot[j], s);
+                        if (m) atomicMin(&s_ba[j], warp * 32 + __ffs(m) - 1);
+                    }
+                }
+            }
+            __syncthreads();
+            if (b < ny) {
+                const int64_t tile = tb + (int64_t)(y0 + b) * Tx + x;
+                const int r = s_rank[b];
+                if (r >= 0) {
+                    ttot[r] = s_tot[b];
+                    atomicAdd((unsigned long long*)(tile_partials + r / kTileChunk),
+                              (unsigned long long)s_tot[b]);
+                    const uint32_t edge = bin_edge(s_ba[b], db);
+                    ClsTileCache c = tile_cache[tile];
+                    const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
+                                      c.zb <= edge;
+                    if (!keep) {
+                        c.zb = s_ba[b] >= kDepthBins ? edge : bin_edge(s_ba[b] - 1, db);
+                        c.n_prefix = CLS_PREFIX_UNKNOWN;
+                    }
+                    c.zmin_active = edge;
+                    tile_cache[tile] = c;
+                    front[tile] = c.n_prefix != CLS_PREFIX_UNKNOWN ? (uint8_t)depth_bin(c.zb, db)
+                                                                   : (uint8_t)0;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Offsets of every (tile, bin) bucket, in place of its count in `cursor`
+// (the emission's slot cursors) and in bin_offsets, and the per-tile ranges,
+// all clamped to the key capacity so every later access stays inside the key
+// buffer; per view the rank of its first rendered tile. One block per chunk
+// of kTileChunk rendered tiles (its base from the scanned partial sums), a
+// warp per tile, eight bins per lane.
+__global__ void __launch_bounds__(256)
+tile_offsets_kernel(const ClsView* __restrict__ views, int n_views,
+                    const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
+                    const int32_t* __restrict__ ttot, const int64_t* __restrict__ tile_partials,
+                    int64_t capacity, int32_t* __restrict__ cursor,
+                    uint32_t* __restrict__ bin_offsets, uint32_t* __restrict__ ranges,
+                    int32_t* __restrict__ rank0) {
+    __shared__ int64_t smem[256 / 32 + 1];
+    __shared__ int64_t s_base[kTileChunk];
+    const int na = *n_active;
+    const int t0 = blockIdx.x * kTileChunk;
+    if (t0 >= na) return;
+    const int i = threadIdx.x;
+    const int64_t v = (i < kTileChunk && t0 + i < na) ? (int64_t)ttot[t0 + i] : 0;
     int64_t tot;
-    block_exclusive_sum<kBinBlock>(cnt, smem, tot);
-    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-}
-
-// Offsets of every (tile, bin) bucket and the per-tile ranges, clamped to the
-// key capacity so every later access stays inside the key buffer; the first
-// depth bin each tile emits (bins entirely in front of a cached prefix
-// boundary hold only prefix pairs and are not written); per view the rank of
-// its first rendered tile.
-__global__ void __launch_bounds__(kBinBlock)
-sub_offsets_kernel(const ClsView* __restrict__ views, int n_views,
-                   const int32_t* __restrict__ active_tiles, const int32_t* __restrict__ n_active,
-                   const int64_t* __restrict__ partials, int64_t capacity,
-                   uint32_t* __restrict__ bin_offsets, int32_t* __restrict__ cursor,
-                   uint32_t* __restrict__ ranges, const ClsTileCache* __restrict__ tile_cache,
-                   const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
-                   uint8_t* __restrict__ front, int32_t* __restrict__ rank0) {
-    __shared__ int64_t smem[kBinBlock / 32 + 1];
-    const int64_t ne = (int64_t)(*n_active) * kDepthBins;
-    int64_t base = partials[blockIdx.x];
-    for (int it = 0; it < kBinItems; ++it) {
-        const int64_t e = (int64_t)blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
-        const int64_t c = e < ne ? cursor[e] : 0;  // the count, replaced by the offset
-        int64_t tot;
-        const int64_t off = base + block_exclusive_sum<kBinBlock>(c, smem, tot);
-        base += tot;
-        if (e < ne) {
-            const uint32_t o = (uint32_t)(off < capacity ? off : capacity);
-            const uint32_t o_end = (uint32_t)(off + c < capacity ? off + c : capacity);
-            bin_offsets[e] = o;
-            cursor[e] = (int32_t)o;
-            const int t = (int)(e / kDepthBins), b = (int)(e - (int64_t)t * kDepthBins);
+    const int64_t ex = block_exclusive_sum<256>(v, smem, tot);
+    if (i < kTileChunk) s_base[i] = tile_partials[blockIdx.x] + ex;
+    __syncthreads();
+    const int lane = i & 31, warp = i >> 5;
+    auto clamp = [&](int64_t o) { return (uint32_t)(o < capacity ? o : capacity); };
+    for (int k = warp; k < kTileChunk && t0 + k < na; k += 8) {
+        const int t = t0 + k;
+        int32_t* cp = cursor + (int64_t)t * kDepthBins + lane * 8;
+        const int4 a = *reinterpret_cast<const int4*>(cp);
+        const int4 c = *reinterpret_cast<const int4*>(cp + 4);
+        const int32_t n8[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+        int32_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sum += n8[j];
+        int32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int64_t off = s_base[k] + (incl - sum);
+        uint32_t o8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            o8[j] = clamp(off);
+            off += n8[j];
+        }
+        const uint4 lo = make_uint4(o8[0], o8[1], o8[2], o8[3]);
+        const uint4 hi = make_uint4(o8[4], o8[5], o8[6], o8[7]);
+        *reinterpret_cast<uint4*>(cp) = lo;
+        *reinterpret_cast<uint4*>(cp + 4) = hi;
+        uint32_t* bo = bin_offsets + (int64_t)t * kDepthBins + lane * 8;
+        *reinterpret_cast<uint4*>(bo) = lo;
+        *reinterpret_cast<uint4*>(bo + 4) = hi;
+        if (lane == 31) {
             const int64_t tile = active_tiles[t];
-            if (b == 0) {
-                ranges[2 * tile] = o;
-                const ClsTileCache c = tile_cache[tile];
-                const int v = view_of_tile(views, n_views, (int)tile);
-                // the first rendered tile of its view
-                if (t == 0 || active_tiles[t - 1] < views[v].tile_base) rank0[v] = t;
-                front[tile] = c.n_prefix != CLS_PREFIX_UNKNOWN
-                                  ? (uint8_t)depth_bin(c.zb, depth_bins(zmin[v], zmax[v]))
-                                  : (uint8_t)0;
-            }
-            if (b == kDepthBins - 1) {
-                ranges[2 * tile + 1] = o_end;
-                bin_offsets[e + 1] = o_end;  // sentinel: end of the tile's last bin
-            }
+            const uint32_t end = clamp(off);
+            ranges[2 * tile] = clamp(s_base[k]);
+            ranges[2 * tile + 1] = end;
+            // the next tile's first offset, or the sentinel after the last tile
+            if (t == na - 1) bin_offsets[(int64_t)na * kDepthBins] = end;
+            const int vv = view_of_tile(views, n_views, (int)tile);
+            if (t == 0 || active_tiles[t - 1] < views[vv].tile_base) rank0[vv] = t;
         }
     }
 }
@@ -1036,8 +1248,9 @@ __global__ void capacity_check_kernel(const int64_t* n_pairs, int64_t capacity,
 }
 
 struct ProjLayout {
-    size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, sub_partials, big_list, big_count,
-        bins, work_list, work_count, front, t_win, rank0, compact, rects, total;
+    size_t partials, sat, diff, zmin, zmax, tile_rank, cursor, tile_partials, big_list,
+        big_count, sbins, abins, arange, ttot, work_list, work_count, front, t_win, rank0, compact,
+        rects, total;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1058,10 +1271,14 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.zmax = o; o = align256(o + (size_t)V * 4);
     L.tile_rank = o; o = align256(o + (size_t)info->total_tiles * 4);
     L.cursor = o; o = align256(o + (size_t)subs * 4);
-    L.sub_partials = o; o = align256(o + (size_t)((subs + kBinChunk - 1) / kBinChunk + 1) * 8);
+    L.tile_partials = o;
+    o = align256(o + (size_t)((info->total_tiles + kTileChunk - 1) / kTileChunk + 1) * 8);
     L.big_list = o; o = align256(o + (size_t)info->total_records * 16);
     L.big_count = o; o = align256(o + 4);
-    L.bins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
+    L.sbins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
+    L.abins = o; o = align256(o + (size_t)kDepthBins * info->total_sat * 4);
+    L.arange = o; o = align256(o + (size_t)V * 8);
+    L.ttot = o; o = align256(o + (size_t)info->total_tiles * 4);
     L.work_list = o; o = align256(o + (size_t)info->total_records * 16);
     L.work_count = o; o = align256(o + (size_t)V * 8);  // + per-view emission counters
     L.front = o; o = align256(o + (size_t)info->total_tiles);
@@ -1120,10 +1337,13 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     uint32_t* zmax = reinterpret_cast<uint32_t*>(ws + L.zmax);
     int32_t* tile_rank = reinterpret_cast<int32_t*>(ws + L.tile_rank);
     int32_t* cursor = reinterpret_cast<int32_t*>(ws + L.cursor);
-    int64_t* sub_partials = reinterpret_cast<int64_t*>(ws + L.sub_partials);
+    int64_t* tile_partials = reinterpret_cast<int64_t*>(ws + L.tile_partials);
     uint4* big_list = reinterpret_cast<uint4*>(ws + L.big_list);
     int32_t* big_count = reinterpret_cast<int32_t*>(ws + L.big_count);
-    int32_t* bins = reinterpret_cast<int32_t*>(ws + L.bins);
+    int32_t* sbins = reinterpret_cast<int32_t*>(ws + L.sbins);
+    int32_t* abins = reinterpret_cast<int32_t*>(ws + L.abins);
+    uint32_t* arange = reinterpret_cast<uint32_t*>(ws + L.arange);
+    int32_t* ttot = reinterpret_cast<int32_t*>(ws + L.ttot);
     uint4* work_list = reinterpret_cast<uint4*>(ws + L.work_list);
     int32_t* work_count = reinterpret_cast<int32_t*>(ws + L.work_count);
     uint8_t* front = reinterpret_cast<uint8_t*>(ws + L.front);
@@ -1139,17 +1359,17 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     const int grid_cap = (int)hmin64(max_view_tiles * 4 + 16 * 1024, 200 * 1024);
     const int sms = per_device(g_proj_sms, [](int dev) {
         for (const void* k : {(const void*)emit_bucketed_kernel, (const void*)tile_mask_kernel,
-                              (const void*)bins_prefix_kernel, (const void*)active_zmin_kernel})
+                              (const void*)active_zmin_kernel})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         return device_sms(dev);
     });
+    const int64_t tchunks = (info->total_tiles + kTileChunk - 1) / kTileChunk;
     // bucketed layout, after the count: bucket offsets (clamped to the
     // capacity), the emission window tables and the emission
-    const int64_t sub_chunks = (subs + kBinChunk - 1) / kBinChunk;
     auto emit_stage = [&]() {
-        sub_offsets_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(
-            views_dev, (int)V, active_tiles, n_active_tiles_dev, sub_partials, capacity,
-            bin_offsets, cursor, ranges, tile_cache, zmin, zmax, front, rank0);
+        tile_offsets_kernel<<<(unsigned)tchunks, 256, 0, s>>>(
+            views_dev, (int)V, active_tiles, n_active_tiles_dev, ttot, tile_partials, capacity,
+            cursor, bin_offsets, ranges, rank0);
         // shared memory for the tables of views up to 2^8 tiles wide
         const int emit_smem =
             (int)hmin64(max_view_tiles * (4 + 2 * 7) + kEmitItemBytes, 200 * 1024);
@@ -1189,7 +1409,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                              0, s>>>(scenes_dev, views_dev, records, rects, diff);
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
                                               grid_cap, tile_ring);
-    if (info->max_active > 0)
+    if (layout == 0 && info->max_active > 0)
         // one warp per active Gaussian; two 1024-thread blocks per SM
         active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads / 32 - 1) /
                                                        (kZminThreads / 32),
@@ -1199,8 +1419,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     {
         const int64_t chunks = (info->total_tiles + kCompactChunk - 1) / kCompactChunk;
         int64_t* cparts = reinterpret_cast<int64_t*>(ws + L.compact);
-        compact_count_kernel<<<(unsigned)chunks, 1024, 0, s>>>(tile_active, info->total_tiles,
-                                                               tile_cache, prefix_mode, cparts);
+        compact_count_kernel<<<(unsigned)chunks, 1024, 0, s>>>(
+            tile_active, info->total_tiles, tile_cache, prefix_mode, layout == 0 ? 1 : 0, cparts);
         scan_partials_kernel<<<1, 1024, 0, s>>>(cparts, chunks, nullptr, n_active_tiles_dev, -1,
                                                 nullptr);
         compact_write_kernel<<<(unsigned)chunks, 1024, 0, s>>>(tile_active, info->total_tiles,
@@ -1214,14 +1434,20 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     }
     const dim3 rec_grid((unsigned)cpv, V);
     if (layout == 1) {
-        cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
-        cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
+        if (project_mode == 0) {  // the views' depth ranges, fixed until the next mode 0 call
+            cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
+            cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
+        }
         cudaMemsetAsync(work_count, 0, (size_t)V * 8, s);
+        cudaMemsetAsync(arange, 0xff, (size_t)V * 4, s);  // lowest occupied active bin
+        cudaMemsetAsync(arange + V, 0, (size_t)V * 4, s);  // highest
+        cudaMemsetAsync(tile_partials, 0, (size_t)tchunks * 8, s);
     }
+    const bool new_range = layout == 1 && project_mode == 0;
     count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, rects, sat,
                                                       (int)cpv, partials,
-                                                      layout == 1 ? zmin : nullptr,
-                                                      layout == 1 ? zmax : nullptr,
+                                                      new_range ? zmin : nullptr,
+                                                      new_range ? zmax : nullptr,
                                                       layout == 1 ? work_list : nullptr,
                                                       work_count);
     if (layout == 0) {
@@ -1233,19 +1459,30 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         emit_big_kernel<<<1024, 256, 0, s>>>(views_dev, rects, tile_active, keys, vals,
                                              capacity, big_list, big_count);
     } else {
-        cudaMemsetAsync(bins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
         cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
-        const unsigned work_blocks = (unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
-                                                      2048);
-        stamp_bins_kernel<<<dim3(work_blocks, V), kBinBlock, 0, s>>>(
-            views_dev, zmin, zmax, work_list, work_count, bins, info->total_sat);
-        // per (rank, bin) counts go to `cursor`, which sub_offsets then
+        // grids of kDepthBins threads stride over the views' rows and columns
+        constexpr unsigned kLines = 128;
+        if (project_mode == 0) {  // the static Gaussians' pairs per (tile, bin)
+            cudaMemsetAsync(sbins, 0, (size_t)kDepthBins * info->total_sat * 4, s);
+            stamp_static_kernel<<<dim3((unsigned)hmin64((info->max_n + kBinBlock - 1) / kBinBlock,
+                                                        2048), V), kBinBlock, 0, s>>>(
+                scenes_dev, views_dev, rects, zmin, zmax, sbins);
+            row_prefix_kernel<<<dim3(kLines, V), kDepthBins, 0, s>>>(views_dev, sbins, nullptr, 0);
+            col_prefix_kernel<<<dim3(kLines, V), kDepthBins, 0, s>>>(views_dev, sbins);
+        }
+        if (info->max_active > 0) {  // the active Gaussians' stamps, prefix-summed along x
+            stamp_active_kernel<<<dim3((unsigned)hmin64(
+                                           (info->max_active + kBinBlock - 1) / kBinBlock, 2048),
+                                       V), kBinBlock, 0, s>>>(scenes_dev, views_dev, rects, zmin,
+                                                              zmax, abins, arange);
+            row_prefix_kernel<<<dim3(kLines, V), kDepthBins, 0, s>>>(views_dev, abins, arange, 1);
+        }
+        // per (rank, bin) counts go to `cursor`, which tile_offsets_kernel
         // turns into the buckets' slot cursors
-        bins_prefix_kernel<<<dim3(kDepthBins, V), 512, grid_cap, s>>>(
-            views_dev, bins, info->total_sat, grid_cap, tile_rank, cursor);
-        sub_count_kernel<<<(unsigned)sub_chunks, kBinBlock, 0, s>>>(n_active_tiles_dev, cursor,
-                                                                   sub_partials);
-        scan_partials_kernel<<<1, 1024, 0, s>>>(sub_partials, sub_chunks, n_pairs_dev, nullptr,
+        col_counts_kernel<<<dim3(kLines, V), kDepthBins, 0, s>>>(
+            views_dev, sbins, abins, arange, zmin, zmax, tile_rank, tile_cache, prefix_mode,
+            cursor, front, ttot, tile_partials);
+        scan_partials_kernel<<<1, 1024, 0, s>>>(tile_partials, tchunks, n_pairs_dev, nullptr,
                                                 capacity, status_dev);
         // counting only (capacity planning): the per-bucket counts stay in
         // `cursor` for a following call in project_mode 2

@@ -324,6 +324,7 @@ class Batch:
             b._epochs = epochs
             b.reset_prefix()
             b.counted = False
+            mode = 0  # project them again (and recount their pairs)
         if b.counted and mode == 1:  # the planning pass counted this binning already
             mode = 2
         b.counted = False
