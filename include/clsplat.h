@@ -50,7 +50,9 @@ enum {
     CLS_ERR_INVALID_ARG = 1, /* bad size, NULL pointer or unsupported option */
     CLS_ERR_CAPACITY = 2,    /* more (Gaussian, tile) pairs than key capacity */
     CLS_ERR_CUDA = 3,        /* a launch failed (cudaGetLastError) */
-    CLS_ERR_TIMEOUT = 4      /* a bounded device wait gave up */
+    CLS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    CLS_ERR_INTERNAL = 5     /* a device-side consistency guard skipped an access
+                                (the call's outputs are not valid) */
 };
 
 #define CLS_TILE 16

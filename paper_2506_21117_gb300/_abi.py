@@ -13,9 +13,10 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libclsplat.so")
 
-CLS_OK, CLS_ERR_INVALID_ARG, CLS_ERR_CAPACITY, CLS_ERR_CUDA, CLS_ERR_TIMEOUT = range(5)
+CLS_OK, CLS_ERR_INVALID_ARG, CLS_ERR_CAPACITY, CLS_ERR_CUDA, CLS_ERR_TIMEOUT, \
+    CLS_ERR_INTERNAL = range(6)
 STATUS_NAMES = {0: "CLS_OK", 1: "CLS_ERR_INVALID_ARG", 2: "CLS_ERR_CAPACITY",
-                3: "CLS_ERR_CUDA", 4: "CLS_ERR_TIMEOUT"}
+                3: "CLS_ERR_CUDA", 4: "CLS_ERR_TIMEOUT", 5: "CLS_ERR_INTERNAL"}
 TILE = 16
 G2_STRIDE = 12
 CLS_SORT_SPIN_LIMIT = 1 << 22

@@ -923,18 +923,28 @@ __host__ __device__ __forceinline__ int row_levels(int Tx) {
     return levels;
 }
 
-// Shared memory of the emission: per warp its group's 32 items (key, end of
-// its cells, corner, width and bin: 20 B each), per tile a packed word
-// (rank in the view's rendered tiles + 1 in the low half, 0 if not rendered;
-// the window in the high half) and, when they fit, the row tables' levels
-// 1 .. L-1. Views whose tables do not fit in `smem_bytes` use the global ones
-// that bin_window_tables_kernel writes.
+// Shared memory of the emission: per tile a packed word (rank in the view's
+// rendered tiles + 1 in the low half, 0 if not rendered; the window in the
+// high half) and, when they fit, the row tables' levels 1 .. L-1. Views whose
+// tables do not fit in `smem_bytes` use the global ones that
+// bin_window_tables_kernel writes.
 constexpr int kEmitThreads = 1024;
-constexpr int kEmitWarps = kEmitThreads / 32;
-constexpr int kEmitItemBytes = kEmitWarps * 32 * 20;
 
 __host__ __device__ __forceinline__ bool emit_tables_fit(int64_t nt, int Tx, int64_t smem_bytes) {
-    return nt * (4 + 2 * (int64_t)(row_levels(Tx) - 1)) + kEmitItemBytes <= smem_bytes;
+    return nt * (4 + 2 * (int64_t)(row_levels(Tx) - 1)) <= smem_bytes;
+}
+
+// First lane of the warp whose inclusive cell prefix `incl` exceeds c (31 if
+// none): a binary search by shuffles, every lane taking part.
+__device__ __forceinline__ int owner_of(int incl, int c) {
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const int pm = __shfl_sync(0xffffffffu, incl, mid);
+        if (pm > c) hi = mid; else lo = mid + 1;
+    }
+    return lo;
 }
 
 __global__ void __launch_bounds__(1024)
@@ -961,35 +971,14 @@ bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __res
     }
 }
 
-// First and last rows of rectangle x0..x1, y0..y1 on which depth bin `bin`
-// can be emitted (a row qualifies when some tile of it admits the bin: two
-// overlapping runs of 2^l tiles cover the row's columns); false if there is
-// none. Conservative: the emission still tests every cell of the rows kept.
-// T: the level's packed windows, element stride st (2 for level 0, read from
-// the high halves of the tile words).
-__device__ __forceinline__ bool bin_window_rows(const uint16_t* T, int st, int Tx, int x0, int x1,
-                                                int y0, int y1, int l, int bin, int& first,
-                                                int& last) {
-    const int d = (x1 - x0 + 1 - (1 << l)) * st, step = Tx * st;
-    const uint16_t* p = T + (int64_t)(y0 * Tx + x0) * st;
-    int y = y0;
-    for (; y <= y1; ++y, p += step)
-        if (fc_admits(fc_merge(p[0], p[d]), bin)) break;
-    if (y > y1) return false;
-    first = y;
-    p = T + (int64_t)(y1 * Tx + x0) * st;
-    for (y = y1; y > first; --y, p -= step)
-        if (fc_admits(fc_merge(p[0], p[d]), bin)) break;
-    last = y;
-    return true;
-}
-
 // Bucketed emission, load-balanced. A warp takes a group of 32 pair-producing
 // records of one view, cuts each rectangle to the rows where its depth bin can
 // be emitted and lays the cells of the cut rectangles end to end; per round
-// each lane walks kCells consecutive cells (one owner search per round, the
-// owner and the cell advanced in place), and a cell whose tile admits the
-// bin claims a slot in its (tile, depth bin) bucket. One 1024-thread block per
+// each lane walks kCells consecutive cells, the owner record found once by a
+// binary search over the warp's cell prefix and advanced in place (a warp vote
+// decides when some lane enters its next record; the owners' fields travel by
+// shuffles, every lane taking part), and a cell whose tile admits the bin
+// claims a slot in its (tile, depth bin) bucket. One 1024-thread block per
 // SM; warps take groups from a per-view counter, the next group claimed and
 // fetched while the current one is processed.
 constexpr int kEmitGroups = 16;  // groups per warp and block lifetime
@@ -1003,18 +992,19 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
                      const uint4* __restrict__ work_list, const int32_t* __restrict__ work_count,
                      int32_t* __restrict__ next_group, const uint8_t* __restrict__ cut,
                      const uint8_t* __restrict__ front, const uint16_t* __restrict__ t_win,
-                     int64_t total_tiles, int smem_bytes) {
-    extern __shared__ uint64_t s_key[];
+                     int64_t total_tiles, int smem_bytes, int32_t* __restrict__ status) {
+    extern __shared__ uint32_t s_tile[];
+    __shared__ int s_leave;
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x;
     const int nt = Tx * view.tiles_y;
     const int n = work_count[blockIdx.x];
-    // blocks past the view's work leave before filling their tables
-    if (*(volatile int32_t*)(next_group + blockIdx.x) * 32 >= n) return;
-    int32_t* s_end = reinterpret_cast<int32_t*>(s_key + kEmitWarps * 32);
-    uint32_t* s_xy = reinterpret_cast<uint32_t*>(s_end + kEmitWarps * 32);
-    uint32_t* s_wb = s_xy + kEmitWarps * 32;
-    uint32_t* s_tile = s_wb + kEmitWarps * 32;
+    // blocks past the view's work leave before filling their tables; one
+    // thread reads the counter (other blocks advance it) so that the whole
+    // block takes the same decision
+    if (threadIdx.x == 0) s_leave = *(volatile int32_t*)(next_group + blockIdx.x) * 32 >= n;
+    __syncthreads();
+    if (s_leave) return;
     uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_tile + nt);
     const int r0 = rank0[blockIdx.x];  // rank of the view's first rendered tile
     const int64_t tb = view.tile_base;
@@ -1039,11 +1029,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t* w_key = s_key + warp * 32;
-    int32_t* w_end = s_end + warp * 32;
-    uint32_t* w_xy = s_xy + warp * 32;
-    uint32_t* w_wb = s_wb + warp * 32;
+    const int lane = threadIdx.x & 31;
     const DepthBins db = depth_bins(zmin[blockIdx.x], zmax[blockIdx.x]);
     const uint4* wl = work_list + view.rec_base;
     int g_next = 0;
@@ -1062,19 +1048,42 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
             if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
         }
         int x0 = 0, x1 = -1, y0 = 0, y1 = -1, bin = 0, area = 0;
-        if (g * 32 + lane < n) {
+        const bool has = g * 32 + lane < n;
+        const uint16_t* T = nullptr;
+        int st = 1, d = 0;
+        if (has) {
             unpack_rect(item, x0, x1, y0, y1);
             bin = depth_bin(item.z, db);
             const int l = 31 - __clz(x1 - x0 + 1);
-            const uint16_t* T = l == 0 ? reinterpret_cast<const uint16_t*>(s_tile) + 1
-                                : fits ? s_lv + (l - 1) * nt
-                                       : t_win + (int64_t)(l - 1) * total_tiles + tb;
-            int ra, rb;
-            if (bin_window_rows(T, l == 0 ? 2 : 1, Tx, x0, x1, y0, y1, l, bin, ra, rb)) {
-                y0 = ra;
-                y1 = rb;
-                area = (x1 - x0 + 1) * (y1 - y0 + 1);
+            T = l == 0 ? reinterpret_cast<const uint16_t*>(s_tile) + 1
+                : fits ? s_lv + (l - 1) * nt
+                       : t_win + (int64_t)(l - 1) * total_tiles + tb;
+            st = l == 0 ? 2 : 1;
+            d = (x1 - x0 + 1 - (1 << l)) * st;
+        }
+        // The rows of the rectangle where the bin can be emitted (a row
+        // qualifies when some tile of it admits the bin; two overlapping runs
+        // of 2^l tiles from the row tables cover its columns): the first and
+        // the last such row. The loop runs to the warp's tallest rectangle
+        // with every lane in it, so that the warp reaches the shuffles below
+        // converged (lanes leaving per-lane loops at different trip counts
+        // were seen to fall out of step with the rest of the warp).
+        const int h = has ? y1 - y0 + 1 : 0;
+        int hmax = h;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+        int ra = -1, rb = -1;
+        int64_t at = (int64_t)(y0 * Tx + x0) * st;
+        for (int k = 0; k < hmax; ++k, at += Tx * st) {
+            if (k < h && fc_admits(fc_merge(T[at], T[at + d]), bin)) {
+                if (ra < 0) ra = y0 + k;
+                rb = y0 + k;
             }
+        }
+        if (ra >= 0) {
+            y0 = ra;
+            y1 = rb;
+            area = (x1 - x0 + 1) * (y1 - y0 + 1);
         }
         int incl = area;
 #pragma unroll
@@ -1083,54 +1092,56 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
             if (lane >= o) incl += y;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (total == 0) continue;
-        __syncwarp();  // the previous group's item fields are no longer read
-        w_key[lane] = ((uint64_t)item.z << 32) | item.w;
-        w_end[lane] = incl;
-        w_xy[lane] = (uint32_t)x0 | ((uint32_t)y0 << 16);
-        w_wb[lane] = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
-        __syncwarp();
+        // this lane's item, as the lanes walking its cells fetch it (by
+        // shuffles, with every lane of the warp taking part)
+        const int first = incl - area;
+        const uint32_t xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
+        const uint32_t wb = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
         for (int c0 = 0; c0 < total; c0 += 32 * kCells) {
             const int cf = c0 + lane * kCells;
-            // owner of cell cf: the first item whose cells end after it
-            int lo = 0, hi = 31;
-#pragma unroll
-            for (int step = 0; step < 5; ++step) {
-                const int mid = (lo + hi) >> 1;
-                const int pm = __shfl_sync(0xffffffffu, incl, mid);
-                if (pm > cf) hi = mid; else lo = mid + 1;
-            }
-            int own = lo;
-            int end = w_end[own];
-            uint32_t xy = w_xy[own], wb = w_wb[own];
-            uint64_t key = w_key[own];
-            int w = (int)(wb & 0xffffu), ob = (int)(wb >> 16);
+            int own = owner_of(incl, cf);
+            int o_end = __shfl_sync(0xffffffffu, incl, own);
+            const int o_first = __shfl_sync(0xffffffffu, first, own);
+            uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
+            uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
+            uint32_t o_kz = __shfl_sync(0xffffffffu, item.z, own);
+            uint32_t o_kr = __shfl_sync(0xffffffffu, item.w, own);
+            int w = max((int)(o_wb & 0xffffu), 1), ob = (int)(o_wb >> 16);
             int q, rem;
-            divmod_small(max(cf - (own > 0 ? w_end[own - 1] : 0), 0), w, q, rem);
-            int cell = ((int)(xy >> 16) + q) * Tx + (int)(xy & 0xffffu) + rem;
+            divmod_small(max(cf - o_first, 0), w, q, rem);
+            int cell = ((int)(o_xy >> 16) + q) * Tx + (int)(o_xy & 0xffffu) + rem;
             int32_t sub[kCells];
             uint64_t kk[kCells];
 #pragma unroll
             for (int u = 0; u < kCells; ++u) {
                 const int c = cf + u;
+                // a lane entering its next item: the whole warp looks the
+                // owners up again (the item starts exactly at c)
+                const bool adv = c < total && c >= o_end;
+                if (__any_sync(0xffffffffu, adv)) {
+                    const int o2 = owner_of(incl, c);
+                    own = adv ? o2 : own;
+                    o_end = __shfl_sync(0xffffffffu, incl, own);
+                    o_xy = __shfl_sync(0xffffffffu, xy, own);
+                    o_wb = __shfl_sync(0xffffffffu, wb, own);
+                    o_kz = __shfl_sync(0xffffffffu, item.z, own);
+                    o_kr = __shfl_sync(0xffffffffu, item.w, own);
+                    if (adv) {
+                        w = max((int)(o_wb & 0xffffu), 1);
+                        ob = (int)(o_wb >> 16);
+                        rem = 0;
+                        cell = (int)(o_xy >> 16) * Tx + (int)(o_xy & 0xffffu);
+                    }
+                }
                 sub[u] = -1;
                 if (c < total) {
-                    if (c >= end) {  // the next item with cells starts at c
-                        do {
-                            ++own;
-                        } while (w_end[own] <= c);
-                        end = w_end[own];
-                        xy = w_xy[own];
-                        wb = w_wb[own];
-                        key = w_key[own];
-                        w = (int)(wb & 0xffffu);
-                        ob = (int)(wb >> 16);
-                        rem = 0;
-                        cell = (int)(xy >> 16) * Tx + (int)(xy & 0xffffu);
-                    }
-                    const uint32_t word = s_tile[cell];
-                    if (fc_admits(word >> 16, ob))
-                        sub[u] = (r0 + (int)(word & 0xffffu) - 1) * kDepthBins + ob;
+                    // guard (never taken): the cell is a tile of the view
+                    const bool in_view = cell >= 0 && cell < nt;
+                    const uint32_t word = in_view ? s_tile[cell] : 0x00ff0000u;
+                    const int r = r0 + (int)(word & 0xffffu) - 1;
+                    const bool admit = fc_admits(word >> 16, ob);
+                    if (admit && r >= 0 && r < total_tiles) sub[u] = r * kDepthBins + ob;
+                    else if (admit || !in_view) set_status(status, CLS_ERR_INTERNAL);
                     if (++rem == w) {
                         rem = 0;
                         cell += Tx - w + 1;
@@ -1138,7 +1149,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
                         ++cell;
                     }
                 }
-                kk[u] = key;
+                kk[u] = ((uint64_t)o_kz << 32) | o_kr;
             }
             int32_t p[kCells];
 #pragma unroll
@@ -1372,7 +1383,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             cursor, bin_offsets, ranges, rank0);
         // shared memory for the tables of views up to 2^8 tiles wide
         const int emit_smem =
-            (int)hmin64(max_view_tiles * (4 + 2 * 7) + kEmitItemBytes, 200 * 1024);
+            (int)hmin64(max_view_tiles * (4 + 2 * 7), 200 * 1024);
         bin_window_tables_kernel<<<V, 1024, 0, s>>>(views_dev, tile_rank, front, bin_cut, t_win,
                                                      info->total_tiles, emit_smem);
         int per_sm = 0;
@@ -1388,7 +1399,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         // the view index varies fastest, so the first wave spreads over all views
         emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
             views_dev, tile_rank, rank0, zmin, zmax, cursor, keys, capacity, work_list,
-            work_count, work_count + V, bin_cut, front, t_win, info->total_tiles, emit_smem);
+            work_count, work_count + V, bin_cut, front, t_win, info->total_tiles, emit_smem,
+            status_dev);
     };
     if (project_mode == 2) {  // the previous call counted these pairs: emit them
         if (cpv > 0) {
