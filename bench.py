@@ -295,6 +295,50 @@ def walk_counts(bt):
             "keys_in_large_bins": big}
 
 
+def _a256(x: int) -> int:
+    return (x + 255) // 256 * 256
+
+
+def proj_workspace_offsets(info) -> dict:
+    """Byte offsets of the projection workspace's regions (the layout the
+    binning entry point uses; their total is checked against
+    cls_project_workspace_size by the host tests)."""
+    V, T = int(info.n_views), int(info.total_tiles)
+    cpv = (int(info.max_n) + 2047) // 2048
+    sizes = [("partials", (cpv * V + 1) * 8), ("sat", info.total_sat * 4),
+             ("diff", info.total_sat * 4), ("zmin", V * 4), ("zmax", V * 4),
+             ("tile_rank", T * 4), ("cursor", T * 256 * 4),
+             ("tile_partials", ((T + 63) // 64 + 1) * 8),
+             ("big_list", info.total_records * 16), ("big_count", 4),
+             ("sbins", 256 * info.total_sat * 4), ("abins", 256 * info.total_sat * 4),
+             ("arange", V * 8), ("ttot", T * 4), ("work_list", info.total_records * 16),
+             ("work_count", V * 8), ("front", T), ("t_win", T * 15 * 2), ("rank0", V * 4),
+             ("compact", ((T + 4095) // 4096 + 1) * 8), ("rects", info.total_records * 16)]
+    off, o = {}, 0
+    for name, size in sizes:
+        off[name] = o
+        o = _a256(o + int(size))
+    off["total"] = o
+    return off
+
+
+def occupied_grid_entries(bt) -> int:
+    """Entries of the active Gaussians' depth-bin grid that one binning call
+    prefix-sums and clears: per view its (Tx + 1)(Ty + 1) cells times the
+    depth bins its active Gaussians occupy (read from the workspace)."""
+    import torch
+    off = proj_workspace_offsets(bt.info)
+    V = bt.n_views
+    ar = bt.proj_ws[off["arange"]: off["arange"] + 8 * V].view(torch.int32).cpu().numpy()
+    lo, hi = ar[:V].view(np.uint32).astype(np.int64), ar[V:].view(np.uint32).astype(np.int64)
+    total = 0
+    for j in range(V):
+        v = bt.view_tab[j]
+        if hi[j] >= lo[j]:
+            total += (int(v.tiles_x) + 1) * (int(v.tiles_y) + 1) * int(hi[j] - lo[j] + 1)
+    return total
+
+
 def design_bytes(lu):
     """Algorithmic DRAM bytes one iteration of this design moves, per stage,
     from one more pass's own counters (run after the timed region):
@@ -308,18 +352,27 @@ def design_bytes(lu):
       per tile (walk start to the deepest pixel's last contributor; for the
       backward, to the tile's last active entry), Pr rendered pixels, Pb those
       the backward walks, Tr rendered tiles, G the summed-area grid entries
-      (per view (Tx+1)(Ty+1)).
+      (per view (Tx+1)(Ty+1)), Go the active depth-bin grid entries one call
+      passes over (occupied_grid_entries). The static Gaussians' counts per
+      (tile, bin) are built once per update (by the call that projects every
+      Gaussian) and are not counted here.
 
       project_and_bin  A V (R + 48 + 16)       rows read, records and packed
                                                rectangles written
-                       + N V 16 + Np 4         rectangles read by the count,
-                                               work list written
-                       + 3 x 256 G 4           depth-bin grid: clear, stamps,
-                                               prefix pass
-                       + 5 x 256 Tr 4          per (tile, bin) counts, offsets,
-                                               cursors
-                       + Np 20 + 8 E           emission: rectangle + list entry
-                                               read, keys written
+                       + N V 16 + Np 16        rectangles read by the count,
+                                               work items (rectangle + record)
+                                               written
+                       + A V 32                active rectangles read, their
+                                               four depth-bin stamps
+                       + Go 16                 active depth-bin grid: row pass
+                                               (read, write), column pass (read,
+                                               clear) over the Go entries of the
+                                               bins the active Gaussians occupy
+                       + 5 x 256 Tr 4          per (tile, bin): static counts
+                                               read, counts written and read,
+                                               offsets and cursors written
+                       + Np 16 + 8 E           emission: work items read, keys
+                                               written
       sort (large bins)  16 per key in a bin above the forward's sort limit
       render_forward   16 S + 48 F             keys sorted in shared memory and
                                                written back, records staged
@@ -352,9 +405,10 @@ def design_bytes(lu):
     Np = pair_producing_records(bt)
     N = sum(bt.scenes[bt.view_tab[j].scene].n for j in range(V))
     G = int(bt.info.total_sat)
+    Go = occupied_grid_entries(bt)
     stages = {
-        "project_and_bin": A * V * (row + 64) + N * 16 + Np * 4 + 3 * 256 * G * 4 +
-        5 * 256 * nt * 4 + Np * 20 + 8 * E,
+        "project_and_bin": A * V * (row + 64) + N * 16 + Np * 16 + A * V * 32 + Go * 16 +
+        5 * 256 * nt * 4 + Np * 16 + 8 * E,
         "sort_keys": 16 * big,
         "render_forward": 16 * S + 48 * F + 64 * Pr,
         "render_backward": 56 * Bn + 44 * Pb + 16 * (Pr - Pb) + A * V * 48 * 3 + 2 * A * row,
@@ -365,7 +419,7 @@ def design_bytes(lu):
                 "keys_sorted_by_forward": S, "keys_in_large_bins": big,
                 "forward_entries": F, "backward_entries": Bn, "forward_pixels": Pf,
                 "backward_pixels": Pb, "rendered_pixels": Pr, "rendered_tiles": nt,
-                "sat_entries": G,
+                "sat_entries": G, "active_bin_grid_entries": Go,
                 "row_bytes": row}
     return stages, counters
 

@@ -1,8 +1,10 @@
 """Host-side accounting of the benchmark (no GPU): the walked-evaluation
 counts behind the render roofline equal a per-pixel brute force."""
+import os
 import types
 
 import numpy as np
+import pytest
 import torch
 
 import bench
@@ -167,3 +169,18 @@ def test_executed_evaluations_bounds():
     assert got["kept_share"] == 1.0
     got = bench.executed_evaluations(_with_records(bt, 4, far=True))
     assert got["forward"] == 0 and got["backward"] == 0 and got["kept_share"] == 0.0
+
+
+def test_projection_workspace_layout_matches_the_library():
+    """The benchmark's copy of the projection workspace layout (it reads the
+    active depth-bin ranges from it) totals the library's own size."""
+    if not os.path.exists(abi.library_path()):
+        pytest.skip("libclsplat.so not built")
+    for nv, tx, ty, n, act in [(4, 120, 68, 1_000_000, 37_948), (2, 8, 6, 500, 17), (1, 240, 135, 3, 3)]:
+        info = abi.ClsBatchInfo()
+        info.n_scenes, info.n_views, info.max_n, info.max_active = 1, nv, n, act
+        info.total_tiles = nv * tx * ty
+        info.total_sat = nv * (tx + 1) * (ty + 1)
+        info.total_records = nv * n
+        info.max_view_tiles = tx * ty
+        assert bench.proj_workspace_offsets(info)["total"] == abi.cls_project_workspace_size(info)
