@@ -973,12 +973,11 @@ bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __res
 
 // Bucketed emission, load-balanced. A warp takes a group of 32 pair-producing
 // records of one view, cuts each rectangle to the rows where its depth bin can
-// be emitted and lays the cells of the cut rectangles end to end; per round
-// each lane walks kCells consecutive cells, the owner record found once by a
-// binary search over the warp's cell prefix and advanced in place (a warp vote
-// decides when some lane enters its next record; the owners' fields travel by
-// shuffles, every lane taking part), and a cell whose tile admits the bin
-// claims a slot in its (tile, depth bin) bucket. One 1024-thread block per
+// be emitted and splits the cells of each cut rectangle into segments of
+// kCells consecutive cells; per round each lane takes one segment, its record
+// found by a binary search over the warp's segment prefix (the record's fields
+// travel by shuffles, every lane taking part), and a cell whose tile admits
+// the bin claims a slot in its (tile, depth bin) bucket. One 1024-thread block per
 // SM; warps take groups from a per-view counter, the next group claimed and
 // fetched while the current one is processed.
 constexpr int kEmitGroups = 16;  // groups per warp and block lifetime
@@ -992,21 +991,51 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
                      const uint4* __restrict__ work_list, const int32_t* __restrict__ work_count,
                      int32_t* __restrict__ next_group, const uint8_t* __restrict__ cut,
                      const uint8_t* __restrict__ front, const uint16_t* __restrict__ t_win,
-                     int64_t total_tiles, int smem_bytes, int32_t* __restrict__ status) {
+                     int64_t total_tiles, int smem_bytes, int n_views, int first_wave,
+                     int32_t* __restrict__ ticket, int32_t* __restrict__ status) {
     extern __shared__ uint32_t s_tile[];
-    __shared__ int s_leave;
-    const ClsView& view = views[blockIdx.x];
+    __shared__ int s_view;
+    // The block's view. Blocks of the first wave are shared out over the views
+    // in proportion to their groups of work items; later blocks join the view
+    // with the most groups left, and leave if there is none. One thread decides
+    // (other blocks advance the counters), so the whole block takes the same view.
+    if (threadIdx.x == 0) {
+        const int t = atomicAdd(ticket, 1);
+        int pick = -1;
+        if (t < first_wave) {
+            int64_t total = 0;
+            for (int v = 0; v < n_views; ++v) total += (work_count[v] + 31) / 32;
+            const int64_t target = ((int64_t)t * total) / first_wave;  // this block's share
+            int64_t cum = 0;
+            for (int v = 0; v < n_views && pick < 0; ++v) {
+                cum += (work_count[v] + 31) / 32;
+                if (target < cum) pick = v;
+            }
+        }
+        int best = 0;
+        if (pick >= 0)
+            best = (work_count[pick] + 31) / 32 - *(volatile int32_t*)(next_group + pick);
+        if (best <= 0) {  // the share's view is done (or a later block): the most left
+            pick = -1;
+            for (int v = 0; v < n_views; ++v) {
+                const int left = (work_count[v] + 31) / 32 - *(volatile int32_t*)(next_group + v);
+                if (left > best) {
+                    best = left;
+                    pick = v;
+                }
+            }
+        }
+        s_view = pick;
+    }
+    __syncthreads();
+    const int vi = s_view;
+    if (vi < 0) return;
+    const ClsView& view = views[vi];
     const int Tx = view.tiles_x;
     const int nt = Tx * view.tiles_y;
-    const int n = work_count[blockIdx.x];
-    // blocks past the view's work leave before filling their tables; one
-    // thread reads the counter (other blocks advance it) so that the whole
-    // block takes the same decision
-    if (threadIdx.x == 0) s_leave = *(volatile int32_t*)(next_group + blockIdx.x) * 32 >= n;
-    __syncthreads();
-    if (s_leave) return;
+    const int n = work_count[vi];
     uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_tile + nt);
-    const int r0 = rank0[blockIdx.x];  // rank of the view's first rendered tile
+    const int r0 = rank0[vi];  // rank of the view's first rendered tile
     const int64_t tb = view.tile_base;
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
         const int r = tile_rank[tb + i];
@@ -1016,24 +1045,31 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
     }
     const int levels = row_levels(Tx);
     const bool fits = emit_tables_fit(nt, Tx, smem_bytes);
-    if (fits) {  // the row tables of the view, built here in shared memory
+    if (fits) {  // the row tables of the view, built here in shared memory (a warp per row)
+        const int Ty = view.tiles_y, wy = threadIdx.x >> 5, lx = threadIdx.x & 31;
         __syncthreads();
-        for (int i = threadIdx.x; i < nt; i += blockDim.x)
-            if (i % Tx + 2 <= Tx) s_lv[i] = (uint16_t)fc_merge(s_tile[i] >> 16, s_tile[i + 1] >> 16);
+        for (int y = wy; y < Ty; y += kEmitThreads / 32)
+            for (int x = lx; x + 2 <= Tx; x += 32) {
+                const int i = y * Tx + x;
+                s_lv[i] = (uint16_t)fc_merge(s_tile[i] >> 16, s_tile[i + 1] >> 16);
+            }
         for (int l = 2; l < levels; ++l) {
             __syncthreads();
             const int h = 1 << (l - 1);
             const int prev = (l - 2) * nt, cur = prev + nt;
-            for (int i = threadIdx.x; i < nt; i += blockDim.x)
-                if (i % Tx + 2 * h <= Tx) s_lv[cur + i] = (uint16_t)fc_merge(s_lv[prev + i], s_lv[prev + i + h]);
+            for (int y = wy; y < Ty; y += kEmitThreads / 32)
+                for (int x = lx; x + 2 * h <= Tx; x += 32) {
+                    const int i = y * Tx + x;
+                    s_lv[cur + i] = (uint16_t)fc_merge(s_lv[prev + i], s_lv[prev + i + h]);
+                }
         }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const DepthBins db = depth_bins(zmin[blockIdx.x], zmax[blockIdx.x]);
+    const DepthBins db = depth_bins(zmin[vi], zmax[vi]);
     const uint4* wl = work_list + view.rec_base;
     int g_next = 0;
-    if (lane == 0) g_next = atomicAdd(next_group + blockIdx.x, 1);
+    if (lane == 0) g_next = atomicAdd(next_group + vi, 1);
     g_next = __shfl_sync(0xffffffffu, g_next, 0);
     uint4 it_next = make_uint4(0u, 0u, 0u, 0u);
     if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
@@ -1043,7 +1079,7 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
         if (g * 32 >= n) break;
         if (taken + 1 < kEmitGroups) {  // claim and fetch the next group now
             int gn = 0;
-            if (lane == 0) gn = atomicAdd(next_group + blockIdx.x, 1);
+            if (lane == 0) gn = atomicAdd(next_group + vi, 1);
             g_next = __shfl_sync(0xffffffffu, gn, 0);
             if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
         }
@@ -1085,56 +1121,41 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
             y1 = rb;
             area = (x1 - x0 + 1) * (y1 - y0 + 1);
         }
-        int incl = area;
+        // The cells of each cut rectangle are split into segments of kCells
+        // consecutive cells; lanes take whole segments (the segment prefix
+        // over the warp gives each lane its record), so a lane's cells never
+        // cross a record boundary.
+        const int segs = (area + kCells - 1) / kCells;
+        int incl = segs;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        // this lane's item, as the lanes walking its cells fetch it (by
-        // shuffles, with every lane of the warp taking part)
-        const int first = incl - area;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);  // segments of the group
+        const int first = incl - segs;
         const uint32_t xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
         const uint32_t wb = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
-        for (int c0 = 0; c0 < total; c0 += 32 * kCells) {
-            const int cf = c0 + lane * kCells;
-            int own = owner_of(incl, cf);
-            int o_end = __shfl_sync(0xffffffffu, incl, own);
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int sg = s0 + lane;
+            const int own = owner_of(incl, sg);
             const int o_first = __shfl_sync(0xffffffffu, first, own);
-            uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
-            uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
-            uint32_t o_kz = __shfl_sync(0xffffffffu, item.z, own);
-            uint32_t o_kr = __shfl_sync(0xffffffffu, item.w, own);
-            int w = max((int)(o_wb & 0xffffu), 1), ob = (int)(o_wb >> 16);
+            const int o_area = __shfl_sync(0xffffffffu, area, own);
+            const uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
+            const uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
+            const uint64_t key = ((uint64_t)__shfl_sync(0xffffffffu, item.z, own) << 32) |
+                                 __shfl_sync(0xffffffffu, item.w, own);
+            const int w = max((int)(o_wb & 0xffffu), 1), ob = (int)(o_wb >> 16);
+            const int k0 = (sg - o_first) * kCells;  // first cell of the segment in its record
+            const int len = sg < total ? min(kCells, o_area - k0) : 0;
             int q, rem;
-            divmod_small(max(cf - o_first, 0), w, q, rem);
+            divmod_small(max(k0, 0), w, q, rem);
             int cell = ((int)(o_xy >> 16) + q) * Tx + (int)(o_xy & 0xffffu) + rem;
             int32_t sub[kCells];
-            uint64_t kk[kCells];
 #pragma unroll
             for (int u = 0; u < kCells; ++u) {
-                const int c = cf + u;
-                // a lane entering its next item: the whole warp looks the
-                // owners up again (the item starts exactly at c)
-                const bool adv = c < total && c >= o_end;
-                if (__any_sync(0xffffffffu, adv)) {
-                    const int o2 = owner_of(incl, c);
-                    own = adv ? o2 : own;
-                    o_end = __shfl_sync(0xffffffffu, incl, own);
-                    o_xy = __shfl_sync(0xffffffffu, xy, own);
-                    o_wb = __shfl_sync(0xffffffffu, wb, own);
-                    o_kz = __shfl_sync(0xffffffffu, item.z, own);
-                    o_kr = __shfl_sync(0xffffffffu, item.w, own);
-                    if (adv) {
-                        w = max((int)(o_wb & 0xffffu), 1);
-                        ob = (int)(o_wb >> 16);
-                        rem = 0;
-                        cell = (int)(o_xy >> 16) * Tx + (int)(o_xy & 0xffffu);
-                    }
-                }
                 sub[u] = -1;
-                if (c < total) {
+                if (u < len) {
                     // guard (never taken): the cell is a tile of the view
                     const bool in_view = cell >= 0 && cell < nt;
                     const uint32_t word = in_view ? s_tile[cell] : 0x00ff0000u;
@@ -1149,14 +1170,13 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
                         ++cell;
                     }
                 }
-                kk[u] = ((uint64_t)o_kz << 32) | o_kr;
             }
             int32_t p[kCells];
 #pragma unroll
             for (int u = 0; u < kCells; ++u) p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
 #pragma unroll
             for (int u = 0; u < kCells; ++u)
-                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = kk[u];
+                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = key;
         }
     }
 }
@@ -1291,7 +1311,8 @@ ProjLayout proj_layout(const ClsBatchInfo* info) {
     L.arange = o; o = align256(o + (size_t)V * 8);
     L.ttot = o; o = align256(o + (size_t)info->total_tiles * 4);
     L.work_list = o; o = align256(o + (size_t)info->total_records * 16);
-    L.work_count = o; o = align256(o + (size_t)V * 8);  // + per-view emission counters
+    L.work_count = o;  // + per-view emission counters + the emission's block ticket
+    o = align256(o + (size_t)V * 8 + 4);
     L.front = o; o = align256(o + (size_t)info->total_tiles);
     L.t_win = o; o = align256(o + (size_t)info->total_tiles * (kRowLevels - 1) * 2);
     L.rank0 = o; o = align256(o + (size_t)V * 4);
@@ -1396,15 +1417,17 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         const unsigned emit_blocks = (unsigned)hmin64(
             std::max<int64_t>((info->max_n + per_block - 1) / per_block, (resident + V - 1) / V),
             65535);
-        // the view index varies fastest, so the first wave spreads over all views
-        emit_bucketed_kernel<<<dim3(V, emit_blocks), kEmitThreads, (size_t)emit_smem, s>>>(
+        // blocks pick their view when they start (the first wave in proportion
+        // to the views' work)
+        emit_bucketed_kernel<<<(unsigned)hmin64((int64_t)V * emit_blocks, 1 << 30), kEmitThreads,
+                               (size_t)emit_smem, s>>>(
             views_dev, tile_rank, rank0, zmin, zmax, cursor, keys, capacity, work_list,
             work_count, work_count + V, bin_cut, front, t_win, info->total_tiles, emit_smem,
-            status_dev);
+            (int)V, (int)hmin64(resident, 1 << 30), work_count + 2 * V, status_dev);
     };
     if (project_mode == 2) {  // the previous call counted these pairs: emit them
         if (cpv > 0) {
-            cudaMemsetAsync(work_count + V, 0, (size_t)V * 4, s);  // emission group counters
+            cudaMemsetAsync(work_count + V, 0, (size_t)V * 4 + 4, s);  // emission counters
             capacity_check_kernel<<<1, 32, 0, s>>>(n_pairs_dev, capacity, status_dev);
             emit_stage();
         }
@@ -1450,7 +1473,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
             cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
         }
-        cudaMemsetAsync(work_count, 0, (size_t)V * 8, s);
+        cudaMemsetAsync(work_count, 0, (size_t)V * 8 + 4, s);
         cudaMemsetAsync(arange, 0xff, (size_t)V * 4, s);  // lowest occupied active bin
         cudaMemsetAsync(arange + V, 0, (size_t)V * 4, s);  // highest
         cudaMemsetAsync(tile_partials, 0, (size_t)tchunks * 8, s);
