@@ -356,8 +356,14 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                 if (__syncthreads_count(p0.done && p1.done) == kFwdThreads) break;
                 const uint32_t w0 = sm.off[bin];
                 const int b0 = bin;
-                int e = bin + 1;
-                while (e <= limit && sm.off[e + 1] - w0 <= (uint32_t)kLazyWin) ++e;
+                // the window: bins b0 .. e - 1, e the first bin past the cut or
+                // whose inclusion would take the window above kLazyWin keys
+                // (at least one bin); a binary search over the monotone offsets
+                int e = bin + 1, e_hi = limit + 1;
+                while (e < e_hi) {
+                    const int mid = (e + e_hi) >> 1;
+                    if (sm.off[mid + 1] - w0 > (uint32_t)kLazyWin) e_hi = mid; else e = mid + 1;
+                }
                 const int n = (int)(sm.off[e] - w0);
                 bin = e;
                 if (n == 0) continue;
