@@ -272,8 +272,15 @@ __device__ __forceinline__ float4 stage_conic_a(float4 r0) {  // (u, v, A, B) ->
 __device__ __forceinline__ float4 stage_conic_b(float4 r1) {  // (C, o, r, g) -> (c2, o, r, g)
     return make_float4(-0.5f * kLog2e * r1.x, r1.y, r1.z, r1.w);
 }
-__device__ __forceinline__ float pair_power2(float dx, float t, float dy, float b2, float c2) {
-    return __fmaf_rn(c2 * dy, dy, dx * __fmaf_rn(b2, dy, t));
+// The base-2 exponent of a staged entry at a pixel, a2 dx^2 + b2 dx dy + c2 dy^2,
+// formed as P + dy (Q + c2 dy) with P = a2 dx^2 and Q = b2 dx computed once per
+// entry for the pixels of one column (pair_column).
+__device__ __forceinline__ void pair_column(float dx, float a2, float b2, float& P, float& Q) {
+    P = (a2 * dx) * dx;
+    Q = b2 * dx;
+}
+__device__ __forceinline__ float pair_power2(float P, float Q, float dy, float c2) {
+    return __fmaf_rn(dy, __fmaf_rn(c2, dy, Q), P);
 }
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;

@@ -47,11 +47,11 @@ struct BwdPixel {
 // kept (a skipped entry has weight exactly zero and leaves T as it was), so
 // the pixels of a thread form independent straight-line chains.
 template <bool ACTIVE>
-__device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float dx, float t,
+__device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float P, float Q,
                                           const float4& a, const float4& bb, float cb, float* gr,
                                           float& dpow, float& dy) {
     dy = p.fy - a.y;
-    const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
+    const float power2 = pair_power2(P, Q, dy, bb.x);
     const float G = ex2_approx(power2);
     const float alpha = fminf(kAlphaMax, bb.y * G);
     const bool live = pos < p.end && power2 <= 0.0f && alpha >= kAlphaMin;
@@ -239,14 +239,15 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const bool active = s_slot[k] >= 0;  // uniform over the block
                     const int pos = s_pos[k];
                     const float dx = p[0].fx - a.x;  // one column: shared by the pixels
-                    const float t = a.z * dx;
+                    float cP, cQ;  // the exponent's terms of this column
+                    pair_column(dx, a.z, a.w, cP, cQ);
                     float P[kPPT], dy[kPPT];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) P[j] = dy[j] = 0.f;
                     if (!active) {
 #pragma unroll
                         for (int j = 0; j < kPPT; ++j)
-                            bwd_entry<false>(p[j], pos, dx, t, a, bb, cb, nullptr, P[j], dy[j]);
+                            bwd_entry<false>(p[j], pos, cP, cQ, a, bb, cb, nullptr, P[j], dy[j]);
                         continue;
                     }
                     any_active = true;
@@ -258,7 +259,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     bool contrib = false;
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j)
-                        contrib |= bwd_entry<true>(p[j], pos, dx, t, a, bb, cb, gr, P[j], dy[j]);
+                        contrib |= bwd_entry<true>(p[j], pos, cP, cQ, a, bb, cb, gr, P[j], dy[j]);
                     {
                         float D = 0.f, Sy = 0.f, Syy = 0.f;
 #pragma unroll

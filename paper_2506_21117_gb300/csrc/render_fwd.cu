@@ -136,10 +136,9 @@ __device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0
 // independent straight-line chains the compiler can interleave. A skipped or
 // stopped entry adds exactly zero to the colour and leaves T and the last
 // contributor as they were, so the result is the same as with branches.
-__device__ __forceinline__ void composite_one(float dx, float t, float dy, const float4& a,
-                                              const float4& bb, float cb, int k,
-                                              PixelState& ps, int& lastk) {
-    const float power2 = pair_power2(dx, t, dy, a.w, bb.x);
+__device__ __forceinline__ void composite_one(float P, float Q, float dy, const float4& bb,
+                                              float cb, int k, PixelState& ps, int& lastk) {
+    const float power2 = pair_power2(P, Q, dy, bb.x);
     const float alpha = fminf(kAlphaMax, bb.y * ex2_approx(power2));
     const float wa = alpha * ps.T;       // the entry's weight if composited
     const float test_T = ps.T - wa;      // T (1 - alpha)
@@ -167,10 +166,10 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
-        const float dx = fx - a.x;
-        const float t = a.z * dx;
-        composite_one(dx, t, fy0 - a.y, a, bb, cb, k, p0, l0);
-        composite_one(dx, t, fy1 - a.y, a, bb, cb, k, p1, l1);
+        float P, Q;
+        pair_column(fx - a.x, a.z, a.w, P, Q);
+        composite_one(P, Q, fy0 - a.y, bb, cb, k, p0, l0);
+        composite_one(P, Q, fy1 - a.y, bb, cb, k, p1, l1);
     }
     if (l0 >= 0) p0.last = sm.pos[l0] + 1;
     if (l1 >= 0) p1.last = sm.pos[l1] + 1;
