@@ -162,7 +162,7 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k
                                                 float fy0, float fy1, PixelState& p0,
                                                 PixelState& p1) {
     int l0 = -1, l1 = -1;
-    for (int k = k0; k < k1 && !(p0.done && p1.done); ++k) {
+    auto entry = [&](int k) {
         const float4 a = sm.a[k];
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
@@ -170,7 +170,15 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k
         pair_column(fx - a.x, a.z, a.w, P, Q);
         composite_one(P, Q, fy0 - a.y, bb, cb, k, p0, l0);
         composite_one(P, Q, fy1 - a.y, bb, cb, k, p1, l1);
+    };
+    // two entries per step (a pixel that stops at the first one leaves the
+    // second unchanged: a done pixel takes nothing)
+    int k = k0;
+    for (; k + 1 < k1 && !(p0.done && p1.done); k += 2) {
+        entry(k);
+        entry(k + 1);
     }
+    if (k < k1 && !(p0.done && p1.done)) entry(k);
     if (l0 >= 0) p0.last = sm.pos[l0] + 1;
     if (l1 >= 0) p1.last = sm.pos[l1] + 1;
 }
