@@ -174,11 +174,13 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k
     // two entries per step (a pixel that stops at the first one leaves the
     // second unchanged: a done pixel takes nothing)
     int k = k0;
-    for (; k + 1 < k1 && !(p0.done && p1.done); k += 2) {
+    for (; k + 3 < k1 && !(p0.done && p1.done); k += 4) {
         entry(k);
         entry(k + 1);
+        entry(k + 2);
+        entry(k + 3);
     }
-    if (k < k1 && !(p0.done && p1.done)) entry(k);
+    for (; k < k1 && !(p0.done && p1.done); ++k) entry(k);
     if (l0 >= 0) p0.last = sm.pos[l0] + 1;
     if (l1 >= 0) p1.last = sm.pos[l1] + 1;
 }
