@@ -183,6 +183,19 @@ __device__ __forceinline__ void prefix2d_smem(int32_t* S, int rows, int cols, in
 // Odd shared-memory pitch for a grid of `cols` columns.
 __host__ __device__ __forceinline__ int smem_pitch(int cols) { return cols | 1; }
 
+// Ring around the covered tiles, with coverage in bit 0 of `cov` (other bits
+// ignored): 2 for an uncovered tile with a covered one among its eight
+// neighbours.
+__device__ __forceinline__ uint8_t ring_value_bit(const int32_t* cov, int pitch, int Tx, int Ty,
+                                                  int x, int y) {
+    for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int xx = x + dx, yy = y + dy;
+            if (xx >= 0 && xx < Tx && yy >= 0 && yy < Ty && (cov[yy * pitch + xx] & 1)) return 2;
+        }
+    return 0;
+}
+
 // Ring around the covered tiles: 2 for an uncovered tile with a covered one
 // among its eight neighbours (cov: 1 covered, 0 not; row pitch `pitch`).
 __device__ __forceinline__ uint8_t ring_value(const int32_t* cov, int pitch, int Tx, int Ty,
@@ -204,7 +217,7 @@ __device__ __forceinline__ uint8_t ring_value(const int32_t* cov, int pitch, int
 __global__ void __launch_bounds__(512)
 tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
                  uint8_t* __restrict__ tile_active, int32_t* __restrict__ sat,
-                 ClsTileCache* __restrict__ tile_cache, int smem_cap, int ring) {
+                 ClsTileCache* __restrict__ tile_cache, int smem_cap, int ring, int reset_zmin) {
     extern __shared__ int32_t s_grid[];
     const ClsView& view = views[blockIdx.x];
     const int Tx = view.tiles_x, Ty = view.tiles_y, Wd = Tx + 1;
@@ -213,43 +226,44 @@ tile_mask_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ diff,
     int32_t* S = sat + view.sat_base;
     const int p = smem_pitch(Tx);
     if ((int64_t)Ty * p * 4 <= smem_cap) {
-#pragma unroll 8
-        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-            const int y = t / Tx, x = t - y * Tx;
-            s_grid[y * p + x] = D[(int64_t)y * Wd + x];
-        }
+        // a warp per row, its lanes over the row's tiles
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int y = warp; y < Ty; y += nw)
+#pragma unroll 4
+            for (int x = lane; x < Tx; x += 32) s_grid[y * p + x] = D[(int64_t)y * Wd + x];
         __syncthreads();
         prefix2d_smem(s_grid, Ty, Tx, p);
-        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-            const int y = t / Tx, x = t - y * Tx;
-            const int32_t a = s_grid[y * p + x] > 0 ? 1 : 0;
-            s_grid[y * p + x] = a;
-            tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
-        }
+        for (int y = warp; y < Ty; y += nw)
+            for (int x = lane; x < Tx; x += 32) {
+                s_grid[y * p + x] = s_grid[y * p + x] > 0 ? 1 : 0;
+                if (reset_zmin) tile_cache[view.tile_base + y * Tx + x].zmin_active = 0xffffffffu;
+            }
         __syncthreads();
-        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-            const int y = t / Tx, x = t - y * Tx;
-            act[t] = s_grid[y * p + x] ? (uint8_t)1
-                                       : (ring ? ring_value(s_grid, p, Tx, Ty, x, y) : (uint8_t)0);
-        }
+        // rendered (covered, or in the ring) into bit 1 of the same entries
+        for (int y = warp; y < Ty; y += nw)
+            for (int x = lane; x < Tx; x += 32) {
+                const uint8_t a = (s_grid[y * p + x] & 1)
+                                      ? (uint8_t)1
+                                      : (ring ? ring_value_bit(s_grid, p, Tx, Ty, x, y) : (uint8_t)0);
+                act[y * Tx + x] = a;
+                // only this thread writes the entry; its neighbours read bit 0
+                if (a) s_grid[y * p + x] |= 2;
+            }
         __syncthreads();
-        for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
-            const int y = t / Tx, x = t - y * Tx;
-            s_grid[y * p + x] = act[t] ? 1 : 0;
-        }
+        for (int y = warp; y < Ty; y += nw)
+            for (int x = lane; x < Tx; x += 32) s_grid[y * p + x] = s_grid[y * p + x] >> 1;
         __syncthreads();
         prefix2d_smem(s_grid, Ty, Tx, p);
-        for (int t = threadIdx.x; t < (Tx + 1) * (Ty + 1); t += blockDim.x) {
-            const int y = t / Wd, x = t - y * Wd;
-            S[t] = (x == 0 || y == 0) ? 0 : s_grid[(y - 1) * p + x - 1];
-        }
+        for (int y = warp; y <= Ty; y += nw)
+            for (int x = lane; x <= Tx; x += 32)
+                S[(int64_t)y * Wd + x] = (x == 0 || y == 0) ? 0 : s_grid[(y - 1) * p + x - 1];
         return;
     }
     prefix2d(D, Ty, Tx, Wd);
     for (int t = threadIdx.x; t < Tx * Ty; t += blockDim.x) {
         const int y = t / Tx, x = t - y * Tx;
         act[t] = D[(int64_t)y * Wd + x] > 0 ? 1 : 0;
-        tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
+        if (reset_zmin) tile_cache[view.tile_base + t].zmin_active = 0xffffffffu;
     }
     __syncthreads();
     if (ring) {  // the coverage counts in D stay > 0 exactly on covered tiles
@@ -1443,7 +1457,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         project_kernel<1><<<dim3((info->max_active + kProjBlock - 1) / kProjBlock, V), kProjBlock,
                              0, s>>>(scenes_dev, views_dev, records, rects, diff);
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
-                                              grid_cap, tile_ring);
+                                              grid_cap, tile_ring, layout == 0 ? 1 : 0);
     if (layout == 0 && info->max_active > 0)
         // one warp per active Gaussian; two 1024-thread blocks per SM
         active_zmin_kernel<<<dim3((unsigned)hmin64((info->max_active + kZminThreads / 32 - 1) /
