@@ -15,7 +15,7 @@
 
 namespace cls {
 
-constexpr int kFwdThreads = kTilePixels / 2;  // two pixels per thread: rows ly and ly + 8
+constexpr int kFwdThreads = kTilePixels / 2;  // two pixels per thread: rows 2 ly and 2 ly + 1
 constexpr int kLazyWin = kTilePixels;  // keys per rank-sorted window
 constexpr int kLazyMax = 1024;         // largest bin the renderer sorts itself
 constexpr int kBins = CLS_DEPTH_BINS;
@@ -299,7 +299,9 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
         const int local = tile - view.tile_base;
         const int tx = local % view.tiles_x, ty = local / view.tiles_x;
         const int W = view.cam.width, H = view.cam.height;
-        const int px = tx * kTile + lx, py0 = ty * kTile + ly, py1 = py0 + 8;
+        // a warp covers a 16 x 4 strip of the tile (its pixels saturate at
+        // similar depths, so the warp leaves the list walk sooner)
+        const int px = tx * kTile + lx, py0 = ty * kTile + 2 * ly, py1 = py0 + 1;
         const float fx = (float)px + 0.5f, fy0 = (float)py0 + 0.5f, fy1 = (float)py1 + 0.5f;
         const float tx0 = (float)(tx * kTile), ty0 = (float)(ty * kTile);
         const uint32_t start = ranges[2 * (int64_t)tile], end = ranges[2 * (int64_t)tile + 1];
