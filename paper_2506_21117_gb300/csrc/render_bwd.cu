@@ -129,7 +129,7 @@ __device__ __forceinline__ void bwd_load_pixel(BwdPixel& p, const ClsView& view,
     p.R2 = image[p3 + 2 * plane] - st.w;
 }
 
-__global__ void __launch_bounds__(kBwdThreads, 16)
+__global__ void __launch_bounds__(kBwdThreads, 14)
 render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                   const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
                   int vals_stride, const uint32_t* __restrict__ ranges,
