@@ -991,11 +991,10 @@ bin_window_tables_kernel(const ClsView* __restrict__ views, const int32_t* __res
 // kCells consecutive cells; per round each lane takes one segment, its record
 // found by a binary search over the warp's segment prefix (the record's fields
 // travel by shuffles, every lane taking part), and a cell whose tile admits
-// the bin claims a slot in its (tile, depth bin) bucket. One 1024-thread block per
-// SM; warps take groups from a per-view counter, the next group claimed and
-// fetched while the current one is processed.
-constexpr int kEmitGroups = 16;  // groups per warp and block lifetime
-constexpr int kCells = 8;        // consecutive cells per lane and round
+// the bin claims a slot in its (tile, depth bin) bucket. Persistent 1024-thread
+// blocks, one wave; warps take groups from a per-view counter, the next group
+// claimed and fetched while the current one is processed.
+constexpr int kCells = 8;  // consecutive cells per lane and round
 
 __global__ void __launch_bounds__(kEmitThreads)
 emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ tile_rank,
@@ -1009,189 +1008,206 @@ emit_bucketed_kernel(const ClsView* __restrict__ views, const int32_t* __restric
                      int32_t* __restrict__ ticket, int32_t* __restrict__ status) {
     extern __shared__ uint32_t s_tile[];
     __shared__ int s_view;
-    // The block's view. Blocks of the first wave are shared out over the views
-    // in proportion to their groups of work items; later blocks join the view
-    // with the most groups left, and leave if there is none. One thread decides
-    // (other blocks advance the counters), so the whole block takes the same view.
-    if (threadIdx.x == 0) {
-        const int t = atomicAdd(ticket, 1);
-        int pick = -1;
-        if (t < first_wave) {
-            int64_t total = 0;
-            for (int v = 0; v < n_views; ++v) total += (work_count[v] + 31) / 32;
-            const int64_t target = ((int64_t)t * total) / first_wave;  // this block's share
-            int64_t cum = 0;
-            for (int v = 0; v < n_views && pick < 0; ++v) {
-                cum += (work_count[v] + 31) / 32;
-                if (target < cum) pick = v;
-            }
-        }
-        int best = 0;
-        if (pick >= 0)
-            best = (work_count[pick] + 31) / 32 - *(volatile int32_t*)(next_group + pick);
-        if (best <= 0) {  // the share's view is done (or a later block): the most left
-            pick = -1;
-            for (int v = 0; v < n_views; ++v) {
-                const int left = (work_count[v] + 31) / 32 - *(volatile int32_t*)(next_group + v);
-                if (left > best) {
-                    best = left;
-                    pick = v;
-                }
-            }
-        }
-        s_view = pick;
-    }
-    __syncthreads();
-    const int vi = s_view;
-    if (vi < 0) return;
-    const ClsView& view = views[vi];
-    const int Tx = view.tiles_x;
-    const int nt = Tx * view.tiles_y;
-    const int n = work_count[vi];
-    uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_tile + nt);
-    const int r0 = rank0[vi];  // rank of the view's first rendered tile
-    const int64_t tb = view.tile_base;
-    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
-        const int r = tile_rank[tb + i];
-        const bool on = r >= 0;
-        const uint32_t win = fc_pack(on, on ? front[tb + i] : 0u, cut ? cut[tb + i] : 255u);
-        s_tile[i] = (on ? (uint32_t)(r - r0 + 1) : 0u) | (win << 16);
-    }
-    const int levels = row_levels(Tx);
-    const bool fits = emit_tables_fit(nt, Tx, smem_bytes);
-    if (fits) {  // the row tables of the view, built here in shared memory (a warp per row)
-        const int Ty = view.tiles_y, wy = threadIdx.x >> 5, lx = threadIdx.x & 31;
-        __syncthreads();
-        for (int y = wy; y < Ty; y += kEmitThreads / 32)
-            for (int x = lx; x + 2 <= Tx; x += 32) {
-                const int i = y * Tx + x;
-                s_lv[i] = (uint16_t)fc_merge(s_tile[i] >> 16, s_tile[i + 1] >> 16);
-            }
-        for (int l = 2; l < levels; ++l) {
-            __syncthreads();
-            const int h = 1 << (l - 1);
-            const int prev = (l - 2) * nt, cur = prev + nt;
-            for (int y = wy; y < Ty; y += kEmitThreads / 32)
-                for (int x = lx; x + 2 * h <= Tx; x += 32) {
-                    const int i = y * Tx + x;
-                    s_lv[cur + i] = (uint16_t)fc_merge(s_lv[prev + i], s_lv[prev + i + h]);
-                }
-        }
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const DepthBins db = depth_bins(zmin[vi], zmax[vi]);
-    const uint4* wl = work_list + view.rec_base;
-    int g_next = 0;
-    if (lane == 0) g_next = atomicAdd(next_group + vi, 1);
-    g_next = __shfl_sync(0xffffffffu, g_next, 0);
-    uint4 it_next = make_uint4(0u, 0u, 0u, 0u);
-    if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
-    for (int taken = 0; taken < kEmitGroups; ++taken) {
-        const int g = g_next;
-        const uint4 item = it_next;
-        if (g * 32 >= n) break;
-        if (taken + 1 < kEmitGroups) {  // claim and fetch the next group now
-            int gn = 0;
-            if (lane == 0) gn = atomicAdd(next_group + vi, 1);
-            g_next = __shfl_sync(0xffffffffu, gn, 0);
-            if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
-        }
-        int x0 = 0, x1 = -1, y0 = 0, y1 = -1, bin = 0, area = 0;
-        const bool has = g * 32 + lane < n;
-        const uint16_t* T = nullptr;
-        int st = 1, d = 0;
-        if (has) {
-            unpack_rect(item, x0, x1, y0, y1);
-            bin = depth_bin(item.z, db);
-            const int l = 31 - __clz(x1 - x0 + 1);
-            T = l == 0 ? reinterpret_cast<const uint16_t*>(s_tile) + 1
-                : fits ? s_lv + (l - 1) * nt
-                       : t_win + (int64_t)(l - 1) * total_tiles + tb;
-            st = l == 0 ? 2 : 1;
-            d = (x1 - x0 + 1 - (1 << l)) * st;
-        }
-        // The rows of the rectangle where the bin can be emitted (a row
-        // qualifies when some tile of it admits the bin; two overlapping runs
-        // of 2^l tiles from the row tables cover its columns): the first and
-        // the last such row. The loop runs to the warp's tallest rectangle
-        // with every lane in it, so that the warp reaches the shuffles below
-        // converged (lanes leaving per-lane loops at different trip counts
-        // were seen to fall out of step with the rest of the warp).
-        const int h = has ? y1 - y0 + 1 : 0;
-        int hmax = h;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-        int ra = -1, rb = -1;
-        int64_t at = (int64_t)(y0 * Tx + x0) * st;
-        for (int k = 0; k < hmax; ++k, at += Tx * st) {
-            if (k < h && fc_admits(fc_merge(T[at], T[at + d]), bin)) {
-                if (ra < 0) ra = y0 + k;
-                rb = y0 + k;
-            }
-        }
-        if (ra >= 0) {
-            y0 = ra;
-            y1 = rb;
-            area = (x1 - x0 + 1) * (y1 - y0 + 1);
-        }
-        // The cells of each cut rectangle are split into segments of kCells
-        // consecutive cells; lanes take whole segments (the segment prefix
-        // over the warp gives each lane its record), so a lane's cells never
-        // cross a record boundary.
-        const int segs = (area + kCells - 1) / kCells;
-        int incl = segs;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);  // segments of the group
-        const int first = incl - segs;
-        const uint32_t xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
-        const uint32_t wb = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
-        for (int s0 = 0; s0 < total; s0 += 32) {
-            const int sg = s0 + lane;
-            const int own = owner_of(incl, sg);
-            const int o_first = __shfl_sync(0xffffffffu, first, own);
-            const int o_area = __shfl_sync(0xffffffffu, area, own);
-            const uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
-            const uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
-            const uint64_t key = ((uint64_t)__shfl_sync(0xffffffffu, item.z, own) << 32) |
-                                 __shfl_sync(0xffffffffu, item.w, own);
-            const int w = max((int)(o_wb & 0xffffu), 1), ob = (int)(o_wb >> 16);
-            const int k0 = (sg - o_first) * kCells;  // first cell of the segment in its record
-            const int len = sg < total ? min(kCells, o_area - k0) : 0;
-            int q, rem;
-            divmod_small(max(k0, 0), w, q, rem);
-            int cell = ((int)(o_xy >> 16) + q) * Tx + (int)(o_xy & 0xffffu) + rem;
-            int32_t sub[kCells];
-#pragma unroll
-            for (int u = 0; u < kCells; ++u) {
-                sub[u] = -1;
-                if (u < len) {
-                    // guard (never taken): the cell is a tile of the view
-                    const bool in_view = cell >= 0 && cell < nt;
-                    const uint32_t word = in_view ? s_tile[cell] : 0x00ff0000u;
-                    const int r = r0 + (int)(word & 0xffffu) - 1;
-                    const bool admit = fc_admits(word >> 16, ob);
-                    if (admit && r >= 0 && r < total_tiles) sub[u] = r * kDepthBins + ob;
-                    else if (admit || !in_view) set_status(status, CLS_ERR_INTERNAL);
-                    if (++rem == w) {
-                        rem = 0;
-                        cell += Tx - w + 1;
-                    } else {
-                        ++cell;
+    // A block takes a view, builds its tables and works through the view's
+    // groups beside the other blocks on it; when the view has none left it takes
+    // the view with the most groups left, and leaves when no view has any, so
+    // every group is processed whatever the grid. The first pick shares the
+    // blocks out over the views in proportion to their groups. One thread
+    // picks (other blocks advance the counters), so the whole block takes the
+    // same view. A pick is of a view with groups left and every warp claims at
+    // least one of its groups before the next pick, so a block's picks are
+    // bounded; past the bound it reports CLS_ERR_INTERNAL and leaves.
+    int64_t total_groups = 0;  // thread 0 only
+    for (int round = 0;; ++round) {
+        if (threadIdx.x == 0) {
+            int pick = -1;
+            if (round == 0) {
+                for (int v = 0; v < n_views; ++v) total_groups += (work_count[v] + 31) / 32;
+                const int t = atomicAdd(ticket, 1);
+                if (t < first_wave) {
+                    const int64_t target = ((int64_t)t * total_groups) / first_wave;  // its share
+                    int64_t cum = 0;
+                    for (int v = 0; v < n_views && pick < 0; ++v) {
+                        cum += (work_count[v] + 31) / 32;
+                        if (target < cum) pick = v;
                     }
                 }
             }
-            int32_t p[kCells];
-#pragma unroll
-            for (int u = 0; u < kCells; ++u) p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
-#pragma unroll
-            for (int u = 0; u < kCells; ++u)
-                if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = key;
+            int best = 0;
+            if (pick >= 0)
+                best = (work_count[pick] + 31) / 32 - *(volatile int32_t*)(next_group + pick);
+            if (best <= 0) {  // the share's view is done, or a later pick: the most left
+                pick = -1;
+                for (int v = 0; v < n_views; ++v) {
+                    const int left =
+                        (work_count[v] + 31) / 32 - *(volatile int32_t*)(next_group + v);
+                    if (left > best) {
+                        best = left;
+                        pick = v;
+                    }
+                }
+            }
+            if (pick >= 0 && round > total_groups + n_views) {  // guard (never taken)
+                set_status(status, CLS_ERR_INTERNAL);
+                pick = -1;
+            }
+            s_view = pick;
         }
+        __syncthreads();
+        const int vi = s_view;
+        if (vi < 0) return;
+        const ClsView& view = views[vi];
+        const int Tx = view.tiles_x;
+        const int nt = Tx * view.tiles_y;
+        const int n = work_count[vi];
+        uint16_t* s_lv = reinterpret_cast<uint16_t*>(s_tile + nt);
+        const int r0 = rank0[vi];  // rank of the view's first rendered tile
+        const int64_t tb = view.tile_base;
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+            const int r = tile_rank[tb + i];
+            const bool on = r >= 0;
+            const uint32_t win = fc_pack(on, on ? front[tb + i] : 0u, cut ? cut[tb + i] : 255u);
+            s_tile[i] = (on ? (uint32_t)(r - r0 + 1) : 0u) | (win << 16);
+        }
+        const int levels = row_levels(Tx);
+        const bool fits = emit_tables_fit(nt, Tx, smem_bytes);
+        if (fits) {  // the row tables of the view, built here in shared memory (a warp per row)
+            const int Ty = view.tiles_y, wy = threadIdx.x >> 5, lx = threadIdx.x & 31;
+            __syncthreads();
+            for (int y = wy; y < Ty; y += kEmitThreads / 32)
+                for (int x = lx; x + 2 <= Tx; x += 32) {
+                    const int i = y * Tx + x;
+                    s_lv[i] = (uint16_t)fc_merge(s_tile[i] >> 16, s_tile[i + 1] >> 16);
+                }
+            for (int l = 2; l < levels; ++l) {
+                __syncthreads();
+                const int h = 1 << (l - 1);
+                const int prev = (l - 2) * nt, cur = prev + nt;
+                for (int y = wy; y < Ty; y += kEmitThreads / 32)
+                    for (int x = lx; x + 2 * h <= Tx; x += 32) {
+                        const int i = y * Tx + x;
+                        s_lv[cur + i] = (uint16_t)fc_merge(s_lv[prev + i], s_lv[prev + i + h]);
+                    }
+            }
+        }
+        __syncthreads();
+        const int lane = threadIdx.x & 31;
+        const DepthBins db = depth_bins(zmin[vi], zmax[vi]);
+        const uint4* wl = work_list + view.rec_base;
+        int g_next = 0;
+        if (lane == 0) g_next = atomicAdd(next_group + vi, 1);
+        g_next = __shfl_sync(0xffffffffu, g_next, 0);
+        uint4 it_next = make_uint4(0u, 0u, 0u, 0u);
+        if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
+        for (;;) {
+            const int g = g_next;
+            const uint4 item = it_next;
+            if (g * 32 >= n) break;
+            {  // claim and fetch the next group now
+                int gn = 0;
+                if (lane == 0) gn = atomicAdd(next_group + vi, 1);
+                g_next = __shfl_sync(0xffffffffu, gn, 0);
+                if (g_next * 32 + lane < n) it_next = wl[g_next * 32 + lane];
+            }
+            int x0 = 0, x1 = -1, y0 = 0, y1 = -1, bin = 0, area = 0;
+            const bool has = g * 32 + lane < n;
+            const uint16_t* T = nullptr;
+            int st = 1, d = 0;
+            if (has) {
+                unpack_rect(item, x0, x1, y0, y1);
+                bin = depth_bin(item.z, db);
+                const int l = 31 - __clz(x1 - x0 + 1);
+                T = l == 0 ? reinterpret_cast<const uint16_t*>(s_tile) + 1
+                    : fits ? s_lv + (l - 1) * nt
+                           : t_win + (int64_t)(l - 1) * total_tiles + tb;
+                st = l == 0 ? 2 : 1;
+                d = (x1 - x0 + 1 - (1 << l)) * st;
+            }
+            // The rows of the rectangle where the bin can be emitted (a row
+            // qualifies when some tile of it admits the bin; two overlapping runs
+            // of 2^l tiles from the row tables cover its columns): the first and
+            // the last such row. The loop runs to the warp's tallest rectangle
+            // with every lane in it, so that the warp reaches the shuffles below
+            // converged (lanes leaving per-lane loops at different trip counts
+            // were seen to fall out of step with the rest of the warp).
+            const int h = has ? y1 - y0 + 1 : 0;
+            int hmax = h;
+    #pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                hmax = max(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+            int ra = -1, rb = -1;
+            int64_t at = (int64_t)(y0 * Tx + x0) * st;
+            for (int k = 0; k < hmax; ++k, at += Tx * st) {
+                if (k < h && fc_admits(fc_merge(T[at], T[at + d]), bin)) {
+                    if (ra < 0) ra = y0 + k;
+                    rb = y0 + k;
+                }
+            }
+            if (ra >= 0) {
+                y0 = ra;
+                y1 = rb;
+                area = (x1 - x0 + 1) * (y1 - y0 + 1);
+            }
+            // The cells of each cut rectangle are split into segments of kCells
+            // consecutive cells; lanes take whole segments (the segment prefix
+            // over the warp gives each lane its record), so a lane's cells never
+            // cross a record boundary.
+            const int segs = (area + kCells - 1) / kCells;
+            int incl = segs;
+    #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);  // segments of the group
+            const int first = incl - segs;
+            const uint32_t xy = (uint32_t)x0 | ((uint32_t)y0 << 16);
+            const uint32_t wb = (uint32_t)(x1 - x0 + 1) | ((uint32_t)bin << 16);
+            for (int s0 = 0; s0 < total; s0 += 32) {
+                const int sg = s0 + lane;
+                const int own = owner_of(incl, sg);
+                const int o_first = __shfl_sync(0xffffffffu, first, own);
+                const int o_area = __shfl_sync(0xffffffffu, area, own);
+                const uint32_t o_xy = __shfl_sync(0xffffffffu, xy, own);
+                const uint32_t o_wb = __shfl_sync(0xffffffffu, wb, own);
+                const uint64_t key = ((uint64_t)__shfl_sync(0xffffffffu, item.z, own) << 32) |
+                                     __shfl_sync(0xffffffffu, item.w, own);
+                const int w = max((int)(o_wb & 0xffffu), 1), ob = (int)(o_wb >> 16);
+                const int k0 = (sg - o_first) * kCells;  // first cell of the segment in its record
+                const int len = sg < total ? min(kCells, o_area - k0) : 0;
+                int q, rem;
+                divmod_small(max(k0, 0), w, q, rem);
+                int cell = ((int)(o_xy >> 16) + q) * Tx + (int)(o_xy & 0xffffu) + rem;
+                int32_t sub[kCells];
+    #pragma unroll
+                for (int u = 0; u < kCells; ++u) {
+                    sub[u] = -1;
+                    if (u < len) {
+                        // guard (never taken): the cell is a tile of the view
+                        const bool in_view = cell >= 0 && cell < nt;
+                        const uint32_t word = in_view ? s_tile[cell] : 0x00ff0000u;
+                        const int r = r0 + (int)(word & 0xffffu) - 1;
+                        const bool admit = fc_admits(word >> 16, ob);
+                        if (admit && r >= 0 && r < total_tiles) sub[u] = r * kDepthBins + ob;
+                        else if (admit || !in_view) set_status(status, CLS_ERR_INTERNAL);
+                        if (++rem == w) {
+                            rem = 0;
+                            cell += Tx - w + 1;
+                        } else {
+                            ++cell;
+                        }
+                    }
+                }
+                int32_t p[kCells];
+    #pragma unroll
+                for (int u = 0; u < kCells; ++u)
+                    p[u] = sub[u] >= 0 ? atomicAdd(cursor + sub[u], 1) : -1;
+    #pragma unroll
+                for (int u = 0; u < kCells; ++u)
+                    if (p[u] >= 0 && p[u] < capacity) keys[p[u]] = key;
+            }
+        }
+        __syncthreads();  // every warp done with the view's tables
     }
 }
 
@@ -1424,20 +1440,14 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_bucketed_kernel,
                                                       kEmitThreads, (size_t)emit_smem);
-        // enough blocks for every view's largest possible work list (blocks
-        // without work leave at once), at least one resident wave
-        const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-        const int64_t per_block = (int64_t)(kEmitThreads / 32) * kEmitGroups * 32;
-        const unsigned emit_blocks = (unsigned)hmin64(
-            std::max<int64_t>((info->max_n + per_block - 1) / per_block, (resident + V - 1) / V),
-            65535);
-        // blocks pick their view when they start (the first wave in proportion
-        // to the views' work)
-        emit_bucketed_kernel<<<(unsigned)hmin64((int64_t)V * emit_blocks, 1 << 30), kEmitThreads,
-                               (size_t)emit_smem, s>>>(
+        // one resident wave of persistent blocks; each picks a view when it
+        // starts (in proportion to the views' work) and again when its view
+        // has no work left
+        const int resident = (int)hmin64((int64_t)sms * (per_sm > 0 ? per_sm : 1), 1 << 20);
+        emit_bucketed_kernel<<<(unsigned)resident, kEmitThreads, (size_t)emit_smem, s>>>(
             views_dev, tile_rank, rank0, zmin, zmax, cursor, keys, capacity, work_list,
             work_count, work_count + V, bin_cut, front, t_win, info->total_tiles, emit_smem,
-            (int)V, (int)hmin64(resident, 1 << 30), work_count + 2 * V, status_dev);
+            (int)V, resident, work_count + 2 * V, status_dev);
     };
     if (project_mode == 2) {  // the previous call counted these pairs: emit them
         if (cpv > 0) {

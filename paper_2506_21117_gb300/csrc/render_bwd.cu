@@ -131,7 +131,8 @@ __device__ __forceinline__ void bwd_load_pixel(BwdPixel& p, const ClsView& view,
 
 __global__ void __launch_bounds__(kBwdThreads, 14)
 render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
-                  const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
+                  const ClsProjected* __restrict__ records, uint32_t n_records,
+                  const uint32_t* __restrict__ vals,
                   int vals_stride, const uint32_t* __restrict__ ranges,
                   const int32_t* __restrict__ active_tiles,
                   const int32_t* __restrict__ n_active_tiles,
@@ -196,8 +197,9 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                 const int i = r * kBwdThreads + threadIdx.x;
                 bool keep = false;
                 rec[r] = 0;
-                if (i < nb) {
-                    rec[r] = vals[(int64_t)(start + lo + i) * vals_stride];
+                if (i < nb) rec[r] = vals[(int64_t)(start + lo + i) * vals_stride];
+                // guard (never taken): an index past the records is dropped unread
+                if (i < nb && rec[r] < n_records) {
                     const float4* q = reinterpret_cast<const float4*>(records + rec[r]);
                     keep = !tile_culled(q[0], q[1], tx0, ty0);
                 }
@@ -565,9 +567,9 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
     const int blocks = (int)hmin64(info->total_tiles, bwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(
-        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
-        n_active_tiles_dev, tile_cache, prefix_state, image, n_contrib, dL_dimage, grad2d,
-        work_counter);
+        views_dev, info->n_views, records, (uint32_t)hmin64(info->total_records, 0xffffffffll),
+        vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, tile_cache, prefix_state,
+        image, n_contrib, dL_dimage, grad2d, work_counter);
     if (info->max_active > 0 && info->total_grad_rows > 0) {
         backward_gaussian_kernel<<<dim3((info->max_active + 127) / 128, info->n_scenes), 128, 0,
                                    s>>>(scenes_dev, views_dev, grad2d, grads);

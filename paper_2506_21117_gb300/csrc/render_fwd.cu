@@ -71,8 +71,8 @@ struct Staged {
 // order-preserving compaction by ballots and per-warp counts.
 template <typename RecOf>
 __device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0, RecOf rec_of,
-                                              const ClsProjected* records, float tx0, float ty0,
-                                              const PrefixWalk& pw) {
+                                              const ClsProjected* records, uint32_t n_records,
+                                              float tx0, float ty0, const PrefixWalk& pw) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool count = pw.rebuild && !pw.crossed;
     uint32_t rec[2];
@@ -83,8 +83,9 @@ __device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0
         const int i = r * kFwdThreads + threadIdx.x;
         bool keep = false, below = false;
         rec[r] = 0;
-        if (i < nb) {
-            rec[r] = rec_of(i);
+        if (i < nb) rec[r] = rec_of(i);
+        // guard (never taken): an index past the records is dropped unread
+        if (i < nb && rec[r] < n_records) {
             const float4* p = reinterpret_cast<const float4*>(records + rec[r]);
             below = count && __float_as_uint(p[2].z) < pw.zb;
             keep = pos0 + (uint32_t)i >= pw.skip_to && !tile_culled(p[0], p[1], tx0, ty0);
@@ -171,8 +172,8 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k
         composite_one(P, Q, fy0 - a.y, bb, cb, k, p0, l0);
         composite_one(P, Q, fy1 - a.y, bb, cb, k, p1, l1);
     };
-    // two entries per step (a pixel that stops at the first one leaves the
-    // second unchanged: a done pixel takes nothing)
+    // four entries per step (a pixel that stops at one of them leaves the
+    // rest unchanged: a done pixel takes nothing)
     int k = k0;
     for (; k + 3 < k1 && !(p0.done && p1.done); k += 4) {
         entry(k);
@@ -267,7 +268,8 @@ __device__ __forceinline__ void finish_pixel(const PixelState& ps, const ClsView
 
 __global__ void __launch_bounds__(kFwdThreads, 8)
 render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
-                  const ClsProjected* __restrict__ records, const uint32_t* __restrict__ vals,
+                  const ClsProjected* __restrict__ records, uint32_t n_records,
+                  const uint32_t* __restrict__ vals,
                   int vals_stride, const uint32_t* __restrict__ ranges,
                   const int32_t* __restrict__ active_tiles,
                   const int32_t* __restrict__ n_active_tiles, uint64_t* __restrict__ lazy_keys,
@@ -328,8 +330,8 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                 const int nb = (int)min((uint32_t)kTilePixels, end - b);
                 const Staged st = stage_batch(
                     sm, nb, b - start,
-                    [&](int i) { return vals[(int64_t)(b + i) * vals_stride]; }, records, tx0,
-                    ty0, pw);
+                    [&](int i) { return vals[(int64_t)(b + i) * vals_stride]; }, records,
+                    n_records, tx0, ty0, pw);
                 __syncthreads();
                 composite_staged(sm, st, nb, b - start, pw, view, px, py0, py1, fx, fy0, fy1, p0,
                                  p1, prefix_state, prefix_last);
@@ -410,7 +412,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
                         [&](int i) {
                             return (uint32_t)(here ? sm.sorted[c0 + i] : lazy_keys[w0 + c0 + i]);
                         },
-                        records, tx0, ty0, pw);
+                        records, n_records, tx0, ty0, pw);
                     __syncthreads();
                     composite_staged(sm, st, nb, pos0, pw, view, px, py0, py1, fx, fy0, fy1, p0,
                                      p1, prefix_state, prefix_last);
@@ -506,11 +508,11 @@ extern "C" int cls_render_forward(const ClsView* views_dev, const ClsBatchInfo* 
     const int blocks = (int)hmin64(info->total_tiles, fwd_blocks);
     cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     render_fwd_kernel<<<blocks, kFwdThreads, sizeof(FwdSmem), s>>>(
-        views_dev, info->n_views, records, vals, vals_stride, ranges, active_tiles,
-        n_active_tiles_dev, lazy_keys, bin_offsets, list_ranks, cut_in, cut_out, trunc,
-        trunc_count, trunc_cap, tile_cache, prefix_state, prefix_last, bg[0],
-        bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage, loss_per_scene,
-        work_counter);
+        views_dev, info->n_views, records, (uint32_t)hmin64(info->total_records, 0xffffffffll),
+        vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, lazy_keys, bin_offsets,
+        list_ranks, cut_in, cut_out, trunc, trunc_count, trunc_cap, tile_cache, prefix_state,
+        prefix_last, bg[0], bg[1], bg[2], target, loss_mode, image, T_final, n_contrib, dL_dimage,
+        loss_per_scene, work_counter);
     CLS_CHECK_LAUNCH();
     return CLS_OK;
 }

@@ -195,7 +195,7 @@ def _tile_max_contrib(lu, cams):
 
 
 @pytest.mark.parametrize("layout,lazy", [(0, False), (1, False), (1, True)])
-@pytest.mark.parametrize("case", ["plain", "local", "large_radii"])
+@pytest.mark.parametrize("case", ["plain", "local", "large_radii", "mixed_views"])
 def test_projection_and_tile_lists_bit_exact(case, layout, lazy):
     if case == "plain":
         scene, cams, targets = S.workload_plain()
@@ -205,6 +205,16 @@ def test_projection_and_tile_lists_bit_exact(case, layout, lazy):
         deg = 3
         active = fx.vote_rule(*fx.votes(scene["means"], cams, masks), len(cams))
         assert 0 < active.sum() < 0.5 * active.size
+    elif case == "mixed_views":
+        # ten views of unequal sizes in one batch, ragged ones among them: the
+        # emission's blocks are shared out over views with very different work
+        scene = S.uniform_scene(20000, 1, 23)
+        sizes = [(320, 240), (48, 32), (160, 96), (16, 16), (400, 300), (64, 64), (96, 200),
+                 (33, 17), (256, 144), (80, 60)]
+        cams = [S.ring_cameras(1, 4.0, W, H, angles=[0.6 * j])[0]
+                for j, (W, H) in enumerate(sizes)]
+        deg = 1
+        active = np.random.default_rng(23).uniform(size=20000) < 0.05
     else:
         # big splats on a 300x200 view: rectangles above the warp-emission
         # threshold, tiles with more pairs than one shared-memory window
