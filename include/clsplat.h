@@ -287,7 +287,7 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
                         ClsProjected* records, uint8_t* tile_active, int32_t* active_tiles,
                         int32_t* n_active_tiles_dev, uint64_t* keys, uint32_t* vals,
                         int64_t capacity, int64_t* n_pairs_dev, uint32_t* ranges,
-                        uint32_t* bin_offsets, const uint8_t* bin_cut,
+                        uint32_t* bin_offsets, uint8_t* bin_cut,
                         ClsTileCache* tile_cache, int32_t prefix_mode, int32_t tile_ring,
                         int32_t* status_dev, void* workspace, size_t workspace_bytes,
                         cls_stream_t stream);
@@ -306,7 +306,11 @@ int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* views_dev,
  * NULL) renders them completely. The result equals rendering without a cut.
  *   trunc  int32 [3 * trunc_cap]: tile ids, their active-tile ranks, old cuts
  *   trunc_cap >= total_tiles; trunc_count device int32 (caller zeroes it)
- * Bins in front of a cached prefix boundary stay unwritten here too. */
+ * Bins in front of a cached prefix boundary stay unwritten here too.
+ * cls_project_and_bin writes bin_cut in one case: a tile whose cached prefix
+ * it drops (the tile is rebuilt from the front) gets a cut of at least the
+ * depth bin of its old boundary plus the margin, since its pixels that stopped
+ * inside the old prefix need no deeper bin. */
 int cls_complete_truncated(const ClsView* views_dev, const ClsBatchInfo* info,
                            const ClsProjected* records, uint64_t* keys, int64_t capacity,
                            const int32_t* trunc, const int32_t* trunc_count, int64_t trunc_cap,

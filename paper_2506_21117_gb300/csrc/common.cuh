@@ -258,25 +258,31 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int degree, 
 
 // Alpha of one (pixel, Gaussian) pair, as the forward and backward kernels
 // both compute it (so they take identical skip decisions). The conic of a
-// staged record is pre-scaled so the exponent comes out in base 2:
-//   a2 = -A/2 log2(e),  b2 = -B log2(e),  c2 = -C/2 log2(e),
-//   power2 = a2 dx^2 + b2 dx dy + c2 dy^2 = power * log2(e),  G = 2^power2,
-// evaluated as dx (a2 dx + b2 dy) + c2 dy^2, with t = a2 dx shared by the two
-// pixels of a thread (they lie in the same column).
+// staged record is pre-scaled so the exponent comes out in base 2, and the
+// opacity o enters the exponent as log2 o (o 2^e = 2^(e + log2 o)):
+//   a2 = -A/2 log2(e),  b2 = -B log2(e),  c2 = -C/2 log2(e),  lo = log2 o,
+//   power2 = a2 dx^2 + b2 dx dy + c2 dy^2 + lo = power * log2(e) + lo,
+//   o G = 2^power2,  alpha = min(0.99, 2^power2),
+// so the test power <= 0 reads power2 <= lo. The exponent is formed as
+// P + dy (Q + c2 dy) with P = a2 dx^2 + lo and Q = b2 dx computed once per
+// entry for the pixels of one column (pair_column).
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float4 stage_conic_a(float4 r0) {  // (u, v, A, B) -> (u, v, a2, b2)
     return make_float4(r0.x, r0.y, -0.5f * kLog2e * r0.z, -kLog2e * r0.w);
 }
-__device__ __forceinline__ float4 stage_conic_b(float4 r1) {  // (C, o, r, g) -> (c2, o, r, g)
-    return make_float4(-0.5f * kLog2e * r1.x, r1.y, r1.z, r1.w);
+__device__ __forceinline__ float4 stage_conic_b(float4 r1) {  // (C, o, r, g) -> (c2, lo, r, g)
+    return make_float4(-0.5f * kLog2e * r1.x, lg2_approx(r1.y), r1.z, r1.w);
 }
-// The base-2 exponent of a staged entry at a pixel, a2 dx^2 + b2 dx dy + c2 dy^2,
-// formed as P + dy (Q + c2 dy) with P = a2 dx^2 and Q = b2 dx computed once per
-// entry for the pixels of one column (pair_column).
-__device__ __forceinline__ void pair_column(float dx, float a2, float b2, float& P, float& Q) {
-    P = (a2 * dx) * dx;
+__device__ __forceinline__ void pair_column(float dx, float a2, float b2, float lo, float& P,
+                                            float& Q) {
+    P = __fmaf_rn(a2 * dx, dx, lo);
     Q = b2 * dx;
 }
 __device__ __forceinline__ float pair_power2(float P, float Q, float dy, float c2) {
@@ -291,6 +297,9 @@ __device__ __forceinline__ float ex2_approx(float x) {
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTMin = 1e-4f;
+// Speculative depth cut (bucketed layout): depth bins emitted beyond the last
+// bin a tile needed in the previous iteration.
+constexpr int kCutMargin = 4;
 
 // Conservative per-tile cull of a list entry: true only if no pixel centre of
 // the tile whose first pixel is (tx0, ty0) can reach alpha >= 1/255, so every

@@ -702,18 +702,29 @@ col_prefix_kernel(const ClsView* __restrict__ views, int32_t* __restrict__ S) {
 // (then every active Gaussian of the tile has bits(z) >= zb); otherwise, or
 // with prefix_mode 0, the boundary moves to edge(ba - 1), one bin in front,
 // so that a nearest active Gaussian moving forward by less than a bin keeps
-// the prefix, and the prefix is rebuilt by the next forward pass.
-// front[tile] = first bin to emit. Rows are processed eight at a time, their
+// the prefix, and the prefix is rebuilt by the next forward pass; the tile's
+// depth cut (if any) is then raised to at least the old boundary's bin plus
+// the margin. front[tile] = first bin to emit. Rows are processed eight at a time, their
 // loads issued together.
 constexpr int kTileChunk = 64;  // tiles per partial sum of the pair totals
 
-__global__ void __launch_bounds__(kDepthBins)
+// A tile whose cached prefix is dropped walks from the front again; its pixels
+// that stopped inside the old prefix need no bin behind the old boundary's, so
+// its cut covers that bin plus the margin. Kept out of line: the rare call
+// would otherwise cost the column walk registers.
+__device__ __noinline__ void raise_cut(uint8_t* cut, uint32_t old_zb, DepthBins db) {
+    const int need = min(kDepthBins - 1, depth_bin(old_zb, db) + kCutMargin);
+    if ((int)*cut < need) *cut = (uint8_t)need;
+}
+
+__global__ void __launch_bounds__(kDepthBins, 3)  // three blocks per SM: the grid in about one wave
 col_counts_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__ S,
                   int32_t* __restrict__ A, const uint32_t* __restrict__ arange,
                   const uint32_t* __restrict__ zmin, const uint32_t* __restrict__ zmax,
                   const int32_t* __restrict__ tile_rank, ClsTileCache* __restrict__ tile_cache,
                   int prefix_mode, int32_t* __restrict__ counts, uint8_t* __restrict__ front,
-                  int32_t* __restrict__ ttot, int64_t* __restrict__ tile_partials) {
+                  uint8_t* __restrict__ bin_cut, int32_t* __restrict__ ttot,
+                  int64_t* __restrict__ tile_partials) {
     __shared__ int32_t s_tot[kDepthBins];
     __shared__ int32_t s_ba[kDepthBins];
     __shared__ int32_t s_rank[kDepthBins];
@@ -781,6 +792,8 @@ col_counts_kernel(const ClsView* __restrict__ views, const int32_t* __restrict__
                     const bool keep = prefix_mode != 0 && c.n_prefix != CLS_PREFIX_UNKNOWN &&
                                       c.zb <= edge;
                     if (!keep) {
+                        if (bin_cut && c.n_prefix != CLS_PREFIX_UNKNOWN)
+                            raise_cut(bin_cut + tile, c.zb, db);
                         c.zb = s_ba[b] >= kDepthBins ? edge : bin_edge(s_ba[b] - 1, db);
                         c.n_prefix = CLS_PREFIX_UNKNOWN;
                     }
@@ -1373,7 +1386,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
                                    int32_t* active_tiles, int32_t* n_active_tiles_dev,
                                    uint64_t* keys, uint32_t* vals, int64_t capacity,
                                    int64_t* n_pairs_dev, uint32_t* ranges, uint32_t* bin_offsets,
-                                   const uint8_t* bin_cut, ClsTileCache* tile_cache,
+                                   uint8_t* bin_cut, ClsTileCache* tile_cache,
                                    int32_t prefix_mode, int32_t tile_ring, int32_t* status_dev,
                                    void* workspace, size_t workspace_bytes, cls_stream_t stream) {
     if (!info || !scenes_dev || !views_dev || !records || !tile_active || !active_tiles ||
@@ -1540,7 +1553,7 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         // turns into the buckets' slot cursors
         col_counts_kernel<<<dim3(kLines, V), kDepthBins, 0, s>>>(
             views_dev, sbins, abins, arange, zmin, zmax, tile_rank, tile_cache, prefix_mode,
-            cursor, front, ttot, tile_partials);
+            cursor, front, bin_cut, ttot, tile_partials);
         scan_partials_kernel<<<1, 1024, 0, s>>>(tile_partials, tchunks, n_pairs_dev, nullptr,
                                                 capacity, status_dev);
         // counting only (capacity planning): the per-bucket counts stay in

@@ -42,7 +42,8 @@ struct BwdPixel {
 // gr[6..8] and dL/dpower (0 unless the entry contributes with alpha below the
 // clamp) returned in `dpow` with the pixel's dy; the caller turns those into
 // the per-thread sums of the centre, conic and opacity gradients.
-// a = (u, v, a2, b2), bb = (c2, opacity, r, g) as staged (base-2 conic).
+// a = (u, v, a2, b2), bb = (c2, log2 opacity, r, g) as staged (base-2 conic,
+// the opacity folded into the exponent).
 // Written without branches: the walk-end and skip decisions select what is
 // kept (a skipped entry has weight exactly zero and leaves T as it was), so
 // the pixels of a thread form independent straight-line chains.
@@ -52,9 +53,9 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float P, float Q
                                           float& dpow, float& dy) {
     dy = p.fy - a.y;
     const float power2 = pair_power2(P, Q, dy, bb.x);
-    const float G = ex2_approx(power2);
-    const float alpha = fminf(kAlphaMax, bb.y * G);
-    const bool live = pos < p.end && power2 <= 0.0f && alpha >= kAlphaMin;
+    const float G = ex2_approx(power2);  // opacity times the Gaussian
+    const float alpha = fminf(kAlphaMax, G);
+    const bool live = pos < p.end && power2 <= bb.y && alpha >= kAlphaMin;
     const float w = live ? alpha * p.T : 0.0f;
     p.R0 = __fmaf_rn(-bb.z, w, p.R0);
     p.R1 = __fmaf_rn(-bb.w, w, p.R1);
@@ -64,7 +65,7 @@ __device__ __forceinline__ bool bwd_entry(BwdPixel& p, int pos, float P, float Q
         const float cg = bb.z * p.g0 + bb.w * p.g1 + cb * p.g2;
         const float gR = p.g0 * p.R0 + p.g1 * p.R1 + p.g2 * p.R2;
         const float dLda = p.T * cg - gR * inv_om;
-        dpow = (live && !(bb.y * G > kAlphaMax)) ? dLda * alpha : 0.f;
+        dpow = (live && !(G > kAlphaMax)) ? dLda * alpha : 0.f;
         gr[6] += w * p.g0;
         gr[7] += w * p.g1;
         gr[8] += w * p.g2;
@@ -242,7 +243,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const int pos = s_pos[k];
                     const float dx = p[0].fx - a.x;  // one column: shared by the pixels
                     float cP, cQ;  // the exponent's terms of this column
-                    pair_column(dx, a.z, a.w, cP, cQ);
+                    pair_column(dx, a.z, a.w, bb.y, cP, cQ);
                     float P[kPPT], dy[kPPT];
 #pragma unroll
                     for (int j = 0; j < kPPT; ++j) P[j] = dy[j] = 0.f;
@@ -316,7 +317,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                             case 2: g = -0.5f * S; break;        // dA
                             case 3: g = -S; break;               // dB
                             case 4: g = -0.5f * S; break;        // dC
-                            case 5: g = S / bb.y; break;         // dopacity
+                            case 5: g = S / ex2_approx(bb.y); break;  // dopacity
                             default: g = S;                      // colour
                         }
                         if (g != 0.f) atomicAdd(grad2d + (int64_t)slot * kG2Stride + comp, g);

@@ -19,7 +19,6 @@ constexpr int kFwdThreads = kTilePixels / 2;  // two pixels per thread: rows 2 l
 constexpr int kLazyWin = kTilePixels;  // keys per rank-sorted window
 constexpr int kLazyMax = 1024;         // largest bin the renderer sorts itself
 constexpr int kBins = CLS_DEPTH_BINS;
-constexpr int kCutMargin = 4;          // depth bins emitted beyond last iteration's need
 
 constexpr int kFwdWarps = kFwdThreads / 32;
 
@@ -139,11 +138,11 @@ __device__ __forceinline__ Staged stage_batch(FwdSmem& sm, int nb, uint32_t pos0
 // contributor as they were, so the result is the same as with branches.
 __device__ __forceinline__ void composite_one(float P, float Q, float dy, const float4& bb,
                                               float cb, int k, PixelState& ps, int& lastk) {
-    const float power2 = pair_power2(P, Q, dy, bb.x);
-    const float alpha = fminf(kAlphaMax, bb.y * ex2_approx(power2));
+    const float power2 = pair_power2(P, Q, dy, bb.x);  // with log2 o (bb.y) folded in
+    const float alpha = fminf(kAlphaMax, ex2_approx(power2));
     const float wa = alpha * ps.T;       // the entry's weight if composited
     const float test_T = ps.T - wa;      // T (1 - alpha)
-    const bool live = !ps.done && power2 <= 0.0f && alpha >= kAlphaMin;
+    const bool live = !ps.done && power2 <= bb.y && alpha >= kAlphaMin;
     const bool stop = live && test_T < kTMin;
     const bool take = live && !stop;
     const float w = take ? wa : 0.0f;
@@ -168,7 +167,7 @@ __device__ __forceinline__ void composite_batch(const FwdSmem& sm, int k0, int k
         const float4 bb = sm.b[k];
         const float cb = sm.c[k];
         float P, Q;
-        pair_column(fx - a.x, a.z, a.w, P, Q);
+        pair_column(fx - a.x, a.z, a.w, bb.y, P, Q);
         composite_one(P, Q, fy0 - a.y, bb, cb, k, p0, l0);
         composite_one(P, Q, fy1 - a.y, bb, cb, k, p1, l1);
     };
