@@ -143,9 +143,9 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                   float* __restrict__ grad2d, int* __restrict__ work_counter) {
     __shared__ float4 s_a[kTilePixels];
     __shared__ float4 s_b[kTilePixels];
-    __shared__ float s_c[kTilePixels];
-    __shared__ int s_slot[kTilePixels];
-    __shared__ int s_pos[kTilePixels];
+    // per staged entry: the bits of its blue colour, its active slot (-1 for a
+    // static Gaussian) and its list position, read with one shared load
+    __shared__ int4 s_e[kTilePixels];
     __shared__ float s_g[kSub][kBwdWarps][kGradComps + 1];
     __shared__ int s_cnt[kStage][kBwdWarps];
     __shared__ int s_tile;
@@ -226,9 +226,8 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     s_a[k] = stage_conic_a(q[0]);
                     s_b[k] = stage_conic_b(q[1]);
                     const float4 cc = q[2];
-                    s_c[k] = cc.x;
-                    s_slot[k] = __float_as_int(cc.y);
-                    s_pos[k] = lo + r * kBwdThreads + threadIdx.x;
+                    s_e[k] = make_int4(__float_as_int(cc.x), __float_as_int(cc.y),
+                                       lo + r * kBwdThreads + threadIdx.x, 0);
                 }
             }
             __syncthreads();
@@ -238,9 +237,10 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                 for (int k = k0; k < k1; ++k) {
                     const float4 a = s_a[k];
                     const float4 bb = s_b[k];
-                    const float cb = s_c[k];
-                    const bool active = s_slot[k] >= 0;  // uniform over the block
-                    const int pos = s_pos[k];
+                    const int4 e = s_e[k];
+                    const float cb = __int_as_float(e.x);
+                    const bool active = e.y >= 0;  // uniform over the block
+                    const int pos = e.z;
                     const float dx = p[0].fx - a.x;  // one column: shared by the pixels
                     float cP, cQ;  // the exponent's terms of this column
                     pair_column(dx, a.z, a.w, bb.y, cP, cQ);
@@ -297,7 +297,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
                     const int cnt = k1 - k0;
                     for (int e = threadIdx.x; e < cnt * kGradComps; e += kBwdThreads) {
                         const int ent = e / kGradComps, comp = e - ent * kGradComps;
-                        const int slot = s_slot[k0 + ent];
+                        const int slot = s_e[k0 + ent].y;
                         if (slot < 0) continue;
                         float S = 0.f, S2 = 0.f;  // this component's sums; S2 the other of du/dv
 #pragma unroll

@@ -240,41 +240,56 @@ sort_tiles_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
     }
 }
 
-// Bins holding at least `min_bin` keys (the renderer sorts smaller ones).
-// With `cut`, bins beyond a tile's cut (not emitted yet) are skipped. With a
-// list of completed tiles (`trunc`), only their bins beyond the old cut are
-// taken.
-__global__ void collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
-                                    const int32_t* __restrict__ n_active,
-                                    const int32_t* __restrict__ active_tiles,
-                                    const uint8_t* __restrict__ cut,
-                                    const int32_t* __restrict__ trunc,
-                                    const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
-                                    const ClsTileCache* __restrict__ tile_cache,
-                                    int min_bin, uint2* __restrict__ list,
-                                    int32_t* __restrict__ count, int64_t list_cap) {
+// Bins holding at least `min_bin` keys (the renderer sorts smaller ones): a
+// warp per tile, eight consecutive bins per lane (the end of a lane's last bin
+// is its right neighbour's first offset). With `cut`, bins beyond a tile's cut
+// (not emitted yet) are skipped. With a list of completed tiles (`trunc`),
+// only their bins beyond the old cut are taken. A bin that ends inside the
+// tile's cached prefix is never read and is skipped too.
+constexpr int kCollectBins = kBinsPerTile / 32;  // bins per lane
+
+__global__ void __launch_bounds__(256)
+collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
+                    const int32_t* __restrict__ n_active,
+                    const int32_t* __restrict__ active_tiles,
+                    const uint8_t* __restrict__ cut,
+                    const int32_t* __restrict__ trunc,
+                    const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
+                    const ClsTileCache* __restrict__ tile_cache,
+                    int min_bin, uint2* __restrict__ list,
+                    int32_t* __restrict__ count, int64_t list_cap) {
+    const int lane = threadIdx.x & 31;
     const int64_t nt = trunc ? min((int64_t)*trunc_count, trunc_cap) : (int64_t)(*n_active);
-    const int64_t ne = nt * kBinsPerTile;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = e / kBinsPerTile;
-        const int b = (int)(e - t * kBinsPerTile);
+    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
+         t += n_warps) {
         int64_t rank = t;
+        int b_lo = 0, b_hi = kBinsPerTile - 1;
+        int64_t tile = -1;
         if (trunc) {
+            tile = trunc[t];
             rank = trunc[trunc_cap + t];
-            if (b <= trunc[2 * trunc_cap + t]) continue;
-        } else if (cut && b > (int)cut[active_tiles[t]]) {
-            continue;
+            b_lo = trunc[2 * trunc_cap + t] + 1;
+        } else if (active_tiles) {
+            tile = active_tiles[t];
+            if (cut) b_hi = cut[tile];
         }
-        const int64_t idx = rank * kBinsPerTile + b;
-        const uint32_t a = bin_offsets[idx], n = bin_offsets[idx + 1] - a;
-        if (n >= (uint32_t)min_bin && tile_cache) {
-            // a bin that ends inside the tile's cached prefix is never read
-            const uint32_t np = tile_cache[trunc ? trunc[t] : active_tiles[t]].n_prefix;
-            if (np != CLS_PREFIX_UNKNOWN && a + n - bin_offsets[rank * kBinsPerTile] <= np)
-                continue;
-        }
-        if (n >= (uint32_t)min_bin) {
+        const uint32_t np = (tile_cache && tile >= 0) ? tile_cache[tile].n_prefix
+                                                      : CLS_PREFIX_UNKNOWN;
+        const uint32_t* off = bin_offsets + rank * kBinsPerTile;
+        const int b0 = lane * kCollectBins;
+        uint32_t o[kCollectBins + 1];
+#pragma unroll
+        for (int k = 0; k < kCollectBins; ++k) o[k] = off[b0 + k];
+        const uint32_t next = __shfl_down_sync(0xffffffffu, o[0], 1);
+        o[kCollectBins] = lane < 31 ? next : off[kBinsPerTile];
+        const uint32_t first = __shfl_sync(0xffffffffu, o[0], 0);
+#pragma unroll
+        for (int k = 0; k < kCollectBins; ++k) {
+            const int b = b0 + k;
+            const uint32_t a = o[k], n = o[k + 1] - o[k];
+            if (b < b_lo || b > b_hi || n < (uint32_t)min_bin) continue;
+            if (np != CLS_PREFIX_UNKNOWN && a + n - first <= np) continue;
             const int slot = atomicAdd(count, 1);
             if (slot < list_cap) list[slot] = make_uint2(a, n);
         }
@@ -288,6 +303,7 @@ sort_bins_kernel(uint64_t* __restrict__ keys, uint64_t* __restrict__ alt,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSortSmem& sm = *reinterpret_cast<TileSortSmem*>(smem_raw);
     const int64_t n_items = min((int64_t)*count, list_cap);
+    if (n_items == 0) return;  // nothing to sort (the usual case): no queue traffic
     for (;;) {
         if (threadIdx.x == 0) sm.tile = atomicAdd(work_counter, 1);
         __syncthreads();
