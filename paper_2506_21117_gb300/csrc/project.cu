@@ -443,8 +443,31 @@ __device__ __forceinline__ int pair_count(const ClsView& view, const uint4* rect
     return rect_count(sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
 }
 
-// Per-chunk pair totals (flat layout) and, per view, the depth range of the
-// Gaussians that produce pairs (bucketed layout).
+// The per-call resets of the bucketed binning, in one launch instead of a
+// memset each: the render-mask difference grid, the flat layout's large-rect
+// counter, the work-list, emission-group and block-ticket counters, the range
+// of occupied active bins (lowest all ones, highest 0), the per-chunk pair
+// totals and the tile ranges.
+__global__ void reset_bucketed_kernel(int32_t* __restrict__ diff, int64_t n_diff,
+                                      int32_t* __restrict__ big_count,
+                                      int32_t* __restrict__ work_count, int n_work,
+                                      uint32_t* __restrict__ arange, int n_views,
+                                      int64_t* __restrict__ tile_partials, int64_t n_partials,
+                                      uint32_t* __restrict__ ranges, int64_t n_ranges) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = i0; i < n_diff; i += stride) diff[i] = 0;
+    for (int64_t i = i0; i < n_ranges; i += stride) ranges[i] = 0u;
+    for (int64_t i = i0; i < n_partials; i += stride) tile_partials[i] = 0;
+    for (int64_t i = i0; i < n_work; i += stride) work_count[i] = 0;
+    for (int64_t i = i0; i < 2 * (int64_t)n_views; i += stride)
+        arange[i] = i < n_views ? 0xffffffffu : 0u;
+    if (i0 == 0) *big_count = 0;
+}
+
+// Per-chunk pair totals (flat layout, `partials`), per view the depth range of
+// the Gaussians that produce pairs and the list of pair-producing records
+// (bucketed layout).
 __global__ void __launch_bounds__(kBinBlock)
 count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                    const uint4* __restrict__ rects, const int32_t* __restrict__ sat,
@@ -462,23 +485,30 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
     int64_t cnt = 0;
     uint32_t lo = 0xffffffffu, hi = 0u;
     unsigned produces = 0;  // bit `it`: item `it` of this thread has pairs
+    uint4 rr[kBinItems];    // the items' packed rectangles, kept for the work list
+#pragma unroll
     for (int it = 0; it < kBinItems; ++it) {
         const int g = blockIdx.x * kBinChunk + it * kBinBlock + threadIdx.x;
-        if (g < n) {
-            int x0, x1, y0, y1;
-            uint32_t zb;
-            const int c = pair_count(view, rects, sat, g, x0, x1, y0, y1, zb);
-            if (c > 0) {
-                cnt += c;
-                lo = min(lo, zb);
-                hi = max(hi, zb);
-                produces |= 1u << it;
-            }
+        rr[it] = g < n ? rects[view.rec_base + g] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int it = 0; it < kBinItems; ++it) {
+        if (rr[it].w == 0u) continue;  // not visible (or past the scene)
+        int x0, x1, y0, y1;
+        unpack_rect(rr[it], x0, x1, y0, y1);
+        const int c = rect_count(sat + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
+        if (c > 0) {
+            cnt += c;
+            lo = min(lo, rr[it].z);
+            hi = max(hi, rr[it].z);
+            produces |= 1u << it;
         }
     }
-    int64_t tot;
-    block_exclusive_sum<kBinBlock>(cnt, smem, tot);
-    if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] = tot;
+    if (partials) {  // chunk pair totals (flat layout)
+        int64_t tot;
+        block_exclusive_sum<kBinBlock>(cnt, smem, tot);
+        if (threadIdx.x == 0) partials[(int64_t)blockIdx.y * chunks_per_view + blockIdx.x] = tot;
+    }
     if (work_list) {  // compact the pair-producing records: one atomic per block
         int32_t nw;
         int32_t k = block_exclusive_sum<kBinBlock>((int32_t)__popc(produces), smem32, nw);
@@ -487,11 +517,12 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
         k += s_base;
         // a work item is the record's packed rectangle with its record index
         // in place of the visible flag
+#pragma unroll
         for (int it = 0; it < kBinItems; ++it)
             if (produces & (1u << it)) {
                 const int64_t rec = view.rec_base + blockIdx.x * kBinChunk + it * kBinBlock +
                                     threadIdx.x;
-                uint4 r = rects[rec];
+                uint4 r = rr[it];
                 r.w = (uint32_t)rec;
                 work_list[view.rec_base + k++] = r;
             }
@@ -1471,8 +1502,14 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         CLS_CHECK_LAUNCH();
         return CLS_OK;
     }
-    cudaMemsetAsync(diff, 0, (size_t)info->total_sat * 4, s);
-    cudaMemsetAsync(big_count, 0, 4, s);
+    if (layout == 1) {
+        reset_bucketed_kernel<<<(unsigned)sms, 256, 0, s>>>(
+            diff, info->total_sat, big_count, work_count, 2 * (int)V + 1, arange, (int)V,
+            tile_partials, tchunks, ranges, info->total_tiles * 2);
+    } else {
+        cudaMemsetAsync(diff, 0, (size_t)info->total_sat * 4, s);
+        cudaMemsetAsync(big_count, 0, 4, s);
+    }
     if (project_mode == 0 && info->max_n > 0)
         project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
                              s>>>(scenes_dev, views_dev, records, rects, diff);
@@ -1510,14 +1547,11 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             cudaMemsetAsync(zmin, 0xff, (size_t)V * 4, s);
             cudaMemsetAsync(zmax, 0, (size_t)V * 4, s);
         }
-        cudaMemsetAsync(work_count, 0, (size_t)V * 8 + 4, s);
-        cudaMemsetAsync(arange, 0xff, (size_t)V * 4, s);  // lowest occupied active bin
-        cudaMemsetAsync(arange + V, 0, (size_t)V * 4, s);  // highest
-        cudaMemsetAsync(tile_partials, 0, (size_t)tchunks * 8, s);
+        // work_count, arange, tile_partials and ranges were reset above
     }
     const bool new_range = layout == 1 && project_mode == 0;
     count_pairs_kernel<<<rec_grid, kBinBlock, 0, s>>>(scenes_dev, views_dev, rects, sat,
-                                                      (int)cpv, partials,
+                                                      (int)cpv, layout == 0 ? partials : nullptr,
                                                       new_range ? zmin : nullptr,
                                                       new_range ? zmax : nullptr,
                                                       layout == 1 ? work_list : nullptr,
@@ -1531,7 +1565,6 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
         emit_big_kernel<<<1024, 256, 0, s>>>(views_dev, rects, tile_active, keys, vals,
                                              capacity, big_list, big_count);
     } else {
-        cudaMemsetAsync(ranges, 0, (size_t)info->total_tiles * 8, s);
         // grids of kDepthBins threads stride over the views' rows and columns
         constexpr unsigned kLines = 128;
         if (project_mode == 0) {  // the static Gaussians' pairs per (tile, bin)
