@@ -5,6 +5,18 @@
 
 namespace cls {
 
+// b^t for t >= 0 by repeated squaring in double (at most 2 x 31 multiplies; a
+// general double pow is a long dependent chain of slow double operations).
+__device__ __forceinline__ double pow_uint(double b, int t) {
+    double r = 1.0;
+    while (t > 0) {
+        if (t & 1) r *= b;
+        b *= b;
+        t >>= 1;
+    }
+    return r;
+}
+
 // t += 1 per scene, then the bias corrections 1 - b1^t and 1 - b2^t.
 __global__ void adam_advance_kernel(const ClsScene* __restrict__ scenes, int n_scenes, float b1,
                                     float b2, float2* __restrict__ bias) {
@@ -14,8 +26,8 @@ __global__ void adam_advance_kernel(const ClsScene* __restrict__ scenes, int n_s
     int32_t* step = scenes[s].adam_step;
     const int t = *step + 1;
     *step = t;
-    bias[s] = make_float2((float)(1.0 - pow((double)b1, (double)t)),
-                          (float)(1.0 - pow((double)b2, (double)t)));
+    bias[s] = make_float2((float)(1.0 - pow_uint((double)b1, t)),
+                          (float)(1.0 - pow_uint((double)b2, t)));
 }
 
 // One thread per float4 of an active row.

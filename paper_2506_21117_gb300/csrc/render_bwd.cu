@@ -331,6 +331,15 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
     }
 }
 
+// Zeroes the 2D gradient sums (float4 at a time) and the tile queue's counter.
+__global__ void bwd_prologue_kernel(float4* __restrict__ grad2d, int64_t n4,
+                                    int32_t* __restrict__ work_counter) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride)
+        grad2d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *work_counter = 0;
+}
+
 // d Y_k / d(x, y, z) contracted with coefficients dY[k], accumulated in g.
 __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, int degree,
                                              const float* dY, float& gx, float& gy, float& gz) {
@@ -560,13 +569,20 @@ extern "C" int cls_render_backward(const ClsScene* scenes_dev, const ClsView* vi
         (info->total_g2 > 0 && !grad2d) || (info->total_grad_rows > 0 && !grads))
         return CLS_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
-    if (info->total_g2 > 0)
-        cudaMemsetAsync(grad2d, 0, (size_t)info->total_g2 * kG2Stride * sizeof(float), s);
     const int bwd_blocks = per_device(g_bwd_blocks, [](int dev) {
         return resident_blocks(dev, render_bwd_kernel, kBwdThreads, 0);
     });
     const int blocks = (int)hmin64(info->total_tiles, bwd_blocks);
-    cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
+    if (info->total_g2 > 0 && ((uintptr_t)grad2d & 15) == 0) {
+        // the 2D gradient sums and the tile queue zeroed in one launch
+        const int64_t n4 = info->total_g2 * (kG2Stride / 4);
+        bwd_prologue_kernel<<<(unsigned)hmin64((n4 + 255) / 256, 1024), 256, 0, s>>>(
+            reinterpret_cast<float4*>(grad2d), n4, work_counter);
+    } else {
+        if (info->total_g2 > 0)
+            cudaMemsetAsync(grad2d, 0, (size_t)info->total_g2 * kG2Stride * sizeof(float), s);
+        cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
+    }
     render_bwd_kernel<<<blocks, kBwdThreads, 0, s>>>(
         views_dev, info->n_views, records, (uint32_t)hmin64(info->total_records, 0xffffffffll),
         vals, vals_stride, ranges, active_tiles, n_active_tiles_dev, tile_cache, prefix_state,

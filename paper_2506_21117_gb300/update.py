@@ -181,7 +181,10 @@ class Batch:
         self.n_contrib = torch.zeros(info.total_pixels, dtype=torch.int32, device=dev)
         self.image = torch.zeros(info.total_pixels * 3, dtype=torch.float32, device=dev)
         self.dL_dimage = torch.zeros(info.total_pixels * 3, dtype=torch.float32, device=dev)
-        self.loss = torch.zeros(S, dtype=torch.float32, device=dev)
+        # the per-scene loss and the truncated-tile count share one buffer, so
+        # one fill clears both before a forward pass
+        self._fwd_acc = torch.zeros(S + 1, dtype=torch.int32, device=dev)
+        self.loss = self._fwd_acc[:S].view(torch.float32)
         # grad2d: zeroed by the backward pass; grads: written for every active row
         self.grad2d = torch.empty(max(info.total_g2, 1) * abi.G2_STRIDE, dtype=torch.float32,
                                   device=dev)
@@ -194,7 +197,7 @@ class Batch:
         self.use_cut = self.lazy
         self.cut = torch.full((info.total_tiles,), 255, dtype=torch.uint8, device=dev)
         self.trunc = torch.zeros(3 * info.total_tiles, dtype=torch.int32, device=dev)
-        self.trunc_count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.trunc_count = self._fwd_acc[S:]
         # static-prefix cache: per tile (ClsTileCache), per pixel state after the prefix
         self.tile_cache = torch.empty(info.total_tiles * abi.TILE_CACHE_BYTES // 4,
                                       dtype=torch.int32, device=dev)
@@ -404,11 +407,9 @@ class Batch:
         if b.target_ready is not None:  # targets still on their way
             torch.cuda.current_stream().wait_event(b.target_ready)
             b.target_ready = None
-        if loss_mode:
-            b.loss.zero_()
         cut = b.use_cut
-        if cut:
-            b.trunc_count.zero_()
+        if loss_mode or cut:
+            b._fwd_acc.zero_()  # the loss and the truncated-tile count
         b._forward_call(loss_mode, bg, _ptr(b.active_tiles), _ptr(b.n_active_tiles),
                         None, _ptr(b.cut) if cut else None, _ptr(b.cut) if cut else None)
         if cut:
