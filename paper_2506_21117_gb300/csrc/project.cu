@@ -96,10 +96,28 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
         const int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
         float col[3] = {0.5f, 0.5f, 0.5f};
         const float* sh = row + 12;
-        for (int k = 0; k < K; ++k) {
-            col[0] += Y[k] * sh[3 * k + 0];
-            col[1] += Y[k] * sh[3 * k + 1];
-            col[2] += Y[k] * sh[3 * k + 2];
+        if (K == 16) {  // degree 3: the 48 coefficients as twelve 16-byte loads, issued together
+            float c[48];
+#pragma unroll
+            for (int j = 0; j < 12; ++j) {
+                const float4 v = reinterpret_cast<const float4*>(sh)[j];
+                c[4 * j] = v.x; c[4 * j + 1] = v.y; c[4 * j + 2] = v.z; c[4 * j + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                col[0] += Y[k] * c[3 * k + 0];
+                col[1] += Y[k] * c[3 * k + 1];
+                col[2] += Y[k] * c[3 * k + 2];
+            }
+        } else {  // unrolled with a guard, so that Y stays in registers
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                if (k < K) {
+                    col[0] += Y[k] * sh[3 * k + 0];
+                    col[1] += Y[k] * sh[3 * k + 1];
+                    col[2] += Y[k] * sh[3 * k + 2];
+                }
+            }
         }
         const float opacity = 1.0f / (1.0f + __expf(-m.w));
         r0 = make_float4(P.u, P.v, P.c * inv_det, -P.b * inv_det);

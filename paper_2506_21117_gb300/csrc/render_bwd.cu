@@ -415,20 +415,30 @@ backward_gaussian_kernel(const ClsScene* __restrict__ scenes, const ClsView* __r
         const float dxn = ddx * il, dyn = ddy * il, dzn = ddz * il;
         float Y[16];
         sh_basis(dxn, dyn, dzn, deg, Y);
+        // the loops run to 16 with a guard so that every index is a constant and
+        // the arrays stay in registers
         float raw[3] = {0.5f, 0.5f, 0.5f};
-        for (int k = 0; k < K; ++k) {
-            raw[0] += Y[k] * sh[3 * k];
-            raw[1] += Y[k] * sh[3 * k + 1];
-            raw[2] += Y[k] * sh[3 * k + 2];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            if (k < K) {
+                raw[0] += Y[k] * sh[3 * k];
+                raw[1] += Y[k] * sh[3 * k + 1];
+                raw[2] += Y[k] * sh[3 * k + 2];
+            }
         }
         float draw[3];
+#pragma unroll
         for (int c = 0; c < 3; ++c) draw[c] = raw[c] >= 0.f ? dcol[c] : 0.f;
         float dY[16];
-        for (int k = 0; k < K; ++k) {
-            dsh[3 * k] += Y[k] * draw[0];
-            dsh[3 * k + 1] += Y[k] * draw[1];
-            dsh[3 * k + 2] += Y[k] * draw[2];
-            dY[k] = sh[3 * k] * draw[0] + sh[3 * k + 1] * draw[1] + sh[3 * k + 2] * draw[2];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            dY[k] = 0.f;
+            if (k < K) {
+                dsh[3 * k] += Y[k] * draw[0];
+                dsh[3 * k + 1] += Y[k] * draw[1];
+                dsh[3 * k + 2] += Y[k] * draw[2];
+                dY[k] = sh[3 * k] * draw[0] + sh[3 * k + 1] * draw[1] + sh[3 * k + 2] * draw[2];
+            }
         }
         float gdx = 0.f, gdy = 0.f, gdz = 0.f;
         sh_basis_vjp(dxn, dyn, dzn, deg, dY, gdx, gdy, gdz);
@@ -536,14 +546,21 @@ backward_gaussian_kernel(const ClsScene* __restrict__ scenes, const ClsView* __r
     reinterpret_cast<float4*>(out)[0] = make_float4(dmean[0], dmean[1], dmean[2], dlogit);
     reinterpret_cast<float4*>(out)[1] = make_float4(dls[0], dls[1], dls[2], 0.f);
     reinterpret_cast<float4*>(out)[2] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-    for (int i = 0; i < sc.row_stride - 12; i += 4) {
-        float4 v;
-        v.x = i < 3 * K ? dsh[i] : 0.f;
-        v.y = i + 1 < 3 * K ? dsh[i + 1] : 0.f;
-        v.z = i + 2 < 3 * K ? dsh[i + 2] : 0.f;
-        v.w = i + 3 < 3 * K ? dsh[i + 3] : 0.f;
-        reinterpret_cast<float4*>(out + 12)[i / 4] = v;
+    // the colour coefficients (constant indices, so dsh stays in registers),
+    // then zeros up to the row's stride
+#pragma unroll
+    for (int i = 0; i < 48; i += 4) {
+        if (i < sc.row_stride - 12) {
+            float4 v;
+            v.x = i < 3 * K ? dsh[i] : 0.f;
+            v.y = i + 1 < 3 * K ? dsh[i + 1] : 0.f;
+            v.z = i + 2 < 3 * K ? dsh[i + 2] : 0.f;
+            v.w = i + 3 < 3 * K ? dsh[i + 3] : 0.f;
+            reinterpret_cast<float4*>(out + 12)[i / 4] = v;
+        }
     }
+    for (int i = 48; i < sc.row_stride - 12; i += 4)
+        reinterpret_cast<float4*>(out + 12)[i / 4] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 static PerDevice g_bwd_blocks;

@@ -257,8 +257,10 @@ collect_bins_kernel(const uint32_t* __restrict__ bin_offsets,
                     const int32_t* __restrict__ trunc_count, int64_t trunc_cap,
                     const ClsTileCache* __restrict__ tile_cache,
                     int min_bin, uint2* __restrict__ list,
-                    int32_t* __restrict__ count, int64_t list_cap) {
+                    int32_t* __restrict__ count, int64_t list_cap,
+                    int32_t* __restrict__ sort_queue) {
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *sort_queue = 0;  // the bin sort's tile queue
     const int64_t nt = trunc ? min((int64_t)*trunc_count, trunc_cap) : (int64_t)(*n_active);
     const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
@@ -352,8 +354,8 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
                              (int)sizeof(TileSortSmem));
         return resident_blocks(dev, sort_tiles_kernel, kTB, sizeof(TileSortSmem));
     });
-    cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
     if (min_bin <= 1) {
+        cudaMemsetAsync(work_counter, 0, sizeof(int32_t), s);
         sort_tiles_kernel<<<(int)hmin64(total_tiles, tiles_blocks), kTB, sizeof(TileSortSmem),
                             s>>>(keys, keys_alt, bin_offsets, n_active_tiles_dev, active_tiles,
                                  tile_cache, work_counter);
@@ -364,7 +366,7 @@ extern "C" int cls_sort_tiles(uint64_t* keys, uint64_t* keys_alt, const uint32_t
         cudaMemsetAsync(count, 0, sizeof(int32_t), s);
         collect_bins_kernel<<<1024, 256, 0, s>>>(bin_offsets, n_active_tiles_dev, active_tiles,
                                                  cut, trunc, trunc_count, trunc_cap, tile_cache,
-                                                 min_bin, list, count, cap);
+                                                 min_bin, list, count, cap, work_counter);
         sort_bins_kernel<<<tiles_blocks, kTB, sizeof(TileSortSmem), s>>>(keys, keys_alt, list,
                                                                           count, cap, work_counter);
     }
