@@ -1290,6 +1290,7 @@ complete_tiles_kernel(const ClsView* __restrict__ views, int n_views,
                       const uint8_t* __restrict__ front, int* __restrict__ item_counter) {
     __shared__ int s_item;
     const int n_items = (int)min((int64_t)*trunc_count, trunc_cap) * kCompleteChunks;
+    if (n_items <= 0) return;  // nothing truncated (the usual case): no queue traffic
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(item_counter, 1);
         __syncthreads();

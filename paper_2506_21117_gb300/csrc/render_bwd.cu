@@ -151,6 +151,7 @@ render_bwd_kernel(const ClsView* __restrict__ views, int n_views,
     __shared__ int s_tile;
     __shared__ int s_maxend;
     const int n_tiles = *n_active_tiles;
+    if (n_tiles <= 0) return;  // nothing rendered: no queue traffic
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, kRowStep)
     for (;;) {

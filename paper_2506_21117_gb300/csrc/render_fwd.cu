@@ -284,6 +284,7 @@ render_fwd_kernel(const ClsView* __restrict__ views, int n_views,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FwdSmem& sm = *reinterpret_cast<FwdSmem*>(smem_raw);
     const int n_tiles = *n_active_tiles;
+    if (n_tiles <= 0) return;  // an empty list (the usual rerun): no queue traffic
     const int lx = threadIdx.x & (kTile - 1), ly = threadIdx.x / kTile;  // ly in [0, 8)
     const bool lazy = bin_offsets != nullptr;
     for (;;) {
