@@ -29,6 +29,47 @@ __device__ __forceinline__ void stamp_rect(int32_t* grid, int Wd, int x0, int x1
     atomicAdd(grid + (int64_t)(y1 + 1) * Wd + x1 + 1, 1);
 }
 
+// Depth bins of a view: its depth range [lo, hi] (float bits of the
+// pair-producing Gaussians' depths) cut into kDepthBins equal parts. The bin
+// of depth bits zb is floor((zb - lo) * scale), clamped; float rounding is
+// monotone, so bins stay monotone in depth, and every kernel derives the same
+// scale from the same lo and hi.
+struct DepthBins {
+    uint32_t lo;
+    float scale;
+};
+
+__device__ __forceinline__ DepthBins depth_bins(uint32_t lo, uint32_t hi) {
+    return DepthBins{lo, (float)kDepthBins / ((float)(hi - lo) + 1.0f)};
+}
+
+__device__ __forceinline__ int depth_bin(uint32_t zb, const DepthBins& d) {
+    if (zb <= d.lo) return 0;
+    return min((int)((float)(zb - d.lo) * d.scale), kDepthBins - 1);
+}
+
+// Smallest depth bits whose depth bin is at least b (0 for b <= 0, all ones
+// for b >= kDepthBins): a binary search, exact because depth_bin is monotone.
+__device__ __forceinline__ uint32_t bin_edge(int b, const DepthBins& d) {
+    if (b <= 0) return 0u;
+    if (b >= kDepthBins) return 0xffffffffu;
+    uint64_t l = (uint64_t)d.lo + 1, h = 0xffffffffull;  // depth_bin(h) = kDepthBins - 1
+    while (l < h) {
+        const uint64_t m = (l + h) >> 1;
+        if (depth_bin((uint32_t)m, d) >= b) h = m; else l = m + 1;
+    }
+    return (uint32_t)l;
+}
+
+// The same, at depth bin b of a bin-fastest grid (entry (cell, b) at cell * kDepthBins + b).
+__device__ __forceinline__ void stamp_rect_bin(int32_t* G, int Wd, int b, int x0, int x1, int y0,
+                                               int y1) {
+    atomicAdd(G + ((int64_t)y0 * Wd + x0) * kDepthBins + b, 1);
+    atomicAdd(G + ((int64_t)y0 * Wd + x1 + 1) * kDepthBins + b, -1);
+    atomicAdd(G + ((int64_t)(y1 + 1) * Wd + x0) * kDepthBins + b, -1);
+    atomicAdd(G + ((int64_t)(y1 + 1) * Wd + x1 + 1) * kDepthBins + b, 1);
+}
+
 // Tile rectangle and depth bits of every record, written by the projection
 // (16 B: x0 | x1 << 16, y0 | y1 << 16, depth bits, and 1 for a visible static
 // record, 2 for a visible active one, 0 if the record has no tiles), so
@@ -60,7 +101,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kProjBlock)
 project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                ClsProjected* __restrict__ records, uint4* __restrict__ rects,
-               int32_t* __restrict__ diff) {
+               int32_t* __restrict__ diff, const uint32_t* __restrict__ zmin,
+               const uint32_t* __restrict__ zmax, int32_t* __restrict__ abins,
+               uint32_t* __restrict__ arange) {
     const ClsView& view = views[blockIdx.y];
     const ClsScene& sc = scenes[view.scene];
     const int i = blockIdx.x * kProjBlock + threadIdx.x;
@@ -83,6 +126,7 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
     project_gaussian(cam, m, ls, q, P);
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
     bool valid = P.valid && tile_rect(P.u, P.v, P.radius, view.tiles_x, view.tiles_y, x0, x1, y0, y1);
+    uint32_t b_lo = 0xffffffffu, b_hi = 0u;  // depth bin of a stamped active record
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;
     int radius = 0;
     if (valid) {
@@ -125,8 +169,19 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
         r2 = make_float4(fmaxf(col[2], 0.f), __int_as_float(slot), P.z, 0.f);
         radius = (int)P.radius;
         if (radius < 1) radius = 1;  // cannot happen for a finite positive lambda
-        // an active Gaussian stamps its tile rectangle into the render mask
-        if (MODE == 1) stamp_rect(diff + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
+        // an active Gaussian stamps its tile rectangle into the render mask and,
+        // with fixed depth bins (`abins`), into the active difference grid A at
+        // its depth bin
+        if (MODE == 1) {
+            stamp_rect(diff + view.sat_base, view.tiles_x + 1, x0, x1, y0, y1);
+            if (abins) {
+                const int b = depth_bin(__float_as_uint(P.z),
+                                        depth_bins(zmin[blockIdx.y], zmax[blockIdx.y]));
+                stamp_rect_bin(abins + (int64_t)view.sat_base * kDepthBins, view.tiles_x + 1, b,
+                               x0, x1, y0, y1);
+                b_lo = b_hi = (uint32_t)b;
+            }
+        }
     } else {
         r2 = make_float4(0.f, __int_as_float(slot), 0.f, 0.f);
     }
@@ -137,6 +192,16 @@ project_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ 
     out[0] = r0;
     out[1] = r1;
     out[2] = r2;
+    if (MODE == 1 && abins) {
+        // the range of occupied bins over the lanes here (lanes past the active
+        // count have left; any subset of lanes gives a correct min and max)
+        const unsigned m = __activemask();
+        const uint32_t lo = __reduce_min_sync(m, b_lo), hi = __reduce_max_sync(m, b_hi);
+        if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && hi >= lo) {
+            atomicMin(arange + blockIdx.y, lo);
+            atomicMax(arange + gridDim.y + blockIdx.y, hi);
+        }
+    }
 }
 
 
@@ -562,38 +627,6 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
     }
 }
 
-// Depth bins of a view: its depth range [lo, hi] (float bits of the
-// pair-producing Gaussians' depths) cut into kDepthBins equal parts. The bin
-// of depth bits zb is floor((zb - lo) * scale), clamped; float rounding is
-// monotone, so bins stay monotone in depth, and every kernel derives the same
-// scale from the same lo and hi.
-struct DepthBins {
-    uint32_t lo;
-    float scale;
-};
-
-__device__ __forceinline__ DepthBins depth_bins(uint32_t lo, uint32_t hi) {
-    return DepthBins{lo, (float)kDepthBins / ((float)(hi - lo) + 1.0f)};
-}
-
-__device__ __forceinline__ int depth_bin(uint32_t zb, const DepthBins& d) {
-    if (zb <= d.lo) return 0;
-    return min((int)((float)(zb - d.lo) * d.scale), kDepthBins - 1);
-}
-
-// Smallest depth bits whose depth bin is at least b (0 for b <= 0, all ones
-// for b >= kDepthBins): a binary search, exact because depth_bin is monotone.
-__device__ __forceinline__ uint32_t bin_edge(int b, const DepthBins& d) {
-    if (b <= 0) return 0u;
-    if (b >= kDepthBins) return 0xffffffffu;
-    uint64_t l = (uint64_t)d.lo + 1, h = 0xffffffffull;  // depth_bin(h) = kDepthBins - 1
-    while (l < h) {
-        const uint64_t m = (l + h) >> 1;
-        if (depth_bin((uint32_t)m, d) >= b) h = m; else l = m + 1;
-    }
-    return (uint32_t)l;
-}
-
 // ---------------------------------------------------------------------------
 // Bucketed layout: pairs per (tile, depth bin).
 //
@@ -609,13 +642,6 @@ __device__ __forceinline__ uint32_t bin_edge(int b, const DepthBins& d) {
 // row or a column with coalesced loads. The passes over A clear every entry
 // they read, so A is zero between calls.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void stamp_rect_bin(int32_t* G, int Wd, int b, int x0, int x1, int y0,
-                                               int y1) {
-    atomicAdd(G + ((int64_t)y0 * Wd + x0) * kDepthBins + b, 1);
-    atomicAdd(G + ((int64_t)y0 * Wd + x1 + 1) * kDepthBins + b, -1);
-    atomicAdd(G + ((int64_t)(y1 + 1) * Wd + x0) * kDepthBins + b, -1);
-    atomicAdd(G + ((int64_t)(y1 + 1) * Wd + x1 + 1) * kDepthBins + b, 1);
-}
 
 // S stamps: every visible static record of the view (rectangle flag 1).
 __global__ void __launch_bounds__(kBinBlock)
@@ -1531,10 +1557,17 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
     }
     if (project_mode == 0 && info->max_n > 0)
         project_kernel<0><<<dim3((info->max_n + kProjBlock - 1) / kProjBlock, V), kProjBlock, 0,
-                             s>>>(scenes_dev, views_dev, records, rects, diff);
+                             s>>>(scenes_dev, views_dev, records, rects, diff, nullptr, nullptr,
+                                  nullptr, nullptr);
+    // with the views' depth bins fixed (bucketed layout, mode 1) the projection
+    // of the active records also makes their stamps in A
+    const bool fused_stamps = layout == 1 && project_mode == 1;
     if (info->max_active > 0)  // active records, and their rectangles stamped into `diff`
         project_kernel<1><<<dim3((info->max_active + kProjBlock - 1) / kProjBlock, V), kProjBlock,
-                             0, s>>>(scenes_dev, views_dev, records, rects, diff);
+                             0, s>>>(scenes_dev, views_dev, records, rects, diff,
+                                     fused_stamps ? zmin : nullptr, fused_stamps ? zmax : nullptr,
+                                     fused_stamps ? abins : nullptr,
+                                     fused_stamps ? arange : nullptr);
     tile_mask_kernel<<<V, 512, grid_cap, s>>>(views_dev, diff, tile_active, sat, tile_cache,
                                               grid_cap, tile_ring, layout == 0 ? 1 : 0);
     if (layout == 0 && info->max_active > 0)
@@ -1595,7 +1628,8 @@ extern "C" int cls_project_and_bin(const ClsScene* scenes_dev, const ClsView* vi
             col_prefix_kernel<<<dim3(kLines, V), kDepthBins, 0, s>>>(views_dev, sbins);
         }
         if (info->max_active > 0) {  // the active Gaussians' stamps, prefix-summed along x
-            stamp_active_kernel<<<dim3((unsigned)hmin64(
+            if (!fused_stamps)
+                stamp_active_kernel<<<dim3((unsigned)hmin64(
                                            (info->max_active + kBinBlock - 1) / kBinBlock, 2048),
                                        V), kBinBlock, 0, s>>>(scenes_dev, views_dev, rects, zmin,
                                                               zmax, abins, arange);
