@@ -1088,7 +1088,9 @@ def run_serving(args, seed=0):
     """Serving workload: resident scenes with log-uniform sizes, Poisson update
     requests (2-8 views at 640x480, 800x800 or 1280x720, a change box holding
     1-10% of the scene, 10 local iterations each), continuous batching against
-    the plain one-at-a-time loop on the same kernels. Saturation first (all
+    the plain one-at-a-time loop on the same kernels (the batched loop holds
+    new admissions while its composition is younger than three steps, unless
+    enough requests wait to fill every free slot). Saturation first (all
     requests queued at once); then open-loop Poisson streams at the configured
     rate (30 s by default, if below the batched saturation rate) and at 50% and
     90% of the batched saturation rate (10 s each)."""
@@ -1121,8 +1123,8 @@ def run_serving(args, seed=0):
     n_sat = 96
     sat_sched = [(0.0, int(rng.integers(0, len(packed)))) for _ in range(n_sat)]
     warm = requests(sat_sched[:8])
-    Server(states, max_slots=args.serving_slots).serve(warm, realtime=False)
-    sat_b = Server(states, max_slots=args.serving_slots).serve(requests(sat_sched), realtime=False)
+    Server(states, max_slots=args.serving_slots, admit_interval=3).serve(warm, realtime=False)
+    sat_b = Server(states, max_slots=args.serving_slots, admit_interval=3).serve(requests(sat_sched), realtime=False)
     sat_p = run_plain(states, requests(sat_sched[: n_sat // 2]), realtime=False)
     # the configured rate (if the batched loop can sustain it), then 50% and
     # 90% of the batched saturation rate (at 90% the plain loop is past its
@@ -1137,7 +1139,7 @@ def run_serving(args, seed=0):
     for rate, secs, what in points:
         sched = S.poisson_arrivals(rate, secs, len(packed), seed=seed + int(rate))
         cut = 2.0 * secs
-        b = Server(states, max_slots=args.serving_slots).serve(requests(sched), realtime=True,
+        b = Server(states, max_slots=args.serving_slots, admit_interval=3).serve(requests(sched), realtime=True,
                                                               deadline=cut)
         p = run_plain(states, requests(sched), realtime=True, deadline=cut)
         open_loop.append({"rate_per_s": rate, "point": what, "seconds": secs,

@@ -205,7 +205,7 @@ class Server:
 
     def __init__(self, states, max_slots: int = 8, budget: Optional[int] = None,
                  graphs: bool = True, loss: str = "l1", lr: float = 1e-3, vote_mode: int = 0,
-                 clock: Callable[[], float] = time.perf_counter):
+                 clock: Callable[[], float] = time.perf_counter, admit_interval: int = 1):
         import torch
         self.torch = torch
         self.states = states
@@ -228,6 +228,11 @@ class Server:
         self.side = torch.cuda.Stream(priority=-1)
         self.capture_stream = torch.cuda.Stream()
         self.scene_free: Dict[int, object] = {}  # event after a scene's last queued step
+        # while requests are in flight, admissions (each one rebuilds the
+        # composition) wait until the composition has run `admit_interval`
+        # steps, unless enough requests wait to fill every free slot
+        self.admit_interval = max(1, int(admit_interval))
+        self._age = 0  # steps run by the current composition
         self.stats = {"steps": 0, "graph_captures": 0, "graph_replays": 0, "rebuilds": 0}
 
     # -- request life cycle ----------------------------------------------------
@@ -284,6 +289,7 @@ class Server:
         self.composition = tuple(r.rid for r in reqs)
         self.graph = None
         self.fresh = True
+        self._age = 0
         self.stats["rebuilds"] += 1
 
     def _iteration(self) -> None:
@@ -318,6 +324,7 @@ class Server:
             self.graph.replay()
             self.stats["graph_replays"] += 1
         self.stats["steps"] += 1
+        self._age += 1
 
     def _finish(self, done: Sequence[Request]) -> None:
         """Read the finished requests' losses, take their scenes out of the
@@ -376,7 +383,10 @@ class Server:
                     break
             while pending and pending[0].arrival <= now:
                 self.submit(pending.popleft())
-            started = self.sched.admit(now)
+            free = self.sched.max_slots - len(self.sched.inflight)
+            hold = (bool(self.sched.inflight) and self._age < self.admit_interval
+                    and len(self.sched.queue) < free)
+            started = [] if hold else self.sched.admit(now)
             for r in started:
                 self._start(r)
                 if r.n_active == 0:  # lifting found nothing to optimise

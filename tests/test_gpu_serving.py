@@ -81,3 +81,38 @@ def test_plain_loop_serves_in_order():
     scenes, reqs = _scene_set()
     st = run_plain(_states(scenes), _requests(reqs, [0, 1, 2, 3]), lr=LR, realtime=False)
     assert st["completed"] == 4 and st["steps"] == 4 * ITERS
+
+
+def test_many_views_of_unequal_sizes_complete_without_error():
+    """A batched stream over several scenes whose requests bring 2-6 views of
+    unequal, partly ragged sizes (the emission shares its blocks out over many
+    views with very different work in one launch), scenes updated again after
+    their earlier request completed: every request completes, with a finite
+    loss and no error status."""
+    from paper_2506_21117_gb300.serving import Request, Server
+    from paper_2506_21117_gb300.update import SceneState
+    sizes = [(320, 240), (96, 64), (200, 152), (33, 17), (256, 144), (64, 64)]
+    scenes = [S.uniform_scene(n, 1, seed=70 + i) for i, n in enumerate([8000, 20000, 40000])]
+    states = [SceneState(sc, 1) for sc in scenes]
+    reqs = []
+    for k in range(18):
+        s = k % len(scenes)
+        nv = 2 + k % 5
+        cams = [S.ring_cameras(1, 4.0, *sizes[(k + j) % len(sizes)],
+                               angles=[0.4 * k + 1.1 * j])[0] for j in range(nv)]
+        box = S.random_box_in_unit_cube(0.08, seed=80 + k)
+        masks = [S.box_change_mask(c, box) for c in cams]
+        if not any(m.any() for m in masks):
+            continue
+        targets = [S.random_image(c, 90 + 7 * k + j) for j, c in enumerate(cams)]
+        m = torch.from_numpy(np.concatenate([x.reshape(-1) for x in masks])).pin_memory()
+        t = torch.from_numpy(np.concatenate([x.reshape(-1) for x in targets])).pin_memory()
+        reqs.append(Request(rid=k, scene=s, cams=cams, masks=m, targets=t, iters=4,
+                            arrival=0.0))
+    assert len(reqs) >= 12
+    st = Server(states, max_slots=6, lr=LR).serve(reqs, realtime=False)
+    lifted = [r for r in reqs if r.n_active > 0]
+    assert st["errors"] == 0 and st["rejected"] == 0
+    assert st["completed"] == len(lifted) and len(lifted) >= 8
+    assert all(np.isfinite(r.loss) for r in lifted)
+    assert st["graph_replays"] > 0
