@@ -635,7 +635,8 @@ count_pairs_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restric
 // later calls, so a static Gaussian's depth bin does not change during an
 // update and its pairs per (tile, bin) form a fixed 2D prefix sum S of
 // difference-grid stamps, computed by that call. Every call stamps only the
-// active Gaussians' rectangles into a second difference grid A, prefix-sums
+// active Gaussians' rectangles into a second difference grid A (in their
+// projection once the bins are fixed), prefix-sums
 // the bins they occupy, and adds the two at the rendered tiles. Both grids are
 // bin-fastest: entry (cell y * (Tx + 1) + x of the view, bin b) at
 // (sat_base + cell) * kDepthBins + b, so a block of kDepthBins threads walks a
@@ -662,7 +663,9 @@ stamp_static_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restri
 }
 
 // A stamps: every visible active record of the view (rectangle flag 2), and
-// the range of bins they occupy (arange[v] lowest, arange[V + v] highest).
+// the range of bins they occupy (arange[v] lowest, arange[V + v] highest). Used
+// by a call that fixes the depth bins (project_mode 0); later calls make the
+// same stamps in the projection of the active records (project_kernel<1>).
 __global__ void __launch_bounds__(kBinBlock)
 stamp_active_kernel(const ClsScene* __restrict__ scenes, const ClsView* __restrict__ views,
                     const uint4* __restrict__ rects, const uint32_t* __restrict__ zmin,
