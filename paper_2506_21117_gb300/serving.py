@@ -147,6 +147,14 @@ class Scheduler:
         req.status = "empty: " + reason
         self.empty.append(req)
 
+    def holds(self, age: int, interval: int) -> bool:
+        """Whether admissions wait this step: requests are in flight, their
+        composition has run fewer than `interval` steps, and fewer requests are
+        queued than there are free slots (a full set of waiting requests is
+        admitted at once)."""
+        free = self.max_slots - len(self.inflight)
+        return bool(self.inflight) and age < interval and len(self.queue) < free
+
     def admit(self, now: float) -> List[Request]:
         """Move every queued request that fits into the in-flight set, in
         arrival order, skipping (not reordering) requests whose scene is busy
@@ -230,7 +238,8 @@ class Server:
         self.scene_free: Dict[int, object] = {}  # event after a scene's last queued step
         # while requests are in flight, admissions (each one rebuilds the
         # composition) wait until the composition has run `admit_interval`
-        # steps, unless enough requests wait to fill every free slot
+        # steps, unless enough requests wait to fill every free slot; the check
+        # comes after a step, so 1 admits at every step
         self.admit_interval = max(1, int(admit_interval))
         self._age = 0  # steps run by the current composition
         self.stats = {"steps": 0, "graph_captures": 0, "graph_replays": 0, "rebuilds": 0}
@@ -383,9 +392,7 @@ class Server:
                     break
             while pending and pending[0].arrival <= now:
                 self.submit(pending.popleft())
-            free = self.sched.max_slots - len(self.sched.inflight)
-            hold = (bool(self.sched.inflight) and self._age < self.admit_interval
-                    and len(self.sched.queue) < free)
+            hold = self.sched.holds(self._age, self.admit_interval)
             started = [] if hold else self.sched.admit(now)
             for r in started:
                 self._start(r)

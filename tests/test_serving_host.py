@@ -1,5 +1,6 @@
 """Host-side policy of the serving loop (no GPU): FIFO admission, slots,
-HBM-footprint budget, one in-flight update per scene, completion, and the
+HBM-footprint budget, one in-flight update per scene, admissions held while a
+composition is young, completion, and the
 rejection of malformed requests (non-finite poses, empty or mismatched change
 masks) before they reach the device."""
 import numpy as np
@@ -54,6 +55,23 @@ def test_busy_scene_waits_and_completion_frees():
     assert s.idle()
     st = latency_stats(s.finished, 3.0)
     assert st["completed"] == 3 and st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_admissions_held_while_a_composition_is_young():
+    s = Scheduler(max_slots=4, budget=1000)
+    assert not s.holds(0, 3)                       # nothing in flight: admit at once
+    s.submit(_req(0, 0, 10))
+    s.admit(0.0)
+    s.submit(_req(1, 1, 10))
+    assert s.holds(0, 3) and s.holds(2, 3)         # one waiting, three slots free
+    assert not s.holds(3, 3)                       # the composition has run 3 steps
+    # interval 1 admits every step: the loop checks after each step, so the
+    # composition has always run at least one step there
+    assert not s.holds(1, 1)
+    for i in (2, 3):
+        s.submit(_req(i, i, 10))
+    assert not s.holds(0, 3)                       # enough waiting to fill every free slot
+    assert [r.rid for r in s.admit(0.0)] == [1, 2, 3]
 
 
 def test_oversized_request_rejected():
